@@ -1,0 +1,197 @@
+/*
+ * tr.h -- C ABI of libtr, the GB300 (sm_103a) implementation of the
+ * per-iteration low-rank proximal step of the GNRHTC / GNHTC ADMM from
+ * "Accelerating Large-Scale Regularized High-Order Tensor Recovery"
+ * (arXiv 2506.09594).
+ *
+ * What one step computes (Alg. 5 with the pure-L prior, Gamma = {I}):
+ *   1. L <- ((M - E + Y/mu) + (G - Lambda/mu)) / 2            (Eq. coef-tensor)
+ *   2. G <- D_{Phi,tau}(L + Lambda/mu, L), tau = 1/mu         (Eq. L_prox, Alg. 4)
+ *        = L^{-1}( per transformed face slice: randomized low-rank
+ *          approximation, shrink singular values with Prox_{Phi,tau} )
+ *   3. E <- Prox_{psi,lambda/mu}(H) on Omega, H off Omega,
+ *        H = M - L + Y/mu                        (Eq. E_prox_ome / E_prox_ome1)
+ *   4. Y += mu (M - L - E); Lambda += mu (L - G);
+ *      mu <- min(mu_max, growth * mu)                  (Eq. lagrange11-22)
+ *   5. five infinity-norm residuals                   (Eq. convercon)
+ * The transform L is the orthonormal DCT-II along modes 3..d (Eq. trans,
+ * Eq. orth with alpha = 1).
+ *
+ * Data layout (all tensors, device memory): the face-slice stack of an
+ * order-d tensor n1 x n2 x n3 x ... x nd, i.e. X[j][i1][i2] row-major with
+ * slice index j = i3 + n3*(i4 + n4*(...)) (i3 fastest; Sec. 2 face slice).
+ * Element type is the problem's dtype (float or double).  N = n1*n2*n3*...*nd.
+ *
+ * Threading: a handle is used by one host thread at a time.  Calls enqueue
+ * work on the handle's CUDA stream and return without synchronising unless
+ * stated.
+ *
+ * Errors: every entry point returns a tr_status.  After any non-OK status
+ * the handle stays valid; tr_last_error() describes the failure; a failed
+ * tr_prox_step poisons the handle (further steps return TR_EINVAL) until
+ * tr_set_state() installs a new iterate.
+ */
+#ifndef TR_H
+#define TR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TR_OK = 0,
+  TR_EINVAL = 1,        /* bad argument, unsupported shape, poisoned handle  */
+  TR_ENOMEM = 2,        /* device allocation failed                          */
+  TR_ECUDA = 3,         /* a CUDA runtime call failed                        */
+  TR_ENUMERIC = 4,      /* NaN / Inf met in the iterate                      */
+  TR_ETIMEOUT = 5,      /* a bounded device wait gave up                     */
+  TR_ENOTCONV = 6,      /* tr_recover hit max_iter with tol > 0              */
+  TR_EUNSUPPORTED = 7   /* option known but not built in this library        */
+} tr_status;
+
+typedef enum { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
+
+/* Phi (singular values, GNHTSVT) and psi (entries, GNHTT): Sec. 4.1 */
+typedef enum { TR_PEN_L1 = 0, TR_PEN_MCP = 1 } tr_penalty;
+
+/* h(.) of the noise term Upsilon (Eq. unified-regular11): none = GNHTC,
+ * entrywise l1 = GNRHTC with entry-wise outliers.                         */
+typedef enum { TR_NOISE_NONE = 0, TR_NOISE_L1 = 1 } tr_noise;
+
+/* Low-rank engine inside GNHTSVT (Alg. 4). */
+typedef enum {
+  TR_LR_FULLSVD = 0,    /* deterministic branch: full SVD of every slice    */
+  TR_LR_RSVD = 1,       /* per-slice Gaussian sketch + power iterations      */
+  TR_LR_ADAPTIVE = 2,   /* per-slice fixed-accuracy block Lanczos (Alg. 3)  */
+  TR_LR_LEARNED = 3     /* per-slice sketch width predicted by an MLP        */
+} tr_engine;
+
+/* Operand precision of the slice contractions (accumulation is FP32). */
+typedef enum { TR_PREC_FP32 = 0, TR_PREC_TF32 = 1, TR_PREC_BF16 = 2 } tr_prec;
+
+typedef struct tr_handle tr_handle;
+
+/* The recovery problem: P_Omega(M) and Omega (Alg. 5 inputs). */
+typedef struct {
+  int order;               /* d >= 2, at most 8                              */
+  int64_t dims[8];         /* n1, n2, n3, ..., nd                            */
+  tr_dtype dtype;          /* element type of `observed` and of all state    */
+  const void *observed;    /* device, N elements, face-slice layout; only
+                              entries on Omega are read                      */
+  const uint8_t *mask;     /* device, N bytes, 1 = observed (Omega), 0 = not */
+} tr_problem;
+
+/* Parameters (Alg. 5 input list; Sec. 6 parameter settings). */
+typedef struct {
+  tr_penalty phi;  double phi_theta, phi_gamma;  /* Phi: weight, MCP gamma  */
+  tr_penalty psi;  double psi_theta, psi_gamma;  /* psi: weight, MCP gamma  */
+  tr_noise noise;  double lambda;                /* lambda of Eq. orin_nonconvex */
+  double mu0, mu_max, growth;                    /* mu^0, mu^max, vartheta   */
+  double tol;                                    /* varpi; <= 0: fixed count */
+  int max_iter;
+  tr_engine engine;
+  int rank, oversample;   /* sketch width l = rank + oversample (clamped to
+                             min(n1, n2))                                    */
+  int power_iters;        /* q                                              */
+  double adapt_eps;       /* adaptive engine: relative accuracy epsilon      */
+  int adapt_block;        /* adaptive engine: block size b                   */
+  tr_prec prec;
+  uint64_t seed;          /* Philox4x32-10 key of the Gaussian sketches      */
+  const char *model_path; /* learned engine weights (unused otherwise)      */
+} tr_params;
+
+/* Per-step report (filled only when a non-NULL pointer is passed, which
+ * synchronises the stream). */
+typedef struct {
+  int iter;               /* iterations completed so far                    */
+  double mu;              /* mu used by this step                            */
+  double tau;             /* 1/mu                                            */
+  double res_inf[5];      /* ||dL||, ||dE||, ||L-G||, ||dG||, ||M-L-E||      */
+  int max_rank;           /* max over slices of #(shrunk sigma > 0)          */
+  int sum_rank;           /* sum over slices                                 */
+  int fallback_slices;    /* learned engine: slices that fell back           */
+  float ms;               /* device time of the step (0 if not timed)       */
+} tr_step_info;
+
+/* Fill `prm` with the defaults: Phi = psi = MCP (theta 1, gamma 4000),
+ * entrywise l1 noise with lambda = 1/sqrt(max(n1,n2) * n3...nd) computed
+ * at tr_init when lambda <= 0, mu0 = 1e-3, mu_max = 1e10, growth 1.1,
+ * tol 1e-4, max_iter 100, RSVD engine, rank 10 + oversample 10, q = 1,
+ * FP32 operands, seed 0.  (Sec. 6 parameter settings.)                     */
+void tr_default_params(tr_params *prm);
+
+/* Create a handle for one problem.  Copies nothing from `observed`/`mask`:
+ * they are caller-owned and must stay valid until tr_free.  Allocates all
+ * workspace (state L, E, Y, Lambda, G and transform-domain scratch) on the
+ * current device and sets the iterate to zero with mu = mu0, t = 0 (Alg. 5
+ * initialisation).  `cuda_stream` is a cudaStream_t (NULL = legacy default
+ * stream).  Errors: TR_EINVAL (shape, dtype, pointers), TR_ENOMEM,
+ * TR_EUNSUPPORTED (engine not built), TR_ECUDA.                             */
+tr_status tr_init(tr_handle **h, const tr_problem *p, const tr_params *prm,
+                  void *cuda_stream);
+
+/* One ADMM iteration (steps 1-5 above) on the handle's state.  Asynchronous
+ * unless `info` is non-NULL.  Errors: TR_EINVAL (poisoned), TR_ENUMERIC
+ * (NaN/Inf, only detectable when info != NULL), TR_ECUDA.                   */
+tr_status tr_prox_step(tr_handle *h, tr_step_info *info);
+
+/* Alg. 5 loop: steps until max(res_inf) <= tol (checked every step when
+ * tol > 0, which synchronises each step) or max_iter steps were taken, then
+ * copies L to `L_out` (device, N elements, caller-owned; may be NULL).
+ * Returns TR_ENOTCONV when tol > 0 and max_iter was reached.                */
+tr_status tr_recover(tr_handle *h, void *L_out, tr_step_info *last);
+
+/* Copy the iterate out of / into the handle.  Each pointer is a device
+ * buffer of N elements of the problem's dtype (NULL = skip that tensor).
+ * tr_set_state clears the poisoned flag.  Both synchronise the stream.      */
+tr_status tr_get_state(tr_handle *h, void *L, void *E, void *Y, void *Lam,
+                       void *G, double *mu, int *t);
+tr_status tr_set_state(tr_handle *h, const void *L, const void *E,
+                       const void *Y, const void *Lam, const void *G,
+                       double mu, int t);
+
+/* Transform-domain building blocks of step 2, exposed for testing and for
+ * callers that bring their own outer loop.  All pointers are device buffers
+ * in the face-slice layout of the handle's problem.
+ *   tr_transform_forward: dst = L(src)    (Eq. trans)
+ *   tr_transform_inverse: dst = L^{-1}(src)
+ *   tr_slice_prox: Gbar^<j> = the handle's engine applied to Abar^<j> with
+ *     threshold tau, for every slice j, sketches drawn for iteration `t`
+ *     (Philox counter word 2).  Abar and Gbar must not alias.               */
+tr_status tr_transform_forward(tr_handle *h, const void *src, void *dst);
+tr_status tr_transform_inverse(tr_handle *h, const void *src, void *dst);
+tr_status tr_slice_prox(tr_handle *h, const void *Abar, void *Gbar,
+                        double tau, int t);
+
+/* Per-slice singular values and kept ranks of the last slice pass (host
+ * buffers: sigma n*l doubles, ranks n ints; either may be NULL).  `l` is
+ * the sketch width in use.  Synchronises.                                   */
+tr_status tr_last_slice_stats(tr_handle *h, double *sigma, int *ranks, int *l);
+
+/* Instrumentation (not part of the method).
+ *   tr_profile_enable: when max_steps > 0, the next max_steps calls of
+ *     tr_prox_step record CUDA events on the handle's stream around the
+ *     tube forward kernel, the slice pass and the tube inverse kernel
+ *     (events are created here, outside any timed region); 0 disables.
+ *   tr_profile_read: mean device milliseconds per recorded step of those
+ *     three phases (ms[0..2]) and the number of recorded steps; synchronises.
+ *   tr_kernel_launches: number of CUDA kernels this handle has launched.    */
+tr_status tr_profile_enable(tr_handle *h, int max_steps);
+tr_status tr_profile_read(tr_handle *h, double ms[3], int *steps);
+tr_status tr_kernel_launches(const tr_handle *h, uint64_t *count);
+
+/* Release all workspace.  Safe on NULL.                                     */
+tr_status tr_free(tr_handle *h);
+
+/* Last error message for `h` (or for the last failed tr_init when h is
+ * NULL).  The string is owned by the library.                               */
+const char *tr_last_error(const tr_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TR_H */

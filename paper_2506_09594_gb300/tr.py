@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libtr (include/tr.h).
+
+Argument marshalling only: every step of the proximal iteration runs in the
+CUDA library.  Device buffers are torch CUDA tensors (PyTorch provides the
+memory and the stream); their data pointers are passed straight through.
+There is no CPU fallback: if libtr.so is missing or fails to load, every call
+raises.
+"""
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtr.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "tr.h")
+
+# tr_status
+TR_OK, TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_ENUMERIC, TR_ETIMEOUT, TR_ENOTCONV, TR_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["TR_OK", "TR_EINVAL", "TR_ENOMEM", "TR_ECUDA", "TR_ENUMERIC", "TR_ETIMEOUT",
+                "TR_ENOTCONV", "TR_EUNSUPPORTED"]
+TR_F32, TR_F64 = 0, 1
+TR_PEN_L1, TR_PEN_MCP = 0, 1
+TR_NOISE_NONE, TR_NOISE_L1 = 0, 1
+TR_LR_FULLSVD, TR_LR_RSVD, TR_LR_ADAPTIVE, TR_LR_LEARNED = 0, 1, 2, 3
+TR_PREC_FP32, TR_PREC_TF32, TR_PREC_BF16 = 0, 1, 2
+
+
+class TrError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s" % (name, msg))
+
+
+class tr_problem(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("dims", ctypes.c_int64 * 8), ("dtype", ctypes.c_int),
+                ("observed", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
+class tr_params(ctypes.Structure):
+    _fields_ = [("phi", ctypes.c_int), ("phi_theta", ctypes.c_double), ("phi_gamma", ctypes.c_double),
+                ("psi", ctypes.c_int), ("psi_theta", ctypes.c_double), ("psi_gamma", ctypes.c_double),
+                ("noise", ctypes.c_int), ("lambda_", ctypes.c_double),
+                ("mu0", ctypes.c_double), ("mu_max", ctypes.c_double), ("growth", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("engine", ctypes.c_int), ("rank", ctypes.c_int), ("oversample", ctypes.c_int),
+                ("power_iters", ctypes.c_int), ("adapt_eps", ctypes.c_double),
+                ("adapt_block", ctypes.c_int), ("prec", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("model_path", ctypes.c_char_p)]
+
+
+class tr_step_info(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int), ("mu", ctypes.c_double), ("tau", ctypes.c_double),
+                ("res_inf", ctypes.c_double * 5), ("max_rank", ctypes.c_int),
+                ("sum_rank", ctypes.c_int), ("fallback_slices", ctypes.c_int), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"iter": self.iter, "mu": self.mu, "tau": self.tau, "res_inf": list(self.res_inf),
+                "max_rank": self.max_rank, "sum_rank": self.sum_rank,
+                "fallback_slices": self.fallback_slices, "ms": self.ms}
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "tr_default_params": (None, [ctypes.POINTER(tr_params)]),
+    "tr_init": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(tr_problem),
+                               ctypes.POINTER(tr_params), _P]),
+    "tr_prox_step": (ctypes.c_int, [_P, ctypes.POINTER(tr_step_info)]),
+    "tr_recover": (ctypes.c_int, [_P, _P, ctypes.POINTER(tr_step_info)]),
+    "tr_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int)]),
+    "tr_set_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int]),
+    "tr_transform_forward": (ctypes.c_int, [_P, _P, _P]),
+    "tr_transform_inverse": (ctypes.c_int, [_P, _P, _P]),
+    "tr_slice_prox": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int]),
+    "tr_last_slice_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
+    "tr_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "tr_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "tr_free": (ctypes.c_int, [_P]),
+    "tr_last_error": (ctypes.c_char_p, [_P]),
+}
+
+
+def load(path=LIB_PATH):
+    """Load libtr.so (raises if it is absent: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libtr.so not built at %s; run paper_2506_09594_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions(header=HEADER):
+    """Names of the functions declared in include/tr.h."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tr_\w+)\s*\(", txt)))
+
+
+def _check(st, h=None):
+    if st != TR_OK:
+        msg = load().tr_last_error(h)
+        raise TrError(st, msg.decode() if msg else "")
+
+
+def default_params(**kw):
+    p = tr_params()
+    load().tr_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "lambda":
+            k = "lambda_"
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """One recovery problem on the current CUDA device (tr_init ... tr_free)."""
+
+    def __init__(self, observed, mask, dims, params=None, stream=None, **kw):
+        import torch
+        lib = load()
+        if not (observed.is_cuda and mask.is_cuda):
+            raise ValueError("observed and mask must be CUDA tensors")
+        if mask.dtype != torch.uint8:
+            raise ValueError("mask must be uint8")
+        self.dtype = observed.dtype
+        dt = {torch.float32: TR_F32, torch.float64: TR_F64}[observed.dtype]
+        self.dims = tuple(int(d) for d in dims)
+        prob = tr_problem()
+        prob.order = len(self.dims)
+        for i, d in enumerate(self.dims):
+            prob.dims[i] = d
+        prob.dtype = dt
+        prob.observed = observed.data_ptr()
+        prob.mask = mask.data_ptr()
+        self._keep = (observed, mask)       # caller-owned buffers stay alive
+        self.params = params if params is not None else default_params(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = lib.tr_init(ctypes.byref(h), ctypes.byref(prob), ctypes.byref(self.params),
+                         ctypes.c_void_p(stream))
+        _check(st, None)
+        self.h = h
+        n = 1
+        for d in self.dims[2:]:
+            n *= d
+        self.shape = (n, self.dims[0], self.dims[1])
+
+    def _new(self):
+        import torch
+        return torch.empty(self.shape, dtype=self.dtype, device="cuda")
+
+    def step(self, info=False):
+        if info:
+            si = tr_step_info()
+            _check(load().tr_prox_step(self.h, ctypes.byref(si)), self.h)
+            return si.as_dict()
+        _check(load().tr_prox_step(self.h, None), self.h)
+        return None
+
+    def recover(self, L_out=None, check=True):
+        si = tr_step_info()
+        st = load().tr_recover(self.h, _ptr(L_out), ctypes.byref(si))
+        if check:
+            _check(st, self.h)
+        return st, si.as_dict()
+
+    def get_state(self):
+        L, E, Y, Lam, G = (self._new() for _ in range(5))
+        mu = ctypes.c_double()
+        t = ctypes.c_int()
+        _check(load().tr_get_state(self.h, _ptr(L), _ptr(E), _ptr(Y), _ptr(Lam), _ptr(G),
+                                   ctypes.byref(mu), ctypes.byref(t)), self.h)
+        return {"L": L, "E": E, "Y": Y, "Lam": Lam, "G": G, "mu": mu.value, "t": t.value}
+
+    def set_state(self, L, E, Y, Lam, G, mu, t):
+        _check(load().tr_set_state(self.h, _ptr(L), _ptr(E), _ptr(Y), _ptr(Lam), _ptr(G),
+                                   float(mu), int(t)), self.h)
+
+    def transform_forward(self, src):
+        dst = self._new()
+        _check(load().tr_transform_forward(self.h, _ptr(src), _ptr(dst)), self.h)
+        return dst
+
+    def transform_inverse(self, src):
+        dst = self._new()
+        _check(load().tr_transform_inverse(self.h, _ptr(src), _ptr(dst)), self.h)
+        return dst
+
+    def slice_prox(self, Abar, tau, t, out=None):
+        Gbar = self._new() if out is None else out
+        _check(load().tr_slice_prox(self.h, _ptr(Abar), _ptr(Gbar), float(tau), int(t)), self.h)
+        return Gbar
+
+    def slice_stats(self):
+        import numpy as np
+        l = ctypes.c_int()
+        _check(load().tr_last_slice_stats(self.h, None, None, ctypes.byref(l)), self.h)
+        n = self.shape[0]
+        sig = np.zeros(n * l.value)
+        ranks = np.zeros(n, dtype=np.int32)
+        _check(load().tr_last_slice_stats(
+            self.h, sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            ranks.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), None), self.h)
+        return sig.reshape(n, l.value), ranks
+
+    def profile_enable(self, max_steps):
+        _check(load().tr_profile_enable(self.h, int(max_steps)), self.h)
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 3)()
+        steps = ctypes.c_int()
+        _check(load().tr_profile_read(self.h, ms, ctypes.byref(steps)), self.h)
+        return {"tube_forward": ms[0], "slice_pass": ms[1], "tube_inverse": ms[2],
+                "steps": steps.value}
+
+    def kernel_launches(self):
+        c = ctypes.c_uint64()
+        _check(load().tr_kernel_launches(self.h, ctypes.byref(c)), self.h)
+        return int(c.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tr_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

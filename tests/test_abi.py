@@ -1,0 +1,82 @@
+"""The C-ABI library loads, exports every function include/tr.h declares, and
+rejects bad arguments before touching the GPU.  No compute calls here."""
+
+import ctypes
+import os
+
+import pytest
+
+from paper_2506_09594_gb300 import tr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(tr.LIB_PATH):
+        from paper_2506_09594_gb300 import build
+        build.build()
+    return tr.load()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = tr.header_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in tr._SIGS, "binding lacks " + name
+
+
+def test_binding_struct_sizes_match_header_layout():
+    # tr_params: 5 ints/enums, 12 doubles, 1 uint64, 1 pointer, with C padding
+    assert ctypes.sizeof(tr.tr_problem) == 4 + 4 + 8 * 8 + 4 + 4 + 8 + 8
+    assert ctypes.alignment(tr.tr_params) == 8
+    assert ctypes.sizeof(tr.tr_step_info) % 8 == 0
+
+
+def test_default_params(lib):
+    p = tr.default_params()
+    assert p.phi == tr.TR_PEN_MCP and p.psi == tr.TR_PEN_MCP
+    assert p.mu0 == 1e-3 and p.mu_max == 1e10 and p.growth == 1.1 and p.tol == 1e-4
+    assert p.engine == tr.TR_LR_RSVD and p.rank == 10 and p.oversample == 10
+    assert p.power_iters == 1 and p.prec == tr.TR_PREC_FP32
+
+
+def _init(lib, order, dims, dtype=tr.TR_F32, observed=1, mask=1, **kw):
+    prob = tr.tr_problem()
+    prob.order = order
+    for i, d in enumerate(dims[:8]):
+        prob.dims[i] = d
+    prob.dtype = dtype
+    prob.observed = observed
+    prob.mask = mask
+    prm = tr.default_params(**kw)
+    h = ctypes.c_void_p()
+    st = lib.tr_init(ctypes.byref(h), ctypes.byref(prob), ctypes.byref(prm), None)
+    return st, h
+
+
+def test_init_rejects_bad_arguments_without_a_gpu(lib):
+    assert _init(lib, 1, [4])[0] == tr.TR_EINVAL                    # order < 2
+    assert _init(lib, 9, [2] * 9)[0] == tr.TR_EINVAL                # order > 8
+    assert _init(lib, 3, [4, 0, 3])[0] == tr.TR_EINVAL              # empty mode
+    assert _init(lib, 3, [4, 4, 3], dtype=7)[0] == tr.TR_EINVAL     # dtype
+    assert _init(lib, 3, [4, 4, 3], observed=None)[0] == tr.TR_EINVAL
+    assert _init(lib, 3, [4, 4, 3], mu0=0.0)[0] == tr.TR_EINVAL
+    assert _init(lib, 3, [4, 4, 3], power_iters=-1)[0] == tr.TR_EINVAL
+    st, _ = _init(lib, 3, [4, 4, 100])                               # mode > 64
+    assert st == tr.TR_EUNSUPPORTED
+    msg = lib.tr_last_error(None).decode()
+    assert "64" in msg
+    assert lib.tr_free(None) == tr.TR_OK
+    assert lib.tr_prox_step(None, None) == tr.TR_EINVAL
+
+
+def test_library_refuses_missing_build(tmp_path):
+    saved = tr._lib
+    try:
+        tr._lib = None
+        with pytest.raises(RuntimeError):
+            tr.load(str(tmp_path / "nope.so"))
+    finally:
+        tr._lib = saved

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative Frobenius error): 1e-10 for the FP64 path (rounding
+order only), 1e-4 for the FP32 path (the stated bound of the FP32 form).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import admm, prox, svt, transform
+from paper_2506_09594_gb300 import synth, tr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+TDT = {"f64": torch.float64, "f32": torch.float32}
+
+
+def dev(x, dt):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=TDT[dt])
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def relF(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make_handle(dims, dt, M=None, mask=None, **kw):
+    n = int(np.prod(dims[2:])) if len(dims) > 2 else 1
+    shape = (n, dims[0], dims[1])
+    if M is None:
+        M = np.zeros(shape)
+    if mask is None:
+        mask = np.ones(shape, np.uint8)
+    Md = dev(M, dt)
+    maskd = torch.from_numpy(np.ascontiguousarray(mask)).cuda()
+    return tr.Handle(Md, maskd, dims, **kw)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    tr.load()
+
+
+# ------------------------------------------------------------- transform
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("dims", [(7, 5, 3), (9, 4, 5, 3), (3, 3, 2, 2, 2), (6, 5, 64),
+                                  (33, 17, 20, 20), (4, 6), (5, 3, 1, 7)])
+def test_transform_parity(dims, dt):
+    rng = np.random.default_rng(1)
+    n = int(np.prod(dims[2:])) if len(dims) > 2 else 1
+    X = rng.standard_normal((n, dims[0], dims[1]))
+    h = make_handle(dims, dt)
+    fwd = host(h.transform_forward(dev(X, dt)))
+    inv = host(h.transform_inverse(dev(X, dt)))
+    tdims = tuple(dims[2:])
+    tol = 1e-13 if dt == "f64" else 3e-6
+    assert relF(fwd, transform.forward(X, tdims)) < tol
+    assert relF(inv, transform.inverse(X, tdims)) < tol
+    back = host(h.transform_inverse(h.transform_forward(dev(X, dt))))
+    assert relF(back, X) < tol
+    h.close()
+
+
+# ------------------------------------------------------------ slice prox
+SLICE_CASES = [
+    # (n, n1, n2, rank, noise, l, q, phi)
+    (16, 64, 64, 5, 0.0, 15, 1, "l1"),       # exactly low rank: randomized == exact
+    (16, 64, 64, 5, 0.0, 15, 1, "mcp"),
+    (6, 70, 45, 8, 0.05, 20, 1, "mcp"),      # ragged tiles, n1 > n2
+    (5, 40, 90, 6, 0.1, 16, 2, "l1"),        # n2 > n1, two power steps
+    (4, 33, 29, 3, 0.2, 12, 0, "l1"),        # no power step
+    (3, 8, 6, 2, 0.1, 20, 1, "mcp"),         # l clamped to min(n1, n2)
+    (2, 1, 5, 1, 0.0, 3, 1, "l1"),           # single-row slices
+]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("case", SLICE_CASES)
+def test_slice_prox_parity(case, dt):
+    n, n1, n2, r, noise, l, q, phi = case
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 * 7 + n2)
+    s1 = np.linalg.svd(Ab[0], compute_uv=False)[0]
+    tau = 0.3 * s1
+    kind = prox.L1 if phi == "l1" else prox.MCP
+    gamma = 3.0 * tau + 1.0
+    dims = (n1, n2, n)
+    pen = tr.TR_PEN_L1 if phi == "l1" else tr.TR_PEN_MCP
+    h = make_handle(dims, dt, rank=l, oversample=0, power_iters=q, phi=pen, phi_theta=1.0,
+                    phi_gamma=gamma, seed=77)
+    G = host(h.slice_prox(dev(Ab, dt), tau, t=5))
+    ref, info = svt.transformed_prox(Ab, tau, kind, 1.0, gamma, engine="rsvd", l=l, q=q,
+                                     seed=77, t=5)
+    assert relF(G, ref) < TOL[dt]
+    sig, ranks = h.slice_stats()
+    ll = min(l, n1, n2)
+    for j in range(n):
+        assert np.allclose(sig[j][:ll], info["sigma"][j][:ll],
+                           rtol=1e-8 if dt == "f64" else 1e-4,
+                           atol=(1e-10 if dt == "f64" else 1e-4) * s1)
+    assert np.array_equal(ranks, info["ranks"]) or dt == "f32"
+    h.close()
+
+
+def test_slice_prox_exact_on_low_rank_matches_full_svd():
+    Ab = synth.lowrank_plus_noise_stack(16, 64, 64, 5, 0.0, seed=3)
+    h = make_handle((64, 64, 16), "f64", rank=5, oversample=10, phi=tr.TR_PEN_L1)
+    G = host(h.slice_prox(dev(Ab, "f64"), 2.0, t=0))
+    ref, _ = svt.transformed_prox(Ab, 2.0, prox.L1, engine="full")
+    assert relF(G, ref) < 1e-10
+    h.close()
+
+
+# ------------------------------------------------------------- ADMM step
+STEP_CASES = [
+    # dims, dtype, noise model, penalty, l, mu
+    ((64, 64, 16), "f64", "none", "mcp", 15, 0.05),
+    ((64, 64, 16), "f32", "l1", "l1", 15, 0.05),
+    ((50, 37, 4, 3), "f32", "l1", "mcp", 12, 0.2),
+    ((50, 37, 4, 3), "f64", "l1", "mcp", 12, 0.2),
+    ((31, 29, 7), "f32", "none", "l1", 9, 1.0),
+]
+
+
+def _problem(dims, seed):
+    rng = np.random.default_rng(seed)
+    X = synth.lowrank_tensor(dims, 4, rng)[0]
+    mask = synth.exact_count_mask(X.size, 0.4, rng).reshape(X.shape)
+    S = synth.exact_count_mask(X.size, 0.05, rng).reshape(X.shape) * rng.uniform(-1, 1, X.shape)
+    M = np.where(mask == 1, X + S, 0.0)
+    return X, M, mask
+
+
+@pytest.mark.parametrize("case", STEP_CASES)
+def test_step_parity_from_random_state(case):
+    dims, dt, noise, pen, l, mu = case
+    X, M, mask = _problem(dims, seed=sum(dims))
+    L0, E0, Y0, La0, G0 = synth.random_state(M.shape, seed=5, scale=0.5)
+    kind = prox.L1 if pen == "l1" else prox.MCP
+    pen_c = tr.TR_PEN_L1 if pen == "l1" else tr.TR_PEN_MCP
+    lam = admm.default_lambda(dims[0], dims[1], dims[2:])
+    p = admm.Params(phi=kind, psi=kind, phi_gamma=60.0, psi_gamma=60.0,
+                    noise=admm.NOISE_NONE if noise == "none" else admm.NOISE_L1, lam=lam,
+                    engine="rsvd", l=l, q=1, seed=11)
+    st = admm.State(L=L0, E=E0, Y=Y0, Lam=La0, G=G0, mu=mu, t=3)
+    ref, res = admm.step(st, M, mask, tuple(dims[2:]), p)
+    h = make_handle(dims, dt, M=M, mask=mask, phi=pen_c, psi=pen_c, phi_gamma=60.0,
+                    psi_gamma=60.0, noise=tr.TR_NOISE_NONE if noise == "none" else tr.TR_NOISE_L1,
+                    rank=l, oversample=0, power_iters=1, seed=11, **{"lambda": lam})
+    h.set_state(*(dev(x, dt) for x in (L0, E0, Y0, La0, G0)), mu=mu, t=3)
+    info = h.step(info=True)
+    got = h.get_state()
+    for name, want in [("L", ref.L), ("E", ref.E), ("Y", ref.Y), ("Lam", ref.Lam), ("G", ref.G)]:
+        err = relF(host(got[name]), want)
+        assert err < TOL[dt], (name, err)
+    assert abs(got["mu"] - ref.mu) <= 1e-15 * ref.mu and got["t"] == 4
+    assert np.allclose(info["res_inf"], res, rtol=TOL[dt] * 10, atol=TOL[dt] * np.max(res))
+    h.close()
+
+
+def test_recovery_small_workload_matches_oracle():
+    w = synth.WORKLOADS["tubal64_r5"]
+    X, M, mask, _ = synth.make_problem(w)
+    iters = w.iters
+    p = admm.Params(phi=prox.MCP, psi=prox.MCP, noise=admm.NOISE_NONE, engine="rsvd", l=w.l,
+                    q=w.q, seed=21, tol=0.0, max_iter=iters)
+    ref, _ = admm.run(M, mask, w.tdims, p)
+    h = make_handle(w.dims, "f64", M=M, mask=mask, noise=tr.TR_NOISE_NONE, rank=w.l,
+                    oversample=0, power_iters=w.q, seed=21, tol=0.0, max_iter=iters)
+    Lout = torch.empty(M.shape, dtype=torch.float64, device="cuda")
+    st, _ = h.recover(Lout)
+    L = host(Lout)
+    assert relF(L, ref.L) < 1e-8
+    e_gpu, e_ref = relF(L, X), relF(ref.L, X)
+    assert abs(e_gpu - e_ref) < 1e-8
+    h.close()
+
+
+def test_recover_converges_and_reports_notconv():
+    w = synth.WORKLOADS["tubal64_r5"]
+    X, M, mask, _ = synth.make_problem(w)
+    h = make_handle(w.dims, "f64", M=M, mask=mask, noise=tr.TR_NOISE_NONE, rank=5,
+                    oversample=10, seed=2, tol=1e-8, max_iter=400)
+    Lout = torch.empty(M.shape, dtype=torch.float64, device="cuda")
+    st, info = h.recover(Lout)
+    assert st == tr.TR_OK and max(info["res_inf"]) <= 1e-8
+    assert relF(host(Lout), X) < 1e-6
+    h.close()
+    h = make_handle(w.dims, "f64", M=M, mask=mask, noise=tr.TR_NOISE_NONE, tol=1e-12, max_iter=3)
+    st, _ = h.recover(None, check=False)
+    assert st == tr.TR_ENOTCONV
+    h.close()
+
+
+def test_nan_input_is_reported_and_poisons():
+    dims = (16, 12, 4)
+    M = np.ones((4, 16, 12))
+    M[1, 3, 4] = np.nan
+    h = make_handle(dims, "f32", M=M)
+    with pytest.raises(tr.TrError) as ei:
+        h.step(info=True)
+    assert ei.value.status == tr.TR_ENUMERIC
+    with pytest.raises(tr.TrError) as ei:
+        h.step()
+    assert ei.value.status == tr.TR_EINVAL
+    z = torch.zeros((4, 16, 12), device="cuda")
+    h.set_state(z, z, z, z, z, mu=1.0, t=0)
+    h.close()
+
+
+def test_state_roundtrip():
+    dims = (10, 9, 3, 2)
+    rng = np.random.default_rng(0)
+    h = make_handle(dims, "f64")
+    xs = [dev(rng.standard_normal((6, 10, 9)), "f64") for _ in range(5)]
+    h.set_state(*xs, mu=0.25, t=7)
+    s = h.get_state()
+    for k, x in zip(["L", "E", "Y", "Lam", "G"], xs):
+        assert torch.equal(s[k], x)
+    assert s["mu"] == 0.25 and s["t"] == 7
+    h.close()
+
+
+# ------------------------------------------------- full-size mid workload
+@pytest.mark.slow
+def test_mid_workload_full_size_step_parity():
+    # 200x200x20x20 FP32 (400 slices), the benchmark launch configuration:
+    # run the GPU for 30 iterations, then one more step from that state on both
+    # sides, compared on every output at full size.
+    w = synth.WORKLOADS["tubal200x400_r10"]
+    X, M, mask, _ = synth.make_problem(w)
+    lam = admm.default_lambda(w.n1, w.n2, w.tdims)
+    h = make_handle(w.dims, "f32", M=M, mask=mask, rank=10, oversample=10, power_iters=1,
+                    seed=5, **{"lambda": lam})
+    for _ in range(30):
+        h.step()
+    s = h.get_state()
+    st = admm.State(L=host(s["L"]), E=host(s["E"]), Y=host(s["Y"]), Lam=host(s["Lam"]),
+                    G=host(s["G"]), mu=s["mu"], t=s["t"])
+    p = admm.Params(lam=lam, engine="rsvd", l=20, q=1, seed=5)
+    ref, res = admm.step(st, M, mask, w.tdims, p)
+    info = h.step(info=True)
+    got = h.get_state()
+    assert info["max_rank"] > 0
+    for name, want in [("L", ref.L), ("E", ref.E), ("Y", ref.Y), ("Lam", ref.Lam), ("G", ref.G)]:
+        err = relF(host(got[name]), want)
+        assert err < TOL["f32"], (name, err)
+    h.close()
