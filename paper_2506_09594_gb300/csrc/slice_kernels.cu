@@ -115,20 +115,52 @@ bgemm_kernel(GemmArgs g) {
 #pragma unroll
     for (int jn = 0; jn < TN; ++jn) acc[i][jn] = T(0);
 
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += NT) {
+  // Register prefetch: the next K-tile is loaded from global memory while the
+  // current one is multiplied out of shared memory.
+  constexpr int NA = (BM * BK + NT - 1) / NT, NB = (BK * BN + NT - 1) / NT;
+  T ra[NA], rb[NB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      const int e = tid + r * NT;
       int i, k;
       if (a_kc) { i = e / BK; k = e % BK; } else { i = e % BM; k = e / BM; }
       const int gi = m0 + i, gk = k0 + k;
-      As[k][i] = (gi < g.M && gk < g.K) ? A[gi * g.sAi + gk * g.sAk] : T(0);
+      ra[r] = (e < BM * BK && gi < g.M && gk < g.K) ? A[gi * g.sAi + gk * g.sAk] : T(0);
     }
-    for (int e = tid; e < BK * BN; e += NT) {
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const int e = tid + r * NT;
       int k, nn;
       if (b_nc) { k = e / BN; nn = e % BN; } else { k = e % BK; nn = e / BK; }
       const int gk = k0 + k, gn = n0 + nn;
-      Bs[k][nn] = (gk < g.K && gn < g.N) ? B[gk * g.sBk + gn * g.sBn] : T(0);
+      rb[r] = (e < BK * BN && gk < g.K && gn < g.N) ? B[gk * g.sBk + gn * g.sBn] : T(0);
     }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      const int e = tid + r * NT;
+      if (e >= BM * BK) break;
+      int i, k;
+      if (a_kc) { i = e / BK; k = e % BK; } else { i = e % BM; k = e / BM; }
+      As[k][i] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const int e = tid + r * NT;
+      if (e >= BK * BN) break;
+      int k, nn;
+      if (b_nc) { k = e / BN; nn = e % BN; } else { k = e % BK; nn = e / BK; }
+      Bs[k][nn] = rb[r];
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
     __syncthreads();
+    stash();
+    __syncthreads();
+    if (k0 + BK < g.K) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[TM], bb[TN];
@@ -141,7 +173,6 @@ bgemm_kernel(GemmArgs g) {
 #pragma unroll
         for (int jn = 0; jn < TN; ++jn) acc[i][jn] = fma(a[i], bb[jn], acc[i][jn]);
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
@@ -369,8 +400,11 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   __syncthreads();
   block_qr_form_q(panel, n2, l, n2, tau);
   for (int e = threadIdx.x; e < n2 * l; e += blockDim.x) P2j[e] = panel[e];
-  const T tol = sizeof(T) == 4 ? T(8.0 * FLT_EPSILON) : T(16.0 * DBL_EPSILON);
-  block_jacobi(W, J, l, flag, tol, sizeof(T) == 4 ? 30 : 60);
+  // Rotate only while a pair's cosine exceeds max(l, 8) * eps: below that the
+  // computed inner product is rounding noise (an l-term dot product).
+  const T eps = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
+  const T tol = T(l > 8 ? l : 8) * eps;
+  block_jacobi(W, J, l, flag, tol, sizeof(T) == 4 ? 16 : 30);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < l; i += nw) {

@@ -29,6 +29,7 @@ struct tr_handle {
   void *Abar = nullptr, *Gbar = nullptr;      // transform-domain scratch
   SliceWork sw{};
   unsigned long long *res = nullptr;          // RES_COUNT slots
+  unsigned long long *res_prev = nullptr;     // slots for a deferred inverse pass
   int *flags = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // instrumentation
@@ -38,6 +39,10 @@ struct tr_handle {
   // host state
   double mu = 0.0;
   int t = 0;
+  // The inverse pass of the last step is deferred and fused into the next
+  // step's forward pass when `pending` is set (steps taken without info).
+  bool pending = false;
+  double mu_prev = 0.0;
   bool poisoned = false;
   char err[512] = {0};
 };
@@ -108,7 +113,8 @@ static void free_profile(tr_handle *h) {
 static void free_all(tr_handle *h) {
   free_profile(h);
   void *bufs[] = {h->mats, h->L, h->E, h->Y, h->Lam, h->G, h->Abar, h->Gbar,
-                  h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->res, h->flags};
+                  h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->res, h->res_prev,
+                  h->flags};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->ev0) cudaEventDestroy(h->ev0);
@@ -259,6 +265,7 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   INIT_CUDA(cudaMalloc(&sw.sig, (size_t)h->n * l * h->esz));
   INIT_CUDA(cudaMalloc((void **)&sw.rank, (size_t)h->n * sizeof(int)));
   INIT_CUDA(cudaMalloc((void **)&h->res, RES_COUNT * sizeof(unsigned long long)));
+  INIT_CUDA(cudaMalloc((void **)&h->res_prev, RES_COUNT * sizeof(unsigned long long)));
   INIT_CUDA(cudaMalloc((void **)&h->flags, sizeof(int)));
   INIT_CUDA(cudaMemsetAsync(sw.rank, 0, (size_t)h->n * sizeof(int), h->stream));
   INIT_CUDA(cudaEventCreate(&h->ev0));
@@ -314,6 +321,21 @@ static tr_status read_info(tr_handle *h, double mu_used, tr_step_info *info) {
   return TR_OK;
 }
 
+// Run the deferred inverse pass (G = L^{-1}(Gbar), Lambda update) of the
+// last step, so that the handle's state is the complete iterate.
+static tr_status finalize(tr_handle *h) {
+  if (!h->pending) return TR_OK;
+  cudaError_t e = launch_tube_inverse(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->L,
+                                      h->G, h->Lam, h->mu_prev, h->res_prev, h->flags, h->stream);
+  if (e != cudaSuccess) {
+    h->poisoned = true;
+    return fail(h, TR_ECUDA, "tube inverse: %s", cudaGetErrorString(e));
+  }
+  h->launches += 1;
+  h->pending = false;
+  return TR_OK;
+}
+
 extern "C" tr_status tr_prox_step(tr_handle *h, tr_step_info *info) {
   if (!h) return TR_EINVAL;
   if (h->poisoned) return fail(h, TR_EINVAL, "handle poisoned by an earlier failure; call tr_set_state");
@@ -330,9 +352,16 @@ extern "C" tr_status tr_prox_step(tr_handle *h, tr_step_info *info) {
   cudaError_t e = cudaMemsetAsync(h->res, 0, RES_COUNT * sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[0], h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess)
-    e = launch_tube_forward(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->mask, h->L, h->E,
-                            h->Y, h->G, h->Lam, h->Abar, sc, h->res, h->flags, h->stream);
+  if (e == cudaSuccess) {
+    if (h->pending)
+      e = launch_tube_fused(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->mu_prev, h->M,
+                            h->mask, h->L, h->E, h->Y, h->G, h->Lam, h->Abar, sc, h->res_prev,
+                            h->res, h->flags, h->stream);
+    else
+      e = launch_tube_forward(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->mask, h->L,
+                              h->E, h->Y, h->G, h->Lam, h->Abar, sc, h->res, h->flags, h->stream);
+  }
+  h->pending = false;
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[1], h->stream);
   if (e != cudaSuccess)
     return guard(fail(h, TR_ECUDA, "tube forward: %s", cudaGetErrorString(e)));
@@ -340,13 +369,19 @@ extern "C" tr_status tr_prox_step(tr_handle *h, tr_step_info *info) {
   tr_status st = slice_pass(h, h->Abar, h->Gbar, 1.0 / mu, h->t);
   if (st != TR_OK) return guard(st);
   if (pev) e = cudaEventRecord(pev[2], h->stream);
-  if (e == cudaSuccess)
-    e = launch_tube_inverse(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->L, h->G, h->Lam,
-                          mu, h->res, h->flags, h->stream);
+  if (info) {
+    if (e == cudaSuccess)
+      e = launch_tube_inverse(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->L, h->G,
+                              h->Lam, mu, h->res, h->flags, h->stream);
+    if (e != cudaSuccess)
+      return guard(fail(h, TR_ECUDA, "tube inverse: %s", cudaGetErrorString(e)));
+    h->launches += 1;
+  } else {
+    h->pending = true;
+    h->mu_prev = mu;
+  }
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[3], h->stream);
-  if (e != cudaSuccess)
-    return guard(fail(h, TR_ECUDA, "tube inverse: %s", cudaGetErrorString(e)));
-  h->launches += 1;
+  if (e != cudaSuccess) return guard(fail(h, TR_ECUDA, "event: %s", cudaGetErrorString(e)));
   if (info) TR_CUDA(h, cudaEventRecord(h->ev1, h->stream));
   h->t += 1;
   double next = h->prm.growth * mu;
@@ -372,6 +407,10 @@ extern "C" tr_status tr_recover(tr_handle *h, void *L_out, tr_step_info *last) {
       }
     }
   }
+  {
+    tr_status fs = finalize(h);
+    if (fs != TR_OK) return fs;
+  }
   if (L_out) {
     TR_CUDA(h, cudaMemcpyAsync(L_out, h->L, (size_t)h->N * h->esz, cudaMemcpyDeviceToDevice, h->stream));
     TR_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -384,6 +423,10 @@ extern "C" tr_status tr_recover(tr_handle *h, void *L_out, tr_step_info *last) {
 extern "C" tr_status tr_get_state(tr_handle *h, void *L, void *E, void *Y, void *Lam, void *G,
                                   double *mu, int *t) {
   if (!h) return TR_EINVAL;
+  {
+    tr_status fs = finalize(h);
+    if (fs != TR_OK) return fs;
+  }
   const size_t bytes = (size_t)h->N * h->esz;
   void *dst[] = {L, E, Y, Lam, G};
   void *src[] = {h->L, h->E, h->Y, h->Lam, h->G};
@@ -408,6 +451,7 @@ extern "C" tr_status tr_set_state(tr_handle *h, const void *L, const void *E, co
   h->mu = mu;
   h->t = t;
   h->poisoned = false;
+  h->pending = false;
   return TR_OK;
 }
 

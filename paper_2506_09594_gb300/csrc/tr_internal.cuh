@@ -57,6 +57,11 @@ cudaError_t launch_tube_inverse(tr_dtype dt, int64_t P, int n, const TransformDe
                                 const void *mats, const void *Gbar, const void *L,
                                 void *G, void *Lam, double mu,
                                 unsigned long long *res, int *flags, cudaStream_t s);
+cudaError_t launch_tube_fused(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
+                              const void *mats, const void *Gbar, double mu_prev, const void *M,
+                              const uint8_t *mask, void *L, void *E, void *Y, void *G, void *Lam,
+                              void *Abar, const TubeScalars &sc, unsigned long long *res_prev,
+                              unsigned long long *res, int *flags, cudaStream_t s);
 cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
                              const void *mats, const void *src, void *dst, bool inverse,
                              cudaStream_t s);

@@ -1,26 +1,33 @@
 // Tube passes: the elementwise ADMM updates fused with the transform L along
 // modes 3..d (Eq. trans).  A CTA owns TP consecutive (i1, i2) positions of
-// every face slice (a "tube tile", TP x n elements), staged once in shared
-// memory: loads and stores are coalesced rows of TP elements per slice, and
-// each mode product runs on fibres held in registers.
+// every face slice (a "tube tile", TP x n elements) staged once in shared
+// memory; global traffic is coalesced 16-byte packs of VEC consecutive
+// positions, UNR packs per thread in flight, and each mode product runs on
+// fibres held in registers.
 //
-// Forward pass (Alg. 5 steps L, E, Y and the start of the G step):
+// Forward pass (first half of Alg. 5 iteration t):
 //   L1 = ((M - E + Y/mu) + (G - Lambda/mu)) / 2          Eq. coef-tensor, nabla = I
 //   H  = M - L1 + Y/mu;  E1 = Prox_{psi,lambda/mu}(H) on Omega, H off Omega
 //                                                         Eq. E_prox_ome(1), GNHTT
 //   Y1 = Y + mu (M - L1 - E1)                             Eq. lagrange11
 //   Abar = L(L1 + Lambda/mu)                              input of Eq. L_prox
-// Inverse pass (end of the G step and the Lambda update):
+// Inverse pass (second half):
 //   G1 = L^{-1}(Gbar);  Lambda1 = Lambda + mu (L1 - G1)   Eq. lagrange11-22
-// Both passes reduce their share of the Eq. convercon infinity norms.
+// Fused pass: the inverse pass of iteration t-1 followed, in the same tile,
+// by the forward pass of iteration t (G and Lambda of t-1 never leave the
+// SM before the forward pass uses them).
+// All three reduce their share of the Eq. convercon infinity norms.
 
 #include <math.h>
+
+#include <initializer_list>
 
 #include "tr_internal.cuh"
 
 namespace {
 
 constexpr int kTubeThreads = 256;
+constexpr int kUnroll = 2;
 
 template <typename T>
 __device__ __forceinline__ T prox_scalar(T v, T thr, int kind, T theta, T gamma) {
@@ -39,6 +46,53 @@ __device__ __forceinline__ T prox_scalar(T v, T thr, int kind, T theta, T gamma)
   return a > theta * sqrt(gamma * thr) ? v : T(0);
 }
 
+// ---- packs of VEC consecutive elements (16-byte vectors when VEC > 1)
+template <typename T, int VEC>
+struct Pk {
+  T v[VEC];
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ Pk<T, VEC> ld(const T *p) {
+  Pk<T, VEC> r;
+  if constexpr (VEC == 1) {
+    r.v[0] = *p;
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    r.v[0] = x.x; r.v[1] = x.y; r.v[2] = x.z; r.v[3] = x.w;
+  } else {
+    const double2 x = *reinterpret_cast<const double2 *>(p);
+    r.v[0] = x.x; r.v[1] = x.y;
+  }
+  return r;
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void st(T *p, const Pk<T, VEC> &r) {
+  if constexpr (VEC == 1) {
+    *p = r.v[0];
+  } else if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else {
+    *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ Pk<uint8_t, VEC> ldm(const uint8_t *p) {
+  Pk<uint8_t, VEC> r;
+  if constexpr (VEC == 1) {
+    r.v[0] = *p;
+  } else if constexpr (VEC == 4) {
+    const uchar4 x = *reinterpret_cast<const uchar4 *>(p);
+    r.v[0] = x.x; r.v[1] = x.y; r.v[2] = x.z; r.v[3] = x.w;
+  } else {
+    const uchar2 x = *reinterpret_cast<const uchar2 *>(p);
+    r.v[0] = x.x; r.v[1] = x.y;
+  }
+  return r;
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *slot, double v) {
   atomicMax(slot, (unsigned long long)__double_as_longlong(v));
 }
@@ -50,14 +104,15 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-// Block-wide max of up to 3 values, one atomic per value per CTA.
+// Block-wide max of K values, one atomic per value per CTA.
 template <typename T, int K>
-__device__ void block_max_to_global(T (&v)[K], unsigned long long *const (&slot)[K]) {
+__device__ void block_max_to_global(const T (&v)[K], unsigned long long *const (&slot)[K]) {
   __shared__ T red[K][32];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    T w = warp_max(v[k]);
+    const T w = warp_max(v[k]);
     if (lane == 0) red[k][warp] = w;
   }
   __syncthreads();
@@ -66,36 +121,36 @@ __device__ void block_max_to_global(T (&v)[K], unsigned long long *const (&slot)
     for (int k = 0; k < K; ++k) {
       T w = lane < nw ? red[k][lane] : T(0);
       w = warp_max(w);
-      if (lane == 0) atomic_max_nonneg(slot[k], (double)w);
+      if (lane == 0 && slot[k]) atomic_max_nonneg(slot[k], (double)w);
     }
   }
 }
 
-// Apply the mode products of the transform (or its inverse) to a tube tile
-// held in shared memory as tile[j * TP + p].  A fibre is the n_k elements of
-// one position p that differ only in mode k; a thread loads its fibre into
-// registers, multiplies by the n_k x n_k matrix (rows zero-padded to NK) and
-// writes the result back in place.
+// Mode products of the transform (or its inverse) on a tube tile in shared
+// memory, tile[j * TP + p].  A fibre is the n_k elements of one position p
+// that differ only in mode k; a thread loads its fibre into registers,
+// multiplies by the n_k x n_k matrix (rows zero-padded to NK) and writes the
+// result back in place.
 template <typename T, int NK>
 __device__ void tile_transform(T *tile, int n, int TP, const T *mats, const TransformDesc &td,
                                bool inverse) {
   for (int mi = 0; mi < td.nt; ++mi) {
     const int k = inverse ? td.nt - 1 - mi : mi;
-    const int nk = td.dim[k], st = td.stride[k];
+    const int nk = td.dim[k], stp = td.stride[k];
     const T *U = mats + (inverse ? td.off_inv[k] : td.off_fwd[k]);
     const int nfib = n / nk;
     for (int w = threadIdx.x; w < nfib * TP; w += blockDim.x) {
       const int p = w % TP, f = w / TP;
-      const int base = (f % st) + (f / st) * (st * nk);
+      const int base = (f % stp) + (f / stp) * (stp * nk);
       T x[NK];
 #pragma unroll
-      for (int m = 0; m < NK; ++m) x[m] = (m < nk) ? tile[(base + m * st) * TP + p] : T(0);
+      for (int m = 0; m < NK; ++m) x[m] = (m < nk) ? tile[(base + m * stp) * TP + p] : T(0);
       for (int i = 0; i < nk; ++i) {
         const T *Ui = U + i * NK;
         T acc = T(0);
 #pragma unroll
         for (int m = 0; m < NK; ++m) acc = fma(Ui[m], x[m], acc);
-        tile[(base + i * st) * TP + p] = acc;
+        tile[(base + i * stp) * TP + p] = acc;
       }
     }
     __syncthreads();
@@ -107,7 +162,84 @@ __device__ __forceinline__ void load_mats(T *dst, const T *src, int len) {
   for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
 }
 
-template <typename T, int NK>
+// Pack e of the tile -> (slice j, first position p within the tile).
+struct PackIdx {
+  int j, p;
+};
+__device__ __forceinline__ PackIdx pack_idx(int e, int per_row, int VEC) {
+  return {e / per_row, (e % per_row) * VEC};
+}
+
+// Copy a tile of a slice-major array into shared memory (zero beyond P).
+template <typename T, int VEC>
+__device__ void tile_load(T *tile, const T *__restrict__ src, int64_t P, int n, int TP,
+                          int64_t p0) {
+  const int per_row = TP / VEC, total = n * per_row;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
+    Pk<T, VEC> v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kTubeThreads;
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      if (e < total && p0 + q.p < P) v[u] = ld<T, VEC>(src + (int64_t)q.j * P + p0 + q.p);
+      else
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) v[u].v[i] = T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kTubeThreads;
+      if (e < total) {
+        const PackIdx q = pack_idx(e, per_row, VEC);
+        st<T, VEC>(tile + q.j * TP + q.p, v[u]);
+      }
+    }
+  }
+}
+
+template <typename T, int VEC>
+__device__ void tile_store(T *__restrict__ dst, const T *tile, int64_t P, int n, int TP,
+                           int64_t p0) {
+  const int per_row = TP / VEC, total = n * per_row;
+  for (int e = threadIdx.x; e < total; e += kTubeThreads) {
+    const PackIdx q = pack_idx(e, per_row, VEC);
+    if (p0 + q.p < P) st<T, VEC>(dst + (int64_t)q.j * P + p0 + q.p, ld<T, VEC>(tile + q.j * TP + q.p));
+  }
+}
+
+// The forward elementwise update on a pack; `gv` holds G^t (from global
+// memory or from the fused inverse), `la` Lambda^t.
+template <typename T, int VEC>
+__device__ __forceinline__ void forward_pack(const Pk<T, VEC> &m_, const Pk<uint8_t, VEC> &om,
+                                             const Pk<T, VEC> &l0, const Pk<T, VEC> &e0,
+                                             const Pk<T, VEC> &y0, const Pk<T, VEC> &gv,
+                                             const Pk<T, VEC> &la, const TubeScalars &sc,
+                                             Pk<T, VEC> &l1, Pk<T, VEC> &e1, Pk<T, VEC> &y1,
+                                             Pk<T, VEC> &a, T &rL, T &rE, T &rC, int &bad) {
+  const T mu = T(sc.mu), imu = T(1.0 / sc.mu), thr = T(sc.lam_over_mu);
+  const T th = T(sc.psi_theta), ga = T(sc.psi_gamma);
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) {
+    const bool o = om.v[i] != 0;
+    const T m = o ? m_.v[i] : T(0);
+    const T l = T(0.5) * ((m - e0.v[i] + y0.v[i] * imu) + (gv.v[i] - la.v[i] * imu));
+    const T h = m - l + y0.v[i] * imu;
+    T e;
+    if (o) e = (sc.noise == TR_NOISE_NONE) ? T(0) : prox_scalar(h, thr, sc.psi, th, ga);
+    else e = h;
+    const T y = y0.v[i] + mu * (m - l - e);
+    l1.v[i] = l;
+    e1.v[i] = e;
+    y1.v[i] = y;
+    a.v[i] = l + la.v[i] * imu;
+    rL = fmax(rL, fabs(l - l0.v[i]));
+    rE = fmax(rE, fabs(e - e0.v[i]));
+    rC = fmax(rC, fabs(m - l - e));
+    bad |= !(isfinite(a.v[i]) && isfinite(e) && isfinite(y));
+  }
+}
+
+template <typename T, int NK, int VEC>
 __global__ void __launch_bounds__(kTubeThreads)
 tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                     const T *__restrict__ M, const uint8_t *__restrict__ mask, T *__restrict__ L,
@@ -118,52 +250,61 @@ tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
   T *mats = reinterpret_cast<T *>(smem_raw);
   T *tile = mats + td.mats_len;
   load_mats(mats, mats_g, td.mats_len);
-
-  const T mu = T(sc.mu), imu = T(1.0 / sc.mu), thr = T(sc.lam_over_mu);
-  const T th = T(sc.psi_theta), ga = T(sc.psi_gamma);
   const int64_t p0 = (int64_t)blockIdx.x * TP;
+  const int per_row = TP / VEC, total = n * per_row;
   T rL = 0, rE = 0, rC = 0;
   int bad = 0;
-  for (int e = threadIdx.x; e < n * TP; e += blockDim.x) {
-    const int j = e / TP, p = e % TP;
-    const int64_t pos = p0 + p;
-    T a = T(0);
-    if (pos < P) {
-      const int64_t idx = (int64_t)j * P + pos;
-      const bool om = mask[idx] != 0;
-      const T m = om ? M[idx] : T(0);
-      const T l0 = L[idx], e0 = E[idx], y0 = Y[idx], g0 = G[idx], la = Lam[idx];
-      const T l1 = T(0.5) * ((m - e0 + y0 * imu) + (g0 - la * imu));
-      const T h = m - l1 + y0 * imu;
-      T e1;
-      if (om) e1 = (sc.noise == TR_NOISE_NONE) ? T(0) : prox_scalar(h, thr, sc.psi, th, ga);
-      else e1 = h;
-      const T y1 = y0 + mu * (m - l1 - e1);
-      a = l1 + la * imu;
-      L[idx] = l1;
-      E[idx] = e1;
-      Y[idx] = y1;
-      rL = fmax(rL, fabs(l1 - l0));
-      rE = fmax(rE, fabs(e1 - e0));
-      rC = fmax(rC, fabs(m - l1 - e1));
-      bad |= !(isfinite(a) && isfinite(e1) && isfinite(y1));
+  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
+    Pk<T, VEC> m[kUnroll], l0[kUnroll], ee[kUnroll], y0[kUnroll], g0[kUnroll], la[kUnroll];
+    Pk<uint8_t, VEC> om[kUnroll];
+    bool in[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kTubeThreads;
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      in[u] = e < total && p0 + q.p < P;
+      if (in[u]) {
+        const int64_t idx = (int64_t)q.j * P + p0 + q.p;
+        m[u] = ld<T, VEC>(M + idx);
+        om[u] = ldm<VEC>(mask + idx);
+        l0[u] = ld<T, VEC>(L + idx);
+        ee[u] = ld<T, VEC>(E + idx);
+        y0[u] = ld<T, VEC>(Y + idx);
+        g0[u] = ld<T, VEC>(G + idx);
+        la[u] = ld<T, VEC>(Lam + idx);
+      }
     }
-    tile[j * TP + p] = a;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kTubeThreads;
+      if (e >= total) continue;
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      Pk<T, VEC> a;
+      if (in[u]) {
+        const int64_t idx = (int64_t)q.j * P + p0 + q.p;
+        Pk<T, VEC> l1, e1, y1;
+        forward_pack<T, VEC>(m[u], om[u], l0[u], ee[u], y0[u], g0[u], la[u], sc, l1, e1, y1, a,
+                             rL, rE, rC, bad);
+        st<T, VEC>(L + idx, l1);
+        st<T, VEC>(E + idx, e1);
+        st<T, VEC>(Y + idx, y1);
+      } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) a.v[i] = T(0);
+      }
+      st<T, VEC>(tile + q.j * TP + q.p, a);
+    }
   }
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, false);
-  for (int e = threadIdx.x; e < n * TP; e += blockDim.x) {
-    const int j = e / TP, p = e % TP;
-    const int64_t pos = p0 + p;
-    if (pos < P) Abar[(int64_t)j * P + pos] = tile[j * TP + p];
-  }
+  tile_store<T, VEC>(Abar, tile, P, n, TP, p0);
   if (bad) atomicOr(flags, 1);
-  T v[3] = {rL, rE, rC};
+  const T v[3] = {rL, rE, rC};
   unsigned long long *const slots[3] = {res + RES_DL, res + RES_DE, res + RES_CONS};
   block_max_to_global<T, 3>(v, slots);
 }
 
-template <typename T, int NK>
+template <typename T, int NK, int VEC>
 __global__ void __launch_bounds__(kTubeThreads)
 tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                     const T *__restrict__ Gbar, const T *__restrict__ L, T *__restrict__ G,
@@ -173,38 +314,136 @@ tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
   T *tile = mats + td.mats_len;
   load_mats(mats, mats_g, td.mats_len);
   const int64_t p0 = (int64_t)blockIdx.x * TP;
-  for (int e = threadIdx.x; e < n * TP; e += blockDim.x) {
-    const int j = e / TP, p = e % TP;
-    const int64_t pos = p0 + p;
-    tile[j * TP + p] = pos < P ? Gbar[(int64_t)j * P + pos] : T(0);
-  }
+  tile_load<T, VEC>(tile, Gbar, P, n, TP, p0);
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, true);
   const T mu = T(mu_d);
+  const int per_row = TP / VEC, total = n * per_row;
   T rLG = 0, rG = 0;
   int bad = 0;
-  for (int e = threadIdx.x; e < n * TP; e += blockDim.x) {
-    const int j = e / TP, p = e % TP;
-    const int64_t pos = p0 + p;
-    if (pos < P) {
-      const int64_t idx = (int64_t)j * P + pos;
-      const T g1 = tile[j * TP + p];
-      const T l1 = L[idx], g0 = G[idx], la = Lam[idx];
-      const T la1 = la + mu * (l1 - g1);
-      G[idx] = g1;
-      Lam[idx] = la1;
-      rLG = fmax(rLG, fabs(l1 - g1));
-      rG = fmax(rG, fabs(g1 - g0));
-      bad |= !(isfinite(g1) && isfinite(la1));
+  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
+    Pk<T, VEC> l1[kUnroll], g0[kUnroll], la[kUnroll];
+    bool in[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kTubeThreads;
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      in[u] = e < total && p0 + q.p < P;
+      if (in[u]) {
+        const int64_t idx = (int64_t)q.j * P + p0 + q.p;
+        l1[u] = ld<T, VEC>(L + idx);
+        g0[u] = ld<T, VEC>(G + idx);
+        la[u] = ld<T, VEC>(Lam + idx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (!in[u]) continue;
+      const int e = e0 + u * kTubeThreads;
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      const int64_t idx = (int64_t)q.j * P + p0 + q.p;
+      const Pk<T, VEC> g1 = ld<T, VEC>(tile + q.j * TP + q.p);
+      Pk<T, VEC> la1;
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) {
+        la1.v[i] = la[u].v[i] + mu * (l1[u].v[i] - g1.v[i]);
+        rLG = fmax(rLG, fabs(l1[u].v[i] - g1.v[i]));
+        rG = fmax(rG, fabs(g1.v[i] - g0[u].v[i]));
+        bad |= !(isfinite(g1.v[i]) && isfinite(la1.v[i]));
+      }
+      st<T, VEC>(G + idx, g1);
+      st<T, VEC>(Lam + idx, la1);
     }
   }
   if (bad) atomicOr(flags, 1);
-  T v[2] = {rLG, rG};
+  const T v[2] = {rLG, rG};
   unsigned long long *const slots[2] = {res + RES_LG, res + RES_DG};
   block_max_to_global<T, 2>(v, slots);
 }
 
-template <typename T, int NK>
+// Inverse pass of iteration t-1 (mu_prev) + forward pass of iteration t (sc).
+template <typename T, int NK, int VEC>
+__global__ void __launch_bounds__(kTubeThreads)
+tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
+                  const T *__restrict__ Gbar, double mu_prev, const T *__restrict__ M,
+                  const uint8_t *__restrict__ mask, T *__restrict__ L, T *__restrict__ E,
+                  T *__restrict__ Y, T *__restrict__ G, T *__restrict__ Lam,
+                  T *__restrict__ Abar, TubeScalars sc, unsigned long long *res_prev,
+                  unsigned long long *res, int *flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *mats = reinterpret_cast<T *>(smem_raw);
+  T *tile = mats + td.mats_len;
+  load_mats(mats, mats_g, td.mats_len);
+  const int64_t p0 = (int64_t)blockIdx.x * TP;
+  tile_load<T, VEC>(tile, Gbar, P, n, TP, p0);
+  __syncthreads();
+  tile_transform<T, NK>(tile, n, TP, mats, td, true);
+  const T mup = T(mu_prev);
+  const int per_row = TP / VEC, total = n * per_row;
+  T rLG = 0, rG = 0, rL = 0, rE = 0, rC = 0;
+  int bad = 0;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
+    Pk<T, VEC> m[kUnroll], l0[kUnroll], ee[kUnroll], y0[kUnroll], g0[kUnroll], la[kUnroll];
+    Pk<uint8_t, VEC> om[kUnroll];
+    bool in[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kTubeThreads;
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      in[u] = e < total && p0 + q.p < P;
+      if (in[u]) {
+        const int64_t idx = (int64_t)q.j * P + p0 + q.p;
+        m[u] = ld<T, VEC>(M + idx);
+        om[u] = ldm<VEC>(mask + idx);
+        l0[u] = ld<T, VEC>(L + idx);
+        ee[u] = ld<T, VEC>(E + idx);
+        y0[u] = ld<T, VEC>(Y + idx);
+        g0[u] = ld<T, VEC>(G + idx);
+        la[u] = ld<T, VEC>(Lam + idx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * kTubeThreads;
+      if (e >= total) continue;
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      Pk<T, VEC> a;
+      if (in[u]) {
+        const int64_t idx = (int64_t)q.j * P + p0 + q.p;
+        const Pk<T, VEC> g1 = ld<T, VEC>(tile + q.j * TP + q.p);   // G^t
+        Pk<T, VEC> la1;                                            // Lambda^t
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+          la1.v[i] = la[u].v[i] + mup * (l0[u].v[i] - g1.v[i]);
+          rLG = fmax(rLG, fabs(l0[u].v[i] - g1.v[i]));
+          rG = fmax(rG, fabs(g1.v[i] - g0[u].v[i]));
+        }
+        Pk<T, VEC> l1, e1, y1;
+        forward_pack<T, VEC>(m[u], om[u], l0[u], ee[u], y0[u], g1, la1, sc, l1, e1, y1, a, rL,
+                             rE, rC, bad);
+        st<T, VEC>(G + idx, g1);
+        st<T, VEC>(Lam + idx, la1);
+        st<T, VEC>(L + idx, l1);
+        st<T, VEC>(E + idx, e1);
+        st<T, VEC>(Y + idx, y1);
+      } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) a.v[i] = T(0);
+      }
+      st<T, VEC>(tile + q.j * TP + q.p, a);
+    }
+  }
+  __syncthreads();
+  tile_transform<T, NK>(tile, n, TP, mats, td, false);
+  tile_store<T, VEC>(Abar, tile, P, n, TP, p0);
+  if (bad) atomicOr(flags, 1);
+  const T v[5] = {rLG, rG, rL, rE, rC};
+  unsigned long long *const slots[5] = {res_prev + RES_LG, res_prev + RES_DG, res + RES_DL,
+                                        res + RES_DE, res + RES_CONS};
+  block_max_to_global<T, 5>(v, slots);
+}
+
+template <typename T, int NK, int VEC>
 __global__ void __launch_bounds__(kTubeThreads)
 transform_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                  const T *__restrict__ src, T *__restrict__ dst, int inverse) {
@@ -213,18 +452,10 @@ transform_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict
   T *tile = mats + td.mats_len;
   load_mats(mats, mats_g, td.mats_len);
   const int64_t p0 = (int64_t)blockIdx.x * TP;
-  for (int e = threadIdx.x; e < n * TP; e += blockDim.x) {
-    const int j = e / TP, p = e % TP;
-    const int64_t pos = p0 + p;
-    tile[j * TP + p] = pos < P ? src[(int64_t)j * P + pos] : T(0);
-  }
+  tile_load<T, VEC>(tile, src, P, n, TP, p0);
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, inverse != 0);
-  for (int e = threadIdx.x; e < n * TP; e += blockDim.x) {
-    const int j = e / TP, p = e % TP;
-    const int64_t pos = p0 + p;
-    if (pos < P) dst[(int64_t)j * P + pos] = tile[j * TP + p];
-  }
+  tile_store<T, VEC>(dst, tile, P, n, TP, p0);
 }
 
 template <typename T>
@@ -241,76 +472,165 @@ int pick_tp(int n, const TransformDesc &td) {
   return tube_smem_for<T>(n, td, tp) > kSmemBudget ? 0 : tp;
 }
 
-// Dispatch on the padded fibre length NK (a multiple of 8, at most 64).
-template <typename T, template <typename, int> class Launcher, typename... Args>
-cudaError_t dispatch_nk(int nkpad, Args... args) {
-  switch (nkpad) {
-    case 8: return Launcher<T, 8>::run(args...);
-    case 16: return Launcher<T, 16>::run(args...);
-    case 24: return Launcher<T, 24>::run(args...);
-    case 32: return Launcher<T, 32>::run(args...);
-    case 40: return Launcher<T, 40>::run(args...);
-    case 48: return Launcher<T, 48>::run(args...);
-    case 56: return Launcher<T, 56>::run(args...);
-    case 64: return Launcher<T, 64>::run(args...);
-    default: return cudaErrorInvalidValue;
-  }
+// Vector width usable for every pointer of a launch: 16-byte packs need
+// P % VEC == 0 and 16-byte aligned bases (mask: VEC-byte aligned).
+template <typename T>
+int pick_vec(int64_t P, int tp, std::initializer_list<const void *> ptrs, const void *mask) {
+  constexpr int V = 16 / sizeof(T);
+  if (P % V != 0 || tp % V != 0) return 1;
+  for (const void *p : ptrs)
+    if (p && ((uintptr_t)p % 16) != 0) return 1;
+  if (mask && ((uintptr_t)mask % V) != 0) return 1;
+  return V;
 }
 
-template <typename T, int NK>
+template <typename K>
+cudaError_t prep(K kern, size_t smem) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Dispatch on (NK, VEC) at run time.
+template <typename T, template <typename, int, int> class Launcher, typename... Args>
+cudaError_t dispatch(int nkpad, int vec, Args... args) {
+  constexpr int V = 16 / sizeof(T);
+#define TR_CASE(NKV)                                                                         \
+  case NKV:                                                                                  \
+    return vec == V ? Launcher<T, NKV, V>::run(args...) : Launcher<T, NKV, 1>::run(args...);
+  switch (nkpad) {
+    TR_CASE(8)
+    TR_CASE(16)
+    TR_CASE(24)
+    TR_CASE(32)
+    TR_CASE(40)
+    TR_CASE(48)
+    TR_CASE(56)
+    TR_CASE(64)
+    default: return cudaErrorInvalidValue;
+  }
+#undef TR_CASE
+}
+
+struct TubeLaunch {
+  int64_t P;
+  int n, tp;
+  size_t smem;
+  unsigned grid;
+};
+
+template <typename T>
+bool tube_geometry(int64_t P, int n, const TransformDesc &td, TubeLaunch &g) {
+  g.P = P;
+  g.n = n;
+  g.tp = pick_tp<T>(n, td);
+  if (!g.tp) return false;
+  g.smem = tube_smem_for<T>(n, td, g.tp);
+  g.grid = (unsigned)((P + g.tp - 1) / g.tp);
+  return true;
+}
+
+template <typename T, int NK, int VEC>
 struct FwdLauncher {
-  static cudaError_t run(int64_t P, int n, const TransformDesc &td, const void *mats,
+  static cudaError_t run(const TubeLaunch &g, const TransformDesc &td, const void *mats,
                          const void *M, const uint8_t *mask, void *L, void *E, void *Y,
                          const void *G, const void *Lam, void *Abar, const TubeScalars &sc,
                          unsigned long long *res, int *flags, cudaStream_t s) {
-    int tp = pick_tp<T>(n, td);
-    if (!tp) return cudaErrorInvalidValue;
-    size_t smem = tube_smem_for<T>(n, td, tp);
-    auto k = tube_forward_kernel<T, NK>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = tube_forward_kernel<T, NK, VEC>;
+    cudaError_t e = prep(k, g.smem);
     if (e != cudaSuccess) return e;
-    int64_t grid = (P + tp - 1) / tp;
-    k<<<(unsigned)grid, kTubeThreads, smem, s>>>(P, n, tp, td, (const T *)mats, (const T *)M, mask,
-                                                (T *)L, (T *)E, (T *)Y, (const T *)G,
-                                                (const T *)Lam, (T *)Abar, sc, res, flags);
+    k<<<g.grid, kTubeThreads, g.smem, s>>>(g.P, g.n, g.tp, td, (const T *)mats, (const T *)M, mask,
+                                          (T *)L, (T *)E, (T *)Y, (const T *)G, (const T *)Lam,
+                                          (T *)Abar, sc, res, flags);
     return cudaGetLastError();
   }
 };
 
-template <typename T, int NK>
+template <typename T, int NK, int VEC>
 struct InvLauncher {
-  static cudaError_t run(int64_t P, int n, const TransformDesc &td, const void *mats,
+  static cudaError_t run(const TubeLaunch &g, const TransformDesc &td, const void *mats,
                          const void *Gbar, const void *L, void *G, void *Lam, double mu,
                          unsigned long long *res, int *flags, cudaStream_t s) {
-    int tp = pick_tp<T>(n, td);
-    if (!tp) return cudaErrorInvalidValue;
-    size_t smem = tube_smem_for<T>(n, td, tp);
-    auto k = tube_inverse_kernel<T, NK>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = tube_inverse_kernel<T, NK, VEC>;
+    cudaError_t e = prep(k, g.smem);
     if (e != cudaSuccess) return e;
-    int64_t grid = (P + tp - 1) / tp;
-    k<<<(unsigned)grid, kTubeThreads, smem, s>>>(P, n, tp, td, (const T *)mats, (const T *)Gbar,
-                                                (const T *)L, (T *)G, (T *)Lam, mu, res, flags);
+    k<<<g.grid, kTubeThreads, g.smem, s>>>(g.P, g.n, g.tp, td, (const T *)mats, (const T *)Gbar,
+                                          (const T *)L, (T *)G, (T *)Lam, mu, res, flags);
     return cudaGetLastError();
   }
 };
 
-template <typename T, int NK>
-struct XfLauncher {
-  static cudaError_t run(int64_t P, int n, const TransformDesc &td, const void *mats,
-                         const void *src, void *dst, bool inverse, cudaStream_t s) {
-    int tp = pick_tp<T>(n, td);
-    if (!tp) return cudaErrorInvalidValue;
-    size_t smem = tube_smem_for<T>(n, td, tp);
-    auto k = transform_kernel<T, NK>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T, int NK, int VEC>
+struct FusedLauncher {
+  static cudaError_t run(const TubeLaunch &g, const TransformDesc &td, const void *mats,
+                         const void *Gbar, double mu_prev, const void *M, const uint8_t *mask,
+                         void *L, void *E, void *Y, void *G, void *Lam, void *Abar,
+                         const TubeScalars &sc, unsigned long long *res_prev,
+                         unsigned long long *res, int *flags, cudaStream_t s) {
+    auto k = tube_fused_kernel<T, NK, VEC>;
+    cudaError_t e = prep(k, g.smem);
     if (e != cudaSuccess) return e;
-    int64_t grid = (P + tp - 1) / tp;
-    k<<<(unsigned)grid, kTubeThreads, smem, s>>>(P, n, tp, td, (const T *)mats, (const T *)src,
-                                                (T *)dst, inverse ? 1 : 0);
+    k<<<g.grid, kTubeThreads, g.smem, s>>>(g.P, g.n, g.tp, td, (const T *)mats, (const T *)Gbar,
+                                          mu_prev, (const T *)M, mask, (T *)L, (T *)E, (T *)Y,
+                                          (T *)G, (T *)Lam, (T *)Abar, sc, res_prev, res, flags);
     return cudaGetLastError();
   }
 };
+
+template <typename T, int NK, int VEC>
+struct XfLauncher {
+  static cudaError_t run(const TubeLaunch &g, const TransformDesc &td, const void *mats,
+                         const void *src, void *dst, bool inverse, cudaStream_t s) {
+    auto k = transform_kernel<T, NK, VEC>;
+    cudaError_t e = prep(k, g.smem);
+    if (e != cudaSuccess) return e;
+    k<<<g.grid, kTubeThreads, g.smem, s>>>(g.P, g.n, g.tp, td, (const T *)mats, (const T *)src,
+                                          (T *)dst, inverse ? 1 : 0);
+    return cudaGetLastError();
+  }
+};
+
+template <typename T>
+cudaError_t fwd_t(int64_t P, int n, const TransformDesc &td, const void *mats, const void *M,
+                  const uint8_t *mask, void *L, void *E, void *Y, const void *G, const void *Lam,
+                  void *Abar, const TubeScalars &sc, unsigned long long *res, int *flags,
+                  cudaStream_t s) {
+  TubeLaunch g;
+  if (!tube_geometry<T>(P, n, td, g)) return cudaErrorInvalidValue;
+  const int vec = pick_vec<T>(P, g.tp, {M, L, E, Y, G, Lam, Abar}, mask);
+  return dispatch<T, FwdLauncher>(td.nkpad, vec, g, td, mats, M, mask, L, E, Y, G, Lam, Abar, sc,
+                                  res, flags, s);
+}
+
+template <typename T>
+cudaError_t inv_t(int64_t P, int n, const TransformDesc &td, const void *mats, const void *Gbar,
+                  const void *L, void *G, void *Lam, double mu, unsigned long long *res,
+                  int *flags, cudaStream_t s) {
+  TubeLaunch g;
+  if (!tube_geometry<T>(P, n, td, g)) return cudaErrorInvalidValue;
+  const int vec = pick_vec<T>(P, g.tp, {Gbar, L, G, Lam}, nullptr);
+  return dispatch<T, InvLauncher>(td.nkpad, vec, g, td, mats, Gbar, L, G, Lam, mu, res, flags, s);
+}
+
+template <typename T>
+cudaError_t fused_t(int64_t P, int n, const TransformDesc &td, const void *mats, const void *Gbar,
+                    double mu_prev, const void *M, const uint8_t *mask, void *L, void *E, void *Y,
+                    void *G, void *Lam, void *Abar, const TubeScalars &sc,
+                    unsigned long long *res_prev, unsigned long long *res, int *flags,
+                    cudaStream_t s) {
+  TubeLaunch g;
+  if (!tube_geometry<T>(P, n, td, g)) return cudaErrorInvalidValue;
+  const int vec = pick_vec<T>(P, g.tp, {Gbar, M, L, E, Y, G, Lam, Abar}, mask);
+  return dispatch<T, FusedLauncher>(td.nkpad, vec, g, td, mats, Gbar, mu_prev, M, mask, L, E, Y,
+                                    G, Lam, Abar, sc, res_prev, res, flags, s);
+}
+
+template <typename T>
+cudaError_t xf_t(int64_t P, int n, const TransformDesc &td, const void *mats, const void *src,
+                 void *dst, bool inverse, cudaStream_t s) {
+  TubeLaunch g;
+  if (!tube_geometry<T>(P, n, td, g)) return cudaErrorInvalidValue;
+  const int vec = pick_vec<T>(P, g.tp, {src, dst}, nullptr);
+  return dispatch<T, XfLauncher>(td.nkpad, vec, g, td, mats, src, dst, inverse, s);
+}
 
 }  // namespace
 
@@ -320,29 +640,35 @@ cudaError_t launch_tube_forward(tr_dtype dt, int64_t P, int n, const TransformDe
                                 const TubeScalars &sc, unsigned long long *res, int *flags,
                                 cudaStream_t s) {
   if (dt == TR_F64)
-    return dispatch_nk<double, FwdLauncher>(td.nkpad, P, n, td, mats, M, mask, L, E, Y, G, Lam,
-                                            Abar, sc, res, flags, s);
-  return dispatch_nk<float, FwdLauncher>(td.nkpad, P, n, td, mats, M, mask, L, E, Y, G, Lam, Abar,
-                                         sc, res, flags, s);
+    return fwd_t<double>(P, n, td, mats, M, mask, L, E, Y, G, Lam, Abar, sc, res, flags, s);
+  return fwd_t<float>(P, n, td, mats, M, mask, L, E, Y, G, Lam, Abar, sc, res, flags, s);
 }
 
 cudaError_t launch_tube_inverse(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
                                 const void *mats, const void *Gbar, const void *L, void *G,
                                 void *Lam, double mu, unsigned long long *res, int *flags,
                                 cudaStream_t s) {
+  if (dt == TR_F64) return inv_t<double>(P, n, td, mats, Gbar, L, G, Lam, mu, res, flags, s);
+  return inv_t<float>(P, n, td, mats, Gbar, L, G, Lam, mu, res, flags, s);
+}
+
+cudaError_t launch_tube_fused(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
+                              const void *mats, const void *Gbar, double mu_prev, const void *M,
+                              const uint8_t *mask, void *L, void *E, void *Y, void *G, void *Lam,
+                              void *Abar, const TubeScalars &sc, unsigned long long *res_prev,
+                              unsigned long long *res, int *flags, cudaStream_t s) {
   if (dt == TR_F64)
-    return dispatch_nk<double, InvLauncher>(td.nkpad, P, n, td, mats, Gbar, L, G, Lam, mu, res,
-                                            flags, s);
-  return dispatch_nk<float, InvLauncher>(td.nkpad, P, n, td, mats, Gbar, L, G, Lam, mu, res, flags,
-                                         s);
+    return fused_t<double>(P, n, td, mats, Gbar, mu_prev, M, mask, L, E, Y, G, Lam, Abar, sc,
+                           res_prev, res, flags, s);
+  return fused_t<float>(P, n, td, mats, Gbar, mu_prev, M, mask, L, E, Y, G, Lam, Abar, sc,
+                        res_prev, res, flags, s);
 }
 
 cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
                              const void *mats, const void *src, void *dst, bool inverse,
                              cudaStream_t s) {
-  if (dt == TR_F64)
-    return dispatch_nk<double, XfLauncher>(td.nkpad, P, n, td, mats, src, dst, inverse, s);
-  return dispatch_nk<float, XfLauncher>(td.nkpad, P, n, td, mats, src, dst, inverse, s);
+  if (dt == TR_F64) return xf_t<double>(P, n, td, mats, src, dst, inverse, s);
+  return xf_t<float>(P, n, td, mats, src, dst, inverse, s);
 }
 
 size_t tube_smem_bytes(tr_dtype dt, int n, const TransformDesc &td, int *tp_out) {
