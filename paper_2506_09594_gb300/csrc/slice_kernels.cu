@@ -207,149 +207,260 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// In-place Householder QR of the m x l panel P (column-major, leading dim
-// ld, l <= m) in shared memory.  Reflector k is H_k = I - tau_k v v^T with
-// v = (1, P[k+1:m, k]); R is left in the upper triangle (LAPACK geqr2
-// convention: H_k x = beta e_1, beta = -sign(x_0) ||x||).
-template <typename T>
-__device__ void block_qr_factor(T *P, int m, int l, int ld, T *tau) {
+// Register-resident Householder QR of an m x l column-major panel
+// (l <= m <= 32*RPL).  Column c lives in the registers of warp c mod nw
+// (slot q = c / nw < CPW); lane `lane` holds rows lane + 32 r, r < RPL.
+// Reflector k (LAPACK geqr2 convention: H_k = I - tau_k v v^T, v = (1,
+// x[k+1:]/(x_k - beta)), H_k x = beta e_k, beta = -sign(x_k) ||x[k:]||) is
+// published in shared memory V (column k, rows > k) with tau[k].  The
+// factorisation needs one barrier per column; forming Q = H_0...H_{l-1}[I;0]
+// needs none, since every warp then updates only its own columns against
+// the read-only reflectors.
+template <typename T, int CPW, int RPL>
+struct RegPanel {
+  T x[CPW][RPL];
+
+  __device__ __forceinline__ static int owner_slot(int c, int warp, int nw) {
+    return (c % nw) == warp ? c / nw : -1;
+  }
+
+  __device__ __forceinline__ void load(const T *P, int ldp, int m, int l, int warp, int nw,
+                                       int lane) {
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp + q * nw;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        x[q][r] = (c < l && i < m) ? P[(size_t)c * ldp + i] : T(0);
+      }
+    }
+  }
+
+  __device__ __forceinline__ void store(T *Q, int ldq, int m, int l, int warp, int nw, int lane) const {
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp + q * nw;
+      if (c >= l) continue;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i < m) Q[(size_t)c * ldq + i] = x[q][r];
+      }
+    }
+  }
+
+  // Householder reflector of slot qs's column (rows k..m-1); v -> V[k],
+  // tau -> tau[k].  The slot is copied out through a static loop so that
+  // the panel stays in registers.
+  __device__ __forceinline__ void reflector(int qs, int k, int m, int lane, T *Vk, T *tau) {
+    T col[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      col[r] = x[0][r];
+#pragma unroll
+      for (int q = 1; q < CPW; ++q)
+        if (q == qs) col[r] = x[q][r];
+    }
+    T ss = T(0), xk = T(0);
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int i = lane + 32 * r;
+      if (i > k && i < m) ss = fma(col[r], col[r], ss);
+      if (r == (k >> 5)) xk = col[r];
+    }
+    ss = warp_sum(ss);
+    const T x0 = __shfl_sync(0xffffffffu, xk, k & 31);
+    T beta = x0, tk = T(0), scale = T(0);
+    if (ss > T(0)) {
+      const T nrm = sqrt(fma(x0, x0, ss));
+      beta = x0 >= T(0) ? -nrm : nrm;
+      tk = (beta - x0) / beta;
+      scale = T(1) / (x0 - beta);
+    }
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int i = lane + 32 * r;
+      if (i > k && i < m) {
+        col[r] *= scale;
+        Vk[i] = col[r];
+      } else if (i == k) {
+        col[r] = beta;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CPW; ++q)
+      if (q == qs)
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) x[q][r] = col[r];
+    if (lane == 0) tau[k] = tk;
+  }
+
+  // Apply H_k to the owned columns c >= c_lo (c < l).
+  __device__ __forceinline__ void apply(const T *Vk, T tk, int k, int m, int l, int c_lo, int warp,
+                                        int nw, int lane) {
+    T v[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int i = lane + 32 * r;
+      v[r] = (i > k && i < m) ? Vk[i] : (i == k ? T(1) : T(0));
+    }
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp + q * nw;
+      if (c < c_lo || c >= l) continue;   // warp-uniform
+      T s = T(0);
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) s = fma(v[r], x[q][r], s);
+      s = tk * warp_sum(s);
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) x[q][r] = fma(-s, v[r], x[q][r]);
+    }
+  }
+};
+
+// QR of the panel P (global, column-major m x l, ld m): R (l x l, column-
+// major, zero below the diagonal) to Rout when non-null, Q overwrites P.
+template <typename T, int CPW, int RPL>
+__device__ void block_reg_qr(T *P, int m, int l, T *V, T *tau, T *Rout) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  RegPanel<T, CPW, RPL> pn;
+  pn.load(P, m, m, l, warp, nw, lane);
+  {
+    const int q0 = RegPanel<T, CPW, RPL>::owner_slot(0, warp, nw);
+    if (q0 >= 0) pn.reflector(q0, 0, m, lane, V, tau);
+  }
+  __syncthreads();
   for (int k = 0; k < l; ++k) {
-    if (warp == 0) {
-      T *col = P + (size_t)k * ld;
-      T ss = T(0);
-      for (int i = k + 1 + lane; i < m; i += 32) ss = fma(col[i], col[i], ss);
-      ss = warp_sum(ss);
-      const T x0 = col[k];
-      T beta = x0, tk = T(0), scale = T(0);
-      if (ss > T(0)) {
-        const T nrm = sqrt(fma(x0, x0, ss));
-        beta = x0 >= T(0) ? -nrm : nrm;
-        tk = (beta - x0) / beta;
-        scale = T(1) / (x0 - beta);
-      }
-      __syncwarp();
-      for (int i = k + 1 + lane; i < m; i += 32) col[i] *= scale;
-      if (lane == 0) {
-        col[k] = beta;
-        tau[k] = tk;
-      }
-    }
-    __syncthreads();
-    const T tk = tau[k];
-    const T *v = P + (size_t)k * ld;
-    for (int c = k + 1 + warp; c < l; c += nw) {
-      T *col = P + (size_t)c * ld;
-      const T ck = col[k];
-      T s = T(0);
-      for (int i = k + 1 + lane; i < m; i += 32) s = fma(v[i], col[i], s);
-      s = warp_sum(s) + ck;
-      const T w = tk * s;
-      for (int i = k + 1 + lane; i < m; i += 32) col[i] = fma(-w, v[i], col[i]);
-      if (lane == 0) col[k] = ck - w;
+    pn.apply(V + (size_t)k * m, tau[k], k, m, l, k + 1, warp, nw, lane);
+    if (k + 1 < l) {
+      const int q1 = RegPanel<T, CPW, RPL>::owner_slot(k + 1, warp, nw);
+      if (q1 >= 0) pn.reflector(q1, k + 1, m, lane, V + (size_t)(k + 1) * m, tau);
     }
     __syncthreads();
   }
-}
-
-// Overwrite the factored panel with the thin Q = H_0 ... H_{l-1} [I; 0]
-// (LAPACK org2r order: backwards, each column formed after its trailing
-// columns).
-template <typename T>
-__device__ void block_qr_form_q(T *P, int m, int l, int ld, const T *tau) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = l - 1; k >= 0; --k) {
-    const T tk = tau[k];
-    const T *v = P + (size_t)k * ld;
-    for (int c = k + 1 + warp; c < l; c += nw) {
-      T *col = P + (size_t)c * ld;
-      const T ck = col[k];
-      T s = T(0);
-      for (int i = k + 1 + lane; i < m; i += 32) s = fma(v[i], col[i], s);
-      s = warp_sum(s) + ck;
-      const T w = tk * s;
-      for (int i = k + 1 + lane; i < m; i += 32) col[i] = fma(-w, v[i], col[i]);
-      if (lane == 0) col[k] = ck - w;
+  if (Rout) {
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp + q * nw;
+      if (c >= l) continue;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i < l) Rout[(size_t)c * l + i] = i <= c ? pn.x[q][r] : T(0);
+      }
     }
-    __syncthreads();
-    T *colk = P + (size_t)k * ld;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      if (i < k) colk[i] = T(0);
-      else if (i == k) colk[i] = T(1) - tk;
-      else colk[i] = -tk * colk[i];
-    }
-    __syncthreads();
   }
+  // form Q in registers: start from [I; 0] on the owned columns
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp + q * nw;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) pn.x[q][r] = (lane + 32 * r == c) ? T(1) : T(0);
+  }
+  for (int k = l - 1; k >= 0; --k) pn.apply(V + (size_t)k * m, tau[k], k, m, l, k, warp, nw, lane);
+  pn.store(P, m, m, l, warp, nw, lane);
 }
 
-template <typename T>
+template <typename T, int CPW, int RPL>
 __global__ void qr_kernel(int m, int l, T *__restrict__ P, int64_t sP) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *panel = reinterpret_cast<T *>(smem_raw);
-  T *tau = panel + (size_t)m * l;
-  T *Pj = P + (int64_t)blockIdx.x * sP;
-  for (int e = threadIdx.x; e < m * l; e += blockDim.x) panel[e] = Pj[e];
-  __syncthreads();
-  block_qr_factor(panel, m, l, m, tau);
-  block_qr_form_q(panel, m, l, m, tau);
-  for (int e = threadIdx.x; e < m * l; e += blockDim.x) Pj[e] = panel[e];
+  T *V = reinterpret_cast<T *>(smem_raw);
+  T *tau = V + (size_t)m * l;
+  block_reg_qr<T, CPW, RPL>(P + (int64_t)blockIdx.x * sP, m, l, V, tau, nullptr);
 }
 
 // ------------------------------------------------------ one-sided Jacobi
 // Hestenes one-sided Jacobi on the l x l matrix W (column-major): rotate
 // column pairs until all are mutually orthogonal, accumulating the
-// rotations in J, so that W_in J = W_out.  Pairs follow the round-robin
-// (circle) ordering so that l/2 disjoint pairs rotate concurrently, one
-// warp per pair.
+// rotations in J (W_in J = W_out).  Pairs follow the round-robin (circle)
+// ordering, l/2 disjoint pairs per round; each pair is handled by a group
+// of G lanes that split the rows, so its inner products need log2(G)
+// shuffle levels.
 template <typename T>
-__device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+__device__ __forceinline__ void jacobi_rotation(T al, T be, T ga, T &c, T &s) {
+  if constexpr (sizeof(T) == 4) {
+    const T zeta = T(0.5) * (be - al) * __frcp_rn(ga);
+    const T az = fabsf(zeta);
+    const T t = az > T(1e10) ? T(0.5) / az : T(1) / (az + sqrtf(fmaf(az, az, T(1))));
+    const T ts = zeta >= T(0) ? t : -t;
+    c = rsqrtf(fmaf(ts, ts, T(1)));
+    s = c * ts;
+  } else {
+    const T zeta = (be - al) / (T(2) * ga);
+    const T az = fabs(zeta);
+    const T t = T(1) / (az + hypot(T(1), az));
+    const T ts = zeta >= T(0) ? t : -t;
+    c = T(1) / sqrt(fma(ts, ts, T(1)));
+    s = c * ts;
+  }
+}
+
+// Only the first `nthr` threads (a multiple of 32) take part; they
+// synchronise among themselves with named barrier 1, so the other warps of
+// the block wait at the caller's next __syncthreads.
+__device__ __forceinline__ void named_sync(int nthr) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+}
+
+template <typename T, int G>
+__device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps, int nthr) {
   const int lp = l + (l & 1);
-  if (lp < 2) return;
+  if (lp < 2 || (int)threadIdx.x >= nthr) return;
+  const int npairs = lp / 2;
+  const int gid = threadIdx.x / G, gl = threadIdx.x % G, ngroups = nthr / G;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
-    __syncthreads();
+    named_sync(nthr);
     for (int r = 0; r < lp - 1; ++r) {
-      for (int pi = warp; pi < lp / 2; pi += nw) {
-        int a, b;
-        if (pi == 0) { a = lp - 1; b = r; }
-        else { a = (r + pi) % (lp - 1); b = (r - pi + lp - 1) % (lp - 1); }
-        const int p = a < b ? a : b, q = a < b ? b : a;
-        if (q >= l) continue;
+      for (int base = 0; base < npairs; base += ngroups) {
+        const int pi = base + gid;
+        int p = 0, q = 0;
+        if (pi < npairs) {
+          int a, b;
+          if (pi == 0) { a = lp - 1; b = r; }
+          else {
+            a = r + pi; if (a >= lp - 1) a -= lp - 1;
+            b = r - pi; if (b < 0) b += lp - 1;
+          }
+          p = a < b ? a : b;
+          q = a < b ? b : a;
+        }
+        const bool valid = pi < npairs && q < l;
         T *wp = W + (size_t)p * l, *wq = W + (size_t)q * l;
         T al = T(0), be = T(0), ga = T(0);
-        for (int i = lane; i < l; i += 32) {
-          const T x = wp[i], y = wq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
+        if (valid)
+          for (int i = gl; i < l; i += G) {
+            const T x = wp[i], y = wq[i];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga != T(0) && fabs(ga) > tol * sqrt(al * be)) {
-          const T zeta = (be - al) / (T(2) * ga);
-          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + hypot(T(1), zeta));
-          const T c = T(1) / sqrt(fma(t, t, T(1)));
-          const T s = c * t;
-          for (int i = lane; i < l; i += 32) {
+        if (valid && ga != T(0) && fabs(ga) > tol * sqrt(al * be)) {
+          T c, s;
+          jacobi_rotation(al, be, ga, c, s);
+          T *jp = J + (size_t)p * l, *jq = J + (size_t)q * l;
+          for (int i = gl; i < l; i += G) {
             const T x = wp[i], y = wq[i];
             wp[i] = c * x - s * y;
             wq[i] = s * x + c * y;
+            const T u = jp[i], w = jq[i];
+            jp[i] = c * u - s * w;
+            jq[i] = s * u + c * w;
           }
-          T *jp = J + (size_t)p * l, *jq = J + (size_t)q * l;
-          for (int i = lane; i < l; i += 32) {
-            const T x = jp[i], y = jq[i];
-            jp[i] = c * x - s * y;
-            jq[i] = s * x + c * y;
-          }
-          if (lane == 0) *flag = 1;
+          if (gl == 0) *flag = 1;
         }
       }
-      __syncthreads();
+      named_sync(nthr);
     }
     const int any = *flag;
-    __syncthreads();
+    named_sync(nthr);
     if (!any) break;
   }
 }
@@ -372,7 +483,7 @@ __device__ __forceinline__ T prox_sv(T s, const ShrinkScalars &sh) {
 
 // Per slice: QR of B^T (P2), Jacobi SVD of R, shrink, core C, then
 // P1 <- P1 C (= Q C) and P2 <- Qb, ready for Gbar = P1 P2^T.
-template <typename T>
+template <typename T, int CPW, int RPL, int G>
 __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64_t sP1,
                                 T *__restrict__ P2, int64_t sP2, ShrinkScalars sh,
                                 T *__restrict__ sig_out, int *__restrict__ rank_out) {
@@ -389,22 +500,21 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   T *P1j = P1 + (int64_t)j * sP1;
   T *P2j = P2 + (int64_t)j * sP2;
 
-  for (int e = threadIdx.x; e < n2 * l; e += blockDim.x) panel[e] = P2j[e];
-  __syncthreads();
-  block_qr_factor(panel, n2, l, n2, tau);
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int r = e % l, c = e / l;
-    W[e] = r <= c ? panel[(size_t)c * n2 + r] : T(0);
-    J[e] = r == c ? T(1) : T(0);
-  }
-  __syncthreads();
-  block_qr_form_q(panel, n2, l, n2, tau);
-  for (int e = threadIdx.x; e < n2 * l; e += blockDim.x) P2j[e] = panel[e];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) J[e] = (e % l == e / l) ? T(1) : T(0);
+  // B^T = Qb R: Qb overwrites P2, R lands in W
+  block_reg_qr<T, CPW, RPL>(P2j, n2, l, panel, tau, W);
   // Rotate only while a pair's cosine exceeds max(l, 8) * eps: below that the
   // computed inner product is rounding noise (an l-term dot product).
   const T eps = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
   const T tol = T(l > 8 ? l : 8) * eps;
-  block_jacobi(W, J, l, flag, tol, sizeof(T) == 4 ? 16 : 30);
+  {
+    const int lp = l + (l & 1);
+    int nthr = ((lp / 2) * G + 31) / 32 * 32;
+    if (nthr > (int)blockDim.x) nthr = blockDim.x;
+    __syncthreads();
+    block_jacobi<T, G>(W, J, l, flag, tol, sizeof(T) == 4 ? 16 : 30, nthr);
+    __syncthreads();
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < l; i += nw) {
@@ -432,20 +542,44 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     for (int i = 0; i < l; ++i) acc = fma(J[(size_t)i * l + a] * ratio[i], W[(size_t)i * l + b], acc);
     C[e] = acc;
   }
-  __syncthreads();
   for (int e = threadIdx.x; e < n1 * l; e += blockDim.x) panel[e] = P1j[e];
   __syncthreads();
-  for (int e = threadIdx.x; e < n1 * l; e += blockDim.x) {
-    const int r = e % n1, b = e / n1;
-    T acc = T(0);
-    for (int a = 0; a < l; ++a) acc = fma(panel[(size_t)a * n1 + r], C[a + (size_t)b * l], acc);
-    P1j[e] = acc;
+  // Z = Q C, four output columns per work item
+  const int nb4 = (l + 3) / 4;
+  for (int e = threadIdx.x; e < n1 * nb4; e += blockDim.x) {
+    const int r = e % n1, b0 = (e / n1) * 4;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int a = 0; a < l; ++a) {
+      const T x = panel[(size_t)a * n1 + r];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (b0 + u < l) acc[u] = fma(x, C[a + (size_t)(b0 + u) * l], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (b0 + u < l) P1j[(size_t)(b0 + u) * n1 + r] = acc[u];
   }
+}
+
+// Threads for the panel kernels: each warp owns at most CPW columns.
+inline int panel_warps(int l, int cpw) {
+  int nw = (l + cpw - 1) / cpw;
+  if (nw < 1) nw = 1;
+  if (nw > 32) nw = 32;
+  return nw;
+}
+
+inline int pick_cpw(int l) { return l <= 64 ? 2 : 4; }
+
+// rows per lane of the register panel: m <= 32 * RPL
+inline int pick_rpl(int m) {
+  const int r = (m + 31) / 32;
+  return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 8 : r <= 16 ? 16 : 32;
 }
 
 template <typename T>
 size_t qr_smem(int m, int l) {
-  return sizeof(T) * ((size_t)m * l + l);
+  return sizeof(T) * ((size_t)m * l + ((l + 3) & ~3));
 }
 
 template <typename T>
@@ -456,14 +590,56 @@ size_t svd_smem(int n1, int n2, int l) {
 
 constexpr size_t kSliceSmemMax = 227 * 1024;
 
+template <typename T, int CPW, int RPL>
+cudaError_t run_qr_t(int m, int l, T *P, int n, cudaStream_t s) {
+  const size_t smem = qr_smem<T>(m, l);
+  auto k = qr_kernel<T, CPW, RPL>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<n, 32 * panel_warps(l, CPW), smem, s>>>(m, l, P, (int64_t)m * l);
+  return cudaGetLastError();
+}
+
+template <typename T, int CPW, int RPL, int G>
+cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh, T *sig,
+                      int *rank, cudaStream_t s) {
+  const size_t smem = svd_smem<T>(n1, n2, l);
+  auto k = svd_core_kernel<T, CPW, RPL, G>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int lp = l + (l & 1);
+  int nw = panel_warps(l, CPW);
+  const int jw = (lp / 2 * G + 31) / 32;   // warps giving every Jacobi pair a lane group
+  if (jw > nw) nw = jw > 32 ? 32 : jw;
+  if (nw < 4) nw = 4;
+  k<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig, rank);
+  return cudaGetLastError();
+}
+
+#define TR_RPL_DISPATCH(RPLV, CALL) \
+  switch (RPLV) {                   \
+    case 1: { constexpr int RPL = 1; return CALL; } \
+    case 2: { constexpr int RPL = 2; return CALL; } \
+    case 4: { constexpr int RPL = 4; return CALL; } \
+    case 8: { constexpr int RPL = 8; return CALL; } \
+    case 16: { constexpr int RPL = 16; return CALL; } \
+    default: { constexpr int RPL = 32; return CALL; } \
+  }
+
 template <typename T>
 cudaError_t run_qr(int m, int l, T *P, int n, cudaStream_t s) {
-  const size_t smem = qr_smem<T>(m, l);
-  cudaError_t e = cudaFuncSetAttribute(qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  qr_kernel<T><<<n, 256, smem, s>>>(m, l, P, (int64_t)m * l);
-  return cudaGetLastError();
+  if (pick_cpw(l) == 2) { TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 2, RPL>(m, l, P, n, s))) }
+  TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 4, RPL>(m, l, P, n, s)))
+}
+
+template <typename T>
+cudaError_t run_svd_core(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh,
+                         T *sig, int *rank, cudaStream_t s) {
+  if (pick_cpw(l) == 2) {
+    if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 4>(n1, n2, l, P1, P2, n, sh, sig, rank, s))) }
+    TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s)))
+  }
+  TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s)))
 }
 
 template <typename T>
@@ -501,18 +677,8 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   }
   if ((e = run_qr<T>(n1, l, P1, n, s)) != cudaSuccess) return e;
   if ((e = gemm_AtX(P1, P2)) != cudaSuccess) return e;
-  {
-    const size_t smem = svd_smem<T>(n1, n2, l);
-    if ((e = cudaFuncSetAttribute(svd_core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-      return e;
-    const int lp = l + (l & 1);
-    int threads = 32 * (lp / 2 > 8 ? lp / 2 : 8);
-    if (threads > 1024) threads = 1024;
-    svd_core_kernel<T><<<n, threads, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2,
-                                                (int64_t)n2 * l, sh, (T *)w.sig, w.rank);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s)) != cudaSuccess)
+    return e;
   // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output
   GemmArgs g{n1, n2, l, P1, (int64_t)n1 * l, 1, n1, P2, (int64_t)n2 * l, n2, 1, Gbar, sA, n2, 1};
   return bgemm<T>(g, n, s);
@@ -530,5 +696,5 @@ size_t slice_smem_limit_ok(tr_dtype dt, int n1, int n2, int l) {
   const int mx = n1 > n2 ? n1 : n2;
   const size_t a = dt == TR_F64 ? svd_smem<double>(n1, n2, l) : svd_smem<float>(n1, n2, l);
   const size_t b = dt == TR_F64 ? qr_smem<double>(mx, l) : qr_smem<float>(mx, l);
-  return (a <= kSliceSmemMax && b <= kSliceSmemMax) ? 1 : 0;
+  return (a <= kSliceSmemMax && b <= kSliceSmemMax && mx <= 1024 && l <= 128) ? 1 : 0;
 }

@@ -27,7 +27,13 @@
 namespace {
 
 constexpr int kTubeThreads = 256;
-constexpr int kUnroll = 2;
+constexpr int kUnroll = 1;
+
+// CTAs per SM the register budget must allow: three for the common small
+// fibres in FP32 (three 256-thread CTAs keep ~80 KB of loads in flight per
+// SM), no constraint for long fibres or FP64.
+template <typename T, int NK>
+constexpr int tube_min_blocks() { return (sizeof(T) == 4 && NK <= 32) ? 3 : 1; }
 
 template <typename T>
 __device__ __forceinline__ T prox_scalar(T v, T thr, int kind, T theta, T gamma) {
@@ -174,11 +180,13 @@ __device__ __forceinline__ PackIdx pack_idx(int e, int per_row, int VEC) {
 template <typename T, int VEC>
 __device__ void tile_load(T *tile, const T *__restrict__ src, int64_t P, int n, int TP,
                           int64_t p0) {
+  // one array only: four packs per thread in flight
+  constexpr int U = 4;
   const int per_row = TP / VEC, total = n * per_row;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
-    Pk<T, VEC> v[kUnroll];
+  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * U) {
+    Pk<T, VEC> v[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int e = e0 + u * kTubeThreads;
       const PackIdx q = pack_idx(e, per_row, VEC);
       if (e < total && p0 + q.p < P) v[u] = ld<T, VEC>(src + (int64_t)q.j * P + p0 + q.p);
@@ -187,7 +195,7 @@ __device__ void tile_load(T *tile, const T *__restrict__ src, int64_t P, int n, 
         for (int i = 0; i < VEC; ++i) v[u].v[i] = T(0);
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int e = e0 + u * kTubeThreads;
       if (e < total) {
         const PackIdx q = pack_idx(e, per_row, VEC);
@@ -222,7 +230,10 @@ __device__ __forceinline__ void forward_pack(const Pk<T, VEC> &m_, const Pk<uint
   for (int i = 0; i < VEC; ++i) {
     const bool o = om.v[i] != 0;
     const T m = o ? m_.v[i] : T(0);
-    const T l = T(0.5) * ((m - e0.v[i] + y0.v[i] * imu) + (gv.v[i] - la.v[i] * imu));
+    // (M - E + Y/mu) + (G - Lambda/mu) summed as (M - E + G) + (Y - Lambda)/mu:
+    // Y/mu and Lambda/mu grow large and nearly cancel (Lambda -> Y at a KKT
+    // point), so subtracting the multipliers first avoids that cancellation.
+    const T l = T(0.5) * ((m - e0.v[i] + gv.v[i]) + (y0.v[i] - la.v[i]) * imu);
     const T h = m - l + y0.v[i] * imu;
     T e;
     if (o) e = (sc.noise == TR_NOISE_NONE) ? T(0) : prox_scalar(h, thr, sc.psi, th, ga);
@@ -240,7 +251,7 @@ __device__ __forceinline__ void forward_pack(const Pk<T, VEC> &m_, const Pk<uint
 }
 
 template <typename T, int NK, int VEC>
-__global__ void __launch_bounds__(kTubeThreads)
+__global__ void __launch_bounds__(kTubeThreads, tube_min_blocks<T, NK>())
 tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                     const T *__restrict__ M, const uint8_t *__restrict__ mask, T *__restrict__ L,
                     T *__restrict__ E, T *__restrict__ Y, const T *__restrict__ G,
@@ -305,7 +316,7 @@ tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
 }
 
 template <typename T, int NK, int VEC>
-__global__ void __launch_bounds__(kTubeThreads)
+__global__ void __launch_bounds__(kTubeThreads, tube_min_blocks<T, NK>())
 tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                     const T *__restrict__ Gbar, const T *__restrict__ L, T *__restrict__ G,
                     T *__restrict__ Lam, double mu_d, unsigned long long *res, int *flags) {
@@ -321,11 +332,12 @@ tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
   const int per_row = TP / VEC, total = n * per_row;
   T rLG = 0, rG = 0;
   int bad = 0;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
-    Pk<T, VEC> l1[kUnroll], g0[kUnroll], la[kUnroll];
-    bool in[kUnroll];
+  constexpr int U = 2;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * U) {
+    Pk<T, VEC> l1[U], g0[U], la[U];
+    bool in[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int e = e0 + u * kTubeThreads;
       const PackIdx q = pack_idx(e, per_row, VEC);
       in[u] = e < total && p0 + q.p < P;
@@ -337,7 +349,7 @@ tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
       }
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       if (!in[u]) continue;
       const int e = e0 + u * kTubeThreads;
       const PackIdx q = pack_idx(e, per_row, VEC);
@@ -363,7 +375,7 @@ tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
 
 // Inverse pass of iteration t-1 (mu_prev) + forward pass of iteration t (sc).
 template <typename T, int NK, int VEC>
-__global__ void __launch_bounds__(kTubeThreads)
+__global__ void __launch_bounds__(kTubeThreads, tube_min_blocks<T, NK>())
 tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                   const T *__restrict__ Gbar, double mu_prev, const T *__restrict__ M,
                   const uint8_t *__restrict__ mask, T *__restrict__ L, T *__restrict__ E,
@@ -444,7 +456,7 @@ tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restric
 }
 
 template <typename T, int NK, int VEC>
-__global__ void __launch_bounds__(kTubeThreads)
+__global__ void __launch_bounds__(kTubeThreads, tube_min_blocks<T, NK>())
 transform_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                  const T *__restrict__ src, T *__restrict__ dst, int inverse) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
