@@ -183,6 +183,28 @@ tr_status tr_profile_enable(tr_handle *h, int max_steps);
 tr_status tr_profile_read(tr_handle *h, double ms[3], int *steps);
 tr_status tr_kernel_launches(const tr_handle *h, uint64_t *count);
 
+/* The slice pass of tr_slice_prox without any device allocation.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a host thread on a latency-critical loop (allocation
+ * synchronises the whole device), or code running inside another
+ * framework's memory pool that owns all device memory.  It needs no handle:
+ * the caller passes the transformed stack Abar (input) and Gbar (output),
+ * both device buffers of n slices of n1 x n2 (face-slice layout, dtype
+ * elements, must not alias); l (clamped to min(n1, n2)) is the sketch width,
+ * q the power iterations, phi/theta/gamma/tau the shrinkage, seed and t the
+ * Philox key and counter word of the sketches (as in tr_slice_prox).  Work
+ * is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy stream).
+ * Scratch comes from one fixed 16 MiB array compiled into the library and
+ * kept on every GPU that loads it until exit; calls needing more return
+ * TR_EUNSUPPORTED with the size in `err`.  The first call on a device looks
+ * up that array's address (make it before any stream capture).  All calls
+ * share the array: calls that overlap on the GPU race.  `err` (may be NULL)
+ * receives a message of at most err_len bytes on failure.                  */
+tr_status tr_slice_prox_noalloc(tr_dtype dtype, int n, int n1, int n2, const void *Abar,
+                                void *Gbar, int l, int q, tr_penalty phi, double theta,
+                                double gamma, double tau, uint64_t seed, int t,
+                                void *cuda_stream, char *err, size_t err_len);
+
 /* Release all workspace.  Safe on NULL.                                     */
 tr_status tr_free(tr_handle *h);
 

@@ -82,6 +82,11 @@ _SIGS = {
     "tr_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "tr_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "tr_slice_prox_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_uint64, ctypes.c_int, _P,
+                                             ctypes.c_char_p, ctypes.c_size_t]),
     "tr_free": (ctypes.c_int, [_P]),
     "tr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -130,6 +135,29 @@ def default_params(**kw):
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def slice_prox_noalloc(Abar, Gbar, l, q, tau, t, seed=0, phi=TR_PEN_MCP, theta=1.0,
+                       gamma=4000.0, stream=None):
+    """tr_slice_prox_noalloc: the slice pass with no device allocation.
+
+    For callers that cannot allocate device memory (latency-critical host
+    loops, code living in another framework's memory pool).  Abar and Gbar
+    are (n, n1, n2) CUDA tensors supplied by the caller; scratch comes from a
+    fixed array inside the library.  Raises TrError on failure.
+    """
+    import torch
+    dt = {torch.float32: TR_F32, torch.float64: TR_F64}[Abar.dtype]
+    n, n1, n2 = Abar.shape
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    buf = ctypes.create_string_buffer(256)
+    st = load().tr_slice_prox_noalloc(dt, n, n1, n2, _ptr(Abar), _ptr(Gbar), int(l), int(q),
+                                      int(phi), float(theta), float(gamma), float(tau),
+                                      int(seed), int(t), ctypes.c_void_p(stream), buf, 256)
+    if st != TR_OK:
+        raise TrError(st, buf.value.decode())
+    return Gbar
 
 
 class Handle:
