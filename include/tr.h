@@ -117,7 +117,7 @@ typedef struct {
 } tr_step_info;
 
 /* Fill `prm` with the defaults: Phi = psi = MCP (theta 1, gamma 4000),
- * entrywise l1 noise with lambda = 1/sqrt(max(n1,n2) * n3...nd) computed
+ * entrywise l1 noise with lambda = 1/sqrt(max(n1,n2)) computed
  * at tr_init when lambda <= 0, mu0 = 1e-3, mu_max = 1e10, growth 1.1,
  * tol 1e-4, max_iter 100, RSVD engine, rank 10 + oversample 10, q = 1,
  * FP32 operands, seed 0.  (Sec. 6 parameter settings.)                     */

@@ -77,11 +77,18 @@ def init_state(shape, mu0):
 
 
 def default_lambda(n1, n2, tdims, xi=1.0):
-    """lambda = xi / sqrt(max(n1, n2) * n3 * ... * nd) (Sec. 6 parameter settings)."""
-    n = 1
-    for v in tdims:
-        n *= int(v)
-    return xi / np.sqrt(max(n1, n2) * n)
+    """lambda for the orthonormal transform: xi / sqrt(max(n1, n2)).
+
+    Sec. 6 sets lambda = xi / sqrt(max(n1, n2) * n3 ... nd) for L = FFT, whose
+    matrices satisfy U U^H = n_i I, so rho = n3 ... nd and the transformed
+    nuclear norm carries a 1/rho factor (Def. gnhtctv).  For the orthonormal
+    DCT (rho = 1) the transformed singular values are sqrt(n) times smaller
+    than the FFT's and the 1/rho factor is gone, so the nuclear term is
+    sqrt(n) times larger relative to ||E||_1; keeping the paper's balance
+    multiplies its lambda by sqrt(n3 ... nd), which leaves xi / sqrt(max(n1, n2)).
+    `tdims` is accepted for the paper's form and not used.
+    """
+    return xi / np.sqrt(max(n1, n2))
 
 
 def step(st, M, mask, tdims, p):

@@ -166,7 +166,9 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   h->stream = (cudaStream_t)cuda_stream;
   if (h->prm.lambda <= 0.0) {
     const double mx = (double)(h->n1 > h->n2 ? h->n1 : h->n2);
-    h->prm.lambda = 1.0 / sqrt(mx * (double)h->n);   // lambda = xi / sqrt(max(n1,n2) n3..nd), xi = 1
+    // Sec. 6 sets xi / sqrt(max(n1,n2) n3..nd) for the FFT (rho = n3..nd); with
+    // the orthonormal DCT (rho = 1) the same balance is xi / sqrt(max(n1,n2)).
+    h->prm.lambda = 1.0 / sqrt(mx);
   }
   if (h->n1 > 65535 * 64LL || h->n > 65535) {
     tr_status st = fail(nullptr, TR_EUNSUPPORTED, "too many slices (%lld) for one launch", (long long)h->n);

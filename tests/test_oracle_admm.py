@@ -42,7 +42,7 @@ def test_l1_fixed_point_satisfies_kkt(full, xi):
     # mu is held fixed (vartheta = 1): then the L-update gives
     # Y - Lambda = mu * O(residual), so the dual conditions become sharp.
     dims, M, mask, = _convex_problem(full=full)
-    lam = admm.default_lambda(dims[0], dims[1], dims[2:], xi=xi)
+    lam = xi / np.sqrt(max(dims[0], dims[1]) * 6)     # a fixed lambda: KKT holds for any
     p = admm.Params(phi=prox.L1, psi=prox.L1, noise=admm.NOISE_L1, lam=lam,
                     engine="full", tol=1e-10, max_iter=5000, mu0=1.0, growth=1.0)
     st, hist = admm.run(M, mask, dims[2:], p)
@@ -94,8 +94,22 @@ def test_mu_schedule():
     assert np.allclose(mus, [1.5e-3, 2e-3, 2e-3, 2e-3])
 
 
-def test_default_lambda():
-    assert abs(admm.default_lambda(200, 100, (20, 20), 1.0) - 1 / np.sqrt(200 * 400)) < 1e-15
+def test_default_lambda_keeps_the_papers_balance_under_the_orthonormal_transform():
+    # Sec. 6: lambda_FFT = xi / sqrt(max(n1,n2) n) with rho = n; with the
+    # orthonormal transform (rho = 1) the TNN of a tensor is sqrt(n) times its
+    # FFT-convention TNN, so the equivalent lambda is sqrt(n) * lambda_FFT.
+    n1, n2, tdims = 200, 100, (20, 20)
+    n = 400
+    lam_fft = 2.0 / np.sqrt(max(n1, n2) * n)
+    assert abs(admm.default_lambda(n1, n2, tdims, 2.0) - np.sqrt(n) * lam_fft) < 1e-15
+    # the TNN scaling itself: for a real tensor, the unnormalised DFT along the
+    # slice modes scales every transformed slice's Frobenius norm by sqrt(n) on
+    # average, while the orthonormal DCT preserves it
+    rng = np.random.default_rng(0)
+    S = rng.standard_normal((n, 6, 5))
+    F = np.fft.fft(np.fft.fft(S.reshape(20, 20, 6, 5), axis=0), axis=1).reshape(n, 6, 5)
+    D = transform.forward(S, tdims)
+    assert abs(np.linalg.norm(F) / np.linalg.norm(D) - np.sqrt(n)) < 1e-9
 
 
 def test_first_step_from_zero_state_closed_form():
