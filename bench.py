@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "bf16x3"],
+                    help="precision of the chosen form's slice products")
     return ap.parse_args()
 
 
@@ -172,6 +174,52 @@ def tube_fused_bytes(N, esz):
     return N * (13 * esz + 1)
 
 
+PREC = {"fp32": 0, "bf16": 2, "bf16x3": 3}
+
+
+def make_handle(tr, torch, w, Md, maskd, stream, rank, prec):
+    rank_k = int(w.rank) if w.rank != "powerlaw" else 10
+    return tr.Handle(Md, maskd, w.dims, stream=stream.cuda_stream, rank=rank_k,
+                     oversample=w.l - rank_k, power_iters=w.q, seed=w.seed + rank, prec=prec,
+                     noise=tr.TR_NOISE_NONE if w.noise_model == "none" else tr.TR_NOISE_L1)
+
+
+def time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, prec, K, W, clocks=None):
+    """Warm up W steps, then time K steps of one form; returns its measurements."""
+    with torch.cuda.stream(stream):
+        h = make_handle(tr, torch, w, Md, maskd, stream, rank, prec)
+    for _ in range(W):
+        h.step()
+    h.profile_enable(K)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
+    launches0 = h.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(K):
+        h.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = h.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks is not None else None
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    phases = h.profile_read()
+    L = h.get_state()["L"]
+    rec = float(torch.linalg.norm((L - X_dev).double()) / torch.linalg.norm(X_dev.double()))
+    return h, {"ms": ms, "phases": phases, "launches": launches, "clocks": clk,
+               "recovery_rel_err": rec, "L": L}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -187,44 +235,26 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     dt = torch.float64 if w.dtype == "f64" else torch.float32
     esz = 8 if w.dtype == "f64" else 4
-    _, M, mask, _ = synth.make_problem(w, seed=w.seed + rank)
+    X, M, mask, _ = synth.make_problem(w, seed=w.seed + rank)
     M_host = torch.from_numpy(M).to(dt).pin_memory()
     mask_host = torch.from_numpy(mask).pin_memory()
     Md = M_host.to("cuda")
     maskd = mask_host.to("cuda")
+    X_dev = torch.from_numpy(X).to("cuda", dt)
     stream = torch.cuda.Stream()
-    rank_k = int(w.rank) if w.rank != "powerlaw" else 10
-    with torch.cuda.stream(stream):
-        h = tr.Handle(Md, maskd, w.dims, stream=stream.cuda_stream, rank=rank_k,
-                      oversample=w.l - rank_k, power_iters=w.q, seed=w.seed + rank,
-                      noise=tr.TR_NOISE_NONE if w.noise_model == "none" else tr.TR_NOISE_L1)
     K, W = args.steps, args.warmup
-    for _ in range(W):
-        h.step()
-    h.profile_enable(K)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    chosen = PREC[args.prec] if w.dtype != "f64" else 0
+
+    # plain form: FP32 SIMT products (the speedup denominator)
+    hp, plain = time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, 0, K, W)
+    hp.close()
+    # chosen form (tensor-core products), timed with the clock sampler running
     clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    launches0 = h.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(K):
-        h.step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    launches = h.kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    phases = h.profile_read()
+    h, ch = time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, chosen, K, W,
+                      clocks)
+    agree = float(torch.linalg.norm((ch["L"] - plain["L"]).double())
+                  / torch.linalg.norm(plain["L"].double()).clamp_min(1e-300))
+    ms, phases = ch["ms"], ch["phases"]
 
     # end to end through the C ABI with host buffers: every step copies the
     # problem's inputs (observed values, mask) from pinned host memory and
@@ -260,6 +290,7 @@ def run_ours(args):
     fwd_gbs = tube_fused_bytes(N, esz) / (fwd_ms * 1e-3) / 1e9 if fwd_ms > 0 else None
     step_bytes = tube_fused_bytes(N, esz) + 2 * N * esz
     value = K * world / (ms * 1e-3)
+    plain_value = K * world / (plain["ms"] * 1e-3)
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -283,11 +314,18 @@ def run_ours(args):
                 "sketch_width": w.l,
                 "power_iters": w.q,
                 "sampling_ratio": w.sr,
-                "form": "plain FP32 SIMT, one problem, no graph",
+                "form": {0: "fp32 simt", 2: "bf16 tcgen05 (split-bf16 refinement)",
+                         3: "split-bf16 tcgen05"}[chosen],
                 "parallelism": "replicas" if world > 1 else "single",
                 "l2": "state 7 x %.0f MB >> 129 MB L2: no flush needed" % (N * esz / 1e6),
             },
-            "gpu_launches": int(launches),
+            "plain": {"value": plain_value, "ms_per_step": plain["ms"] / K,
+                      "form": "fp32 simt", "phases_ms": plain["phases"],
+                      "recovery_rel_err": plain["recovery_rel_err"]},
+            "speedup_vs_plain": value / plain_value,
+            "recovery_rel_err": ch["recovery_rel_err"],
+            "chosen_vs_plain_L_rel_diff": agree,
+            "gpu_launches": int(ch["launches"]),
             "roofline": {
                 "kernel": "tube_fused_kernel",
                 "bound": "hbm",
@@ -304,7 +342,7 @@ def run_ours(args):
             "e2e": {"value": KE * world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(N * esz + N),
                     "d2h_bytes_per_step": int(8 * 5 + 4 + 4 * n)},
-            "clocks": clk,
+            "clocks": ch["clocks"],
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)

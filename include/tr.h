@@ -69,8 +69,16 @@ typedef enum {
   TR_LR_LEARNED = 3     /* per-slice sketch width predicted by an MLP        */
 } tr_engine;
 
-/* Operand precision of the slice contractions (accumulation is FP32). */
-typedef enum { TR_PREC_FP32 = 0, TR_PREC_TF32 = 1, TR_PREC_BF16 = 2 } tr_prec;
+/* Operand precision of the slice contractions (accumulation is FP32).
+ *   FP32:   SIMT FP32 FMA (the plain form).
+ *   BF16:   tcgen05 tensor cores; the sketch and first power-iteration
+ *           products in BF16, the last power product and B^T = Abar^T Q in
+ *           split BF16 (x = hi + lo, three products: ~16-bit operands), so
+ *           the final basis is refined at FP32-level accuracy (rel-F 1e-3).
+ *   BF16X3: tcgen05 tensor cores, all four skinny products in split BF16
+ *           (FP32-level accuracy, rel-F 1e-4).
+ * The tensor-core forms need FP32 problems; TF32 is not built.             */
+typedef enum { TR_PREC_FP32 = 0, TR_PREC_TF32 = 1, TR_PREC_BF16 = 2, TR_PREC_BF16X3 = 3 } tr_prec;
 
 typedef struct tr_handle tr_handle;
 

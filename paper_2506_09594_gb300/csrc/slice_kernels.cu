@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include "tr_internal.cuh"
+#include "umma_gemm.cuh"
 
 namespace {
 
@@ -197,6 +198,29 @@ cudaError_t bgemm(const GemmArgs &g, int batch, cudaStream_t s) {
     bgemm_kernel<T, 64, 64, 16, 4, 4><<<grid, 256, 0, s>>>(g);
   }
   return cudaGetLastError();
+}
+
+// Skinny product on the tensor cores (N <= 64, FP32 in/out): split = 1 is
+// BF16 operands, split = 3 the hi/lo split (FP32-level accuracy).
+cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || batch <= 0) return cudaSuccess;
+  umma::Args a{g.M, g.N, g.K, (const float *)g.A, g.sAb, g.sAi, g.sAk, (const float *)g.B,
+               g.sBb, g.sBk, g.sBn, (float *)g.C, g.sCb, g.sCi, g.sCn};
+  const dim3 grid((g.M + umma::kBM - 1) / umma::kBM, 1, batch);
+#define TR_UMMA(NP, SP)                                                                        \
+  {                                                                                            \
+    auto k = umma::gemm_kernel<NP, SP>;                                                        \
+    const int smem = umma::Layout<NP, SP>::total;                                              \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    if (e != cudaSuccess) return e;                                                            \
+    k<<<grid, umma::kThreads, smem, s>>>(a, err);                                              \
+    return cudaGetLastError();                                                                 \
+  }
+  if (g.N <= 32) {
+    if (split > 1) TR_UMMA(32, 3) else TR_UMMA(32, 1)
+  }
+  if (split > 1) TR_UMMA(64, 3) else TR_UMMA(64, 1)
+#undef TR_UMMA
 }
 
 // -------------------------------------------------- block Householder QR
@@ -658,25 +682,36 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
                                           (uint32_t)(w.seed >> 32), (uint32_t)t, 0u);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // Y = Abar X (X: n2 x l column-major panel with batch stride sX)
-  auto gemm_AX = [&](const T *X, T *Y) {
+  // Precision of each skinny product: 0 = SIMT FP32, 1 = BF16, 3 = split
+  // BF16.  The BF16 form keeps the sketch and the early power products in
+  // BF16 and computes the last power product and B^T = Abar^T Q in split
+  // BF16, so the final basis and B are refined at FP32-level accuracy.
+  const bool tc = sizeof(T) == 4 && w.l <= 64 &&
+                  (w.prec == TR_PREC_BF16 || w.prec == TR_PREC_BF16X3);
+  const int early = !tc ? 0 : (w.prec == TR_PREC_BF16 ? 1 : 3);
+  const int late = !tc ? 0 : 3;
+  auto run_gemm = [&](const GemmArgs &g, int mode) {
+    if (mode == 0) return bgemm<T>(g, n, s);
+    return umma_gemm(g, n, mode, w.err, s);
+  };
+  auto AX = [&](const T *X, T *Y, int mode) {
     GemmArgs g{n1, l, n2, Abar, sA, n2, 1, X, (int64_t)n2 * l, 1, n2, Y, (int64_t)n1 * l, 1, n1};
-    return bgemm<T>(g, n, s);
+    return run_gemm(g, mode);
   };
-  // W = Abar^T Q (Q: n1 x l)
-  auto gemm_AtX = [&](const T *X, T *Wt) {
+  auto AtX = [&](const T *X, T *Wt, int mode) {
     GemmArgs g{n2, l, n1, Abar, sA, 1, n2, X, (int64_t)n1 * l, 1, n1, Wt, (int64_t)n2 * l, 1, n2};
-    return bgemm<T>(g, n, s);
+    return run_gemm(g, mode);
   };
-  if ((e = gemm_AX(Om, P1)) != cudaSuccess) return e;
+  if ((e = AX(Om, P1, w.q > 0 ? early : late)) != cudaSuccess) return e;
   for (int it = 0; it < w.q; ++it) {
+    const bool last = it == w.q - 1;
     if ((e = run_qr<T>(n1, l, P1, n, s)) != cudaSuccess) return e;
-    if ((e = gemm_AtX(P1, P2)) != cudaSuccess) return e;
+    if ((e = AtX(P1, P2, early)) != cudaSuccess) return e;
     if ((e = run_qr<T>(n2, l, P2, n, s)) != cudaSuccess) return e;
-    if ((e = gemm_AX(P2, P1)) != cudaSuccess) return e;
+    if ((e = AX(P2, P1, last ? late : early)) != cudaSuccess) return e;
   }
   if ((e = run_qr<T>(n1, l, P1, n, s)) != cudaSuccess) return e;
-  if ((e = gemm_AtX(P1, P2)) != cudaSuccess) return e;
+  if ((e = AtX(P1, P2, late)) != cudaSuccess) return e;
   if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s)) != cudaSuccess)
     return e;
   // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output

@@ -113,8 +113,8 @@ static void free_profile(tr_handle *h) {
 static void free_all(tr_handle *h) {
   free_profile(h);
   void *bufs[] = {h->mats, h->L, h->E, h->Y, h->Lam, h->G, h->Abar, h->Gbar,
-                  h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->res, h->res_prev,
-                  h->flags};
+                  h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->sw.err, h->res,
+                  h->res_prev, h->flags};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->ev0) cudaEventDestroy(h->ev0);
@@ -142,8 +142,10 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     if (p->dims[i] < 1) return fail(nullptr, TR_EINVAL, "dims[%d] = %lld < 1", i, (long long)p->dims[i]);
   if (prm->engine != TR_LR_RSVD)
     return fail(nullptr, TR_EUNSUPPORTED, "engine %d not built (only TR_LR_RSVD)", (int)prm->engine);
-  if (prm->prec != TR_PREC_FP32)
-    return fail(nullptr, TR_EUNSUPPORTED, "precision %d not built (only TR_PREC_FP32)", (int)prm->prec);
+  if (prm->prec != TR_PREC_FP32 && prm->prec != TR_PREC_BF16 && prm->prec != TR_PREC_BF16X3)
+    return fail(nullptr, TR_EUNSUPPORTED, "precision %d not built", (int)prm->prec);
+  if (prm->prec != TR_PREC_FP32 && p->dtype != TR_F32)
+    return fail(nullptr, TR_EUNSUPPORTED, "tensor-core precisions need an FP32 problem");
   if (!(prm->mu0 > 0) || !(prm->growth >= 1.0) || !(prm->mu_max >= prm->mu0))
     return fail(nullptr, TR_EINVAL, "need mu0 > 0, growth >= 1, mu_max >= mu0");
   if (prm->power_iters < 0 || prm->rank < 0 || prm->oversample < 0)
@@ -269,6 +271,9 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   INIT_CUDA(cudaMalloc((void **)&h->res, RES_COUNT * sizeof(unsigned long long)));
   INIT_CUDA(cudaMalloc((void **)&h->res_prev, RES_COUNT * sizeof(unsigned long long)));
   INIT_CUDA(cudaMalloc((void **)&h->flags, sizeof(int)));
+  INIT_CUDA(cudaMalloc((void **)&sw.err, sizeof(int)));
+  INIT_CUDA(cudaMemsetAsync(sw.err, 0, sizeof(int), h->stream));
+  sw.prec = (int)prm->prec;
   INIT_CUDA(cudaMemsetAsync(sw.rank, 0, (size_t)h->n * sizeof(int), h->stream));
   INIT_CUDA(cudaEventCreate(&h->ev0));
   INIT_CUDA(cudaEventCreate(&h->ev1));
@@ -316,6 +321,12 @@ static tr_status read_info(tr_handle *h, double mu_used, tr_step_info *info) {
   info->sum_rank = (int)sum;
   info->fallback_slices = 0;
   info->ms = ms;
+  int tc_err = 0;
+  TR_CUDA(h, cudaMemcpy(&tc_err, h->sw.err, sizeof tc_err, cudaMemcpyDeviceToHost));
+  if (tc_err) {
+    h->poisoned = true;
+    return fail(h, TR_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
+  }
   if (flag) {
     h->poisoned = true;
     return fail(h, TR_ENUMERIC, "NaN or Inf in the iterate at iteration %d", h->t);

@@ -76,6 +76,8 @@ struct SliceWork {
   void *P2;     // n * n2 * l, column-major per slice (ld n2)
   void *sig;    // n * l singular values of B
   int *rank;    // n kept ranks
+  int prec;     // tr_prec of the skinny products (FP32 problems only)
+  int *err;     // device flag set by a tensor-core GEMM whose bounded wait expired
 };
 cudaError_t launch_slice_rsvd(tr_dtype dt, const SliceWork &w, const void *Abar, void *Gbar,
                               const ShrinkScalars &sh, int t, cudaStream_t s);

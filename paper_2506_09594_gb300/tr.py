@@ -23,7 +23,7 @@ TR_F32, TR_F64 = 0, 1
 TR_PEN_L1, TR_PEN_MCP = 0, 1
 TR_NOISE_NONE, TR_NOISE_L1 = 0, 1
 TR_LR_FULLSVD, TR_LR_RSVD, TR_LR_ADAPTIVE, TR_LR_LEARNED = 0, 1, 2, 3
-TR_PREC_FP32, TR_PREC_TF32, TR_PREC_BF16 = 0, 1, 2
+TR_PREC_FP32, TR_PREC_TF32, TR_PREC_BF16, TR_PREC_BF16X3 = 0, 1, 2, 3
 
 
 class TrError(RuntimeError):

@@ -80,3 +80,10 @@ def test_library_refuses_missing_build(tmp_path):
             tr.load(str(tmp_path / "nope.so"))
     finally:
         tr._lib = saved
+
+
+def test_tensor_core_precisions_need_fp32(lib):
+    st, _ = _init(lib, 3, [8, 8, 4], dtype=tr.TR_F64, prec=tr.TR_PREC_BF16)
+    assert st == tr.TR_EUNSUPPORTED
+    st, _ = _init(lib, 3, [8, 8, 4], prec=tr.TR_PREC_TF32)
+    assert st == tr.TR_EUNSUPPORTED

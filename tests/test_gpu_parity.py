@@ -296,3 +296,59 @@ def test_mid_workload_full_size_step_parity():
     assert info["max_rank"] > 0
     assert np.allclose(info["res_inf"], res, rtol=1e-3, atol=1e-4 * np.max(res))
     h.close()
+
+
+# ------------------------------------------- tensor-core (tcgen05) forms
+PREC_TOL = {tr.TR_PREC_BF16: 1e-3, tr.TR_PREC_BF16X3: 1e-4}
+
+
+@pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
+@pytest.mark.parametrize("case", [(16, 64, 64, 5, 0.0, 15, 1, "l1"), (6, 70, 45, 8, 0.05, 20, 1, "mcp"),
+                                  (5, 140, 90, 6, 0.1, 40, 2, "l1"), (4, 33, 29, 3, 0.2, 12, 0, "l1"),
+                                  (3, 200, 200, 10, 1e-3, 20, 1, "mcp")])
+def test_slice_prox_tensor_core_forms(case, prec):
+    n, n1, n2, r, noise, l, q, phi = case
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 * 7 + n2 + 1)
+    s1 = np.linalg.svd(Ab[0], compute_uv=False)[0]
+    tau = 0.3 * s1
+    kind = prox.L1 if phi == "l1" else prox.MCP
+    gamma = 3.0 * tau + 1.0
+    pen = tr.TR_PEN_L1 if phi == "l1" else tr.TR_PEN_MCP
+    A32 = as_dtype(Ab, "f32")
+    ref, _ = svt.transformed_prox(A32, tau, kind, 1.0, gamma, engine="rsvd", l=l, q=q, seed=31, t=2)
+    outs = {}
+    for pr in (tr.TR_PREC_FP32, prec):
+        h = make_handle((n1, n2, n), "f32", rank=l, oversample=0, power_iters=q, phi=pen,
+                        phi_gamma=gamma, seed=31, prec=pr)
+        outs[pr] = host(h.slice_prox(dev(Ab, "f32"), tau, t=2))
+        h.close()
+    err = relF(outs[prec], ref)
+    assert err < PREC_TOL[prec], err
+    # and against the plain FP32 GPU form
+    assert relF(outs[prec], outs[tr.TR_PREC_FP32]) < PREC_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
+def test_step_tensor_core_forms(prec):
+    dims = (96, 80, 5, 4)
+    X, M, mask = _problem(dims, seed=77)
+    state = synth.random_state(M.shape, seed=2, scale=0.5)
+    lam = admm.default_lambda(dims[0], dims[1], dims[2:])
+    p = admm.Params(lam=lam, phi_gamma=60.0, psi_gamma=60.0, engine="rsvd", l=12, q=1, seed=8)
+    st = admm.State(*(as_dtype(x, "f32") for x in state), mu=0.2, t=1)
+    ref, _ = admm.step(st, as_dtype(M, "f32"), mask, tuple(dims[2:]), p)
+    h = make_handle(dims, "f32", M=M, mask=mask, phi_gamma=60.0, psi_gamma=60.0, rank=12,
+                    oversample=0, power_iters=1, seed=8, prec=prec, **{"lambda": lam})
+    h.set_state(*(dev(x, "f32") for x in state), mu=0.2, t=1)
+    h.step(info=True)
+    got = h.get_state()
+    # L, E, Y are elementwise in the (identical) state: FP32 rounding only.
+    for name, want in [("L", ref.L), ("E", ref.E), ("Y", ref.Y)]:
+        assert relF(host(got[name]), want) < 1e-5, name
+    # G is the prox output: the form's tolerance.
+    errG = relF(host(got["G"]), ref.G)
+    assert errG < PREC_TOL[prec], errG
+    # Lambda_new - Lambda_ref = mu (G_ref - G): bounded through G's error.
+    dLam = np.linalg.norm(host(got["Lam"]) - ref.Lam)
+    assert dLam <= 0.2 * np.linalg.norm(host(got["G"]) - ref.G) * 1.001 + 1e-6 * np.linalg.norm(ref.Lam)
+    h.close()
