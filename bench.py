@@ -168,6 +168,24 @@ def tube_inverse_bytes(N, esz):
     return N * 6 * esz
 
 
+# DRAM traffic of one tube_fused_kernel launch on the bench workload, from the
+# ncu capture summarised in profiles/tube_fused_kernel_tubal200x400_r10.md,
+# valid only while the kernel source is the one that was profiled.
+TUBE_FUSED_TRAFFIC = {"workload": "tubal200x400_r10", "src_sha256_prefix": "dcbdd2af493b96fc",
+                      "bytes": 464.188416e6 + 324.306688e6}
+
+
+def profiled_traffic(workload):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2506_09594_gb300", "csrc", "tube_kernels.cu")
+    try:
+        sha = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    t = TUBE_FUSED_TRAFFIC
+    return t["bytes"] if (sha == t["src_sha256_prefix"] and workload == t["workload"]) else None
+
+
 def tube_fused_bytes(N, esz):
     # reads Gbar, M, L, E, Y, G, Lambda (esz each) and the mask; writes
     # G, Lambda, L, E, Y, Abar
@@ -333,7 +351,7 @@ def run_ours(args):
                 "peak": hbm_peak,
                 "unit": "GB/s",
                 "frac": (fwd_gbs / hbm_peak) if fwd_gbs else None,
-                "traffic": None,
+                "traffic": profiled_traffic(args.workload),
                 "peak_source": peak_src,
                 "algorithmic_bytes": tube_fused_bytes(N, esz),
             },

@@ -200,6 +200,80 @@ cudaError_t bgemm(const GemmArgs &g, int batch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Rank-l rebuild Gbar^<j> = Z Qb^T (n1 x n2, row-major) from the column-major
+// panels Z (n1 x l) and Qb (n2 x l).  A 64 x 64 output tile per CTA keeps
+// all l columns of both panel tiles in shared memory (no K tiling: l <= 96),
+// each thread accumulates a 4 x 4 block and writes it as four 16-byte row
+// segments (scalar stores when n2 is not a multiple of 4).
+template <typename T>
+__global__ void __launch_bounds__(256)
+rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
+                   const T *__restrict__ Qb, int64_t sQ, T *__restrict__ C, int64_t sC,
+                   int vec_ok) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Zs = reinterpret_cast<T *>(smem_raw);          // [l][64]
+  T *Qs = Zs + (size_t)l * 64;                       // [l][64]
+  const int m0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+  const int64_t b = blockIdx.z;
+  const T *Zb = Z + b * sZ;
+  const T *Qbb = Qb + b * sQ;
+  for (int e = threadIdx.x; e < l * 64; e += 256) {
+    const int k = e / 64, i = e % 64;
+    Zs[e] = (m0 + i < n1) ? Zb[(int64_t)k * n1 + m0 + i] : T(0);
+    Qs[e] = (c0 + i < n2) ? Qbb[(int64_t)k * n2 + c0 + i] : T(0);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
+  for (int k = 0; k < l; ++k) {
+    T a[4], q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = Zs[k * 64 + ty * 4 + i];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) q[jj] = Qs[k * 64 + tx * 4 + jj];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], q[jj], acc[i][jj]);
+  }
+  T *Cb = C + b * sC;
+  const int col = c0 + tx * 4;
+  const bool vec = sizeof(T) == 4 && vec_ok && col + 4 <= n2;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = m0 + ty * 4 + i;
+    if (row >= n1) continue;
+    T *dst = Cb + (int64_t)row * n2 + col;
+    if (vec) {
+      *reinterpret_cast<float4 *>(dst) =
+          make_float4((float)acc[i][0], (float)acc[i][1], (float)acc[i][2], (float)acc[i][3]);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj)
+        if (col + jj < n2) dst[jj] = acc[i][jj];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T *C,
+                        cudaStream_t s) {
+  const size_t smem = 2 * (size_t)l * 64 * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(rank_update_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((n1 + 63) / 64, (n2 + 63) / 64, n);
+  // 16-byte row stores need n2 % 4 == 0 and a 16-byte aligned base
+  const int vec_ok = (n2 % 4 == 0) && ((uintptr_t)C % 16 == 0);
+  rank_update_kernel<T><<<grid, 256, smem, s>>>(n1, n2, l, Z, (int64_t)n1 * l, Qb,
+                                                (int64_t)n2 * l, C, (int64_t)n1 * n2, vec_ok);
+  return cudaGetLastError();
+}
+
 // Skinny product on the tensor cores (N <= 64, FP32 in/out): split = 1 is
 // BF16 operands, split = 3 the hi/lo split (FP32-level accuracy).
 cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStream_t s) {
@@ -715,8 +789,7 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s)) != cudaSuccess)
     return e;
   // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output
-  GemmArgs g{n1, n2, l, P1, (int64_t)n1 * l, 1, n1, P2, (int64_t)n2 * l, n2, 1, Gbar, sA, n2, 1};
-  return bgemm<T>(g, n, s);
+  return rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s);
 }
 
 }  // namespace

@@ -330,9 +330,17 @@ def test_slice_prox_tensor_core_forms(case, prec):
 
 @pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
 def test_step_tensor_core_forms(prec):
+    # The BF16 form keeps the sketch in BF16: its subspace matches the FP32
+    # one only where the transformed slices' spectra decay beyond the sketch
+    # width (the regime the randomized engine is for).  So the iterate here is
+    # structured -- L and G near the low-rank truth, small multipliers --
+    # rather than white noise (a flat spectrum, where any perturbation of the
+    # sketch moves the captured subspace).
     dims = (96, 80, 5, 4)
     X, M, mask = _problem(dims, seed=77)
-    state = synth.random_state(M.shape, seed=2, scale=0.5)
+    rs = np.random.default_rng(2)
+    noise = lambda s: s * rs.standard_normal(M.shape)
+    state = [X + noise(0.01), noise(0.01), noise(0.05), noise(0.05), X + noise(0.01)]
     lam = admm.default_lambda(dims[0], dims[1], dims[2:])
     p = admm.Params(lam=lam, phi_gamma=60.0, psi_gamma=60.0, engine="rsvd", l=12, q=1, seed=8)
     st = admm.State(*(as_dtype(x, "f32") for x in state), mu=0.2, t=1)
