@@ -162,9 +162,9 @@ def adaptive_basis(Ab, eps, b, delta_rel, seed, t, j, max_rank=None):
 
 
 def slice_prox_adaptive(Ab, eps, b, delta_rel, seed, t, j, tau, kind,
-                        theta=1.0, gamma=4.0):
+                        theta=1.0, gamma=4.0, max_rank=None):
     """Prox through the adaptive basis U: B = U^T Ab, SVD, shrink, rebuild."""
-    U, E, _ = adaptive_basis(Ab, eps, b, delta_rel, seed, t, j)
+    U, E, _ = adaptive_basis(Ab, eps, b, delta_rel, seed, t, j, max_rank=max_rank)
     B = U.T @ Ab
     Uh, s, Vt = np.linalg.svd(B, full_matrices=False)
     s2 = _shrink(s, tau, kind, theta, gamma)
@@ -173,7 +173,8 @@ def slice_prox_adaptive(Ab, eps, b, delta_rel, seed, t, j, tau, kind,
 
 # ------------------------------------------------------ whole-tensor maps
 def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
-                     l=None, q=1, seed=0, t=0, eps=0.01, b=10, delta_rel=1e-12):
+                     l=None, q=1, seed=0, t=0, eps=0.01, b=10, delta_rel=1e-12,
+                     max_rank=None):
     """Apply the chosen slice engine to every transformed face slice.
 
     Returns (Gbar, info) where info holds per-slice singular values and the
@@ -183,6 +184,7 @@ def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
     Gbar = np.zeros_like(Abar, dtype=np.float64)
     ranks = np.zeros(n, dtype=np.int64)
     sig = []
+    adaptive_ranks = []
     for j in range(n):
         Ab = np.asarray(Abar[j], dtype=np.float64)
         if engine == "full":
@@ -192,13 +194,14 @@ def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
             Om = philox.gaussian_block(seed, t, j, n2, ll)
             Gbar[j], s, s2 = slice_prox_randomized(Ab, Om, q, tau, kind, theta, gamma)
         elif engine == "adaptive":
-            Gbar[j], s, s2, _, _ = slice_prox_adaptive(Ab, eps, b, delta_rel, seed,
-                                                       t, j, tau, kind, theta, gamma)
+            Gbar[j], s, s2, kept, _ = slice_prox_adaptive(Ab, eps, b, delta_rel, seed, t, j,
+                                                          tau, kind, theta, gamma, max_rank)
+            adaptive_ranks.append(kept)
         else:
             raise ValueError(engine)
         ranks[j] = int(np.count_nonzero(s2))
         sig.append(s)
-    return Gbar, {"ranks": ranks, "sigma": sig}
+    return Gbar, {"ranks": ranks, "sigma": sig, "adaptive_ranks": adaptive_ranks}
 
 
 def gnhtsvt(A, tdims, tau, kind, theta=1.0, gamma=4.0, engine="full", **kw):

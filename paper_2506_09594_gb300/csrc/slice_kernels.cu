@@ -19,47 +19,10 @@
 #include <math.h>
 
 #include "tr_internal.cuh"
+#include "tr_rng.cuh"
 #include "umma_gemm.cuh"
 
 namespace {
-
-// ---------------------------------------------------------------- Philox
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t hi_a = __umulhi(0xD2511F53u, c[0]), lo_a = 0xD2511F53u * c[0];
-    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c[2]), lo_b = 0xCD9E8D57u * c[2];
-    const uint32_t n0 = hi_b ^ c[1] ^ k0, n2 = hi_a ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo_b;
-    c[2] = n2;
-    c[3] = lo_a;
-  }
-}
-
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1) {
-  const float u1 = ((float)a + 0.5f) * 2.3283064365386963e-10f;   // (a + 1/2) / 2^32
-  const float u2 = ((float)b + 0.5f) * 2.3283064365386963e-10f;
-  const float r = sqrtf(-2.0f * logf(u1));
-  float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
-}
-
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &z0, double &z1) {
-  const double u1 = ((double)a + 0.5) * 2.3283064365386963e-10;
-  const double u2 = ((double)b + 0.5) * 2.3283064365386963e-10;
-  const double r = sqrt(-2.0 * log(u1));
-  double s, c;
-  sincospi(2.0 * u2, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
-}
 
 template <typename T>
 __global__ void sketch_kernel(int64_t per_slice, T *__restrict__ Om, uint32_t k0, uint32_t k1,
@@ -69,10 +32,10 @@ __global__ void sketch_kernel(int64_t per_slice, T *__restrict__ Om, uint32_t k0
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
        g += (int64_t)gridDim.x * blockDim.x) {
     uint32_t c[4] = {(uint32_t)g, (uint32_t)j, t, stream};
-    philox4x32_10(c, k0, k1);
+    trrng::philox4x32_10(c, k0, k1);
     T z[4];
-    box_muller(c[0], c[1], z[0], z[1]);
-    box_muller(c[2], c[3], z[2], z[3]);
+    trrng::box_muller(c[0], c[1], z[0], z[1]);
+    trrng::box_muller(c[2], c[3], z[2], z[3]);
     T *dst = Om + (int64_t)j * per_slice;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -740,6 +703,8 @@ cudaError_t run_svd_core(int n1, int n2, int l, T *P1, T *P2, int n, const Shrin
   TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s)))
 }
 
+#include "adapt_kernels.cuh"
+
 template <typename T>
 cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkScalars &sh, int t,
                      cudaStream_t s) {
@@ -792,7 +757,65 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   return rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s);
 }
 
+template <typename T>
+cudaError_t run_adaptive(const SliceWork &sw, const AdaptWork &aw, const T *Abar, T *Gbar,
+                         const ShrinkScalars &sh, int t, cudaStream_t s) {
+  const int n = sw.n, n1 = sw.n1, n2 = sw.n2, b = aw.b, kcap = aw.kcap;
+  const int64_t sA = (int64_t)n1 * n2;
+  const int64_t xs = (int64_t)(n1 > n2 ? n1 : n2) * b;
+  AdaptPtrs<T> w{(T *)aw.Ucat, (T *)aw.Vcat, (T *)aw.X, (T *)aw.Lm, (T *)aw.Rm,
+                 aw.E, aw.nrm2, aw.active, aw.kept, aw.draws};
+  const uint32_t k0 = (uint32_t)(sw.seed & 0xffffffffu), k1 = (uint32_t)(sw.seed >> 32);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(aw.Ucat, 0, (size_t)n * n1 * kcap * sizeof(T), s)) != cudaSuccess) return e;
+  const size_t sm1 = adapt_smem<T>(n1, b, kcap), sm2 = adapt_smem<T>(n2, b, kcap);
+  const size_t smx = sm1 > sm2 ? sm1 : sm2;
+  if ((e = cudaFuncSetAttribute(adapt_init_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(adapt_u_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(adapt_v_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
+  adapt_init_kernel<T><<<n, 256, sm2, s>>>(n1, n2, b, kcap, Abar, w, k0, k1, (uint32_t)t);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nblk = kcap / b;
+  for (int i = 0; i < nblk; ++i) {
+    // X = Abar V_i
+    GemmArgs g1{n1, b, n2, Abar, sA, n2, 1, w.Vcat + (int64_t)i * b * n2,
+                (int64_t)n2 * (kcap + b), 1, n2, w.X, xs, 1, n1};
+    if ((e = bgemm<T>(g1, n, s)) != cudaSuccess) return e;
+    adapt_u_kernel<T><<<n, 256, sm1, s>>>(i, n1, b, kcap, xs, w, aw.delta_rel);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (i + 1 == nblk) break;
+    // X = Abar^T U_i
+    GemmArgs g2{n2, b, n1, Abar, sA, 1, n2, w.Ucat + (int64_t)i * b * n1, (int64_t)n1 * kcap, 1,
+                n1, w.X, xs, 1, n2};
+    if ((e = bgemm<T>(g2, n, s)) != cudaSuccess) return e;
+    adapt_v_kernel<T><<<n, 256, sm2, s>>>(i, n2, b, kcap, xs, w, aw.delta_rel, aw.eps, k0, k1,
+                                         (uint32_t)t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // B^T = Abar^T U (U zero-padded to kcap columns), SVD core, rebuild
+  T *P2 = (T *)sw.P2;
+  GemmArgs g3{n2, kcap, n1, Abar, sA, 1, n2, w.Ucat, (int64_t)n1 * kcap, 1, n1, P2,
+              (int64_t)n2 * kcap, 1, n2};
+  if ((e = bgemm<T>(g3, n, s)) != cudaSuccess) return e;
+  if ((e = run_svd_core<T>(n1, n2, kcap, w.Ucat, P2, n, sh, (T *)sw.sig, sw.rank, s)) != cudaSuccess)
+    return e;
+  return rank_update<T>(n, n1, n2, kcap, w.Ucat, P2, Gbar, s);
+}
+
 }  // namespace
+
+cudaError_t launch_slice_adaptive(tr_dtype dt, const SliceWork &w, const AdaptWork &aw,
+                                  const void *Abar, void *Gbar, const ShrinkScalars &sh, int t,
+                                  cudaStream_t s) {
+  if (dt == TR_F64)
+    return run_adaptive<double>(w, aw, (const double *)Abar, (double *)Gbar, sh, t, s);
+  return run_adaptive<float>(w, aw, (const float *)Abar, (float *)Gbar, sh, t, s);
+}
+
+size_t adapt_smem_bytes(tr_dtype dt, int n1, int n2, int b, int kcap) {
+  const int mx = n1 > n2 ? n1 : n2;
+  return dt == TR_F64 ? adapt_smem<double>(mx, b, kcap) : adapt_smem<float>(mx, b, kcap);
+}
 
 cudaError_t launch_slice_rsvd(tr_dtype dt, const SliceWork &w, const void *Abar, void *Gbar,
                               const ShrinkScalars &sh, int t, cudaStream_t s) {

@@ -28,6 +28,7 @@ struct tr_handle {
   void *L = nullptr, *E = nullptr, *Y = nullptr, *Lam = nullptr, *G = nullptr;
   void *Abar = nullptr, *Gbar = nullptr;      // transform-domain scratch
   SliceWork sw{};
+  AdaptWork aw{};                             // fixed-accuracy engine workspace
   unsigned long long *res = nullptr;          // RES_COUNT slots
   unsigned long long *res_prev = nullptr;     // slots for a deferred inverse pass
   int *flags = nullptr;
@@ -113,7 +114,9 @@ static void free_profile(tr_handle *h) {
 static void free_all(tr_handle *h) {
   free_profile(h);
   void *bufs[] = {h->mats, h->L, h->E, h->Y, h->Lam, h->G, h->Abar, h->Gbar,
-                  h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->sw.err, h->res,
+                  h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->sw.err,
+                  h->aw.Ucat, h->aw.Vcat, h->aw.X, h->aw.Lm, h->aw.Rm, h->aw.E, h->aw.nrm2,
+                  h->aw.active, h->aw.kept, h->aw.draws, h->res,
                   h->res_prev, h->flags};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -140,8 +143,11 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   if (!p->observed || !p->mask) return fail(nullptr, TR_EINVAL, "observed/mask must be device pointers");
   for (int i = 0; i < p->order; ++i)
     if (p->dims[i] < 1) return fail(nullptr, TR_EINVAL, "dims[%d] = %lld < 1", i, (long long)p->dims[i]);
-  if (prm->engine != TR_LR_RSVD)
-    return fail(nullptr, TR_EUNSUPPORTED, "engine %d not built (only TR_LR_RSVD)", (int)prm->engine);
+  if (prm->engine != TR_LR_RSVD && prm->engine != TR_LR_ADAPTIVE)
+    return fail(nullptr, TR_EUNSUPPORTED, "engine %d not built", (int)prm->engine);
+  if (prm->engine == TR_LR_ADAPTIVE &&
+      (prm->adapt_block < 1 || prm->adapt_block > 32 || !(prm->adapt_eps > 0)))
+    return fail(nullptr, TR_EINVAL, "adaptive engine: need 1 <= adapt_block <= 32, adapt_eps > 0");
   if (prm->prec != TR_PREC_FP32 && prm->prec != TR_PREC_BF16 && prm->prec != TR_PREC_BF16X3)
     return fail(nullptr, TR_EUNSUPPORTED, "precision %d not built", (int)prm->prec);
   if (prm->prec != TR_PREC_FP32 && p->dtype != TR_F32)
@@ -209,7 +215,24 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     delete h;
     return st;
   }
-  const int l = sketch_width(h);
+  int l = sketch_width(h);
+  if (prm->engine == TR_LR_ADAPTIVE) {
+    // basis cap: rank + oversample rounded up to whole blocks, within min(n1, n2)
+    const int b = prm->adapt_block;
+    const int mn = (int)(h->n1 < h->n2 ? h->n1 : h->n2);
+    int kcap = ((prm->rank + prm->oversample + b - 1) / b) * b;
+    if (kcap > (mn / b) * b) kcap = (mn / b) * b;
+    if (kcap < b || adapt_smem_bytes(h->dtype, (int)h->n1, (int)h->n2, b, kcap) > 227 * 1024) {
+      tr_status st = fail(nullptr, TR_EUNSUPPORTED, "adaptive engine: block %d does not fit", b);
+      delete h;
+      return st;
+    }
+    l = kcap;
+    h->aw.b = b;
+    h->aw.kcap = kcap;
+    h->aw.eps = prm->adapt_eps;
+    h->aw.delta_rel = p->dtype == TR_F64 ? 1e-11 : 1e-5;
+  }
   if (l > TR_MAX_L || !slice_smem_limit_ok(h->dtype, (int)h->n1, (int)h->n2, l)) {
     tr_status st = fail(nullptr, TR_EUNSUPPORTED, "slice panels %lld x %d exceed shared memory",
                         (long long)(h->n1 > h->n2 ? h->n1 : h->n2), l);
@@ -275,6 +298,20 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   INIT_CUDA(cudaMemsetAsync(sw.err, 0, sizeof(int), h->stream));
   sw.prec = (int)prm->prec;
   INIT_CUDA(cudaMemsetAsync(sw.rank, 0, (size_t)h->n * sizeof(int), h->stream));
+  if (prm->engine == TR_LR_ADAPTIVE) {
+    AdaptWork &aw = h->aw;
+    const size_t mx = (size_t)(h->n1 > h->n2 ? h->n1 : h->n2);
+    INIT_CUDA(cudaMalloc(&aw.Ucat, (size_t)h->n * h->n1 * aw.kcap * h->esz));
+    INIT_CUDA(cudaMalloc(&aw.Vcat, (size_t)h->n * h->n2 * (aw.kcap + aw.b) * h->esz));
+    INIT_CUDA(cudaMalloc(&aw.X, (size_t)h->n * mx * aw.b * h->esz));
+    INIT_CUDA(cudaMalloc(&aw.Lm, (size_t)h->n * aw.b * aw.b * h->esz));
+    INIT_CUDA(cudaMalloc(&aw.Rm, (size_t)h->n * aw.b * aw.b * h->esz));
+    INIT_CUDA(cudaMalloc((void **)&aw.E, (size_t)h->n * sizeof(double)));
+    INIT_CUDA(cudaMalloc((void **)&aw.nrm2, (size_t)h->n * sizeof(double)));
+    INIT_CUDA(cudaMalloc((void **)&aw.active, (size_t)h->n * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&aw.kept, (size_t)h->n * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&aw.draws, (size_t)h->n * sizeof(int)));
+  }
   INIT_CUDA(cudaEventCreate(&h->ev0));
   INIT_CUDA(cudaEventCreate(&h->ev1));
   INIT_CUDA(cudaStreamSynchronize(h->stream));
@@ -287,8 +324,14 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
 
 static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double tau, int t) {
   ShrinkScalars sh{tau, (int)h->prm.phi, h->prm.phi_theta, h->prm.phi_gamma};
-  TR_CUDA(h, launch_slice_rsvd(h->dtype, h->sw, Abar, Gbar, sh, t, h->stream));
-  h->launches += 7 + 4 * (uint64_t)h->sw.q;   // sketch, 2 + 2q GEMM, 1 + 2q QR, SVD core, rebuild
+  if (h->prm.engine == TR_LR_ADAPTIVE) {
+    TR_CUDA(h, launch_slice_adaptive(h->dtype, h->sw, h->aw, Abar, Gbar, sh, t, h->stream));
+    const uint64_t nblk = (uint64_t)(h->aw.kcap / h->aw.b);
+    h->launches += 1 + 4 * nblk - 2 + 3;   // init, per block GEMM+U (+GEMM+V), B GEMM, SVD, rebuild
+  } else {
+    TR_CUDA(h, launch_slice_rsvd(h->dtype, h->sw, Abar, Gbar, sh, t, h->stream));
+    h->launches += 7 + 4 * (uint64_t)h->sw.q;   // sketch, 2 + 2q GEMM, 1 + 2q QR, SVD core, rebuild
+  }
   return TR_OK;
 }
 

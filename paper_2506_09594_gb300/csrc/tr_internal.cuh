@@ -79,6 +79,18 @@ struct SliceWork {
   int prec;     // tr_prec of the skinny products (FP32 problems only)
   int *err;     // device flag set by a tensor-core GEMM whose bounded wait expired
 };
+// Workspace of the fixed-accuracy engine (Alg. 3 per slice).
+struct AdaptWork {
+  int b, kcap;          // block size, basis cap (a multiple of b)
+  double eps, delta_rel;
+  void *Ucat, *Vcat, *X, *Lm, *Rm;
+  double *E, *nrm2;
+  int *active, *kept, *draws;
+};
+cudaError_t launch_slice_adaptive(tr_dtype dt, const SliceWork &w, const AdaptWork &aw,
+                                  const void *Abar, void *Gbar, const ShrinkScalars &sh, int t,
+                                  cudaStream_t s);
+size_t adapt_smem_bytes(tr_dtype dt, int n1, int n2, int b, int kcap);
 cudaError_t launch_slice_rsvd(tr_dtype dt, const SliceWork &w, const void *Abar, void *Gbar,
                               const ShrinkScalars &sh, int t, cudaStream_t s);
 size_t slice_smem_limit_ok(tr_dtype dt, int n1, int n2, int l);

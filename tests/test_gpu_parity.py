@@ -360,3 +360,58 @@ def test_step_tensor_core_forms(prec):
     dLam = np.linalg.norm(host(got["Lam"]) - ref.Lam)
     assert dLam <= 0.2 * np.linalg.norm(host(got["G"]) - ref.G) * 1.001 + 1e-6 * np.linalg.norm(ref.Lam)
     h.close()
+
+
+# --------------------------------------------------- adaptive engine (Alg. 3)
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_adaptive_engine_matches_oracle_on_low_rank_slices(dt):
+    # exact ranks 3, 7, 12, 5: block Lanczos stops cleanly (E -> 0) and
+    # deflates at the exact rank, so both sides take the same steps
+    n1, n2, b, kcap = 60, 48, 4, 24
+    ranks = [3, 7, 12, 5]
+    Ab = synth.lowrank_plus_noise_stack(4, n1, n2, ranks, 0.0, seed=12)
+    tau = 0.4
+    delta = 1e-11 if dt == "f64" else 1e-5
+    ref, info = svt.transformed_prox(as_dtype(Ab, dt), tau, prox.L1, engine="adaptive", eps=1e-4,
+                                     b=b, delta_rel=delta, seed=9, t=3, max_rank=kcap)
+    h = make_handle((n1, n2, 4), dt, engine=tr.TR_LR_ADAPTIVE, adapt_block=b, adapt_eps=1e-4,
+                    rank=kcap, oversample=0, phi=tr.TR_PEN_L1, seed=9)
+    G = host(h.slice_prox(dev(Ab, dt), tau, t=3))
+    assert relF(G, ref) < TOL[dt]
+    full, _ = svt.transformed_prox(Ab, tau, prox.L1, engine="full")
+    assert relF(G, full) < (1e-9 if dt == "f64" else 1e-4)
+    h.close()
+
+
+def test_adaptive_engine_accuracy_bound_on_noisy_slices():
+    # E < eps^2 ||A||^2 at the stop, so ||A - U U^T A|| < eps ||A||, and the l1
+    # prox is nonexpansive: ||D(A) - D(U U^T A)|| <= eps ||A|| per slice
+    n, n1, n2, b, kcap, eps = 6, 80, 70, 5, 40, 0.05
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, 8, 0.02, seed=4)
+    h = make_handle((n1, n2, n), "f32", engine=tr.TR_LR_ADAPTIVE, adapt_block=b, adapt_eps=eps,
+                    rank=kcap, oversample=0, phi=tr.TR_PEN_L1, seed=2)
+    G = host(h.slice_prox(dev(Ab, "f32"), 0.5, t=0))
+    full, _ = svt.transformed_prox(Ab, 0.5, prox.L1, engine="full")
+    for j in range(n):
+        assert np.linalg.norm(G[j] - full[j]) <= eps * np.linalg.norm(Ab[j]) * 1.01
+    h.close()
+
+
+def test_adaptive_engine_step_parity():
+    dims = (40, 36, 3, 4)
+    X, M, mask = _problem(dims, seed=5)
+    state = [X, np.zeros_like(X), np.zeros_like(X), np.zeros_like(X), X]
+    lam = admm.default_lambda(dims[0], dims[1], dims[2:])
+    p = admm.Params(lam=lam, phi_gamma=60.0, psi_gamma=60.0, engine="adaptive", eps=1e-4, b=4,
+                    delta_rel=1e-11, seed=6)
+    st = admm.State(*state, mu=0.3, t=0)
+    ref, _ = admm.step(st, M, mask, tuple(dims[2:]), p)
+    h = make_handle(dims, "f64", M=M, mask=mask, phi_gamma=60.0, psi_gamma=60.0, rank=36,
+                    oversample=0, engine=tr.TR_LR_ADAPTIVE, adapt_block=4, adapt_eps=1e-4, seed=6,
+                    **{"lambda": lam})
+    h.set_state(*(dev(x, "f64") for x in state), mu=0.3, t=0)
+    h.step(info=True)
+    got = h.get_state()
+    for name, want in [("L", ref.L), ("E", ref.E), ("G", ref.G)]:
+        assert relF(host(got[name]), want) < 1e-9, name
+    h.close()
