@@ -26,8 +26,10 @@ namespace {
 
 template <typename T>
 __global__ void sketch_kernel(int64_t per_slice, T *__restrict__ Om, uint32_t k0, uint32_t k1,
-                              uint32_t t, uint32_t stream) {
-  const int j = blockIdx.y;
+                              uint32_t t, uint32_t stream, SliceSel sel) {
+  const int b = blockIdx.y;
+  if (sel.count && b >= *sel.count) return;
+  const int j = sel.ids ? sel.ids[b] : b;
   const int64_t ngroups = (per_slice + 3) / 4;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -36,7 +38,7 @@ __global__ void sketch_kernel(int64_t per_slice, T *__restrict__ Om, uint32_t k0
     T z[4];
     trrng::box_muller(c[0], c[1], z[0], z[1]);
     trrng::box_muller(c[2], c[3], z[2], z[3]);
-    T *dst = Om + (int64_t)j * per_slice;
+    T *dst = Om + (int64_t)b * per_slice;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int64_t m = 4 * g + i;
@@ -56,6 +58,10 @@ struct GemmArgs {
   int64_t sBb, sBk, sBn;
   void *C;
   int64_t sCb, sCi, sCn;
+  // optional batch indirection (see SliceSel): A and/or C of entry b come
+  // from batch sel.ids[b]; B always from entry b
+  SliceSel sel{};
+  int a_by_id = 0, c_by_id = 0;
 };
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
@@ -68,9 +74,11 @@ bgemm_kernel(GemmArgs g) {
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int64_t b = blockIdx.z;
-  const T *A = (const T *)g.A + b * g.sAb;
+  if (g.sel.count && b >= *g.sel.count) return;
+  const int64_t jb = g.sel.ids ? g.sel.ids[b] : b;
+  const T *A = (const T *)g.A + (g.a_by_id ? jb : b) * g.sAb;
   const T *B = (const T *)g.B + b * g.sBb;
-  T *C = (T *)g.C + b * g.sCb;
+  T *C = (T *)g.C + (g.c_by_id ? jb : b) * g.sCb;
   const bool a_kc = g.sAk == 1;
   const bool b_nc = g.sBn == 1;
   T acc[TM][TN];
@@ -172,12 +180,14 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
                    const T *__restrict__ Qb, int64_t sQ, T *__restrict__ C, int64_t sC,
-                   int vec_ok) {
+                   int vec_ok, SliceSel sel) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Zs = reinterpret_cast<T *>(smem_raw);          // [l][64]
   T *Qs = Zs + (size_t)l * 64;                       // [l][64]
   const int m0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
   const int64_t b = blockIdx.z;
+  if (sel.count && b >= *sel.count) return;
+  const int64_t jb = sel.ids ? sel.ids[b] : b;
   const T *Zb = Z + b * sZ;
   const T *Qbb = Qb + b * sQ;
   for (int e = threadIdx.x; e < l * 64; e += 256) {
@@ -203,7 +213,7 @@ rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], q[jj], acc[i][jj]);
   }
-  T *Cb = C + b * sC;
+  T *Cb = C + jb * sC;
   const int col = c0 + tx * 4;
   const bool vec = sizeof(T) == 4 && vec_ok && col + 4 <= n2;
 #pragma unroll
@@ -224,7 +234,7 @@ rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
 
 template <typename T>
 cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T *C,
-                        cudaStream_t s) {
+                        cudaStream_t s, SliceSel sel = SliceSel{}) {
   const size_t smem = 2 * (size_t)l * 64 * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(rank_update_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -233,7 +243,8 @@ cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T
   // 16-byte row stores need n2 % 4 == 0 and a 16-byte aligned base
   const int vec_ok = (n2 % 4 == 0) && ((uintptr_t)C % 16 == 0);
   rank_update_kernel<T><<<grid, 256, smem, s>>>(n1, n2, l, Z, (int64_t)n1 * l, Qb,
-                                                (int64_t)n2 * l, C, (int64_t)n1 * n2, vec_ok);
+                                                (int64_t)n2 * l, C, (int64_t)n1 * n2, vec_ok,
+                                                sel);
   return cudaGetLastError();
 }
 
@@ -242,7 +253,8 @@ cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T
 cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return cudaSuccess;
   umma::Args a{g.M, g.N, g.K, (const float *)g.A, g.sAb, g.sAi, g.sAk, (const float *)g.B,
-               g.sBb, g.sBk, g.sBn, (float *)g.C, g.sCb, g.sCi, g.sCn};
+               g.sBb, g.sBk, g.sBn, (float *)g.C, g.sCb, g.sCi, g.sCn,
+               g.sel.ids, g.sel.count, g.a_by_id, g.c_by_id};
   const dim3 grid((g.M + umma::kBM - 1) / umma::kBM, 1, batch);
 #define TR_UMMA(NP, SP)                                                                        \
   {                                                                                            \
@@ -424,7 +436,8 @@ __device__ void block_reg_qr(T *P, int m, int l, T *V, T *tau, T *Rout) {
 }
 
 template <typename T, int CPW, int RPL>
-__global__ void qr_kernel(int m, int l, T *__restrict__ P, int64_t sP) {
+__global__ void qr_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel sel) {
+  if (sel.count && (int)blockIdx.x >= *sel.count) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *V = reinterpret_cast<T *>(smem_raw);
   T *tau = V + (size_t)m * l;
@@ -547,7 +560,9 @@ __device__ __forceinline__ T prox_sv(T s, const ShrinkScalars &sh) {
 template <typename T, int CPW, int RPL, int G>
 __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64_t sP1,
                                 T *__restrict__ P2, int64_t sP2, ShrinkScalars sh,
-                                T *__restrict__ sig_out, int *__restrict__ rank_out) {
+                                T *__restrict__ sig_out, int *__restrict__ rank_out,
+                                SliceSel sel) {
+  if (sel.count && (int)blockIdx.x >= *sel.count) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int mx = n1 > n2 ? n1 : n2;
   T *panel = reinterpret_cast<T *>(smem_raw);
@@ -557,9 +572,10 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   T *tau = C + l * l;
   T *ratio = tau + l;
   int *flag = reinterpret_cast<int *>(ratio + l);
-  const int j = blockIdx.x;
-  T *P1j = P1 + (int64_t)j * sP1;
-  T *P2j = P2 + (int64_t)j * sP2;
+  const int bb = blockIdx.x;                       // panel entry
+  const int j = sel.ids ? sel.ids[bb] : bb;        // slice id (statistics)
+  T *P1j = P1 + (int64_t)bb * sP1;
+  T *P2j = P2 + (int64_t)bb * sP2;
 
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) J[e] = (e % l == e / l) ? T(1) : T(0);
   // B^T = Qb R: Qb overwrites P2, R lands in W
@@ -652,18 +668,18 @@ size_t svd_smem(int n1, int n2, int l) {
 constexpr size_t kSliceSmemMax = 227 * 1024;
 
 template <typename T, int CPW, int RPL>
-cudaError_t run_qr_t(int m, int l, T *P, int n, cudaStream_t s) {
+cudaError_t run_qr_t(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) {
   const size_t smem = qr_smem<T>(m, l);
   auto k = qr_kernel<T, CPW, RPL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<n, 32 * panel_warps(l, CPW), smem, s>>>(m, l, P, (int64_t)m * l);
+  k<<<n, 32 * panel_warps(l, CPW), smem, s>>>(m, l, P, (int64_t)m * l, sel);
   return cudaGetLastError();
 }
 
 template <typename T, int CPW, int RPL, int G>
 cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh, T *sig,
-                      int *rank, cudaStream_t s) {
+                      int *rank, cudaStream_t s, SliceSel sel) {
   const size_t smem = svd_smem<T>(n1, n2, l);
   auto k = svd_core_kernel<T, CPW, RPL, G>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -673,7 +689,8 @@ cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkSc
   const int jw = (lp / 2 * G + 31) / 32;   // warps giving every Jacobi pair a lane group
   if (jw > nw) nw = jw > 32 ? 32 : jw;
   if (nw < 4) nw = 4;
-  k<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig, rank);
+  k<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig, rank,
+                             sel);
   return cudaGetLastError();
 }
 
@@ -688,19 +705,19 @@ cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkSc
   }
 
 template <typename T>
-cudaError_t run_qr(int m, int l, T *P, int n, cudaStream_t s) {
-  if (pick_cpw(l) == 2) { TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 2, RPL>(m, l, P, n, s))) }
-  TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 4, RPL>(m, l, P, n, s)))
+cudaError_t run_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel = SliceSel{}) {
+  if (pick_cpw(l) == 2) { TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 2, RPL>(m, l, P, n, s, sel))) }
+  TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 4, RPL>(m, l, P, n, s, sel)))
 }
 
 template <typename T>
 cudaError_t run_svd_core(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh,
-                         T *sig, int *rank, cudaStream_t s) {
+                         T *sig, int *rank, cudaStream_t s, SliceSel sel = SliceSel{}) {
   if (pick_cpw(l) == 2) {
-    if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 4>(n1, n2, l, P1, P2, n, sh, sig, rank, s))) }
-    TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s)))
+    if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 4>(n1, n2, l, P1, P2, n, sh, sig, rank, s, sel))) }
+    TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s, sel)))
   }
-  TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s)))
+  TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s, sel)))
 }
 
 #include "adapt_kernels.cuh"
@@ -718,7 +735,7 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
     const int64_t groups = (per + 3) / 4;
     dim3 grid((unsigned)((groups + 255) / 256), n);
     sketch_kernel<T><<<grid, 256, 0, s>>>(per, Om, (uint32_t)(w.seed & 0xffffffffu),
-                                          (uint32_t)(w.seed >> 32), (uint32_t)t, 0u);
+                                          (uint32_t)(w.seed >> 32), (uint32_t)t, 0u, w.sel);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // Precision of each skinny product: 0 = SIMT FP32, 1 = BF16, 3 = split
@@ -733,28 +750,31 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
     if (mode == 0) return bgemm<T>(g, n, s);
     return umma_gemm(g, n, mode, w.err, s);
   };
+  // Abar is indexed by slice id, the panels by batch entry
   auto AX = [&](const T *X, T *Y, int mode) {
-    GemmArgs g{n1, l, n2, Abar, sA, n2, 1, X, (int64_t)n2 * l, 1, n2, Y, (int64_t)n1 * l, 1, n1};
+    GemmArgs g{n1, l, n2, Abar, sA, n2, 1, X, (int64_t)n2 * l, 1, n2, Y, (int64_t)n1 * l, 1, n1,
+               w.sel, 1, 0};
     return run_gemm(g, mode);
   };
   auto AtX = [&](const T *X, T *Wt, int mode) {
-    GemmArgs g{n2, l, n1, Abar, sA, 1, n2, X, (int64_t)n1 * l, 1, n1, Wt, (int64_t)n2 * l, 1, n2};
+    GemmArgs g{n2, l, n1, Abar, sA, 1, n2, X, (int64_t)n1 * l, 1, n1, Wt, (int64_t)n2 * l, 1, n2,
+               w.sel, 1, 0};
     return run_gemm(g, mode);
   };
   if ((e = AX(Om, P1, w.q > 0 ? early : late)) != cudaSuccess) return e;
   for (int it = 0; it < w.q; ++it) {
     const bool last = it == w.q - 1;
-    if ((e = run_qr<T>(n1, l, P1, n, s)) != cudaSuccess) return e;
+    if ((e = run_qr<T>(n1, l, P1, n, s, w.sel)) != cudaSuccess) return e;
     if ((e = AtX(P1, P2, early)) != cudaSuccess) return e;
-    if ((e = run_qr<T>(n2, l, P2, n, s)) != cudaSuccess) return e;
+    if ((e = run_qr<T>(n2, l, P2, n, s, w.sel)) != cudaSuccess) return e;
     if ((e = AX(P2, P1, last ? late : early)) != cudaSuccess) return e;
   }
-  if ((e = run_qr<T>(n1, l, P1, n, s)) != cudaSuccess) return e;
+  if ((e = run_qr<T>(n1, l, P1, n, s, w.sel)) != cudaSuccess) return e;
   if ((e = AtX(P1, P2, late)) != cudaSuccess) return e;
-  if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s)) != cudaSuccess)
+  if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s, w.sel)) != cudaSuccess)
     return e;
   // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output
-  return rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s);
+  return rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s, w.sel);
 }
 
 template <typename T>

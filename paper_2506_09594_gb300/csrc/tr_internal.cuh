@@ -68,6 +68,15 @@ cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc 
 size_t tube_smem_bytes(tr_dtype dt, int n, const TransformDesc &td, int *tp_out);
 
 // ---- slice pass (slice_kernels.cu) ----
+// Optional selection of slices for one launch: batch entry b (a block
+// index) works on slice ids[b]; entries b >= *count exit at once.  Panels
+// are indexed by b, the transformed tensors, Philox counters and per-slice
+// statistics by the slice id.  Null pointers mean "all slices, in order".
+struct SliceSel {
+  const int *ids = nullptr;
+  const int *count = nullptr;
+};
+
 struct SliceWork {
   int n, n1, n2, l, q;
   uint64_t seed;
@@ -78,6 +87,7 @@ struct SliceWork {
   int *rank;    // n kept ranks
   int prec;     // tr_prec of the skinny products (FP32 problems only)
   int *err;     // device flag set by a tensor-core GEMM whose bounded wait expired
+  SliceSel sel; // which slices this pass works on (default: all)
 };
 // Workspace of the fixed-accuracy engine (Alg. 3 per slice).
 struct AdaptWork {

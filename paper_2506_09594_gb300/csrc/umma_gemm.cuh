@@ -130,6 +130,11 @@ struct Args {
   int64_t sBb, sBk, sBn;
   float *C;
   int64_t sCb, sCi, sCn;
+  // optional batch indirection: entry b uses A/C of batch ids[b] when
+  // a_by_id/c_by_id; entries b >= *count exit (null: identity, all)
+  const int *ids = nullptr;
+  const int *count = nullptr;
+  int a_by_id = 0, c_by_id = 0;
 };
 
 // Round x to BF16 (hi) and, for the split form, its remainder (lo).
@@ -224,9 +229,11 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(Args g, int *err) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM;
   const int64_t b = blockIdx.z;
-  const float *A = g.A + b * g.sAb;
+  if (g.count && b >= *g.count) return;   // block-uniform, before any TMEM use
+  const int64_t jb = g.ids ? g.ids[b] : b;
+  const float *A = g.A + (g.a_by_id ? jb : b) * g.sAb;
   const float *B = g.B + b * g.sBb;
-  float *C = g.C + b * g.sCb;
+  float *C = g.C + (g.c_by_id ? jb : b) * g.sCb;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
