@@ -108,7 +108,10 @@ typedef struct {
   int adapt_block;        /* adaptive engine: block size b                   */
   tr_prec prec;
   uint64_t seed;          /* Philox4x32-10 key of the Gaussian sketches      */
-  const char *model_path; /* learned engine weights (unused otherwise)      */
+  const char *model_path; /* learned engine: rank-predictor weights file
+                             (format under tr_set_model); NULL = a randomly
+                             initialised predictor keyed by `seed`; unused
+                             by the other engines                            */
 } tr_params;
 
 /* Per-step report (filled only when a non-NULL pointer is passed, which
@@ -212,6 +215,97 @@ tr_status tr_slice_prox_noalloc(tr_dtype dtype, int n, int n1, int n2, const voi
                                 void *Gbar, int l, int q, tr_penalty phi, double theta,
                                 double gamma, double tau, uint64_t seed, int t,
                                 void *cuda_stream, char *err, size_t err_len);
+
+/* ---- Learned sketch widths (engine TR_LR_LEARNED) ----------------------
+ * Not in the paper, which fixes one sketch rank (Alg. 1) or grows the basis
+ * to an accuracy (Alg. 3) and leaves learned sketching to future work
+ * (Sec. 7).  Per slice pass, for every transformed slice j:
+ *   features F_j (TR_MLP_FEATURES floats, tr_features) of the previous pass;
+ *   y_j = MLP(F_j) ~ log(1 + kept rank), an MLP 16 -> 128 -> 128 -> 128 -> 1
+ *     with ReLU, FP16 weights, FP32 biases and accumulation;
+ *   l_j = round_up(round(exp(y_j) - 1) + oversample, 8) clipped to
+ *     [min(8, l_max), l_max], l_max = rank + oversample (tr_plan_widths);
+ *   the randomized slice prox of TR_LR_RSVD with width l_j;
+ *   certificate: if the kept rank exceeds l_j - oversample and l_j < l_max,
+ *     slice j is recomputed at l_max (counted in fallback_slices).
+ * The first pass of a handle (and the first after tr_set_state) has no
+ * history and runs every slice at l_max.  A slice pass synchronises the
+ * stream twice (width plan, certificate count).
+ *
+ * MLP parameter vector (FP32, TR_MLP_PARAMS = 35329 values): for each layer
+ * in order (16 -> 128, 128 -> 128, 128 -> 128, 128 -> 1) its weights W
+ * (out x in, row-major) then its biases (out).                              */
+#define TR_MLP_FEATURES 16
+#define TR_MLP_PARAMS 35329
+
+/* Number of MLP parameters (TR_MLP_PARAMS).                                */
+int64_t tr_mlp_param_count(void);
+
+/* Install predictor weights in a TR_LR_LEARNED handle: `params` is a host
+ * array of `count` (= TR_MLP_PARAMS) floats.  Weights files (model_path)
+ * hold the 8 bytes "TRRANK01", four little-endian int32 (16, 128, 3, 0),
+ * one int64 count, then `count` float32 parameters.  Synchronises.
+ * Errors: TR_EINVAL (not a learned handle, wrong count).                    */
+tr_status tr_set_model(tr_handle *h, const float *params, int64_t count);
+
+/* Sketch width used for every slice in the last slice pass (host buffer of
+ * n ints; the RSVD engine reports l, the adaptive engine the basis size).
+ * Synchronises.                                                             */
+tr_status tr_last_slice_widths(tr_handle *h, int *widths);
+
+/* Features of the handle's last slice pass as the learned engine would see
+ * them before a pass with threshold parameter `tau` at iteration t (device
+ * buffer of n x TR_MLP_FEATURES floats).  Works for every engine, so that
+ * traces of the adaptive engine can train the predictor.  Errors: TR_EINVAL
+ * when no slice pass has run yet.                                           */
+tr_status tr_slice_features(tr_handle *h, double tau, int t, float *features);
+
+/* Stateless building blocks (device pointers, work on `cuda_stream`).
+ *   tr_features: F (n x 16) from the rows of `sig` (n rows of stride ldsig,
+ *     dtype elements; row j holds width[j] singular values in any order),
+ *     kept ranks `rank`, widths `width`, the current and previous shrink
+ *     thresholds thr and thr0 and the run fraction tfrac:
+ *       f0 = log(1 + rank)/log 129         f1 = log(w)/log 129
+ *       f2 = clip(log(s1/thr), -8, 8)/8    f3 = clip(log(s1/thr0), -8, 8)/8
+ *       f4..f9 = s_(i)/s1, i in {2,4,8,16,32,64} (i-th largest, 0 if i > w)
+ *       f10..f12 = log(1 + #{s > x})/log 129 for x = thr, thr/2, 2 thr
+ *       f13 = (w - #{s > thr})/w          f14 = clip(log(thr/thr0), -1, 1)
+ *       f15 = clip(tfrac, 0, 1)
+ *     with s1 = max s; s1 = 0 gives f2 = f3 = -1, f4..f9 = 0; a threshold
+ *     <= 0 gives f2 (f3) = 1 and f14 = 0.  Negative or NaN s count as 0.
+ *   tr_plan_widths: width[j] from yhat[j] as above (1 <= lmax <= 96), ids =
+ *     slice ids stably sorted by width class (l - 1)/8, counts[c] per class
+ *     (ceil(lmax/8) classes).
+ *   tr_mlp_init: He-uniform weights U(-a, a), a = sqrt(6/fan_in), zero
+ *     biases, from Philox4x32-10 keyed by `seed`.
+ *   tr_mlp_forward: yhat (B) = MLP(X) for X (B x 16).
+ *   tr_mlp_loss_grad: loss = (1/B) sum w_r (yhat_r - y_r)^2 with
+ *     w_r = 1 + under_weight [yhat_r < y_r]; grad (TR_MLP_PARAMS floats) =
+ *     dloss/dparams (the FP16 rounding of the weights passes the gradient
+ *     straight through); `loss` (1 float) may be NULL.  Allocates its
+ *     workspace with stream-ordered allocation.
+ *   tr_mlp_adam: one Adam step (step >= 1) on params with moments m, v.
+ *   tr_mlp_train: `steps` Adam steps on minibatches of `batch` rows drawn
+ *     with replacement (Philox keyed by `seed`) from (X, y), n rows;
+ *     loss_hist (steps floats) may be NULL.  Allocates its workspace with
+ *     stream-ordered allocation.
+ * Errors: TR_EINVAL (sizes), TR_ECUDA.                                      */
+tr_status tr_features(tr_dtype dtype, int n, const void *sig, int ldsig, const int *rank,
+                      const int *width, double thr, double thr0, double tfrac,
+                      float *features, void *cuda_stream);
+tr_status tr_plan_widths(int n, const float *yhat, int oversample, int lmax, int *width,
+                         int *ids, int *counts, void *cuda_stream);
+tr_status tr_mlp_init(float *params, uint64_t seed, void *cuda_stream);
+tr_status tr_mlp_forward(const float *params, const float *X, int B, float *yhat,
+                         void *cuda_stream);
+tr_status tr_mlp_loss_grad(const float *params, const float *X, const float *y, int B,
+                           double under_weight, float *grad, float *loss, void *cuda_stream);
+tr_status tr_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t count,
+                      double lr, double beta1, double beta2, double eps, int step,
+                      void *cuda_stream);
+tr_status tr_mlp_train(float *params, const float *X, const float *y, int n, int batch,
+                       int steps, double lr, double under_weight, uint64_t seed,
+                       float *loss_hist, void *cuda_stream);
 
 /* Release all workspace.  Safe on NULL.                                     */
 tr_status tr_free(tr_handle *h);

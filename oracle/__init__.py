@@ -28,6 +28,9 @@ paper's order and notation:
                 fixed-accuracy block-Lanczos engine restated from Alg. 3.
 * ``admm``      one iteration of Alg. 5 in the pure-L form (Gamma = {I})
                 and the loop around it.
+* ``learned``   the learned sketch-width engine (not in the paper): slice
+                features, width plan, certificate and the rank-predictor
+                MLP (forward, backpropagation, Adam).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force, library routines it does not itself
@@ -35,4 +38,4 @@ call, or published known-answer vectors, except where a docstring says
 "parity unpinned".
 """
 
-from . import philox, transform, prox, svt, admm  # noqa: F401
+from . import philox, transform, prox, svt, admm, learned  # noqa: F401

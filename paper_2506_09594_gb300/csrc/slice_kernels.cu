@@ -248,7 +248,7 @@ cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T
   return cudaGetLastError();
 }
 
-// Skinny product on the tensor cores (N <= 64, FP32 in/out): split = 1 is
+// Skinny product on the tensor cores (N <= 128, FP32 in/out): split = 1 is
 // BF16 operands, split = 3 the hi/lo split (FP32-level accuracy).
 cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return cudaSuccess;
@@ -268,7 +268,11 @@ cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStr
   if (g.N <= 32) {
     if (split > 1) TR_UMMA(32, 3) else TR_UMMA(32, 1)
   }
-  if (split > 1) TR_UMMA(64, 3) else TR_UMMA(64, 1)
+  if (g.N <= 64) {
+    if (split > 1) TR_UMMA(64, 3) else TR_UMMA(64, 1)
+  }
+  if (g.N > 128) return cudaErrorInvalidValue;
+  if (split > 1) TR_UMMA(128, 3) else TR_UMMA(128, 1)
 #undef TR_UMMA
 }
 
@@ -435,6 +439,94 @@ __device__ void block_reg_qr(T *P, int m, int l, T *V, T *tau, T *Rout) {
   pn.store(P, m, m, l, warp, nw, lane);
 }
 
+// Shared-memory Householder QR, for panels too large for the register file
+// (same reflectors as block_reg_qr).  The panel S (column-major, ld m) holds
+// v_k below the diagonal of column k and R on and above it.  Column c
+// belongs to warp c mod nw; the owner of column k+1 builds reflector k+1 as
+// soon as it has applied H_k, so the factorisation needs one barrier per
+// column.  Q is then formed in place backwards (LAPACK org2r order), two
+// barriers per column.
+template <typename T>
+__device__ void smem_reflector(T *col, int k, int m, int lane, T *tau) {
+  T ss = T(0);
+  for (int i = k + 1 + lane; i < m; i += 32) ss = fma(col[i], col[i], ss);
+  ss = warp_sum(ss);
+  const T x0 = col[k];
+  T beta = x0, tk = T(0), scale = T(0);
+  if (ss > T(0)) {
+    const T nrm = sqrt(fma(x0, x0, ss));
+    beta = x0 >= T(0) ? -nrm : nrm;
+    tk = (beta - x0) / beta;
+    scale = T(1) / (x0 - beta);
+  }
+  __syncwarp();
+  for (int i = k + 1 + lane; i < m; i += 32) col[i] *= scale;
+  if (lane == 0) {
+    col[k] = beta;
+    tau[k] = tk;
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ void smem_apply(const T *v, T tk, T *col, int k, int m, int lane) {
+  const T ck = col[k];
+  T s = T(0);
+  for (int i = k + 1 + lane; i < m; i += 32) s = fma(v[i], col[i], s);
+  s = warp_sum(s) + ck;
+  const T w = tk * s;
+  for (int i = k + 1 + lane; i < m; i += 32) col[i] = fma(-w, v[i], col[i]);
+  __syncwarp();
+  if (lane == 0) col[k] = ck - w;
+  __syncwarp();
+}
+
+// QR of P (global, column-major m x l, ld m) through the shared panel S
+// (m * l) and tau (l): R to Rout when non-null, Q overwrites P.
+template <typename T>
+__device__ void block_smem_qr(T *P, int m, int l, T *S, T *tau, T *Rout) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < m * l; e += blockDim.x) S[e] = P[e];
+  __syncthreads();
+  if (warp == 0) smem_reflector(S, 0, m, lane, tau);
+  __syncthreads();
+  for (int k = 0; k < l; ++k) {
+    const T tk = tau[k];
+    const T *v = S + (size_t)k * m;
+    for (int c = warp; c < l; c += nw) {
+      if (c <= k) continue;
+      smem_apply(v, tk, S + (size_t)c * m, k, m, lane);
+      if (c == k + 1) smem_reflector(S + (size_t)c * m, c, m, lane, tau);
+    }
+    __syncthreads();
+  }
+  if (Rout)
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+      const int i = e % l, c = e / l;
+      Rout[e] = i <= c ? S[(size_t)c * m + i] : T(0);
+    }
+  for (int k = l - 1; k >= 0; --k) {
+    const T tk = tau[k];
+    const T *v = S + (size_t)k * m;
+    for (int c = warp; c < l; c += nw)
+      if (c > k) smem_apply(v, tk, S + (size_t)c * m, k, m, lane);
+    __syncthreads();
+    T *colk = S + (size_t)k * m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      colk[i] = i < k ? T(0) : (i == k ? T(1) - tk : -tk * colk[i]);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < m * l; e += blockDim.x) P[e] = S[e];
+}
+
+template <typename T>
+__global__ void qr_smem_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel sel) {
+  if (sel.count && (int)blockIdx.x >= *sel.count) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *S = reinterpret_cast<T *>(smem_raw);
+  block_smem_qr<T>(P + (int64_t)blockIdx.x * sP, m, l, S, S + (size_t)m * l, nullptr);
+}
+
 template <typename T, int CPW, int RPL>
 __global__ void qr_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel sel) {
   if (sel.count && (int)blockIdx.x >= *sel.count) return;
@@ -557,10 +649,11 @@ __device__ __forceinline__ T prox_sv(T s, const ShrinkScalars &sh) {
 
 // Per slice: QR of B^T (P2), Jacobi SVD of R, shrink, core C, then
 // P1 <- P1 C (= Q C) and P2 <- Qb, ready for Gbar = P1 P2^T.
-template <typename T, int CPW, int RPL, int G>
+template <typename T, int CPW, int RPL, int G, bool REG>
 __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64_t sP1,
                                 T *__restrict__ P2, int64_t sP2, ShrinkScalars sh,
-                                T *__restrict__ sig_out, int *__restrict__ rank_out,
+                                T *__restrict__ sig_out, int ldsig,
+                                int *__restrict__ rank_out, int *__restrict__ width_out,
                                 SliceSel sel) {
   if (sel.count && (int)blockIdx.x >= *sel.count) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -579,7 +672,8 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
 
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) J[e] = (e % l == e / l) ? T(1) : T(0);
   // B^T = Qb R: Qb overwrites P2, R lands in W
-  block_reg_qr<T, CPW, RPL>(P2j, n2, l, panel, tau, W);
+  if constexpr (REG) block_reg_qr<T, CPW, RPL>(P2j, n2, l, panel, tau, W);
+  else block_smem_qr<T>(P2j, n2, l, panel, tau, W);
   // Rotate only while a pair's cosine exceeds max(l, 8) * eps: below that the
   // computed inner product is rounding noise (an l-term dot product).
   const T eps = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
@@ -602,7 +696,7 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
       const T sg = sqrt(ss);
       const T sp = prox_sv(sg, sh);
       ratio[i] = sg > T(0) ? sp / sg : T(0);
-      sig_out[(int64_t)j * l + i] = sg;
+      sig_out[(int64_t)j * ldsig + i] = sg;
       tau[i] = sp;   // reuse tau[] for the shrunk values
     }
   }
@@ -611,7 +705,9 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     int k = 0;
     for (int i = 0; i < l; ++i) k += tau[i] > T(0);
     rank_out[j] = k;
+    if (width_out) width_out[j] = l;
   }
+  for (int i = l + threadIdx.x; i < ldsig; i += blockDim.x) sig_out[(int64_t)j * ldsig + i] = T(0);
   // C[a][b] = sum_i J[a][i] ratio_i W[b][i]   (column-major C[a + b*l])
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int a = e % l, b = e / l;
@@ -667,21 +763,45 @@ size_t svd_smem(int n1, int n2, int l) {
 
 constexpr size_t kSliceSmemMax = 227 * 1024;
 
+// Whether one block of `threads` threads of kernel k fits on an SM (the
+// register-resident panels of large slices need more registers than an SM
+// has; those take the shared-memory variant).
+template <typename K>
+cudaError_t fits_one_block(K k, int threads, size_t smem, bool &fits) {
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
+  fits = nb >= 1;
+  return e;
+}
+
+constexpr int kSmemPanelWarps = 16;
+
 template <typename T, int CPW, int RPL>
 cudaError_t run_qr_t(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) {
   const size_t smem = qr_smem<T>(m, l);
   auto k = qr_kernel<T, CPW, RPL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<n, 32 * panel_warps(l, CPW), smem, s>>>(m, l, P, (int64_t)m * l, sel);
+  const int threads = 32 * panel_warps(l, CPW);
+  bool fits = false;
+  if ((e = fits_one_block(k, threads, smem, fits)) != cudaSuccess) return e;
+  if (fits) {
+    k<<<n, threads, smem, s>>>(m, l, P, (int64_t)m * l, sel);
+  } else {
+    auto k2 = qr_smem_kernel<T>;
+    if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    k2<<<n, 32 * kSmemPanelWarps, smem, s>>>(m, l, P, (int64_t)m * l, sel);
+  }
   return cudaGetLastError();
 }
 
 template <typename T, int CPW, int RPL, int G>
 cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh, T *sig,
-                      int *rank, cudaStream_t s, SliceSel sel) {
+                      int ldsig, int *rank, int *width, cudaStream_t s, SliceSel sel) {
   const size_t smem = svd_smem<T>(n1, n2, l);
-  auto k = svd_core_kernel<T, CPW, RPL, G>;
+  auto k = svd_core_kernel<T, CPW, RPL, G, true>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int lp = l + (l & 1);
@@ -689,8 +809,20 @@ cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkSc
   const int jw = (lp / 2 * G + 31) / 32;   // warps giving every Jacobi pair a lane group
   if (jw > nw) nw = jw > 32 ? 32 : jw;
   if (nw < 4) nw = 4;
-  k<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig, rank,
-                             sel);
+  bool fits = false;
+  if ((e = fits_one_block(k, 32 * nw, smem, fits)) != cudaSuccess) return e;
+  if (!fits) {
+    auto k2 = svd_core_kernel<T, 4, 1, G, false>;
+    if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    nw = jw > kSmemPanelWarps ? (jw > 32 ? 32 : jw) : kSmemPanelWarps;
+    k2<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig,
+                                ldsig > l ? ldsig : l, rank, width, sel);
+    return cudaGetLastError();
+  }
+  k<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig,
+                             ldsig > l ? ldsig : l, rank, width, sel);
   return cudaGetLastError();
 }
 
@@ -712,12 +844,15 @@ cudaError_t run_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel = Sli
 
 template <typename T>
 cudaError_t run_svd_core(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh,
-                         T *sig, int *rank, cudaStream_t s, SliceSel sel = SliceSel{}) {
+                         T *sig, int *rank, cudaStream_t s, SliceSel sel = SliceSel{},
+                         int ldsig = 0, int *width = nullptr) {
+#define TR_SVD_ARGS n1, n2, l, P1, P2, n, sh, sig, ldsig, rank, width, s, sel
   if (pick_cpw(l) == 2) {
-    if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 4>(n1, n2, l, P1, P2, n, sh, sig, rank, s, sel))) }
-    TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s, sel)))
+    if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 4>(TR_SVD_ARGS))) }
+    TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8>(TR_SVD_ARGS)))
   }
-  TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8>(n1, n2, l, P1, P2, n, sh, sig, rank, s, sel)))
+  TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8>(TR_SVD_ARGS)))
+#undef TR_SVD_ARGS
 }
 
 #include "adapt_kernels.cuh"
@@ -742,7 +877,7 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   // BF16.  The BF16 form keeps the sketch and the early power products in
   // BF16 and computes the last power product and B^T = Abar^T Q in split
   // BF16, so the final basis and B are refined at FP32-level accuracy.
-  const bool tc = sizeof(T) == 4 && w.l <= 64 &&
+  const bool tc = sizeof(T) == 4 && w.l <= 128 &&
                   (w.prec == TR_PREC_BF16 || w.prec == TR_PREC_BF16X3);
   const int early = !tc ? 0 : (w.prec == TR_PREC_BF16 ? 1 : 3);
   const int late = !tc ? 0 : 3;
@@ -771,7 +906,8 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   }
   if ((e = run_qr<T>(n1, l, P1, n, s, w.sel)) != cudaSuccess) return e;
   if ((e = AtX(P1, P2, late)) != cudaSuccess) return e;
-  if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s, w.sel)) != cudaSuccess)
+  if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s, w.sel, w.ldsig,
+                           w.width)) != cudaSuccess)
     return e;
   // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output
   return rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s, w.sel);

@@ -29,6 +29,10 @@ struct tr_handle {
   void *Abar = nullptr, *Gbar = nullptr;      // transform-domain scratch
   SliceWork sw{};
   AdaptWork aw{};                             // fixed-accuracy engine workspace
+  LearnedWork lw{};                           // learned-width engine state
+  int *width = nullptr;                       // sketch width per slice, last pass
+  bool have_pass = false;                     // a slice pass has run
+  double thr_last = 0.0;                      // its shrink threshold
   unsigned long long *res = nullptr;          // RES_COUNT slots
   unsigned long long *res_prev = nullptr;     // slots for a deferred inverse pass
   int *flags = nullptr;
@@ -113,6 +117,17 @@ static void free_profile(tr_handle *h) {
 
 static void free_all(tr_handle *h) {
   free_profile(h);
+  LearnedWork &lw = h->lw;
+  void *lbufs[] = {lw.params, lw.feat, lw.pred, lw.ids, lw.counts, lw.fb_ids, lw.fb_count};
+  for (void *b : lbufs)
+    if (b) cudaFree(b);
+  if (lw.h_counts) cudaFreeHost(lw.h_counts);
+  for (int i = 0; i < TR_LEARNED_STREAMS; ++i) {
+    if (lw.aux[i]) cudaStreamDestroy(lw.aux[i]);
+    if (lw.join[i]) cudaEventDestroy(lw.join[i]);
+  }
+  if (lw.fork) cudaEventDestroy(lw.fork);
+  if (h->width) cudaFree(h->width);
   void *bufs[] = {h->mats, h->L, h->E, h->Y, h->Lam, h->G, h->Abar, h->Gbar,
                   h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->sw.err,
                   h->aw.Ucat, h->aw.Vcat, h->aw.X, h->aw.Lm, h->aw.Rm, h->aw.E, h->aw.nrm2,
@@ -122,6 +137,35 @@ static void free_all(tr_handle *h) {
     if (b) cudaFree(b);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+}
+
+// Weights file: "TRRANK01", int32 16, 128, 3, 0, int64 count, count float32.
+static bool read_model(const char *path, std::vector<float> &w, char *err, size_t errlen) {
+  FILE *f = fopen(path, "rb");
+  if (!f) {
+    snprintf(err, errlen, "cannot open model file %s", path);
+    return false;
+  }
+  char magic[8];
+  int32_t dims[4];
+  int64_t count = 0;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TRRANK01", 8) == 0 &&
+            fread(dims, 4, 4, f) == 4 && dims[0] == TR_MLP_IN && dims[1] == TR_MLP_HIDDEN &&
+            dims[2] == TR_MLP_LAYERS && fread(&count, 8, 1, f) == 1 && count == mlp_param_count();
+  if (ok) {
+    w.resize((size_t)count);
+    ok = fread(w.data(), 4, (size_t)count, f) == (size_t)count;
+  }
+  fclose(f);
+  if (!ok) snprintf(err, errlen, "model file %s: bad header or size", path);
+  return ok;
+}
+
+// Smallest singular value the shrink keeps nonzero: tau theta (l1, and MCP
+// with gamma > tau), theta sqrt(gamma tau) (MCP hard-threshold regime).
+static double shrink_threshold(const tr_params &p, double tau) {
+  if (p.phi == TR_PEN_L1 || p.phi_gamma > tau) return tau * p.phi_theta;
+  return p.phi_theta * sqrt(p.phi_gamma * tau);
 }
 
 static int sketch_width(const tr_handle *h) {
@@ -143,7 +187,7 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   if (!p->observed || !p->mask) return fail(nullptr, TR_EINVAL, "observed/mask must be device pointers");
   for (int i = 0; i < p->order; ++i)
     if (p->dims[i] < 1) return fail(nullptr, TR_EINVAL, "dims[%d] = %lld < 1", i, (long long)p->dims[i]);
-  if (prm->engine != TR_LR_RSVD && prm->engine != TR_LR_ADAPTIVE)
+  if (prm->engine != TR_LR_RSVD && prm->engine != TR_LR_ADAPTIVE && prm->engine != TR_LR_LEARNED)
     return fail(nullptr, TR_EUNSUPPORTED, "engine %d not built", (int)prm->engine);
   if (prm->engine == TR_LR_ADAPTIVE &&
       (prm->adapt_block < 1 || prm->adapt_block > 32 || !(prm->adapt_eps > 0)))
@@ -286,9 +330,15 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   sw.l = l;
   sw.q = prm->power_iters;
   sw.seed = prm->seed;
-  INIT_CUDA(cudaMalloc(&sw.Om, (size_t)h->n * h->n2 * l * h->esz));
-  INIT_CUDA(cudaMalloc(&sw.P1, (size_t)h->n * h->n1 * l * h->esz));
-  INIT_CUDA(cudaMalloc(&sw.P2, (size_t)h->n * h->n2 * l * h->esz));
+  // the learned engine packs width groups into the panels, each group's
+  // region rounded up to 64 elements
+  const size_t slack = prm->engine == TR_LR_LEARNED ? (size_t)64 * plan_classes(l) : 0;
+  INIT_CUDA(cudaMalloc(&sw.Om, ((size_t)h->n * h->n2 * l + slack) * h->esz));
+  INIT_CUDA(cudaMalloc(&sw.P1, ((size_t)h->n * h->n1 * l + slack) * h->esz));
+  INIT_CUDA(cudaMalloc(&sw.P2, ((size_t)h->n * h->n2 * l + slack) * h->esz));
+  INIT_CUDA(cudaMalloc((void **)&h->width, (size_t)h->n * sizeof(int)));
+  sw.width = h->width;
+  sw.ldsig = l;
   INIT_CUDA(cudaMalloc(&sw.sig, (size_t)h->n * l * h->esz));
   INIT_CUDA(cudaMalloc((void **)&sw.rank, (size_t)h->n * sizeof(int)));
   INIT_CUDA(cudaMalloc((void **)&h->res, RES_COUNT * sizeof(unsigned long long)));
@@ -312,6 +362,34 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     INIT_CUDA(cudaMalloc((void **)&aw.kept, (size_t)h->n * sizeof(int)));
     INIT_CUDA(cudaMalloc((void **)&aw.draws, (size_t)h->n * sizeof(int)));
   }
+  if (prm->engine == TR_LR_LEARNED) {
+    LearnedWork &lw = h->lw;
+    lw.lmax = l;
+    lw.p = prm->oversample;
+    const int C = plan_classes(l);
+    INIT_CUDA(cudaMalloc((void **)&lw.params, (size_t)mlp_param_count() * sizeof(float)));
+    INIT_CUDA(cudaMalloc((void **)&lw.feat, (size_t)h->n * TR_MLP_IN * sizeof(float)));
+    INIT_CUDA(cudaMalloc((void **)&lw.pred, (size_t)h->n * sizeof(float)));
+    INIT_CUDA(cudaMalloc((void **)&lw.ids, (size_t)h->n * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&lw.counts, (size_t)C * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&lw.fb_ids, (size_t)h->n * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&lw.fb_count, sizeof(int)));
+    INIT_CUDA(cudaMallocHost((void **)&lw.h_counts, ((TR_MAX_L + 7) / 8 + 1) * sizeof(int)));
+    lw.width = h->width;
+    for (int i = 0; i < TR_LEARNED_STREAMS; ++i) {
+      INIT_CUDA(cudaStreamCreateWithFlags(&lw.aux[i], cudaStreamNonBlocking));
+      INIT_CUDA(cudaEventCreateWithFlags(&lw.join[i], cudaEventDisableTiming));
+    }
+    INIT_CUDA(cudaEventCreateWithFlags(&lw.fork, cudaEventDisableTiming));
+    if (prm->model_path) {
+      std::vector<float> w;
+      if (!read_model(prm->model_path, w, h->err, sizeof h->err))
+        return cleanup(TR_EINVAL);
+      INIT_CUDA(cudaMemcpy(lw.params, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+      INIT_CUDA(launch_mlp_init(lw.params, prm->seed, h->stream));
+    }
+  }
   INIT_CUDA(cudaEventCreate(&h->ev0));
   INIT_CUDA(cudaEventCreate(&h->ev1));
   INIT_CUDA(cudaStreamSynchronize(h->stream));
@@ -324,14 +402,25 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
 
 static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double tau, int t) {
   ShrinkScalars sh{tau, (int)h->prm.phi, h->prm.phi_theta, h->prm.phi_gamma};
+  const double thr = shrink_threshold(h->prm, tau);
   if (h->prm.engine == TR_LR_ADAPTIVE) {
     TR_CUDA(h, launch_slice_adaptive(h->dtype, h->sw, h->aw, Abar, Gbar, sh, t, h->stream));
     const uint64_t nblk = (uint64_t)(h->aw.kcap / h->aw.b);
     h->launches += 1 + 4 * nblk - 2 + 3;   // init, per block GEMM+U (+GEMM+V), B GEMM, SVD, rebuild
+    // the width of an adaptive slice is its basis size
+    TR_CUDA(h, cudaMemcpyAsync(h->width, h->aw.kept, (size_t)h->n * sizeof(int),
+                               cudaMemcpyDeviceToDevice, h->stream));
+  } else if (h->prm.engine == TR_LR_LEARNED) {
+    cudaError_t e = launch_slice_learned(h->dtype, h->sw, h->lw, Abar, Gbar, sh, thr, t,
+                                         h->prm.max_iter, h->stream, &h->launches);
+    if (e != cudaSuccess)
+      return fail(h, TR_ECUDA, "learned slice pass: %s", cudaGetErrorString(e));
   } else {
     TR_CUDA(h, launch_slice_rsvd(h->dtype, h->sw, Abar, Gbar, sh, t, h->stream));
     h->launches += 7 + 4 * (uint64_t)h->sw.q;   // sketch, 2 + 2q GEMM, 1 + 2q QR, SVD core, rebuild
   }
+  h->have_pass = true;
+  h->thr_last = thr;
   return TR_OK;
 }
 
@@ -362,7 +451,7 @@ static tr_status read_info(tr_handle *h, double mu_used, tr_step_info *info) {
   }
   info->max_rank = mx;
   info->sum_rank = (int)sum;
-  info->fallback_slices = 0;
+  info->fallback_slices = h->prm.engine == TR_LR_LEARNED ? h->lw.last_fallback : 0;
   info->ms = ms;
   int tc_err = 0;
   TR_CUDA(h, cudaMemcpy(&tc_err, h->sw.err, sizeof tc_err, cudaMemcpyDeviceToHost));
@@ -508,6 +597,7 @@ extern "C" tr_status tr_set_state(tr_handle *h, const void *L, const void *E, co
   h->t = t;
   h->poisoned = false;
   h->pending = false;
+  h->lw.have_hist = false;
   return TR_OK;
 }
 
@@ -585,6 +675,135 @@ extern "C" tr_status tr_profile_read(tr_handle *h, double ms[3], int *steps) {
 extern "C" tr_status tr_kernel_launches(const tr_handle *h, uint64_t *count) {
   if (!h || !count) return TR_EINVAL;
   *count = h->launches;
+  return TR_OK;
+}
+
+extern "C" int64_t tr_mlp_param_count(void) { return mlp_param_count(); }
+
+extern "C" tr_status tr_set_model(tr_handle *h, const float *params, int64_t count) {
+  if (!h || !params) return TR_EINVAL;
+  if (h->prm.engine != TR_LR_LEARNED) return fail(h, TR_EINVAL, "not a learned-engine handle");
+  if (count != mlp_param_count())
+    return fail(h, TR_EINVAL, "expected %lld parameters, got %lld", (long long)mlp_param_count(),
+                (long long)count);
+  TR_CUDA(h, cudaMemcpyAsync(h->lw.params, params, (size_t)count * sizeof(float),
+                             cudaMemcpyHostToDevice, h->stream));
+  TR_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_last_slice_widths(tr_handle *h, int *widths) {
+  if (!h || !widths) return TR_EINVAL;
+  TR_CUDA(h, cudaMemcpyAsync(widths, h->width, (size_t)h->n * sizeof(int), cudaMemcpyDeviceToHost,
+                             h->stream));
+  TR_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_slice_features(tr_handle *h, double tau, int t, float *features) {
+  if (!h || !features) return TR_EINVAL;
+  if (!h->have_pass) return fail(h, TR_EINVAL, "no slice pass has run yet");
+  if (!(tau >= 0) || t < 0) return fail(h, TR_EINVAL, "need tau >= 0, t >= 0");
+  const double T = h->prm.max_iter > 0 ? (double)h->prm.max_iter : 1.0;
+  TR_CUDA(h, launch_features(h->dtype, (int)h->n, h->sw.sig, h->sw.ldsig, h->sw.rank, h->width,
+                             shrink_threshold(h->prm, tau), h->thr_last, (double)t / T, features,
+                             h->stream));
+  h->launches += 1;
+  return TR_OK;
+}
+
+#define TR_STATELESS(call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(nullptr, e_ == cudaErrorMemoryAllocation ? TR_ENOMEM : TR_ECUDA,      \
+                  "%s: %s", #call, cudaGetErrorString(e_));                             \
+  } while (0)
+
+extern "C" tr_status tr_features(tr_dtype dtype, int n, const void *sig, int ldsig, const int *rank,
+                                 const int *width, double thr, double thr0, double tfrac,
+                                 float *features, void *stream) {
+  if (n < 0 || (n > 0 && (!sig || !rank || !width || !features)) || ldsig < 1 ||
+      (dtype != TR_F32 && dtype != TR_F64))
+    return fail(nullptr, TR_EINVAL, "tr_features: bad arguments");
+  TR_STATELESS(launch_features(dtype, n, sig, ldsig, rank, width, thr, thr0, tfrac, features,
+                               (cudaStream_t)stream));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_plan_widths(int n, const float *yhat, int oversample, int lmax, int *width,
+                                    int *ids, int *counts, void *stream) {
+  if (n < 0 || oversample < 0 || lmax < 1 || lmax > TR_MAX_L || !counts ||
+      (n > 0 && (!yhat || !width || !ids)))
+    return fail(nullptr, TR_EINVAL, "tr_plan_widths: bad arguments");
+  TR_STATELESS(launch_plan(n, yhat, oversample, lmax, width, ids, counts, (cudaStream_t)stream));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_mlp_init(float *params, uint64_t seed, void *stream) {
+  if (!params) return fail(nullptr, TR_EINVAL, "tr_mlp_init: NULL params");
+  TR_STATELESS(launch_mlp_init(params, seed, (cudaStream_t)stream));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_mlp_forward(const float *params, const float *X, int B, float *yhat,
+                                    void *stream) {
+  if (B < 0 || (B > 0 && (!params || !X || !yhat)))
+    return fail(nullptr, TR_EINVAL, "tr_mlp_forward: bad arguments");
+  TR_STATELESS(launch_mlp_forward(params, X, B, yhat, nullptr, (cudaStream_t)stream));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_mlp_loss_grad(const float *params, const float *X, const float *y, int B,
+                                      double under_weight, float *grad, float *loss, void *stream) {
+  if (B < 1 || !params || !X || !y || !grad || !(under_weight >= 0))
+    return fail(nullptr, TR_EINVAL, "tr_mlp_loss_grad: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  float *work = nullptr;
+  const size_t nf = mlp_workspace_floats(B) + (size_t)B;
+  TR_STATELESS(cudaMallocAsync((void **)&work, nf * sizeof(float), s));
+  cudaError_t e = launch_mlp_loss_grad(params, X, y, B, (float)under_weight, work,
+                                       work + mlp_workspace_floats(B), grad, loss, s);
+  cudaFreeAsync(work, s);
+  TR_STATELESS(e);
+  return TR_OK;
+}
+
+extern "C" tr_status tr_mlp_adam(float *params, const float *grad, float *m, float *v,
+                                 int64_t count, double lr, double beta1, double beta2, double eps,
+                                 int step, void *stream) {
+  if (count < 0 || step < 1 || (count > 0 && (!params || !grad || !m || !v)) ||
+      !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return fail(nullptr, TR_EINVAL, "tr_mlp_adam: bad arguments");
+  TR_STATELESS(launch_mlp_adam(params, grad, m, v, count, lr, beta1, beta2, eps, step,
+                               (cudaStream_t)stream));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_mlp_train(float *params, const float *X, const float *y, int n, int batch,
+                                  int steps, double lr, double under_weight, uint64_t seed,
+                                  float *loss_hist, void *stream) {
+  if (!params || !X || !y || n < 1 || batch < 1 || steps < 0 || !(under_weight >= 0))
+    return fail(nullptr, TR_EINVAL, "tr_mlp_train: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t P = mlp_param_count();
+  const size_t nw = mlp_workspace_floats(batch);
+  const size_t total = nw + (size_t)batch /* yhat */ + (size_t)batch * TR_MLP_IN + batch +
+                       3 * (size_t)P;
+  float *buf = nullptr;
+  TR_STATELESS(cudaMallocAsync((void **)&buf, total * sizeof(float), s));
+  float *work = buf, *yhat = work + nw, *Xb = yhat + batch, *yb = Xb + (size_t)batch * TR_MLP_IN;
+  float *grad = yb + batch, *m = grad + P, *v = m + P;
+  cudaError_t e = cudaMemsetAsync(m, 0, 2 * (size_t)P * sizeof(float), s);
+  for (int it = 0; it < steps && e == cudaSuccess; ++it) {
+    e = launch_mlp_gather(X, y, n, batch, it, seed, Xb, yb, s);
+    if (e == cudaSuccess)
+      e = launch_mlp_loss_grad(params, Xb, yb, batch, (float)under_weight, work, yhat, grad,
+                               loss_hist ? loss_hist + it : nullptr, s);
+    if (e == cudaSuccess) e = launch_mlp_adam(params, grad, m, v, P, lr, 0.9, 0.999, 1e-8, it + 1, s);
+  }
+  cudaFreeAsync(buf, s);
+  TR_STATELESS(e);
   return TR_OK;
 }
 

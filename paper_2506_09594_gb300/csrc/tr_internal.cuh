@@ -10,6 +10,10 @@
 #define TR_MAX_TMODES 6
 #define TR_MAX_NK 64          // largest transformed-mode size handled in registers
 #define TR_MAX_L 96           // largest sketch width handled by the slice kernels
+#define TR_MLP_IN 16          // rank-predictor features per slice
+#define TR_MLP_HIDDEN 128     // units per hidden layer
+#define TR_MLP_LAYERS 3       // hidden layers
+#define TR_LEARNED_STREAMS 4  // streams the learned engine spreads width groups over
 
 // The transformed modes 3..d of a problem as seen from the slice index j.
 // Mode k (0-based among the transformed modes) has size dim[k] and stride
@@ -83,11 +87,13 @@ struct SliceWork {
   void *Om;     // n * n2 * l, column-major per slice
   void *P1;     // n * n1 * l, column-major per slice (ld n1)
   void *P2;     // n * n2 * l, column-major per slice (ld n2)
-  void *sig;    // n * l singular values of B
-  int *rank;    // n kept ranks
+  void *sig;    // singular values of B: row j (slice id) at sig + j * ldsig
+  int *rank;    // kept rank per slice id
   int prec;     // tr_prec of the skinny products (FP32 problems only)
   int *err;     // device flag set by a tensor-core GEMM whose bounded wait expired
   SliceSel sel; // which slices this pass works on (default: all)
+  int ldsig;    // row stride of sig (0: l); entries l..ldsig-1 are zeroed
+  int *width;   // optional: sketch width used, per slice id
 };
 // Workspace of the fixed-accuracy engine (Alg. 3 per slice).
 struct AdaptWork {
@@ -104,3 +110,42 @@ size_t adapt_smem_bytes(tr_dtype dt, int n1, int n2, int b, int kcap);
 cudaError_t launch_slice_rsvd(tr_dtype dt, const SliceWork &w, const void *Abar, void *Gbar,
                               const ShrinkScalars &sh, int t, cudaStream_t s);
 size_t slice_smem_limit_ok(tr_dtype dt, int n1, int n2, int l);
+
+// ---- learned sketch widths and the rank-predictor MLP (learned.cu) ----
+struct LearnedWork {
+  int lmax = 0, p = 0;       // plain width (cap), oversampling
+  int merge_min = 8;         // width groups with fewer slices join the next wider one
+  float *params = nullptr;   // MLP parameters (FP32 master copy)
+  float *feat = nullptr;     // n x TR_MLP_IN features
+  float *pred = nullptr;     // n predicted log(1 + rank)
+  int *width = nullptr;      // sketch width used per slice (history of the last pass)
+  int *ids = nullptr, *counts = nullptr;     // plan: slice ids sorted by width class
+  int *fb_ids = nullptr, *fb_count = nullptr;
+  int *h_counts = nullptr;   // pinned host mirror: class counts, then the fallback count
+  bool have_hist = false;
+  double thr_prev = 0.0;
+  int last_fallback = 0, last_groups = 0;
+  cudaStream_t aux[TR_LEARNED_STREAMS] = {};
+  cudaEvent_t fork = nullptr, join[TR_LEARNED_STREAMS] = {};
+};
+int64_t mlp_param_count();
+size_t mlp_workspace_floats(int B);
+cudaError_t launch_mlp_init(float *prm, uint64_t seed, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float *prm, const float *X, int B, float *yhat, float *H,
+                               cudaStream_t s);
+cudaError_t launch_mlp_loss_grad(const float *prm, const float *X, const float *y, int B,
+                                 float under, float *work, float *yhat, float *grad, float *loss,
+                                 cudaStream_t s);
+cudaError_t launch_mlp_adam(float *prm, const float *g, float *m, float *v, int64_t n, double lr,
+                            double b1, double b2, double eps, int step, cudaStream_t s);
+cudaError_t launch_mlp_gather(const float *X, const float *y, int n, int B, int step,
+                              uint64_t seed, float *Xb, float *yb, cudaStream_t s);
+cudaError_t launch_features(tr_dtype dt, int n, const void *sig, int ldsig, const int *rank,
+                            const int *width, double thr, double thr0, double tfrac, float *F,
+                            cudaStream_t s);
+int plan_classes(int lmax);
+cudaError_t launch_plan(int n, const float *yhat, int p, int lmax, int *width, int *ids,
+                        int *counts, cudaStream_t s);
+cudaError_t launch_slice_learned(tr_dtype dt, const SliceWork &w, LearnedWork &lw,
+                                 const void *Abar, void *Gbar, const ShrinkScalars &sh,
+                                 double thr, int t, int T, cudaStream_t s, uint64_t *launches);

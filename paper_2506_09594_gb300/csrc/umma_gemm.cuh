@@ -1,6 +1,6 @@
 // Batched skinny GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out, N <= 64.
+// C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out, N <= 128.
 // One CTA (4 warps) owns a 128-row tile of one batch entry.  K is consumed
 // in chunks of 64: the 128 threads load the FP32 operands from global
 // memory, round them to BF16 (optionally split x = hi + lo, both BF16) and

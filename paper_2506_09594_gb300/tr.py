@@ -24,6 +24,9 @@ TR_PEN_L1, TR_PEN_MCP = 0, 1
 TR_NOISE_NONE, TR_NOISE_L1 = 0, 1
 TR_LR_FULLSVD, TR_LR_RSVD, TR_LR_ADAPTIVE, TR_LR_LEARNED = 0, 1, 2, 3
 TR_PREC_FP32, TR_PREC_TF32, TR_PREC_BF16, TR_PREC_BF16X3 = 0, 1, 2, 3
+TR_MLP_FEATURES, TR_MLP_PARAMS = 16, 35329
+MODEL_MAGIC = b"TRRANK01"
+DEFAULT_MODEL = os.path.join(PKG, "rank_mlp.bin")
 
 
 class TrError(RuntimeError):
@@ -87,6 +90,22 @@ _SIGS = {
                                              ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_int, _P,
                                              ctypes.c_char_p, ctypes.c_size_t]),
+    "tr_mlp_param_count": (ctypes.c_int64, []),
+    "tr_set_model": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "tr_last_slice_widths": (ctypes.c_int, [_P, _P]),
+    "tr_slice_features": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _P]),
+    "tr_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P]),
+    "tr_plan_widths": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                      _P]),
+    "tr_mlp_init": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
+    "tr_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+    "tr_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
+    "tr_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, _P]),
+    "tr_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_uint64, _P, _P]),
     "tr_free": (ctypes.c_int, [_P]),
     "tr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -158,6 +177,102 @@ def slice_prox_noalloc(Abar, Gbar, l, q, tau, t, seed=0, phi=TR_PEN_MCP, theta=1
     if st != TR_OK:
         raise TrError(st, buf.value.decode())
     return Gbar
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    return ctypes.c_void_p(stream)
+
+
+def save_model(path, params):
+    """Write a weights file (layout documented at tr_set_model in tr.h)."""
+    import numpy as np
+    w = np.ascontiguousarray(np.asarray(params, dtype="<f4").ravel())
+    if w.size != TR_MLP_PARAMS:
+        raise ValueError("expected %d parameters, got %d" % (TR_MLP_PARAMS, w.size))
+    with open(path, "wb") as f:
+        f.write(MODEL_MAGIC)
+        f.write(np.array([TR_MLP_FEATURES, 128, 3, 0], dtype="<i4").tobytes())
+        f.write(np.array([w.size], dtype="<i8").tobytes())
+        f.write(w.tobytes())
+
+
+def load_model(path):
+    """Read a weights file into a float32 numpy array."""
+    import numpy as np
+    with open(path, "rb") as f:
+        raw = f.read()
+    if raw[:8] != MODEL_MAGIC:
+        raise ValueError("%s: not a rank-predictor weights file" % path)
+    dims = np.frombuffer(raw[8:24], dtype="<i4")
+    count = int(np.frombuffer(raw[24:32], dtype="<i8")[0])
+    if tuple(dims) != (TR_MLP_FEATURES, 128, 3, 0) or count != TR_MLP_PARAMS:
+        raise ValueError("%s: unexpected architecture %s / %d" % (path, tuple(dims), count))
+    return np.frombuffer(raw[32:32 + 4 * count], dtype="<f4").copy()
+
+
+def features(sig, rank, width, thr, thr0, tfrac, stream=None):
+    """tr_features: (n, 16) float32 features from per-slice singular values."""
+    import torch
+    n, ldsig = sig.shape
+    dt = {torch.float32: TR_F32, torch.float64: TR_F64}[sig.dtype]
+    out = torch.empty((n, TR_MLP_FEATURES), dtype=torch.float32, device=sig.device)
+    _check(load().tr_features(dt, n, _ptr(sig), ldsig, _ptr(rank), _ptr(width), float(thr),
+                              float(thr0), float(tfrac), _ptr(out), _stream(stream)))
+    return out
+
+
+def plan_widths(yhat, oversample, lmax, stream=None):
+    """tr_plan_widths: (width per slice, ids sorted by class, class counts)."""
+    import torch
+    n = yhat.shape[0]
+    width = torch.empty(n, dtype=torch.int32, device=yhat.device)
+    ids = torch.empty(n, dtype=torch.int32, device=yhat.device)
+    counts = torch.empty((lmax + 7) // 8, dtype=torch.int32, device=yhat.device)
+    _check(load().tr_plan_widths(n, _ptr(yhat), int(oversample), int(lmax), _ptr(width),
+                                 _ptr(ids), _ptr(counts), _stream(stream)))
+    return width, ids, counts
+
+
+def mlp_init(seed, device="cuda", stream=None):
+    import torch
+    prm = torch.empty(TR_MLP_PARAMS, dtype=torch.float32, device=device)
+    _check(load().tr_mlp_init(_ptr(prm), int(seed), _stream(stream)))
+    return prm
+
+
+def mlp_forward(params, X, stream=None):
+    import torch
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(load().tr_mlp_forward(_ptr(params), _ptr(X), int(X.shape[0]), _ptr(y), _stream(stream)))
+    return y
+
+
+def mlp_loss_grad(params, X, y, under_weight, stream=None):
+    import torch
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(load().tr_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(y), int(X.shape[0]),
+                                   float(under_weight), _ptr(grad), _ptr(loss), _stream(stream)))
+    return loss, grad
+
+
+def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().tr_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(params.numel()),
+                              float(lr), float(beta1), float(beta2), float(eps), int(step),
+                              _stream(stream)))
+
+
+def mlp_train(params, X, y, batch, steps, lr, under_weight, seed, stream=None):
+    """tr_mlp_train in place on `params`; returns the per-step loss (device)."""
+    import torch
+    hist = torch.empty(max(int(steps), 1), dtype=torch.float32, device=params.device)
+    _check(load().tr_mlp_train(_ptr(params), _ptr(X), _ptr(y), int(X.shape[0]), int(batch),
+                               int(steps), float(lr), float(under_weight), int(seed), _ptr(hist),
+                               _stream(stream)))
+    return hist[:int(steps)]
 
 
 class Handle:
@@ -252,6 +367,23 @@ class Handle:
             self.h, sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             ranks.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), None), self.h)
         return sig.reshape(n, l.value), ranks
+
+    def slice_widths(self):
+        import numpy as np
+        w = np.zeros(self.shape[0], dtype=np.int32)
+        _check(load().tr_last_slice_widths(self.h, ctypes.c_void_p(w.ctypes.data)), self.h)
+        return w
+
+    def slice_features(self, tau, t):
+        import torch
+        out = torch.empty((self.shape[0], TR_MLP_FEATURES), dtype=torch.float32, device="cuda")
+        _check(load().tr_slice_features(self.h, float(tau), int(t), _ptr(out)), self.h)
+        return out
+
+    def set_model(self, params):
+        import numpy as np
+        w = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        _check(load().tr_set_model(self.h, ctypes.c_void_p(w.ctypes.data), int(w.size)), self.h)
 
     def profile_enable(self, max_steps):
         _check(load().tr_profile_enable(self.h, int(max_steps)), self.h)

@@ -87,3 +87,20 @@ def test_tensor_core_precisions_need_fp32(lib):
     assert st == tr.TR_EUNSUPPORTED
     st, _ = _init(lib, 3, [8, 8, 4], prec=tr.TR_PREC_TF32)
     assert st == tr.TR_EUNSUPPORTED
+
+
+def test_model_file_roundtrip(tmp_path):
+    import numpy as np
+    w = np.random.default_rng(0).standard_normal(tr.TR_MLP_PARAMS).astype(np.float32)
+    path = tmp_path / "m.bin"
+    tr.save_model(str(path), w)
+    raw = path.read_bytes()
+    assert raw[:8] == b"TRRANK01" and len(raw) == 32 + 4 * tr.TR_MLP_PARAMS
+    assert np.array_equal(tr.load_model(str(path)), w)
+    with pytest.raises(ValueError):
+        tr.save_model(str(path), w[:-1])
+
+
+def test_mlp_param_count_export():
+    from oracle import learned
+    assert tr.load().tr_mlp_param_count() == tr.TR_MLP_PARAMS == learned.param_count()

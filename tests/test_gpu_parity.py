@@ -112,6 +112,27 @@ def test_slice_prox_parity(case, dt):
     h.close()
 
 
+@pytest.mark.parametrize("dt,case", [("f32", (2, 512, 512, 20, 0.01, 74, 1, "mcp")),
+                                     ("f32", (3, 300, 420, 12, 0.05, 60, 1, "l1")),
+                                     ("f64", (2, 300, 200, 10, 0.01, 40, 1, "l1"))])
+def test_slice_prox_large_panels(dt, case):
+    # panels too large for the register-resident QR take the shared-memory QR
+    n, n1, n2, r, noise, l, q, phi = case
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 + n2)
+    s1 = np.linalg.svd(Ab[0], compute_uv=False)[0]
+    tau = 0.05 * s1
+    kind = prox.L1 if phi == "l1" else prox.MCP
+    gamma = 3.0 * tau + 1.0
+    pen = tr.TR_PEN_L1 if phi == "l1" else tr.TR_PEN_MCP
+    h = make_handle((n1, n2, n), dt, rank=l, oversample=0, power_iters=q, phi=pen,
+                    phi_gamma=gamma, seed=13)
+    G = host(h.slice_prox(dev(Ab, dt), tau, t=1))
+    ref, _ = svt.transformed_prox(as_dtype(Ab, dt), tau, kind, 1.0, gamma, engine="rsvd", l=l,
+                                  q=q, seed=13, t=1)
+    assert relF(G, ref) < TOL[dt]
+    h.close()
+
+
 def test_slice_prox_exact_on_low_rank_matches_full_svd():
     Ab = synth.lowrank_plus_noise_stack(16, 64, 64, 5, 0.0, seed=3)
     h = make_handle((64, 64, 16), "f64", rank=5, oversample=10, phi=tr.TR_PEN_L1)
@@ -305,7 +326,8 @@ PREC_TOL = {tr.TR_PREC_BF16: 1e-3, tr.TR_PREC_BF16X3: 1e-4}
 @pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
 @pytest.mark.parametrize("case", [(16, 64, 64, 5, 0.0, 15, 1, "l1"), (6, 70, 45, 8, 0.05, 20, 1, "mcp"),
                                   (5, 140, 90, 6, 0.1, 40, 2, "l1"), (4, 33, 29, 3, 0.2, 12, 0, "l1"),
-                                  (3, 200, 200, 10, 1e-3, 20, 1, "mcp")])
+                                  (3, 200, 200, 10, 1e-3, 20, 1, "mcp"),
+                                  (3, 200, 160, 50, 1e-3, 80, 1, "l1")])   # 128-column MMA tile
 def test_slice_prox_tensor_core_forms(case, prec):
     n, n1, n2, r, noise, l, q, phi = case
     Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 * 7 + n2 + 1)
