@@ -307,6 +307,55 @@ tr_status tr_mlp_train(float *params, const float *X, const float *y, int n, int
                        int steps, double lr, double under_weight, uint64_t seed,
                        float *loss_hist, void *cuda_stream);
 
+/* ---- Graph replay, tile autotuning and batches (not in the paper) ------
+ * The penalty schedule (mu, the previous mu and the iteration index t of
+ * the sketches' Philox counters) lives on the device and the last kernel of
+ * a step advances it (mu <- min(growth mu, mu_max), t += 1), so the launch
+ * sequence of a steady-state step -- a step taken without tr_step_info after
+ * another such step -- is the same at every iteration.
+ *
+ * tr_graph_mode: when on, steady-state steps of this handle replay one
+ *   captured CUDA graph (captured at the first such step, on a stream the
+ *   handle owns, ordered after the handle's stream by events).  Results are
+ *   identical to eager steps.  The learned engine plans on the host and
+ *   returns TR_EUNSUPPORTED.
+ * tr_set_tube_tile: tubes per block of the tube kernels (4, 8, 16 or 32;
+ *   0 = the default, the largest that fits).  Every tile computes the same
+ *   values.  Errors: TR_EINVAL (not a power of two in range or too large).
+ * tr_autotune: time every fitting tube tile on the transform kernel over the
+ *   handle's transform-domain scratch (`reps` launches each, no state is
+ *   touched), install the fastest and cache it per shape class (dtype, slice
+ *   count, transformed mode sizes, n1 n2) for the process; reps = 0 reuses a
+ *   cached choice when there is one.  `tile` and `ms` (per launch) may be
+ *   NULL.  Synchronises.                                                      */
+tr_status tr_graph_mode(tr_handle *h, int on);
+tr_status tr_set_tube_tile(tr_handle *h, int tubes_per_block);
+tr_status tr_autotune(tr_handle *h, int reps, int *tile, float *ms);
+
+/* A batch: independent problems of any shapes, each with its own handle
+ * (workspace, parameters, state), stepped together.  Problems are spread
+ * over `nstreams` internal streams (<= 0: 8); each step of the batch is one
+ * CUDA graph launch covering every problem's steady-state step (captured at
+ * the first such step; eager launches otherwise, or when graph mode is off).
+ *   tr_batch_create: problems[i] with params[i] (any engine but
+ *     TR_LR_LEARNED); `cuda_stream` is the caller's stream, which every
+ *     batch step is ordered after and before.
+ *   tr_batch_step: one iteration of every problem; `infos` (NULL or nprob
+ *     entries) requests the per-problem reports, which synchronises.
+ *   tr_batch_handle: the handle of problem i (for tr_get_state and the
+ *     other per-handle calls; do not tr_free it).
+ *   tr_batch_launches: kernels launched by the batch so far.
+ *   tr_batch_last_error: message of the last failed batch call.            */
+typedef struct tr_batch tr_batch;
+tr_status tr_batch_create(tr_batch **b, int nprob, const tr_problem *problems,
+                          const tr_params *params, int nstreams, void *cuda_stream);
+tr_status tr_batch_step(tr_batch *b, tr_step_info *infos);
+tr_status tr_batch_handle(tr_batch *b, int i, tr_handle **h);
+tr_status tr_batch_graph_mode(tr_batch *b, int on);
+tr_status tr_batch_launches(const tr_batch *b, uint64_t *count);
+tr_status tr_batch_free(tr_batch *b);
+const char *tr_batch_last_error(void);
+
 /* Release all workspace.  Safe on NULL.                                     */
 tr_status tr_free(tr_handle *h);
 

@@ -209,7 +209,9 @@ size_t adapt_smem(int m, int b, int kcap) {
 // Start: ||A||^2, E, flags, V_1 = qr(G) into Vcat block 0.
 template <typename T>
 __global__ void adapt_init_kernel(int n1, int n2, int b, int kcap, const T *__restrict__ Abar,
-                                  AdaptPtrs<T> w, uint32_t k0, uint32_t k1, uint32_t t) {
+                                  AdaptPtrs<T> w, uint32_t k0, uint32_t k1, uint32_t t_host,
+                                  const int *dt) {
+  const uint32_t t = dt ? (uint32_t)*dt : t_host;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *P = reinterpret_cast<T *>(smem_raw);
   T *Q = P + (size_t)n2 * b;
@@ -307,7 +309,8 @@ __global__ void adapt_u_kernel(int i, int n1, int b, int kcap, int64_t xs, Adapt
 template <typename T>
 __global__ void adapt_v_kernel(int i, int n2, int b, int kcap, int64_t xs, AdaptPtrs<T> w,
                                double delta_rel, double eps, uint32_t k0, uint32_t k1,
-                               uint32_t t) {
+                               uint32_t t_host, const int *dt) {
+  const uint32_t t = dt ? (uint32_t)*dt : t_host;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = blockIdx.x;
   if (!w.active[j]) return;

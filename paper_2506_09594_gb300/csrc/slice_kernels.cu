@@ -26,7 +26,8 @@ namespace {
 
 template <typename T>
 __global__ void sketch_kernel(int64_t per_slice, T *__restrict__ Om, uint32_t k0, uint32_t k1,
-                              uint32_t t, uint32_t stream, SliceSel sel) {
+                              uint32_t t_host, const int *dt, uint32_t stream, SliceSel sel) {
+  const uint32_t t = dt ? (uint32_t)*dt : t_host;
   const int b = blockIdx.y;
   if (sel.count && b >= *sel.count) return;
   const int j = sel.ids ? sel.ids[b] : b;
@@ -665,6 +666,8 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   T *tau = C + l * l;
   T *ratio = tau + l;
   int *flag = reinterpret_cast<int *>(ratio + l);
+  ShrinkScalars shr = sh;
+  if (sh.dmu) shr.tau = 1.0 / *sh.dmu;
   const int bb = blockIdx.x;                       // panel entry
   const int j = sel.ids ? sel.ids[bb] : bb;        // slice id (statistics)
   T *P1j = P1 + (int64_t)bb * sP1;
@@ -694,7 +697,7 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     ss = warp_sum(ss);
     if (lane == 0) {
       const T sg = sqrt(ss);
-      const T sp = prox_sv(sg, sh);
+      const T sp = prox_sv(sg, shr);
       ratio[i] = sg > T(0) ? sp / sg : T(0);
       sig_out[(int64_t)j * ldsig + i] = sg;
       tau[i] = sp;   // reuse tau[] for the shrunk values
@@ -870,7 +873,8 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
     const int64_t groups = (per + 3) / 4;
     dim3 grid((unsigned)((groups + 255) / 256), n);
     sketch_kernel<T><<<grid, 256, 0, s>>>(per, Om, (uint32_t)(w.seed & 0xffffffffu),
-                                          (uint32_t)(w.seed >> 32), (uint32_t)t, 0u, w.sel);
+                                          (uint32_t)(w.seed >> 32), (uint32_t)t, w.dt, 0u,
+                                          w.sel);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // Precision of each skinny product: 0 = SIMT FP32, 1 = BF16, 3 = split
@@ -929,7 +933,7 @@ cudaError_t run_adaptive(const SliceWork &sw, const AdaptWork &aw, const T *Abar
   if ((e = cudaFuncSetAttribute(adapt_init_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(adapt_u_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(adapt_v_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
-  adapt_init_kernel<T><<<n, 256, sm2, s>>>(n1, n2, b, kcap, Abar, w, k0, k1, (uint32_t)t);
+  adapt_init_kernel<T><<<n, 256, sm2, s>>>(n1, n2, b, kcap, Abar, w, k0, k1, (uint32_t)t, sw.dt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nblk = kcap / b;
   for (int i = 0; i < nblk; ++i) {
@@ -945,7 +949,7 @@ cudaError_t run_adaptive(const SliceWork &sw, const AdaptWork &aw, const T *Abar
                 n1, w.X, xs, 1, n2};
     if ((e = bgemm<T>(g2, n, s)) != cudaSuccess) return e;
     adapt_v_kernel<T><<<n, 256, sm2, s>>>(i, n2, b, kcap, xs, w, aw.delta_rel, aw.eps, k0, k1,
-                                         (uint32_t)t);
+                                         (uint32_t)t, sw.dt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // B^T = Abar^T U (U zero-padded to kcap columns), SVD core, rebuild

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -33,6 +34,13 @@ struct tr_handle {
   int *width = nullptr;                       // sketch width per slice, last pass
   bool have_pass = false;                     // a slice pass has run
   double thr_last = 0.0;                      // its shrink threshold
+  DevSched *sched = nullptr;                  // device copy of mu, mu_prev, t
+  // graph replay of steady-state steps (tr_graph_mode)
+  bool graph_on = false;
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  uint64_t graph_kernels = 0;                 // kernels in one replay
   unsigned long long *res = nullptr;          // RES_COUNT slots
   unsigned long long *res_prev = nullptr;     // slots for a deferred inverse pass
   int *flags = nullptr;
@@ -128,6 +136,11 @@ static void free_all(tr_handle *h) {
   }
   if (lw.fork) cudaEventDestroy(lw.fork);
   if (h->width) cudaFree(h->width);
+  if (h->sched) cudaFree(h->sched);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
+  if (h->gev_in) cudaEventDestroy(h->gev_in);
+  if (h->gev_out) cudaEventDestroy(h->gev_out);
   void *bufs[] = {h->mats, h->L, h->E, h->Y, h->Lam, h->G, h->Abar, h->Gbar,
                   h->sw.Om, h->sw.P1, h->sw.P2, h->sw.sig, h->sw.rank, h->sw.err,
                   h->aw.Ucat, h->aw.Vcat, h->aw.X, h->aw.Lm, h->aw.Rm, h->aw.E, h->aw.nrm2,
@@ -390,6 +403,11 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
       INIT_CUDA(launch_mlp_init(lw.params, prm->seed, h->stream));
     }
   }
+  INIT_CUDA(cudaMalloc((void **)&h->sched, sizeof(DevSched)));
+  {
+    const DevSched d0{prm->mu0, prm->mu0, 0, 0};
+    INIT_CUDA(cudaMemcpy(h->sched, &d0, sizeof d0, cudaMemcpyHostToDevice));
+  }
   INIT_CUDA(cudaEventCreate(&h->ev0));
   INIT_CUDA(cudaEventCreate(&h->ev1));
   INIT_CUDA(cudaStreamSynchronize(h->stream));
@@ -400,8 +418,13 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   return TR_OK;
 }
 
-static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double tau, int t) {
+// One slice pass.  `sched`: take tau = 1/mu and the iteration index from the
+// device schedule (a step) rather than from the arguments (tr_slice_prox).
+static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double tau, int t,
+                            bool sched = false) {
   ShrinkScalars sh{tau, (int)h->prm.phi, h->prm.phi_theta, h->prm.phi_gamma};
+  if (sched) sh.dmu = &h->sched->mu;
+  h->sw.dt = sched ? &h->sched->t : nullptr;
   const double thr = shrink_threshold(h->prm, tau);
   if (h->prm.engine == TR_LR_ADAPTIVE) {
     TR_CUDA(h, launch_slice_adaptive(h->dtype, h->sw, h->aw, Abar, Gbar, sh, t, h->stream));
@@ -471,7 +494,8 @@ static tr_status read_info(tr_handle *h, double mu_used, tr_step_info *info) {
 static tr_status finalize(tr_handle *h) {
   if (!h->pending) return TR_OK;
   cudaError_t e = launch_tube_inverse(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->L,
-                                      h->G, h->Lam, h->mu_prev, h->res_prev, h->flags, h->stream);
+                                      h->G, h->Lam, h->mu_prev, &h->sched->mu_prev, h->res_prev,
+                                      h->flags, h->stream);
   if (e != cudaSuccess) {
     h->poisoned = true;
     return fail(h, TR_ECUDA, "tube inverse: %s", cudaGetErrorString(e));
@@ -481,57 +505,135 @@ static tr_status finalize(tr_handle *h) {
   return TR_OK;
 }
 
-extern "C" tr_status tr_prox_step(tr_handle *h, tr_step_info *info) {
-  if (!h) return TR_EINVAL;
-  if (h->poisoned) return fail(h, TR_EINVAL, "handle poisoned by an earlier failure; call tr_set_state");
+// Enqueue one iteration on h->stream.  pending: fuse the deferred inverse
+// pass of the last step into this step's forward pass; with_inverse: finish
+// the step now (needed for the residuals of tr_step_info), otherwise defer
+// it.  mu^t and t come from the device schedule, which the last kernel
+// advances, so the enqueued work is the same for every steady-state step.
+static tr_status enqueue_step(tr_handle *h, bool pending, bool with_inverse, cudaEvent_t *pev) {
   const double mu = h->mu;
   TubeScalars sc{mu, h->prm.lambda / mu, (int)h->prm.noise, (int)h->prm.psi, h->prm.psi_theta,
                  h->prm.psi_gamma};
-  auto guard = [&](tr_status st) {
-    if (st != TR_OK) h->poisoned = true;
-    return st;
-  };
-  if (info) TR_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-  cudaEvent_t *pev = nullptr;
-  if (h->prof_used < h->prof_cap) pev = &h->prof_ev[(size_t)4 * h->prof_used++];
+  sc.dmu = &h->sched->mu;
+  sc.lambda = h->prm.lambda;
   cudaError_t e = cudaMemsetAsync(h->res, 0, RES_COUNT * sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[0], h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) {
-    if (h->pending)
-      e = launch_tube_fused(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->mu_prev, h->M,
-                            h->mask, h->L, h->E, h->Y, h->G, h->Lam, h->Abar, sc, h->res_prev,
-                            h->res, h->flags, h->stream);
+    if (pending)
+      e = launch_tube_fused(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->mu_prev,
+                            &h->sched->mu_prev, h->M, h->mask, h->L, h->E, h->Y, h->G, h->Lam,
+                            h->Abar, sc, h->res_prev, h->res, h->flags, h->stream);
     else
       e = launch_tube_forward(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->mask, h->L,
                               h->E, h->Y, h->G, h->Lam, h->Abar, sc, h->res, h->flags, h->stream);
   }
-  h->pending = false;
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[1], h->stream);
-  if (e != cudaSuccess)
-    return guard(fail(h, TR_ECUDA, "tube forward: %s", cudaGetErrorString(e)));
+  if (e != cudaSuccess) return fail(h, TR_ECUDA, "tube forward: %s", cudaGetErrorString(e));
   h->launches += 1;
-  tr_status st = slice_pass(h, h->Abar, h->Gbar, 1.0 / mu, h->t);
-  if (st != TR_OK) return guard(st);
+  tr_status st = slice_pass(h, h->Abar, h->Gbar, 1.0 / mu, h->t, true);
+  if (st != TR_OK) return st;
   if (pev) e = cudaEventRecord(pev[2], h->stream);
-  if (info) {
+  if (with_inverse) {
     if (e == cudaSuccess)
       e = launch_tube_inverse(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->L, h->G,
-                              h->Lam, mu, h->res, h->flags, h->stream);
-    if (e != cudaSuccess)
-      return guard(fail(h, TR_ECUDA, "tube inverse: %s", cudaGetErrorString(e)));
+                              h->Lam, mu, &h->sched->mu, h->res, h->flags, h->stream);
+    if (e != cudaSuccess) return fail(h, TR_ECUDA, "tube inverse: %s", cudaGetErrorString(e));
     h->launches += 1;
-  } else {
-    h->pending = true;
-    h->mu_prev = mu;
   }
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[3], h->stream);
-  if (e != cudaSuccess) return guard(fail(h, TR_ECUDA, "event: %s", cudaGetErrorString(e)));
-  if (info) TR_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  if (e == cudaSuccess) e = launch_schedule(h->sched, h->prm.growth, h->prm.mu_max, h->stream);
+  if (e != cudaSuccess) return fail(h, TR_ECUDA, "schedule: %s", cudaGetErrorString(e));
+  h->launches += 1;
+  return TR_OK;
+}
+
+// Host mirror of the schedule kernel (same double arithmetic).
+static void advance_host(tr_handle *h, bool deferred) {
+  h->pending = deferred;
+  h->mu_prev = h->mu;
   h->t += 1;
-  double next = h->prm.growth * mu;
+  const double next = h->prm.growth * h->mu;
   h->mu = next < h->prm.mu_max ? next : h->prm.mu_max;
+}
+
+// Capture one steady-state step (pending, deferred inverse) on the private
+// stream; the graph is replayed for every later step of that kind.
+static tr_status capture_step(tr_handle *h) {
+  cudaStream_t user = h->stream;
+  h->stream = h->gstream;
+  const uint64_t before = h->launches;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeRelaxed);
+  tr_status st = TR_OK;
+  if (e == cudaSuccess) {
+    st = enqueue_step(h, true, false, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(h->gstream, &g);
+    if (st == TR_OK && e2 != cudaSuccess) st = fail(h, TR_ECUDA, "capture: %s", cudaGetErrorString(e2));
+  } else {
+    st = fail(h, TR_ECUDA, "capture: %s", cudaGetErrorString(e));
+  }
+  h->stream = user;
+  h->graph_kernels = h->launches - before;
+  h->launches = before;
+  if (st == TR_OK) {
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    if (e != cudaSuccess) st = fail(h, TR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  if (g) cudaGraphDestroy(g);
+  return st;
+}
+
+static tr_status replay_step(tr_handle *h) {
+  if (!h->gexec) {
+    tr_status st = capture_step(h);
+    if (st != TR_OK) return st;
+  }
+  TR_CUDA(h, cudaEventRecord(h->gev_in, h->stream));
+  TR_CUDA(h, cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
+  TR_CUDA(h, cudaGraphLaunch(h->gexec, h->gstream));
+  TR_CUDA(h, cudaEventRecord(h->gev_out, h->gstream));
+  TR_CUDA(h, cudaStreamWaitEvent(h->stream, h->gev_out, 0));
+  h->launches += h->graph_kernels;
+  return TR_OK;
+}
+
+extern "C" tr_status tr_prox_step(tr_handle *h, tr_step_info *info) {
+  if (!h) return TR_EINVAL;
+  if (h->poisoned) return fail(h, TR_EINVAL, "handle poisoned by an earlier failure; call tr_set_state");
+  const double mu = h->mu;
+  auto guard = [&](tr_status st) {
+    if (st != TR_OK) h->poisoned = true;
+    return st;
+  };
+  cudaEvent_t *pev = nullptr;
+  if (h->prof_used < h->prof_cap) pev = &h->prof_ev[(size_t)4 * h->prof_used++];
+  if (!info && !pev && h->graph_on && h->pending) {
+    tr_status st = replay_step(h);
+    if (st != TR_OK) return guard(st);
+    h->thr_last = shrink_threshold(h->prm, 1.0 / mu);
+    advance_host(h, true);
+    return TR_OK;
+  }
+  if (info) TR_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  tr_status st = enqueue_step(h, h->pending, info != nullptr, pev);
+  if (st != TR_OK) return guard(st);
+  if (info) TR_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  advance_host(h, info == nullptr);
   if (info) return guard(read_info(h, mu, info));
+  return TR_OK;
+}
+
+extern "C" tr_status tr_graph_mode(tr_handle *h, int on) {
+  if (!h) return TR_EINVAL;
+  if (on && h->prm.engine == TR_LR_LEARNED)
+    return fail(h, TR_EUNSUPPORTED, "the learned engine plans on the host: no graph replay");
+  if (on && !h->gstream) {
+    TR_CUDA(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    TR_CUDA(h, cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
+    TR_CUDA(h, cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
+  }
+  h->graph_on = on != 0;
   return TR_OK;
 }
 
@@ -593,7 +695,13 @@ extern "C" tr_status tr_set_state(tr_handle *h, const void *L, const void *E, co
   for (int i = 0; i < 5; ++i)
     if (src[i]) TR_CUDA(h, cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToDevice, h->stream));
   TR_CUDA(h, cudaStreamSynchronize(h->stream));
+  {
+    const DevSched d{mu, mu, t, 0};
+    TR_CUDA(h, cudaMemcpyAsync(h->sched, &d, sizeof d, cudaMemcpyHostToDevice, h->stream));
+    TR_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
   h->mu = mu;
+  h->mu_prev = mu;
   h->t = t;
   h->poisoned = false;
   h->pending = false;
@@ -806,6 +914,290 @@ extern "C" tr_status tr_mlp_train(float *params, const float *X, const float *y,
   TR_STATELESS(e);
   return TR_OK;
 }
+
+// ---- autotuner -------------------------------------------------------------
+// Tube tile (tubes per block) per shape class, chosen by timing the pure
+// transform kernel on the handle's transform-domain scratch (no state is
+// touched).  Every candidate computes the same values; only the partition
+// of tubes among blocks changes.  Choices are cached per process.
+struct TuneKey {
+  int dt, n, nt, dims[TR_MAX_TMODES];
+  int64_t P;
+  bool operator==(const TuneKey &o) const {
+    if (dt != o.dt || n != o.n || nt != o.nt || P != o.P) return false;
+    for (int k = 0; k < nt; ++k)
+      if (dims[k] != o.dims[k]) return false;
+    return true;
+  }
+};
+static std::vector<std::pair<TuneKey, int>> g_tune_cache;
+static std::mutex g_tune_mu;
+
+extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, float *ms_best) {
+  if (!h || reps < 0) return TR_EINVAL;
+  TuneKey key{(int)h->dtype, (int)h->n, h->td.nt, {0}, h->P};
+  for (int k = 0; k < h->td.nt; ++k) key.dims[k] = h->td.dim[k];
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : g_tune_cache)
+      if (kv.first == key && reps == 0) {
+        h->td.tp = kv.second;
+        if (tile) *tile = kv.second;
+        if (ms_best) *ms_best = 0.f;
+        return TR_OK;
+      }
+  }
+  int cand[4];
+  const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 4);
+  if (nc == 0) return fail(h, TR_EUNSUPPORTED, "no tube tile fits");
+  const int r = reps > 0 ? reps : 3;
+  float best = 0.f;
+  int best_tp = cand[0];
+  TR_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < nc; ++c) {
+    TransformDesc td = h->td;
+    td.tp = cand[c];
+    TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, td, h->mats, h->Abar, h->Gbar, false,
+                                h->stream));   // warm-up
+    TR_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+    for (int i = 0; i < r; ++i)
+      TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, td, h->mats, h->Abar, h->Gbar,
+                                  (i & 1) != 0, h->stream));
+    TR_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+    TR_CUDA(h, cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    TR_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->launches += 1 + (uint64_t)r;
+    if (c == 0 || ms < best) {
+      best = ms;
+      best_tp = cand[c];
+    }
+  }
+  h->td.tp = best_tp;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    bool found = false;
+    for (auto &kv : g_tune_cache)
+      if (kv.first == key) {
+        kv.second = best_tp;
+        found = true;
+      }
+    if (!found) g_tune_cache.push_back({key, best_tp});
+  }
+  if (h->gexec) {   // a captured step holds the old tile
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  if (tile) *tile = best_tp;
+  if (ms_best) *ms_best = best / r;
+  return TR_OK;
+}
+
+extern "C" tr_status tr_set_tube_tile(tr_handle *h, int tp) {
+  if (!h) return TR_EINVAL;
+  if (tp != 0) {
+    int cand[4];
+    const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 4);
+    bool ok = false;
+    for (int c = 0; c < nc; ++c) ok = ok || cand[c] == tp;
+    if (!ok) return fail(h, TR_EINVAL, "tube tile %d does not fit", tp);
+  }
+  h->td.tp = tp;
+  if (h->gexec) {
+    TR_CUDA(h, cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return TR_OK;
+}
+
+// ---- batches of independent problems ----------------------------------------
+struct tr_batch {
+  std::vector<tr_handle *> hs;
+  std::vector<cudaStream_t> pool;
+  std::vector<cudaEvent_t> join;
+  cudaStream_t stream = nullptr;      // caller's stream
+  cudaStream_t cap = nullptr;         // private stream the batch graph runs on
+  cudaEvent_t fork = nullptr, done = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t graph_kernels = 0;
+  uint64_t launches = 0;
+  bool graph_on = true;
+};
+
+static char g_batch_err[512] = {0};
+
+static tr_status batch_fail(tr_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_batch_err, sizeof g_batch_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+extern "C" tr_status tr_batch_free(tr_batch *b) {
+  if (!b) return TR_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (cudaStream_t s : b->pool) cudaStreamSynchronize(s);
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  for (tr_handle *h : b->hs) tr_free(h);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  delete b;
+  return TR_OK;
+}
+
+extern "C" tr_status tr_batch_create(tr_batch **out, int nprob, const tr_problem *probs,
+                                     const tr_params *prms, int nstreams, void *cuda_stream) {
+  if (!out || nprob < 1 || !probs || !prms) return batch_fail(TR_EINVAL, "tr_batch_create: bad arguments");
+  *out = nullptr;
+  tr_batch *b = new (std::nothrow) tr_batch();
+  if (!b) return batch_fail(TR_ENOMEM, "host allocation failed");
+  b->stream = (cudaStream_t)cuda_stream;
+  const int S = nstreams < 1 ? 8 : (nstreams > 32 ? 32 : nstreams);
+  auto bail = [&](tr_status st) {
+    tr_batch_free(b);
+    return st;
+  };
+#define BATCH_CUDA(call)                                                                 \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bail(batch_fail(e_ == cudaErrorMemoryAllocation ? TR_ENOMEM : TR_ECUDA, "%s: %s", \
+                             #call, cudaGetErrorString(e_)));                            \
+  } while (0)
+  for (int i = 0; i < S && i < nprob; ++i) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    BATCH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    b->pool.push_back(st);
+    BATCH_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b->join.push_back(ev);
+  }
+  BATCH_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  BATCH_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  BATCH_CUDA(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+  for (int i = 0; i < nprob; ++i) {
+    if (prms[i].engine == TR_LR_LEARNED)
+      return bail(batch_fail(TR_EUNSUPPORTED, "problem %d: the learned engine cannot join a batch graph", i));
+    tr_handle *h = nullptr;
+    tr_status st = tr_init(&h, &probs[i], &prms[i], b->pool[(size_t)i % b->pool.size()]);
+    if (st != TR_OK) return bail(batch_fail(st, "problem %d: %s", i, g_init_err));
+    b->hs.push_back(h);
+  }
+#undef BATCH_CUDA
+  *out = b;
+  return TR_OK;
+}
+
+extern "C" tr_status tr_batch_handle(tr_batch *b, int i, tr_handle **h) {
+  if (!b || !h || i < 0 || i >= (int)b->hs.size()) return batch_fail(TR_EINVAL, "tr_batch_handle: bad index");
+  *h = b->hs[(size_t)i];
+  return TR_OK;
+}
+
+extern "C" tr_status tr_batch_graph_mode(tr_batch *b, int on) {
+  if (!b) return TR_EINVAL;
+  b->graph_on = on != 0;
+  return TR_OK;
+}
+
+extern "C" tr_status tr_batch_launches(const tr_batch *b, uint64_t *count) {
+  if (!b || !count) return TR_EINVAL;
+  uint64_t c = b->launches;
+  for (const tr_handle *h : b->hs) c += h->launches;
+  *count = c;
+  return TR_OK;
+}
+
+// Fork every pool stream from `from`, join them back into `to`.
+static cudaError_t batch_fork(tr_batch *b, cudaStream_t from) {
+  cudaError_t e = cudaEventRecord(b->fork, from);
+  for (cudaStream_t s : b->pool)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->fork, 0);
+  return e;
+}
+static cudaError_t batch_join(tr_batch *b, cudaStream_t to) {
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < b->pool.size() && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->join[k], b->pool[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, b->join[k], 0);
+  }
+  return e;
+}
+
+static tr_status batch_capture(tr_batch *b) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return batch_fail(TR_ECUDA, "capture: %s", cudaGetErrorString(e));
+  tr_status st = TR_OK;
+  if ((e = batch_fork(b, b->cap)) != cudaSuccess) st = batch_fail(TR_ECUDA, "fork: %s", cudaGetErrorString(e));
+  uint64_t kernels = 0;
+  for (size_t i = 0; i < b->hs.size() && st == TR_OK; ++i) {
+    tr_handle *h = b->hs[i];
+    const uint64_t before = h->launches;
+    st = enqueue_step(h, true, false, nullptr);
+    if (st != TR_OK) batch_fail(st, "problem %zu: %s", i, h->err);
+    kernels += h->launches - before;
+    h->launches = before;
+  }
+  if (st == TR_OK && (e = batch_join(b, b->cap)) != cudaSuccess)
+    st = batch_fail(TR_ECUDA, "join: %s", cudaGetErrorString(e));
+  cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+  if (st == TR_OK && e2 != cudaSuccess) st = batch_fail(TR_ECUDA, "capture: %s", cudaGetErrorString(e2));
+  if (st == TR_OK && (e = cudaGraphInstantiate(&b->gexec, g, 0)) != cudaSuccess)
+    st = batch_fail(TR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  if (g) cudaGraphDestroy(g);
+  b->graph_kernels = kernels;
+  return st;
+}
+
+extern "C" tr_status tr_batch_step(tr_batch *b, tr_step_info *infos) {
+  if (!b) return TR_EINVAL;
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (b->hs[i]->poisoned) return batch_fail(TR_EINVAL, "problem %zu is poisoned", i);
+  cudaError_t e;
+  bool all_pending = true;
+  for (tr_handle *h : b->hs) all_pending = all_pending && h->pending;
+  if (!infos && b->graph_on && all_pending) {
+    // one graph launch runs the whole iteration of every problem
+    if (!b->gexec) {
+      tr_status st = batch_capture(b);
+      if (st != TR_OK) return st;
+    }
+    if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->cap, b->fork, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(b->gexec, b->cap)) != cudaSuccess ||
+        (e = cudaEventRecord(b->done, b->cap)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->stream, b->done, 0)) != cudaSuccess)
+      return batch_fail(TR_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    for (cudaStream_t s : b->pool)
+      if ((e = cudaStreamWaitEvent(s, b->done, 0)) != cudaSuccess)
+        return batch_fail(TR_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    b->launches += b->graph_kernels;
+    for (tr_handle *h : b->hs) {
+      h->thr_last = shrink_threshold(h->prm, 1.0 / h->mu);
+      h->have_pass = true;
+      advance_host(h, true);
+    }
+    return TR_OK;
+  }
+  if ((e = batch_fork(b, b->stream)) != cudaSuccess)
+    return batch_fail(TR_ECUDA, "fork: %s", cudaGetErrorString(e));
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    tr_status st = tr_prox_step(b->hs[i], infos ? &infos[i] : nullptr);
+    if (st != TR_OK) return batch_fail(st, "problem %zu: %s", i, b->hs[i]->err);
+  }
+  if ((e = batch_join(b, b->stream)) != cudaSuccess)
+    return batch_fail(TR_ECUDA, "join: %s", cudaGetErrorString(e));
+  return TR_OK;
+}
+
+extern "C" const char *tr_batch_last_error(void) { return g_batch_err; }
 
 extern "C" tr_status tr_free(tr_handle *h) {
   if (!h) return TR_OK;

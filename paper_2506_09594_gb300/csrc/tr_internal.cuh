@@ -29,6 +29,7 @@ struct TransformDesc {
   int off_fwd[TR_MAX_TMODES];
   int off_inv[TR_MAX_TMODES];
   int mats_len;   // elements in the matrix buffer (multiple of 4)
+  int tp = 0;     // tubes per block (0: the largest of 32, 16, 8, 4 that fits)
 };
 
 // Scalars of one ADMM iteration used by the elementwise passes.
@@ -38,13 +39,25 @@ struct TubeScalars {
   int noise;          // tr_noise
   int psi;            // tr_penalty of GNHTT
   double psi_theta, psi_gamma;
+  const double *dmu = nullptr;  // when set: mu^t = *dmu (device), lam_over_mu = lambda / mu^t
+  double lambda = 0.0;
 };
+
+// Device copy of the penalty schedule, so that a captured step stays valid
+// from one iteration to the next: the step reads mu and t here, and its last
+// kernel advances them (mu_prev <- mu, mu <- min(growth mu, mu_max), t += 1).
+struct DevSched {
+  double mu, mu_prev;
+  int t, pad;
+};
+cudaError_t launch_schedule(DevSched *d, double growth, double mu_max, cudaStream_t s);
 
 // Shrinkage of singular values in the slice pass.
 struct ShrinkScalars {
   double tau;
   int phi;
   double theta, gamma;
+  const double *dmu = nullptr;  // when set: tau = 1 / *dmu (device)
 };
 
 // Residual slots written with atomicMax on the bit pattern of a
@@ -59,16 +72,18 @@ cudaError_t launch_tube_forward(tr_dtype dt, int64_t P, int n, const TransformDe
                                 unsigned long long *res, int *flags, cudaStream_t s);
 cudaError_t launch_tube_inverse(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
                                 const void *mats, const void *Gbar, const void *L,
-                                void *G, void *Lam, double mu,
+                                void *G, void *Lam, double mu, const double *dmu,
                                 unsigned long long *res, int *flags, cudaStream_t s);
 cudaError_t launch_tube_fused(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
-                              const void *mats, const void *Gbar, double mu_prev, const void *M,
-                              const uint8_t *mask, void *L, void *E, void *Y, void *G, void *Lam,
-                              void *Abar, const TubeScalars &sc, unsigned long long *res_prev,
+                              const void *mats, const void *Gbar, double mu_prev,
+                              const double *dmu_prev, const void *M, const uint8_t *mask, void *L,
+                              void *E, void *Y, void *G, void *Lam, void *Abar,
+                              const TubeScalars &sc, unsigned long long *res_prev,
                               unsigned long long *res, int *flags, cudaStream_t s);
 cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
                              const void *mats, const void *src, void *dst, bool inverse,
                              cudaStream_t s);
+int tube_tile_candidates(tr_dtype dt, int n, const TransformDesc &td, int *tps, int cap);
 size_t tube_smem_bytes(tr_dtype dt, int n, const TransformDesc &td, int *tp_out);
 
 // ---- slice pass (slice_kernels.cu) ----
@@ -94,6 +109,7 @@ struct SliceWork {
   SliceSel sel; // which slices this pass works on (default: all)
   int ldsig;    // row stride of sig (0: l); entries l..ldsig-1 are zeroed
   int *width;   // optional: sketch width used, per slice id
+  const int *dt;  // optional: iteration index of the Philox counters (device)
 };
 // Workspace of the fixed-accuracy engine (Alg. 3 per slice).
 struct AdaptWork {

@@ -215,6 +215,17 @@ __device__ void tile_store(T *__restrict__ dst, const T *tile, int64_t P, int n,
   }
 }
 
+// Scalars of the forward update with mu^t taken from the device schedule
+// when the launch carries one.
+__device__ __forceinline__ TubeScalars resolve(const TubeScalars &sc) {
+  TubeScalars r = sc;
+  if (sc.dmu) {
+    r.mu = *sc.dmu;
+    r.lam_over_mu = sc.lambda / r.mu;
+  }
+  return r;
+}
+
 // The forward elementwise update on a pack; `gv` holds G^t (from global
 // memory or from the fused inverse), `la` Lambda^t.
 template <typename T, int VEC>
@@ -263,6 +274,7 @@ tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
   load_mats(mats, mats_g, td.mats_len);
   const int64_t p0 = (int64_t)blockIdx.x * TP;
   const int per_row = TP / VEC, total = n * per_row;
+  const TubeScalars scr = resolve(sc);
   T rL = 0, rE = 0, rC = 0;
   int bad = 0;
   for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
@@ -294,7 +306,7 @@ tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
       if (in[u]) {
         const int64_t idx = (int64_t)q.j * P + p0 + q.p;
         Pk<T, VEC> l1, e1, y1;
-        forward_pack<T, VEC>(m[u], om[u], l0[u], ee[u], y0[u], g0[u], la[u], sc, l1, e1, y1, a,
+        forward_pack<T, VEC>(m[u], om[u], l0[u], ee[u], y0[u], g0[u], la[u], scr, l1, e1, y1, a,
                              rL, rE, rC, bad);
         st<T, VEC>(L + idx, l1);
         st<T, VEC>(E + idx, e1);
@@ -319,7 +331,8 @@ template <typename T, int NK, int VEC>
 __global__ void __launch_bounds__(kTubeThreads, tube_min_blocks<T, NK>())
 tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
                     const T *__restrict__ Gbar, const T *__restrict__ L, T *__restrict__ G,
-                    T *__restrict__ Lam, double mu_d, unsigned long long *res, int *flags) {
+                    T *__restrict__ Lam, double mu_d, const double *dmu,
+                    unsigned long long *res, int *flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *mats = reinterpret_cast<T *>(smem_raw);
   T *tile = mats + td.mats_len;
@@ -328,7 +341,7 @@ tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
   tile_load<T, VEC>(tile, Gbar, P, n, TP, p0);
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, true);
-  const T mu = T(mu_d);
+  const T mu = T(dmu ? *dmu : mu_d);
   const int per_row = TP / VEC, total = n * per_row;
   T rLG = 0, rG = 0;
   int bad = 0;
@@ -377,7 +390,8 @@ tube_inverse_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
 template <typename T, int NK, int VEC>
 __global__ void __launch_bounds__(kTubeThreads, tube_min_blocks<T, NK>())
 tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restrict__ mats_g,
-                  const T *__restrict__ Gbar, double mu_prev, const T *__restrict__ M,
+                  const T *__restrict__ Gbar, double mu_prev, const double *dmu_prev,
+                  const T *__restrict__ M,
                   const uint8_t *__restrict__ mask, T *__restrict__ L, T *__restrict__ E,
                   T *__restrict__ Y, T *__restrict__ G, T *__restrict__ Lam,
                   T *__restrict__ Abar, TubeScalars sc, unsigned long long *res_prev,
@@ -390,7 +404,8 @@ tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restric
   tile_load<T, VEC>(tile, Gbar, P, n, TP, p0);
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, true);
-  const T mup = T(mu_prev);
+  const T mup = T(dmu_prev ? *dmu_prev : mu_prev);
+  const TubeScalars scr = resolve(sc);
   const int per_row = TP / VEC, total = n * per_row;
   T rLG = 0, rG = 0, rL = 0, rE = 0, rC = 0;
   int bad = 0;
@@ -431,7 +446,7 @@ tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restric
           rG = fmax(rG, fabs(g1.v[i] - g0[u].v[i]));
         }
         Pk<T, VEC> l1, e1, y1;
-        forward_pack<T, VEC>(m[u], om[u], l0[u], ee[u], y0[u], g1, la1, sc, l1, e1, y1, a, rL,
+        forward_pack<T, VEC>(m[u], om[u], l0[u], ee[u], y0[u], g1, la1, scr, l1, e1, y1, a, rL,
                              rE, rC, bad);
         st<T, VEC>(G + idx, g1);
         st<T, VEC>(Lam + idx, la1);
@@ -535,6 +550,7 @@ bool tube_geometry(int64_t P, int n, const TransformDesc &td, TubeLaunch &g) {
   g.n = n;
   g.tp = pick_tp<T>(n, td);
   if (!g.tp) return false;
+  if (td.tp > 0 && td.tp <= 32 && tube_smem_for<T>(n, td, td.tp) <= kSmemBudget) g.tp = td.tp;
   g.smem = tube_smem_for<T>(n, td, g.tp);
   g.grid = (unsigned)((P + g.tp - 1) / g.tp);
   return true;
@@ -560,12 +576,13 @@ template <typename T, int NK, int VEC>
 struct InvLauncher {
   static cudaError_t run(const TubeLaunch &g, const TransformDesc &td, const void *mats,
                          const void *Gbar, const void *L, void *G, void *Lam, double mu,
-                         unsigned long long *res, int *flags, cudaStream_t s) {
+                         const double *dmu, unsigned long long *res, int *flags,
+                         cudaStream_t s) {
     auto k = tube_inverse_kernel<T, NK, VEC>;
     cudaError_t e = prep(k, g.smem);
     if (e != cudaSuccess) return e;
     k<<<g.grid, kTubeThreads, g.smem, s>>>(g.P, g.n, g.tp, td, (const T *)mats, (const T *)Gbar,
-                                          (const T *)L, (T *)G, (T *)Lam, mu, res, flags);
+                                          (const T *)L, (T *)G, (T *)Lam, mu, dmu, res, flags);
     return cudaGetLastError();
   }
 };
@@ -573,15 +590,17 @@ struct InvLauncher {
 template <typename T, int NK, int VEC>
 struct FusedLauncher {
   static cudaError_t run(const TubeLaunch &g, const TransformDesc &td, const void *mats,
-                         const void *Gbar, double mu_prev, const void *M, const uint8_t *mask,
-                         void *L, void *E, void *Y, void *G, void *Lam, void *Abar,
-                         const TubeScalars &sc, unsigned long long *res_prev,
-                         unsigned long long *res, int *flags, cudaStream_t s) {
+                         const void *Gbar, double mu_prev, const double *dmu_prev,
+                         const void *M, const uint8_t *mask, void *L, void *E, void *Y, void *G,
+                         void *Lam, void *Abar, const TubeScalars &sc,
+                         unsigned long long *res_prev, unsigned long long *res, int *flags,
+                         cudaStream_t s) {
     auto k = tube_fused_kernel<T, NK, VEC>;
     cudaError_t e = prep(k, g.smem);
     if (e != cudaSuccess) return e;
     k<<<g.grid, kTubeThreads, g.smem, s>>>(g.P, g.n, g.tp, td, (const T *)mats, (const T *)Gbar,
-                                          mu_prev, (const T *)M, mask, (T *)L, (T *)E, (T *)Y,
+                                          mu_prev, dmu_prev, (const T *)M, mask, (T *)L, (T *)E,
+                                          (T *)Y,
                                           (T *)G, (T *)Lam, (T *)Abar, sc, res_prev, res, flags);
     return cudaGetLastError();
   }
@@ -614,25 +633,26 @@ cudaError_t fwd_t(int64_t P, int n, const TransformDesc &td, const void *mats, c
 
 template <typename T>
 cudaError_t inv_t(int64_t P, int n, const TransformDesc &td, const void *mats, const void *Gbar,
-                  const void *L, void *G, void *Lam, double mu, unsigned long long *res,
-                  int *flags, cudaStream_t s) {
+                  const void *L, void *G, void *Lam, double mu, const double *dmu,
+                  unsigned long long *res, int *flags, cudaStream_t s) {
   TubeLaunch g;
   if (!tube_geometry<T>(P, n, td, g)) return cudaErrorInvalidValue;
   const int vec = pick_vec<T>(P, g.tp, {Gbar, L, G, Lam}, nullptr);
-  return dispatch<T, InvLauncher>(td.nkpad, vec, g, td, mats, Gbar, L, G, Lam, mu, res, flags, s);
+  return dispatch<T, InvLauncher>(td.nkpad, vec, g, td, mats, Gbar, L, G, Lam, mu, dmu, res,
+                                  flags, s);
 }
 
 template <typename T>
 cudaError_t fused_t(int64_t P, int n, const TransformDesc &td, const void *mats, const void *Gbar,
-                    double mu_prev, const void *M, const uint8_t *mask, void *L, void *E, void *Y,
-                    void *G, void *Lam, void *Abar, const TubeScalars &sc,
-                    unsigned long long *res_prev, unsigned long long *res, int *flags,
-                    cudaStream_t s) {
+                    double mu_prev, const double *dmu_prev, const void *M, const uint8_t *mask,
+                    void *L, void *E, void *Y, void *G, void *Lam, void *Abar,
+                    const TubeScalars &sc, unsigned long long *res_prev, unsigned long long *res,
+                    int *flags, cudaStream_t s) {
   TubeLaunch g;
   if (!tube_geometry<T>(P, n, td, g)) return cudaErrorInvalidValue;
   const int vec = pick_vec<T>(P, g.tp, {Gbar, M, L, E, Y, G, Lam, Abar}, mask);
-  return dispatch<T, FusedLauncher>(td.nkpad, vec, g, td, mats, Gbar, mu_prev, M, mask, L, E, Y,
-                                    G, Lam, Abar, sc, res_prev, res, flags, s);
+  return dispatch<T, FusedLauncher>(td.nkpad, vec, g, td, mats, Gbar, mu_prev, dmu_prev, M, mask,
+                                    L, E, Y, G, Lam, Abar, sc, res_prev, res, flags, s);
 }
 
 template <typename T>
@@ -658,22 +678,35 @@ cudaError_t launch_tube_forward(tr_dtype dt, int64_t P, int n, const TransformDe
 
 cudaError_t launch_tube_inverse(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
                                 const void *mats, const void *Gbar, const void *L, void *G,
-                                void *Lam, double mu, unsigned long long *res, int *flags,
-                                cudaStream_t s) {
-  if (dt == TR_F64) return inv_t<double>(P, n, td, mats, Gbar, L, G, Lam, mu, res, flags, s);
-  return inv_t<float>(P, n, td, mats, Gbar, L, G, Lam, mu, res, flags, s);
+                                void *Lam, double mu, const double *dmu, unsigned long long *res,
+                                int *flags, cudaStream_t s) {
+  if (dt == TR_F64) return inv_t<double>(P, n, td, mats, Gbar, L, G, Lam, mu, dmu, res, flags, s);
+  return inv_t<float>(P, n, td, mats, Gbar, L, G, Lam, mu, dmu, res, flags, s);
 }
 
 cudaError_t launch_tube_fused(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
-                              const void *mats, const void *Gbar, double mu_prev, const void *M,
-                              const uint8_t *mask, void *L, void *E, void *Y, void *G, void *Lam,
-                              void *Abar, const TubeScalars &sc, unsigned long long *res_prev,
+                              const void *mats, const void *Gbar, double mu_prev,
+                              const double *dmu_prev, const void *M, const uint8_t *mask, void *L,
+                              void *E, void *Y, void *G, void *Lam, void *Abar,
+                              const TubeScalars &sc, unsigned long long *res_prev,
                               unsigned long long *res, int *flags, cudaStream_t s) {
   if (dt == TR_F64)
-    return fused_t<double>(P, n, td, mats, Gbar, mu_prev, M, mask, L, E, Y, G, Lam, Abar, sc,
-                           res_prev, res, flags, s);
-  return fused_t<float>(P, n, td, mats, Gbar, mu_prev, M, mask, L, E, Y, G, Lam, Abar, sc,
-                        res_prev, res, flags, s);
+    return fused_t<double>(P, n, td, mats, Gbar, mu_prev, dmu_prev, M, mask, L, E, Y, G, Lam,
+                           Abar, sc, res_prev, res, flags, s);
+  return fused_t<float>(P, n, td, mats, Gbar, mu_prev, dmu_prev, M, mask, L, E, Y, G, Lam, Abar,
+                        sc, res_prev, res, flags, s);
+}
+
+__global__ void schedule_kernel(DevSched *d, double growth, double mu_max) {
+  const double next = growth * d->mu;
+  d->mu_prev = d->mu;
+  d->mu = next < mu_max ? next : mu_max;
+  d->t += 1;
+}
+
+cudaError_t launch_schedule(DevSched *d, double growth, double mu_max, cudaStream_t s) {
+  schedule_kernel<<<1, 1, 0, s>>>(d, growth, mu_max);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
@@ -681,6 +714,17 @@ cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc 
                              cudaStream_t s) {
   if (dt == TR_F64) return xf_t<double>(P, n, td, mats, src, dst, inverse, s);
   return xf_t<float>(P, n, td, mats, src, dst, inverse, s);
+}
+
+// Tile widths (tubes per block) that fit, for the autotuner.  The tile only
+// partitions the tubes among blocks: every tube's arithmetic is the same.
+int tube_tile_candidates(tr_dtype dt, int n, const TransformDesc &td, int *tps, int cap) {
+  int k = 0;
+  for (int tp = 32; tp >= 4 && k < cap; tp >>= 1) {
+    const size_t b = dt == TR_F64 ? tube_smem_for<double>(n, td, tp) : tube_smem_for<float>(n, td, tp);
+    if (b <= kSmemBudget) tps[k++] = tp;
+  }
+  return k;
 }
 
 size_t tube_smem_bytes(tr_dtype dt, int n, const TransformDesc &td, int *tp_out) {

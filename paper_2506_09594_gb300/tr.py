@@ -106,6 +106,18 @@ _SIGS = {
                                    ctypes.c_int, _P]),
     "tr_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, _P, _P]),
+    "tr_graph_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tr_set_tube_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tr_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_float)]),
+    "tr_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_int,
+                                       _P]),
+    "tr_batch_step": (ctypes.c_int, [_P, _P]),
+    "tr_batch_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "tr_batch_graph_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tr_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "tr_batch_free": (ctypes.c_int, [_P]),
+    "tr_batch_last_error": (ctypes.c_char_p, []),
     "tr_free": (ctypes.c_int, [_P]),
     "tr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -385,6 +397,18 @@ class Handle:
         w = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
         _check(load().tr_set_model(self.h, ctypes.c_void_p(w.ctypes.data), int(w.size)), self.h)
 
+    def graph_mode(self, on=True):
+        _check(load().tr_graph_mode(self.h, int(bool(on))), self.h)
+
+    def set_tube_tile(self, tp):
+        _check(load().tr_set_tube_tile(self.h, int(tp)), self.h)
+
+    def autotune(self, reps=5):
+        tile = ctypes.c_int()
+        ms = ctypes.c_float()
+        _check(load().tr_autotune(self.h, int(reps), ctypes.byref(tile), ctypes.byref(ms)), self.h)
+        return tile.value, ms.value
+
     def profile_enable(self, max_steps):
         _check(load().tr_profile_enable(self.h, int(max_steps)), self.h)
 
@@ -404,6 +428,99 @@ class Handle:
         if getattr(self, "h", None):
             load().tr_free(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_batch(st):
+    if st != TR_OK:
+        msg = load().tr_batch_last_error()
+        raise TrError(st, msg.decode() if msg else "")
+
+
+class BorrowedHandle(Handle):
+    """The handle of one problem of a Batch (owned by the batch)."""
+
+    def __init__(self, h, dims, dtype, params, stream):
+        self.h = h
+        self.dims = tuple(dims)
+        self.dtype = dtype
+        self.params = params
+        self.stream = stream
+        n = 1
+        for d in self.dims[2:]:
+            n *= d
+        self.shape = (n, self.dims[0], self.dims[1])
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Independent problems of any shapes stepped together (tr_batch_*)."""
+
+    def __init__(self, problems, params, nstreams=8, stream=None):
+        """problems: list of (observed, mask, dims) CUDA tensors; params: a
+        tr_params per problem (or one for all)."""
+        import torch
+        lib = load()
+        if isinstance(params, tr_params):
+            params = [params] * len(problems)
+        n = len(problems)
+        probs = (tr_problem * n)()
+        prms = (tr_params * n)()
+        self._keep = []
+        self.meta = []
+        for i, (obs, mask, dims) in enumerate(problems):
+            probs[i].order = len(dims)
+            for k, d in enumerate(dims):
+                probs[i].dims[k] = int(d)
+            probs[i].dtype = {torch.float32: TR_F32, torch.float64: TR_F64}[obs.dtype]
+            probs[i].observed = obs.data_ptr()
+            probs[i].mask = mask.data_ptr()
+            prms[i] = params[i]
+            self._keep.append((obs, mask))
+            self.meta.append((tuple(dims), obs.dtype, params[i]))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        b = ctypes.c_void_p()
+        _check_batch(lib.tr_batch_create(ctypes.byref(b), n, ctypes.cast(probs, _P),
+                                         ctypes.cast(prms, _P), int(nstreams),
+                                         ctypes.c_void_p(stream)))
+        self.b = b
+        self.n = n
+
+    def step(self, info=False):
+        if info:
+            infos = (tr_step_info * self.n)()
+            _check_batch(load().tr_batch_step(self.b, ctypes.cast(infos, _P)))
+            return [x.as_dict() for x in infos]
+        _check_batch(load().tr_batch_step(self.b, None))
+        return None
+
+    def handle(self, i):
+        h = ctypes.c_void_p()
+        _check_batch(load().tr_batch_handle(self.b, int(i), ctypes.byref(h)))
+        dims, dtype, prm = self.meta[i]
+        return BorrowedHandle(h, dims, dtype, prm, self.stream)
+
+    def graph_mode(self, on=True):
+        _check_batch(load().tr_batch_graph_mode(self.b, int(bool(on))))
+
+    def launches(self):
+        c = ctypes.c_uint64()
+        _check_batch(load().tr_batch_launches(self.b, ctypes.byref(c)))
+        return int(c.value)
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().tr_batch_free(self.b)
+            self.b = None
 
     def __del__(self):
         try:

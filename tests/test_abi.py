@@ -104,3 +104,14 @@ def test_model_file_roundtrip(tmp_path):
 def test_mlp_param_count_export():
     from oracle import learned
     assert tr.load().tr_mlp_param_count() == tr.TR_MLP_PARAMS == learned.param_count()
+
+
+def test_batch_and_graph_calls_validate_without_gpu(lib):
+    b = ctypes.c_void_p()
+    assert lib.tr_batch_create(ctypes.byref(b), 0, None, None, 0, None) == tr.TR_EINVAL
+    assert b"bad arguments" in lib.tr_batch_last_error()
+    assert lib.tr_batch_step(None, None) == tr.TR_EINVAL
+    assert lib.tr_batch_free(None) == tr.TR_OK
+    assert lib.tr_graph_mode(None, 1) == tr.TR_EINVAL
+    assert lib.tr_set_tube_tile(None, 8) == tr.TR_EINVAL
+    assert lib.tr_autotune(None, 1, None, None) == tr.TR_EINVAL

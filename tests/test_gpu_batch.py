@@ -1,0 +1,185 @@
+"""Graph replay, tube-tile autotuning and batches of uneven problems.
+
+A replayed step runs the same kernels with the same arguments as an eager
+step (the schedule is read on the device), and every tube tile computes the
+same values, so these are compared bit for bit with the eager single-handle
+path, which the parity tests pin to the oracle.  One multi-step comparison
+with the oracle itself checks the device schedule (mu, t) end to end.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import admm
+from paper_2506_09594_gb300 import synth, tr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TDT = {"f64": torch.float64, "f32": torch.float32}
+
+
+def dev(x, dt):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=TDT[dt])
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def relF(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def as_dtype(x, dt):
+    return x.astype(np.float32).astype(np.float64) if dt == "f32" else x
+
+
+def problem(dims, seed, rank=4, sr=0.4):
+    rng = np.random.default_rng(seed)
+    X = synth.lowrank_tensor(dims, rank, rng)[0]
+    mask = synth.exact_count_mask(X.size, sr, rng).reshape(X.shape)
+    S = synth.exact_count_mask(X.size, 0.05, rng).reshape(X.shape) * rng.uniform(-1, 1, X.shape)
+    M = np.where(mask == 1, X + S, 0.0)
+    return X, M, mask
+
+
+def handle(dims, dt, M, mask, **kw):
+    return tr.Handle(dev(M, dt), torch.from_numpy(mask).cuda(), dims, **kw)
+
+
+def states_equal(a, b):
+    for k in ("L", "E", "Y", "Lam", "G"):
+        if not torch.equal(a[k], b[k]):
+            return False, k
+    return a["mu"] == b["mu"] and a["t"] == b["t"], "mu/t"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    tr.load()
+
+
+ENGINES = [("f32", dict(engine=tr.TR_LR_RSVD, rank=8, oversample=4)),
+           ("f32", dict(engine=tr.TR_LR_RSVD, rank=8, oversample=4, prec=tr.TR_PREC_BF16)),
+           ("f64", dict(engine=tr.TR_LR_RSVD, rank=8, oversample=4)),
+           ("f32", dict(engine=tr.TR_LR_ADAPTIVE, rank=8, oversample=4, adapt_block=4))]
+
+
+@pytest.mark.parametrize("dt,kw", ENGINES)
+def test_graph_steps_identical_to_eager(dt, kw):
+    dims = (48, 40, 6, 3)
+    _, M, mask = problem(dims, 1)
+    outs = []
+    for graph in (False, True):
+        h = handle(dims, dt, M, mask, seed=3, **kw)
+        if graph:
+            h.graph_mode(True)
+        for _ in range(6):
+            h.step()
+        outs.append(h.get_state())
+        launches = h.kernel_launches()
+        h.close()
+    ok, what = states_equal(outs[0], outs[1])
+    assert ok, what
+    assert launches > 6
+
+
+def test_graph_steps_match_oracle():
+    dims, dt = (40, 44, 5, 4), "f32"
+    _, M, mask = problem(dims, 3 * sum(dims))
+    state = synth.random_state(M.shape, seed=9, scale=0.5)
+    lam = admm.default_lambda(dims[0], dims[1], dims[2:])
+    p = admm.Params(lam=lam, phi_gamma=60.0, psi_gamma=60.0, engine="rsvd", l=10, q=1, seed=4)
+    st = admm.State(*(as_dtype(x, dt) for x in state), mu=0.1, t=0)
+    for _ in range(5):
+        st, _ = admm.step(st, as_dtype(M, dt), mask, tuple(dims[2:]), p)
+    h = handle(dims, dt, M, mask, phi_gamma=60.0, psi_gamma=60.0, rank=10, oversample=0,
+               power_iters=1, seed=4, **{"lambda": lam})
+    h.set_state(*(dev(x, dt) for x in state), mu=0.1, t=0)
+    h.graph_mode(True)
+    for _ in range(5):       # one eager step, then four replays
+        h.step()
+    got = h.get_state()
+    h.close()
+    for name, want in [("L", st.L), ("E", st.E), ("Y", st.Y), ("Lam", st.Lam), ("G", st.G)]:
+        assert relF(host(got[name]), want) < 4e-4, name
+    assert got["t"] == 5 and abs(got["mu"] - st.mu) < 1e-15
+
+
+def test_graph_mode_refuses_learned_engine():
+    dims = (32, 32, 4)
+    _, M, mask = problem(dims, 2)
+    h = handle(dims, "f32", M, mask, engine=tr.TR_LR_LEARNED, rank=8, oversample=8)
+    with pytest.raises(tr.TrError):
+        h.graph_mode(True)
+    h.close()
+
+
+def test_tube_tiles_compute_identical_steps():
+    dims = (64, 40, 20, 20)
+    _, M, mask = problem(dims, 4)
+    outs = []
+    for tp in (0, 8, 16):
+        h = handle(dims, "f32", M, mask, rank=8, oversample=4)
+        h.set_tube_tile(tp)
+        for _ in range(3):
+            h.step()
+        h.step(info=True)
+        outs.append(h.get_state())
+        h.close()
+    for o in outs[1:]:
+        ok, what = states_equal(outs[0], o)
+        assert ok, what
+    h = handle(dims, "f32", M, mask, rank=8, oversample=4)
+    tile, ms = h.autotune(3)
+    assert tile in (4, 8, 16, 32) and ms > 0
+    tile2, ms2 = h.autotune(0)      # cached choice
+    assert tile2 == tile
+    with pytest.raises(tr.TrError):
+        h.set_tube_tile(12)
+    h.close()
+
+
+BATCH = [((64, 48, 8), "f32", 5, 0.3), ((40, 72, 4, 3), "f32", 3, 0.5),
+         ((96, 96, 6), "f32", 6, 0.2), ((33, 29, 5, 2), "f32", 4, 0.4),
+         ((50, 50, 12), "f64", 5, 0.35)]
+
+
+@pytest.mark.parametrize("nstreams", [1, 3])
+def test_batch_matches_individual_handles(nstreams):
+    probs, prms, singles = [], [], []
+    for i, (dims, dt, r, sr) in enumerate(BATCH):
+        _, M, mask = problem(dims, 100 + i, rank=r, sr=sr)
+        p = tr.default_params(rank=r + 4, oversample=4, seed=7 + i, mu0=0.05,
+                              prec=tr.TR_PREC_BF16X3 if i == 2 else tr.TR_PREC_FP32)
+        obs, mk = dev(M, dt), torch.from_numpy(mask).cuda()
+        probs.append((obs, mk, dims))
+        prms.append(p)
+        singles.append((dims, dt, M, mask, p))
+    b = tr.Batch(probs, prms, nstreams=nstreams)
+    for _ in range(5):
+        b.step()                      # eager first step, then graph launches
+    infos = b.step(info=True)
+    assert len(infos) == len(BATCH) and all(x["iter"] == 6 for x in infos)
+    assert b.launches() > 0
+    for i, (dims, dt, M, mask, p) in enumerate(singles):
+        h = tr.Handle(dev(M, dt), torch.from_numpy(mask).cuda(), dims, params=p)
+        for _ in range(5):
+            h.step()
+        ref_info = h.step(info=True)
+        ref = h.get_state()
+        got = b.handle(i).get_state()
+        ok, what = states_equal(ref, got)
+        assert ok, (i, what)
+        assert np.allclose(ref_info["res_inf"], infos[i]["res_inf"], rtol=0, atol=0)
+        h.close()
+    b.close()
+
+
+def test_batch_rejects_learned_and_reports():
+    dims = (32, 32, 4)
+    _, M, mask = problem(dims, 5)
+    p = tr.default_params(engine=tr.TR_LR_LEARNED, rank=8, oversample=8)
+    with pytest.raises(tr.TrError):
+        tr.Batch([(dev(M, "f32"), torch.from_numpy(mask).cuda(), dims)], p)
