@@ -43,6 +43,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "bf16x3"],
                     help="precision of the chosen form's slice products")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-width A/B on the power-law workload")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batch of 64 uneven problems")
+    ap.add_argument("--learned-iters", type=int, default=100)
+    ap.add_argument("--batch-steps", type=int, default=8)
     return ap.parse_args()
 
 
@@ -202,13 +208,24 @@ def make_handle(tr, torch, w, Md, maskd, stream, rank, prec):
                      noise=tr.TR_NOISE_NONE if w.noise_model == "none" else tr.TR_NOISE_L1)
 
 
-def time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, prec, K, W, clocks=None):
-    """Warm up W steps, then time K steps of one form; returns its measurements."""
+def time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, prec, K, W, clocks=None,
+              chosen=False):
+    """Warm up W steps, then time K steps of one form; returns its measurements.
+
+    The plain form runs eager launches with per-phase events in the timed
+    region.  The chosen form replays one CUDA graph per step with the
+    autotuned tube tile; its phases come from a profiled eager window of the
+    same kernels right after the timed region."""
     with torch.cuda.stream(stream):
         h = make_handle(tr, torch, w, Md, maskd, stream, rank, prec)
+    tune = None
+    if chosen:
+        tune = h.autotune(5)
+        h.graph_mode(True)
     for _ in range(W):
         h.step()
-    h.profile_enable(K)
+    if not chosen:
+        h.profile_enable(K)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -231,11 +248,16 @@ def time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, prec, K
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    phases = h.profile_read()
     L = h.get_state()["L"]
     rec = float(torch.linalg.norm((L - X_dev).double()) / torch.linalg.norm(X_dev.double()))
+    if chosen:
+        KP = max(3, min(K, 10))
+        h.profile_enable(KP)
+        for _ in range(KP):
+            h.step()
+    phases = h.profile_read()
     return h, {"ms": ms, "phases": phases, "launches": launches, "clocks": clk,
-               "recovery_rel_err": rec, "L": L}
+               "recovery_rel_err": rec, "L": L, "tube_tile": tune}
 
 
 def run_ours(args):
@@ -269,7 +291,7 @@ def run_ours(args):
     # chosen form (tensor-core products), timed with the clock sampler running
     clocks = ClockSampler(local)
     h, ch = time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, chosen, K, W,
-                      clocks)
+                      clocks, chosen=True)
     agree = float(torch.linalg.norm((ch["L"] - plain["L"]).double())
                   / torch.linalg.norm(plain["L"].double()).clamp_min(1e-300))
     ms, phases = ch["ms"], ch["phases"]
@@ -278,6 +300,7 @@ def run_ours(args):
     # problem's inputs (observed values, mask) from pinned host memory and
     # reads the step's result (residuals, ranks) back.
     KE = max(3, min(K, 20))
+    h.graph_mode(False)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(KE):
@@ -333,7 +356,8 @@ def run_ours(args):
                 "power_iters": w.q,
                 "sampling_ratio": w.sr,
                 "form": {0: "fp32 simt", 2: "bf16 tcgen05 (split-bf16 refinement)",
-                         3: "split-bf16 tcgen05"}[chosen],
+                         3: "split-bf16 tcgen05"}[chosen] + ", graph replay, autotuned tube tile",
+                "tube_tile": ch["tube_tile"][0] if ch["tube_tile"] else None,
                 "parallelism": "replicas" if world > 1 else "single",
                 "l2": "state 7 x %.0f MB >> 129 MB L2: no flush needed" % (N * esz / 1e6),
             },
@@ -362,12 +386,150 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(8 * 5 + 4 + 4 * n)},
             "clocks": ch["clocks"],
         }
+    h.close()
+    del Md, maskd, X_dev
+    torch.cuda.empty_cache()
+    if rank == 0:
+        if not args.no_learned and world == 1:
+            line["learned"] = learned_ab(tr, torch, args.learned_iters, chosen)
+            torch.cuda.empty_cache()
+        if not args.no_batch and world == 1:
+            line["batch"] = batch_bench(tr, torch, args.batch_steps, chosen)
+            torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def learned_ab(tr, torch, iters, prec):
+    """Plain fixed width vs learned widths (+ the chosen precision) on the
+    512x512x32x16 power-law workload: time per iteration and recovery error
+    after the same number of iterations."""
+    from paper_2506_09594_gb300 import synth
+    w = synth.WORKLOADS["tubal512x512_powerlaw"]
+    X, M, mask, ranks = synth.make_problem(w)
+    Md = torch.from_numpy(M).float().cuda()
+    maskd = torch.from_numpy(mask).cuda()
+    Xd = torch.from_numpy(X).float().cuda()
+    del X, M, mask
+    out = {"workload": w.name, "dims": list(w.dims), "sampling_ratio": w.sr,
+           "slice_ranks": "power law on [2, 64], mean %.1f" % float(ranks.mean()),
+           "iters": iters, "l_max": 74, "schedule": "mu0 1e-3, growth 1.1"}
+    stream = torch.cuda.Stream()
+    for name, eng, pr in (("plain", tr.TR_LR_RSVD, 0), ("learned", tr.TR_LR_LEARNED, prec)):
+        kw = dict(engine=eng, rank=64, oversample=10, noise=tr.TR_NOISE_NONE, seed=w.seed,
+                  tol=0.0, max_iter=iters, prec=pr, stream=stream.cuda_stream)
+        if eng == tr.TR_LR_LEARNED:
+            kw["model_path"] = tr.DEFAULT_MODEL.encode()
+        h = tr.Handle(Md, maskd, w.dims, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fb = 0
+        for _ in range(iters):
+            fb += h.step(info=True)["fallback_slices"]
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        L = h.get_state()["L"]
+        err = float(torch.linalg.norm((L - Xd).double()) / torch.linalg.norm(Xd.double()))
+        widths = h.slice_widths()
+        out[name] = {"iters_per_s": iters / el, "recovery_rel_err": err,
+                     "mean_width_last": float(widths.mean()), "fallback_slices_total": fb,
+                     "kernel_launches": h.kernel_launches(),
+                     "form": ("fp32 simt, l = 74" if name == "plain" else
+                              "learned widths, %s" % {0: "fp32 simt", 2: "bf16 tcgen05",
+                                                      3: "split-bf16 tcgen05"}[pr])}
+        h.close()
+    out["speedup"] = out["learned"]["iters_per_s"] / out["plain"]["iters_per_s"]
+    out["err_gap"] = out["learned"]["recovery_rel_err"] - out["plain"]["recovery_rel_err"]
+    out["equal_error_within_1e-4"] = out["err_gap"] <= 1e-4
+    out["timing"] = "wall clock over all iterations, each step reporting (synchronising)"
+    return out
+
+
+def batch_problems(torch, tr, count, seed):
+    """64 problems of uneven shapes, generated on the device: transform-domain
+    slices A_j B_j^T / sqrt(r) (N(0,1) factors), mapped back with the
+    problem's own inverse transform, Bernoulli(SR) mask."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(count):
+        n1, n2 = int(rng.integers(128, 769)), int(rng.integers(128, 769))
+        n3 = int(rng.integers(8, 65))
+        dims = (n1, n2, n3) if rng.random() < 0.5 else (n1, n2, n3, int(rng.integers(4, 17)))
+        specs.append({"dims": dims, "rank": int(rng.integers(4, 41)),
+                      "sr": float(rng.uniform(0.10, 0.50))})
+    return specs
+
+
+def batch_bench(tr, torch, K, prec):
+    specs = batch_problems(torch, tr, 64, 2000)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2000)
+    probs, prms, elems = [], [], 0
+    for i, sp in enumerate(specs):
+        dims = sp["dims"]
+        n = 1
+        for d in dims[2:]:
+            n *= d
+        n1, n2, r = dims[0], dims[1], sp["rank"]
+        A = torch.randn((n, n1, r), generator=g, device="cuda")
+        B = torch.randn((n, n2, r), generator=g, device="cuda")
+        Xbar = torch.bmm(A, B.transpose(1, 2)) / (r ** 0.5)
+        del A, B
+        mask = (torch.rand((n, n1, n2), generator=g, device="cuda") < sp["sr"]).to(torch.uint8)
+        probs.append([Xbar, mask, dims])
+        prms.append(tr.default_params(rank=r, oversample=10, seed=2000 + i, prec=prec,
+                                      noise=tr.TR_NOISE_NONE))
+        elems += n * n1 * n2
+    out = {"problems": len(specs), "elements": elems,
+           "shapes": "n1, n2 ~ U{128..768}, n3 ~ U{8..64}, order 4 w.p. 1/2 with n4 ~ U{4..16}",
+           "ranks": "U{4..40}, sketch width rank + 10", "sampling": "Bernoulli, SR ~ U[0.10, 0.50]",
+           "steps": K}
+    stream = torch.cuda.Stream()
+    res = {}
+    for mode in ("sequential", "graph"):
+        b = tr.Batch([(p[0], p[1], p[2]) for p in probs], prms,
+                     nstreams=1 if mode == "sequential" else 8, stream=stream.cuda_stream)
+        if mode == "sequential":
+            b.graph_mode(False)
+        if not res:
+            # turn the generated transform-domain stacks into observed data
+            # with each problem's own inverse transform (in place of Xbar)
+            for i, p in enumerate(probs):
+                h = b.handle(i)
+                X = h.transform_inverse(p[0])
+                torch.cuda.synchronize()
+                p[0].copy_(X * p[1])
+                del X
+            torch.cuda.synchronize()
+        b.step()
+        b.step()
+        torch.cuda.synchronize()
+        l0 = b.launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(K):
+            b.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        res[mode] = {"batch_iters_per_s": K / (ms * 1e-3),
+                     "problem_iters_per_s": K * len(specs) / (ms * 1e-3),
+                     "elements_per_s": K * elems / (ms * 1e-3),
+                     "ms_per_batch_iter": ms / K,
+                     "kernels_per_batch_iter": (b.launches() - l0) / K,
+                     "host_launches_per_batch_iter": 1 if mode == "graph" else
+                     (b.launches() - l0) / K}
+        b.close()
+        torch.cuda.synchronize()
+    out.update(res)
+    out["graph_vs_sequential"] = res["graph"]["batch_iters_per_s"] / res["sequential"]["batch_iters_per_s"]
+    out["form"] = "%s, 8 streams, one CUDA graph launch per batch iteration" % (
+        {0: "fp32 simt", 2: "bf16 tcgen05", 3: "split-bf16 tcgen05"}[prec])
+    return out
 
 
 # ---------------------------------------------------------- reference arm
