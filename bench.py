@@ -219,10 +219,13 @@ def time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, prec, K
     with torch.cuda.stream(stream):
         h = make_handle(tr, torch, w, Md, maskd, stream, rank, prec)
     tune = None
+    warm = W
     if chosen:
-        tune = h.autotune(5)
+        h.step()                  # first warm-up step, then tune on L(M)
+        warm -= 1
+        tune = h.autotune(5)      # leaves the iterate as it was
         h.graph_mode(True)
-    for _ in range(W):
+    for _ in range(warm):
         h.step()
     if not chosen:
         h.profile_enable(K)
@@ -356,8 +359,10 @@ def run_ours(args):
                 "power_iters": w.q,
                 "sampling_ratio": w.sr,
                 "form": {0: "fp32 simt", 2: "bf16 tcgen05 (split-bf16 refinement)",
-                         3: "split-bf16 tcgen05"}[chosen] + ", graph replay, autotuned tube tile",
+                         3: "split-bf16 tcgen05"}[chosen] + ", graph replay, autotuned tube tile "
+                         "and slice split",
                 "tube_tile": ch["tube_tile"][0] if ch["tube_tile"] else None,
+                "slice_groups": ch["tube_tile"][1] if ch["tube_tile"] else None,
                 "parallelism": "replicas" if world > 1 else "single",
                 "l2": "state 7 x %.0f MB >> 129 MB L2: no flush needed" % (N * esz / 1e6),
             },

@@ -322,15 +322,23 @@ tr_status tr_mlp_train(float *params, const float *X, const float *y, int n, int
  * tr_set_tube_tile: tubes per block of the tube kernels (4, 8, 16 or 32;
  *   0 = the default, the largest that fits).  Every tile computes the same
  *   values.  Errors: TR_EINVAL (not a power of two in range or too large).
- * tr_autotune: time every fitting tube tile on the transform kernel over the
- *   handle's transform-domain scratch (`reps` launches each, no state is
- *   touched), install the fastest and cache it per shape class (dtype, slice
- *   count, transformed mode sizes, n1 n2) for the process; reps = 0 reuses a
- *   cached choice when there is one.  `tile` and `ms` (per launch) may be
- *   NULL.  Synchronises.                                                      */
+ * tr_set_slice_groups: split the RSVD slice pass into `groups` (1..4)
+ *   contiguous slice ranges run on side streams, so that latency-bound
+ *   kernels of one range overlap bandwidth-bound products of another.  Same
+ *   values for every split.  Errors: TR_EINVAL (range), TR_EUNSUPPORTED
+ *   (other engines).
+ * tr_autotune: time every fitting tube tile on the transform kernel and
+ *   (RSVD engine) every slice split on slice passes of L(M), using the
+ *   handle's transform-domain scratch (`reps` runs each; the iterate is
+ *   not touched -- a deferred inverse pass is completed first), install the
+ *   fastest and cache them per shape class (dtype, n1, n2, transformed mode
+ *   sizes, engine, sketch width, power steps, precision) for the process;
+ *   reps = 0 reuses a cached choice when there is one.  `tile` and `groups`
+ *   may be NULL.  Synchronises.                                               */
 tr_status tr_graph_mode(tr_handle *h, int on);
 tr_status tr_set_tube_tile(tr_handle *h, int tubes_per_block);
-tr_status tr_autotune(tr_handle *h, int reps, int *tile, float *ms);
+tr_status tr_set_slice_groups(tr_handle *h, int groups);
+tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups);
 
 /* A batch: independent problems of any shapes, each with its own handle
  * (workspace, parameters, state), stepped together.  Problems are spread

@@ -13,6 +13,8 @@
 
 #include "tr_internal.cuh"
 
+constexpr int kSideStreams = 4;
+
 struct tr_handle {
   // problem
   int order = 0;
@@ -35,6 +37,13 @@ struct tr_handle {
   bool have_pass = false;                     // a slice pass has run
   double thr_last = 0.0;                      // its shrink threshold
   DevSched *sched = nullptr;                  // device copy of mu, mu_prev, t
+  // the RSVD slice pass split into `slice_groups` independent slice ranges on
+  // side streams, so latency-bound kernels of one range overlap the
+  // bandwidth-bound products of another (tr_set_slice_groups, tr_autotune)
+  int slice_groups = 1;
+  int *iota = nullptr;                        // 0, 1, ..., n-1 (slice ids of the ranges)
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t side_fork = nullptr, side_join[kSideStreams] = {};
   // graph replay of steady-state steps (tr_graph_mode)
   bool graph_on = false;
   cudaStream_t gstream = nullptr;
@@ -137,6 +146,12 @@ static void free_all(tr_handle *h) {
   if (lw.fork) cudaEventDestroy(lw.fork);
   if (h->width) cudaFree(h->width);
   if (h->sched) cudaFree(h->sched);
+  if (h->iota) cudaFree(h->iota);
+  for (int i = 0; i < kSideStreams; ++i) {
+    if (h->side[i]) cudaStreamDestroy(h->side[i]);
+    if (h->side_join[i]) cudaEventDestroy(h->side_join[i]);
+  }
+  if (h->side_fork) cudaEventDestroy(h->side_fork);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
@@ -438,6 +453,31 @@ static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double t
                                          h->prm.max_iter, h->stream, &h->launches);
     if (e != cudaSuccess)
       return fail(h, TR_ECUDA, "learned slice pass: %s", cudaGetErrorString(e));
+  } else if (h->slice_groups > 1) {
+    // contiguous slice ranges on side streams; each range's panels sit at
+    // its own offset of the workspace (same width, so no overlap)
+    const int G = h->slice_groups, n = (int)h->n;
+    TR_CUDA(h, cudaEventRecord(h->side_fork, h->stream));
+    for (int g = 0; g < G; ++g) TR_CUDA(h, cudaStreamWaitEvent(h->side[g], h->side_fork, 0));
+    int start = 0;
+    for (int g = 0; g < G; ++g) {
+      const int cnt = n / G + (g < n % G ? 1 : 0);
+      SliceWork gw = h->sw;
+      gw.n = cnt;
+      gw.sel.ids = h->iota + start;
+      gw.Om = (char *)h->sw.Om + (size_t)start * h->n2 * h->sw.l * h->esz;
+      gw.P1 = (char *)h->sw.P1 + (size_t)start * h->n1 * h->sw.l * h->esz;
+      gw.P2 = (char *)h->sw.P2 + (size_t)start * h->n2 * h->sw.l * h->esz;
+      if (cnt > 0) {
+        TR_CUDA(h, launch_slice_rsvd(h->dtype, gw, Abar, Gbar, sh, t, h->side[g]));
+        h->launches += 7 + 4 * (uint64_t)h->sw.q;
+      }
+      start += cnt;
+    }
+    for (int g = 0; g < G; ++g) {
+      TR_CUDA(h, cudaEventRecord(h->side_join[g], h->side[g]));
+      TR_CUDA(h, cudaStreamWaitEvent(h->stream, h->side_join[g], 0));
+    }
   } else {
     TR_CUDA(h, launch_slice_rsvd(h->dtype, h->sw, Abar, Gbar, sh, t, h->stream));
     h->launches += 7 + 4 * (uint64_t)h->sw.q;   // sketch, 2 + 2q GEMM, 1 + 2q QR, SVD core, rebuild
@@ -916,57 +956,86 @@ extern "C" tr_status tr_mlp_train(float *params, const float *X, const float *y,
 }
 
 // ---- autotuner -------------------------------------------------------------
-// Tube tile (tubes per block) per shape class, chosen by timing the pure
-// transform kernel on the handle's transform-domain scratch (no state is
-// touched).  Every candidate computes the same values; only the partition
-// of tubes among blocks changes.  Choices are cached per process.
+// Two launch choices per shape class, each timed with CUDA events on the
+// handle's own buffers: the tube tile (tubes per block) on the transform
+// kernel, and (RSVD engine) the number of slice ranges the slice pass is
+// split into, on a slice pass of L(M) -- the observed data -- held in the
+// transform-domain scratch.  Every candidate computes the same values: a
+// tile only partitions tubes among blocks, a range split only partitions
+// slices among streams.  Choices are cached per process.
 struct TuneKey {
   int dt, n, nt, dims[TR_MAX_TMODES];
-  int64_t P;
+  int64_t n1, n2;
+  int engine, l, q, prec;
   bool operator==(const TuneKey &o) const {
-    if (dt != o.dt || n != o.n || nt != o.nt || P != o.P) return false;
+    if (dt != o.dt || n != o.n || nt != o.nt || n1 != o.n1 || n2 != o.n2 ||
+        engine != o.engine || l != o.l || q != o.q || prec != o.prec)
+      return false;
     for (int k = 0; k < nt; ++k)
       if (dims[k] != o.dims[k]) return false;
     return true;
   }
 };
-static std::vector<std::pair<TuneKey, int>> g_tune_cache;
+struct TuneChoice {
+  int tp, groups;
+};
+static std::vector<std::pair<TuneKey, TuneChoice>> g_tune_cache;
 static std::mutex g_tune_mu;
+extern "C" tr_status tr_set_slice_groups(tr_handle *h, int groups);
 
-extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, float *ms_best) {
+// Mean milliseconds of `reps` runs of `body` on the handle's stream.
+template <typename F>
+static tr_status time_ms(tr_handle *h, int reps, float &ms, F body) {
+  TR_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  for (int i = 0; i < reps; ++i) {
+    tr_status st = body(i);
+    if (st != TR_OK) return st;
+  }
+  TR_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  TR_CUDA(h, cudaEventSynchronize(h->ev1));
+  TR_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  ms /= reps;
+  return TR_OK;
+}
+
+extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups) {
   if (!h || reps < 0) return TR_EINVAL;
-  TuneKey key{(int)h->dtype, (int)h->n, h->td.nt, {0}, h->P};
+  TuneKey key{(int)h->dtype, (int)h->n, h->td.nt, {0}, h->n1, h->n2, (int)h->prm.engine,
+              h->sw.l, h->sw.q, h->sw.prec};
   for (int k = 0; k < h->td.nt; ++k) key.dims[k] = h->td.dim[k];
-  {
+  if (reps == 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto &kv : g_tune_cache)
-      if (kv.first == key && reps == 0) {
-        h->td.tp = kv.second;
-        if (tile) *tile = kv.second;
-        if (ms_best) *ms_best = 0.f;
-        return TR_OK;
+      if (kv.first == key) {
+        h->td.tp = kv.second.tp;
+        if (tile) *tile = kv.second.tp;
+        if (groups) *groups = kv.second.groups;
+        return tr_set_slice_groups(h, kv.second.groups);
       }
   }
+  const int r = reps > 0 ? reps : 3;
+  {
+    tr_status fs = finalize(h);   // the scratch below may hold a deferred step's Gbar
+    if (fs != TR_OK) return fs;
+  }
+  // tube tile
   int cand[4];
   const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 4);
   if (nc == 0) return fail(h, TR_EUNSUPPORTED, "no tube tile fits");
-  const int r = reps > 0 ? reps : 3;
   float best = 0.f;
   int best_tp = cand[0];
-  TR_CUDA(h, cudaStreamSynchronize(h->stream));
   for (int c = 0; c < nc; ++c) {
     TransformDesc td = h->td;
     td.tp = cand[c];
     TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, td, h->mats, h->Abar, h->Gbar, false,
-                                h->stream));   // warm-up
-    TR_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-    for (int i = 0; i < r; ++i)
+                                h->stream));
+    float ms = 0.f;
+    tr_status st = time_ms(h, r, ms, [&](int i) -> tr_status {
       TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, td, h->mats, h->Abar, h->Gbar,
                                   (i & 1) != 0, h->stream));
-    TR_CUDA(h, cudaEventRecord(h->ev1, h->stream));
-    TR_CUDA(h, cudaEventSynchronize(h->ev1));
-    float ms = 0.f;
-    TR_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+      return TR_OK;
+    });
+    if (st != TR_OK) return st;
     h->launches += 1 + (uint64_t)r;
     if (c == 0 || ms < best) {
       best = ms;
@@ -974,22 +1043,46 @@ extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, float *ms_be
     }
   }
   h->td.tp = best_tp;
+  // slice ranges
+  int best_g = 1;
+  if (h->prm.engine == TR_LR_RSVD) {
+    TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->Abar, false,
+                                h->stream));
+    h->launches += 1;
+    const double tau = 1.0 / h->mu;
+    float bestg = 0.f;
+    for (int G = 1; G <= kSideStreams; G *= 2) {
+      if (G > 1 && G > h->n) break;
+      tr_status st = tr_set_slice_groups(h, G);
+      if (st != TR_OK) return st;
+      if ((st = slice_pass(h, h->Abar, h->Gbar, tau, h->t)) != TR_OK) return st;
+      float ms = 0.f;
+      st = time_ms(h, r, ms, [&](int) { return slice_pass(h, h->Abar, h->Gbar, tau, h->t); });
+      if (st != TR_OK) return st;
+      if (G == 1 || ms < bestg) {
+        bestg = ms;
+        best_g = G;
+      }
+    }
+    tr_status st = tr_set_slice_groups(h, best_g);
+    if (st != TR_OK) return st;
+  }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     bool found = false;
     for (auto &kv : g_tune_cache)
       if (kv.first == key) {
-        kv.second = best_tp;
+        kv.second = TuneChoice{best_tp, best_g};
         found = true;
       }
-    if (!found) g_tune_cache.push_back({key, best_tp});
+    if (!found) g_tune_cache.push_back({key, TuneChoice{best_tp, best_g}});
   }
-  if (h->gexec) {   // a captured step holds the old tile
+  if (h->gexec) {   // a captured step holds the old choices
     cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
   }
   if (tile) *tile = best_tp;
-  if (ms_best) *ms_best = best / r;
+  if (groups) *groups = best_g;
   return TR_OK;
 }
 
@@ -1005,6 +1098,32 @@ extern "C" tr_status tr_set_tube_tile(tr_handle *h, int tp) {
   h->td.tp = tp;
   if (h->gexec) {
     TR_CUDA(h, cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return TR_OK;
+}
+
+extern "C" tr_status tr_set_slice_groups(tr_handle *h, int groups) {
+  if (!h) return TR_EINVAL;
+  if (groups < 1 || groups > kSideStreams)
+    return fail(h, TR_EINVAL, "slice groups %d not in [1, %d]", groups, kSideStreams);
+  if (groups > 1 && h->prm.engine != TR_LR_RSVD)
+    return fail(h, TR_EUNSUPPORTED, "slice groups apply to the RSVD engine");
+  if (groups > 1 && !h->iota) {
+    std::vector<int> ids((size_t)h->n);
+    for (size_t j = 0; j < ids.size(); ++j) ids[j] = (int)j;
+    TR_CUDA(h, cudaMalloc((void **)&h->iota, ids.size() * sizeof(int)));
+    TR_CUDA(h, cudaMemcpy(h->iota, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice));
+    for (int i = 0; i < kSideStreams; ++i) {
+      TR_CUDA(h, cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking));
+      TR_CUDA(h, cudaEventCreateWithFlags(&h->side_join[i], cudaEventDisableTiming));
+    }
+    TR_CUDA(h, cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming));
+  }
+  TR_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->slice_groups = groups;
+  if (h->gexec) {
     cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
   }

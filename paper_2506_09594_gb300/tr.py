@@ -108,8 +108,9 @@ _SIGS = {
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, _P, _P]),
     "tr_graph_mode": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_set_tube_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tr_set_slice_groups": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                   ctypes.POINTER(ctypes.c_float)]),
+                                   ctypes.POINTER(ctypes.c_int)]),
     "tr_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_int,
                                        _P]),
     "tr_batch_step": (ctypes.c_int, [_P, _P]),
@@ -403,11 +404,16 @@ class Handle:
     def set_tube_tile(self, tp):
         _check(load().tr_set_tube_tile(self.h, int(tp)), self.h)
 
+    def set_slice_groups(self, groups):
+        _check(load().tr_set_slice_groups(self.h, int(groups)), self.h)
+
     def autotune(self, reps=5):
+        """Returns (tube tile, slice groups) installed by the autotuner."""
         tile = ctypes.c_int()
-        ms = ctypes.c_float()
-        _check(load().tr_autotune(self.h, int(reps), ctypes.byref(tile), ctypes.byref(ms)), self.h)
-        return tile.value, ms.value
+        groups = ctypes.c_int()
+        _check(load().tr_autotune(self.h, int(reps), ctypes.byref(tile), ctypes.byref(groups)),
+               self.h)
+        return tile.value, groups.value
 
     def profile_enable(self, max_steps):
         _check(load().tr_profile_enable(self.h, int(max_steps)), self.h)

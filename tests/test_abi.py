@@ -115,3 +115,4 @@ def test_batch_and_graph_calls_validate_without_gpu(lib):
     assert lib.tr_graph_mode(None, 1) == tr.TR_EINVAL
     assert lib.tr_set_tube_tile(None, 8) == tr.TR_EINVAL
     assert lib.tr_autotune(None, 1, None, None) == tr.TR_EINVAL
+    assert lib.tr_set_slice_groups(None, 2) == tr.TR_EINVAL

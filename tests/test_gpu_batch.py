@@ -132,12 +132,36 @@ def test_tube_tiles_compute_identical_steps():
         ok, what = states_equal(outs[0], o)
         assert ok, what
     h = handle(dims, "f32", M, mask, rank=8, oversample=4)
-    tile, ms = h.autotune(3)
-    assert tile in (4, 8, 16, 32) and ms > 0
-    tile2, ms2 = h.autotune(0)      # cached choice
-    assert tile2 == tile
+    h.step()
+    tile, groups = h.autotune(3)
+    assert tile in (4, 8, 16, 32) and groups in (1, 2, 4)
+    assert h.autotune(0) == (tile, groups)      # cached choice
+    h.step(info=True)                            # the deferred pass was completed first
     with pytest.raises(tr.TrError):
         h.set_tube_tile(12)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", [tr.TR_PREC_FP32, tr.TR_PREC_BF16])
+def test_slice_groups_compute_identical_steps(prec):
+    dims = (60, 52, 10, 7)              # 70 slices: uneven ranges
+    _, M, mask = problem(dims, 6)
+    outs = []
+    for groups, graph in ((1, False), (2, False), (4, False), (3, True)):
+        h = handle(dims, "f32", M, mask, rank=8, oversample=4, prec=prec)
+        h.set_slice_groups(groups)
+        h.graph_mode(graph)
+        for _ in range(4):
+            h.step()
+        outs.append(h.get_state())
+        h.close()
+    for o in outs[1:]:
+        ok, what = states_equal(outs[0], o)
+        assert ok, what
+    h = handle(dims, "f32", M, mask, engine=tr.TR_LR_ADAPTIVE, rank=8, oversample=4,
+               adapt_block=4)
+    with pytest.raises(tr.TrError):
+        h.set_slice_groups(2)
     h.close()
 
 
