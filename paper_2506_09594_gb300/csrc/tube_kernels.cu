@@ -132,14 +132,48 @@ __device__ void block_max_to_global(const T (&v)[K], unsigned long long *const (
   }
 }
 
+// Dot product of a matrix row (shared memory, NK entries, 16-byte aligned:
+// rows are padded to a multiple of 8) with a register fibre.  The row is read
+// with 16-byte shared loads, which every lane of a warp reads at the same
+// address (broadcast), so a row costs NK/4 (float) or NK/2 (double) load
+// instructions instead of NK.
+template <int NK>
+__device__ __forceinline__ float row_dot(const float *Ui, const float (&x)[NK]) {
+  const float4 *U4 = reinterpret_cast<const float4 *>(Ui);
+  float acc = 0.f;
+#pragma unroll
+  for (int m = 0; m < NK / 4; ++m) {
+    const float4 u = U4[m];
+    acc = fmaf(u.x, x[4 * m], acc);
+    acc = fmaf(u.y, x[4 * m + 1], acc);
+    acc = fmaf(u.z, x[4 * m + 2], acc);
+    acc = fmaf(u.w, x[4 * m + 3], acc);
+  }
+  return acc;
+}
+template <int NK>
+__device__ __forceinline__ double row_dot(const double *Ui, const double (&x)[NK]) {
+  const double2 *U2 = reinterpret_cast<const double2 *>(Ui);
+  double acc = 0.0;
+#pragma unroll
+  for (int m = 0; m < NK / 2; ++m) {
+    const double2 u = U2[m];
+    acc = fma(u.x, x[2 * m], acc);
+    acc = fma(u.y, x[2 * m + 1], acc);
+  }
+  return acc;
+}
+
 // Mode products of the transform (or its inverse) on a tube tile in shared
 // memory, tile[j * TP + p].  A fibre is the n_k elements of one position p
 // that differ only in mode k; a thread loads its fibre into registers,
 // multiplies by the n_k x n_k matrix (rows zero-padded to NK) and writes the
-// result back in place.
+// result back in place.  The summation order over m is the same as a plain
+// loop m = 0..NK-1.
 template <typename T, int NK>
 __device__ void tile_transform(T *tile, int n, int TP, const T *mats, const TransformDesc &td,
                                bool inverse) {
+  static_assert(NK % 4 == 0, "rows padded to a multiple of 4");
   for (int mi = 0; mi < td.nt; ++mi) {
     const int k = inverse ? td.nt - 1 - mi : mi;
     const int nk = td.dim[k], stp = td.stride[k];
@@ -151,13 +185,7 @@ __device__ void tile_transform(T *tile, int n, int TP, const T *mats, const Tran
       T x[NK];
 #pragma unroll
       for (int m = 0; m < NK; ++m) x[m] = (m < nk) ? tile[(base + m * stp) * TP + p] : T(0);
-      for (int i = 0; i < nk; ++i) {
-        const T *Ui = U + i * NK;
-        T acc = T(0);
-#pragma unroll
-        for (int m = 0; m < NK; ++m) acc = fma(Ui[m], x[m], acc);
-        tile[(base + i * stp) * TP + p] = acc;
-      }
+      for (int i = 0; i < nk; ++i) tile[(base + i * stp) * TP + p] = row_dot<NK>(U + i * NK, x);
     }
     __syncthreads();
   }
