@@ -350,6 +350,12 @@ class Handle:
                                    ctypes.byref(mu), ctypes.byref(t)), self.h)
         return {"L": L, "E": E, "Y": Y, "Lam": Lam, "G": G, "mu": mu.value, "t": t.value}
 
+    def get_L(self):
+        """The low-rank iterate L only (completes a deferred step first)."""
+        L = self._new()
+        _check(load().tr_get_state(self.h, _ptr(L), None, None, None, None, None, None), self.h)
+        return L
+
     def set_state(self, L, E, Y, Lam, G, mu, t):
         _check(load().tr_set_state(self.h, _ptr(L), _ptr(E), _ptr(Y), _ptr(Lam), _ptr(G),
                                    float(mu), int(t)), self.h)

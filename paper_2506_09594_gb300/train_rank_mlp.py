@@ -1,7 +1,7 @@
 """Train the rank predictor of the learned sketch-width engine.
 
-Traces: seeded power-law problems (slice ranks p(r) ~ r^-1.5 on [2, 64])
-are recovered with the fixed-accuracy engine (Alg. 3 per slice).  Before
+Traces: seeded power-law problems (slice ranks p(r) ~ r^-1.5 on [2, 64];
+slices of 128^2, 256^2 and 512^2 in turn) are recovered with the fixed-accuracy engine (Alg. 3 per slice).  Before
 each slice pass t >= 1 the features of the previous pass are recorded
 (tr_slice_features, exactly what the learned engine will see), and after the
 pass the target log(1 + kept rank).  The MLP is then trained on the GPU
@@ -26,10 +26,20 @@ def trace(seed, dims, sr, iters, growth, rank_cap, oversample, eps, block):
     w = synth.Workload("trace", dims, "powerlaw", sr, dtype="f32", iters=iters, seed=seed,
                        noise_model="none")
     _, M, mask, _ = synth.make_problem(w)
-    h = tr.Handle(torch.from_numpy(M).float().cuda(), torch.from_numpy(mask).cuda(), dims,
-                  engine=tr.TR_LR_ADAPTIVE, rank=rank_cap, oversample=oversample,
-                  adapt_eps=eps, adapt_block=block, noise=tr.TR_NOISE_NONE, tol=0.0,
-                  max_iter=iters, growth=growth, seed=seed)
+    Md, maskd = torch.from_numpy(M).float().cuda(), torch.from_numpy(mask).cuda()
+    h = None
+    # the basis cap is rank + oversample rounded up to blocks; on the largest
+    # slices a smaller oversample keeps the slice core within shared memory
+    for ov in range(oversample, -1, -2):
+        try:
+            h = tr.Handle(Md, maskd, dims, engine=tr.TR_LR_ADAPTIVE, rank=rank_cap, oversample=ov,
+                          adapt_eps=eps, adapt_block=block, noise=tr.TR_NOISE_NONE, tol=0.0,
+                          max_iter=iters, growth=growth, seed=seed)
+            break
+        except tr.TrError:
+            continue
+    if h is None:
+        raise RuntimeError("no basis cap fits for %s" % (dims,))
     feats, targets = [], []
     mu_next = None
     try:
@@ -51,7 +61,8 @@ def main(argv=None):
     ap.add_argument("--out", required=True)
     ap.add_argument("--seeds", type=int, default=200)
     ap.add_argument("--seed0", type=int, default=3000)
-    ap.add_argument("--dims", default="128x128x8x8")
+    ap.add_argument("--dims", default="128x128x8x8,256x256x4x4,512x512x2x2",
+                    help="comma-separated trace shapes, used in turn")
     ap.add_argument("--iters", type=int, default=60)
     ap.add_argument("--growth", type=float, default=1.1)
     ap.add_argument("--rank-cap", type=int, default=64)
@@ -59,18 +70,19 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--under", type=float, default=4.0)
+    ap.add_argument("--under", type=float, default=8.0)
     ap.add_argument("--holdout", type=int, default=10)
     args = ap.parse_args(argv)
     import torch
 
-    dims = tuple(int(x) for x in args.dims.split("x"))
+    shapes = [tuple(int(x) for x in d.split("x")) for d in args.dims.split(",")]
     rng = np.random.default_rng(args.seed0)
     t0 = time.time()
     X, Y = [], []
     for k in range(args.seeds + args.holdout):
         seed = args.seed0 + k if k < args.seeds else 4000 + (k - args.seeds)
         sr = float(rng.uniform(0.15, 0.5))
+        dims = shapes[k % len(shapes)]
         f, y = trace(seed, dims, sr, args.iters, args.growth, args.rank_cap, args.oversample,
                      0.01, 10)
         X.append(f)
