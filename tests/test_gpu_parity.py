@@ -437,3 +437,63 @@ def test_adaptive_engine_step_parity():
     for name, want in [("L", ref.L), ("E", ref.E), ("G", ref.G)]:
         assert relF(host(got[name]), want) < 1e-9, name
     h.close()
+
+
+# ------------------------------------------------------------- edge cases
+def test_zero_problem_stays_zero():
+    # M = 0: every iterate stays exactly 0 (no NaN from 0/0 in the prox or the
+    # sketch of an all-zero slice), ranks are 0
+    dims = (40, 36, 5, 3)
+    h = make_handle(dims, "f32", rank=8, oversample=4)
+    for _ in range(3):
+        info = h.step(info=True)
+    s = h.get_state()
+    for k in ("L", "E", "Y", "Lam", "G"):
+        assert float(s[k].abs().max()) == 0.0, k
+    assert info["max_rank"] == 0 and max(info["res_inf"]) == 0.0
+    h.close()
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_no_shrink_gives_the_rank_l_projection(dt):
+    # tau = 0 with l1: Prox is the identity, so Gbar = Q Q^T Abar, the sketch's
+    # rank-l projection, as in the oracle's randomized engine
+    Ab = synth.lowrank_plus_noise_stack(5, 50, 44, 6, 0.2, seed=8)
+    h = make_handle((50, 44, 5), dt, rank=12, oversample=0, power_iters=1,
+                    phi=tr.TR_PEN_L1, seed=21)
+    G = host(h.slice_prox(dev(Ab, dt), 0.0, t=3))
+    ref, _ = svt.transformed_prox(as_dtype(Ab, dt), 0.0, prox.L1, engine="rsvd", l=12, q=1,
+                                  seed=21, t=3)
+    assert relF(G, ref) < TOL[dt]
+    h.close()
+
+
+def test_sketch_width_clamped_to_slice_size():
+    # rank + oversample above min(n1, n2): the sketch takes every column, so
+    # the randomized prox is the exact (full-SVD) prox
+    Ab = synth.lowrank_plus_noise_stack(4, 30, 20, 20, 0.0, seed=9)
+    h = make_handle((30, 20, 4), "f64", rank=25, oversample=10, phi=tr.TR_PEN_L1)
+    G = host(h.slice_prox(dev(Ab, "f64"), 0.5, t=0))
+    ref, _ = svt.transformed_prox(Ab, 0.5, prox.L1, engine="full")
+    assert relF(G, ref) < 1e-10
+    sig, _ = h.slice_stats()
+    assert sig.shape[1] == 20
+    h.close()
+
+
+def test_single_slice_order3():
+    # n3 = 1: one slice, the transform is the identity
+    X, M, mask = _problem((40, 30, 1), seed=12)
+    lam = admm.default_lambda(40, 30, (1,))
+    p = admm.Params(lam=lam, engine="rsvd", l=8, q=1, seed=2)
+    st = admm.State(*synth.random_state(M.shape, seed=3, scale=0.5), mu=0.5, t=0)
+    ref, _ = admm.step(admm.State(*(as_dtype(x, "f32") for x in (st.L, st.E, st.Y, st.Lam, st.G)),
+                                  mu=0.5, t=0), as_dtype(M, "f32"), mask, (1,), p)
+    h = make_handle((40, 30, 1), "f32", M=M, mask=mask, rank=8, oversample=0, seed=2,
+                    **{"lambda": lam})
+    h.set_state(*(dev(x, "f32") for x in (st.L, st.E, st.Y, st.Lam, st.G)), mu=0.5, t=0)
+    h.step(info=True)
+    got = h.get_state()
+    for name, want in [("L", ref.L), ("G", ref.G), ("Lam", ref.Lam)]:
+        assert relF(host(got[name]), want) < TOL["f32"], name
+    h.close()
