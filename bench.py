@@ -47,6 +47,8 @@ def parse():
                     help="skip the learned-width A/B on the power-law workload")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batch of 64 uneven problems")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision forms on the 1024x1024x64 workload")
     ap.add_argument("--learned-iters", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=8)
     return ap.parse_args()
@@ -401,6 +403,9 @@ def run_ours(args):
         if not args.no_batch and world == 1:
             line["batch"] = batch_bench(tr, torch, args.batch_steps, chosen)
             torch.cuda.empty_cache()
+        if not args.no_precision and world == 1:
+            line["precision"] = precision_forms(tr, torch, 20)
+            torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -475,6 +480,52 @@ def learned_ab(tr, torch, iters, prec):
                                          else None) for k in ("learned", "adaptive")}
     out["speedup_per_iteration"] = {k: out[k]["iters_per_s"] / out["plain"]["iters_per_s"]
                                     for k in ("learned", "adaptive")}
+    return out
+
+
+def precision_forms(tr, torch, K):
+    """The three operand forms on the 1024x1024x64 workload (rank 32, 20%
+    observed, l = 48): device ms per step (graph replay, K steps after 5
+    warm-up steps) and the relative Frobenius difference of L from the plain
+    FP32 form after the same steps.  Sampled parity with the FP64 oracle at
+    this size is a GPU test."""
+    from paper_2506_09594_gb300 import synth
+    w = synth.WORKLOADS["tubal1024x64_r32"]
+    X, M, mask, _ = synth.make_problem(w)
+    Md = torch.from_numpy(M).float().cuda()
+    maskd = torch.from_numpy(mask).cuda()
+    Xd = torch.from_numpy(X).float().cuda()
+    del X, M, mask
+    stream = torch.cuda.Stream()
+    out = {"workload": w.name, "dims": list(w.dims), "rank": w.rank, "sketch_width": w.l,
+           "sampling_ratio": w.sr, "steps": K, "schedule": "mu0 0.05, growth 1.1"}
+    Ls = {}
+    for name, pr in (("fp32", 0), ("bf16x3", 3), ("bf16", 2)):
+        # mu0 0.05: after the warm-up steps tau = 1/mu has fallen below the
+        # observed slices' leading singular values, so the prox keeps ranks
+        h = tr.Handle(Md, maskd, w.dims, rank=w.l, oversample=0, power_iters=w.q, seed=w.seed,
+                      prec=pr, noise=tr.TR_NOISE_NONE, mu0=0.05, stream=stream.cuda_stream)
+        h.graph_mode(True)
+        for _ in range(5):
+            h.step()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(K):
+            h.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        L = h.get_L()
+        Ls[name] = L
+        out[name] = {"ms_per_step": ev0.elapsed_time(ev1) / K,
+                     "recovery_rel_err": float(torch.linalg.norm((L - Xd).double())
+                                               / torch.linalg.norm(Xd.double()))}
+        h.close()
+    base = Ls["fp32"].double()
+    for name in ("bf16x3", "bf16"):
+        out[name]["L_rel_diff_vs_fp32"] = float(torch.linalg.norm(Ls[name].double() - base)
+                                                / torch.linalg.norm(base).clamp_min(1e-300))
+        out[name]["speedup_vs_fp32"] = out["fp32"]["ms_per_step"] / out[name]["ms_per_step"]
     return out
 
 

@@ -7,7 +7,7 @@ order only), 1e-4 for the FP32 path (the stated bound of the FP32 form).
 import numpy as np
 import pytest
 
-from oracle import admm, prox, svt, transform
+from oracle import admm, philox, prox, svt, transform
 from paper_2506_09594_gb300 import synth, tr
 
 torch = pytest.importorskip("torch")
@@ -497,3 +497,28 @@ def test_single_slice_order3():
     for name, want in [("L", ref.L), ("G", ref.G), ("Lam", ref.Lam)]:
         assert relF(host(got[name]), want) < TOL["f32"], name
     h.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [tr.TR_PREC_FP32, tr.TR_PREC_BF16X3, tr.TR_PREC_BF16])
+def test_precision_config_full_size_sampled(prec):
+    # 1024 x 1024 x 64 FP32 stack, rank 32 + noise, l = 48, q = 1, on the GPU
+    # in the launch configuration of a step; the FP64 oracle recomputes four
+    # sampled slices (all 64 would take minutes), and the mixed forms are also
+    # compared with the plain FP32 GPU form on the whole stack
+    n, n1, n2, r, l = 64, 1024, 1024, 32, 48
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, 1e-2, seed=1024)
+    A32 = as_dtype(Ab, "f32")
+    tau = 0.05 * np.linalg.svd(A32[0], compute_uv=False)[0]
+    outs = {}
+    for pr in sorted({tr.TR_PREC_FP32, prec}):
+        h = make_handle((n1, n2, n), "f32", rank=l, oversample=0, power_iters=1,
+                        phi=tr.TR_PEN_L1, seed=17, prec=pr)
+        outs[pr] = host(h.slice_prox(dev(Ab, "f32"), tau, t=4))
+        h.close()
+    tol = PREC_TOL.get(prec, TOL["f32"])
+    for j in (0, 17, 40, 63):
+        Om = philox.gaussian_block(17, 4, j, n2, l)
+        ref, _, _ = svt.slice_prox_randomized(A32[j], Om, 1, tau, prox.L1)
+        assert relF(outs[prec][j], ref) < tol, (j, relF(outs[prec][j], ref))
+    assert relF(outs[prec], outs[tr.TR_PREC_FP32]) < tol
