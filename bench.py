@@ -54,6 +54,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(dist, value, device):
+    """MAX of a float over all ranks: a job's time is its slowest rank's."""
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, timed by the slowest rank (weak scaling)."""
+    return units_per_rank * world / seconds
+
+
+def replica_seed(base_seed, rank):
+    """Each rank recovers its own replica of the workload."""
+    return base_seed + rank
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -206,7 +225,7 @@ PREC = {"fp32": 0, "bf16": 2, "bf16x3": 3}
 def make_handle(tr, torch, w, Md, maskd, stream, rank, prec):
     rank_k = int(w.rank) if w.rank != "powerlaw" else 10
     return tr.Handle(Md, maskd, w.dims, stream=stream.cuda_stream, rank=rank_k,
-                     oversample=w.l - rank_k, power_iters=w.q, seed=w.seed + rank, prec=prec,
+                     oversample=w.l - rank_k, power_iters=w.q, seed=replica_seed(w.seed, rank), prec=prec,
                      noise=tr.TR_NOISE_NONE if w.noise_model == "none" else tr.TR_NOISE_L1)
 
 
@@ -249,9 +268,7 @@ def time_form(tr, torch, dist, w, Md, maskd, X_dev, stream, rank, world, prec, K
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if clocks is not None else None
     if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(dist, ms, "cuda")
         dist.barrier()
     L = h.get_state()["L"]
     rec = float(torch.linalg.norm((L - X_dev).double()) / torch.linalg.norm(X_dev.double()))
@@ -280,7 +297,7 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     dt = torch.float64 if w.dtype == "f64" else torch.float32
     esz = 8 if w.dtype == "f64" else 4
-    X, M, mask, _ = synth.make_problem(w, seed=w.seed + rank)
+    X, M, mask, _ = synth.make_problem(w, seed=replica_seed(w.seed, rank))
     M_host = torch.from_numpy(M).to(dt).pin_memory()
     mask_host = torch.from_numpy(mask).pin_memory()
     Md = M_host.to("cuda")
@@ -316,9 +333,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(dist, e2e_s, "cuda")
 
     N = w.numel
     n = w.nslices
@@ -335,8 +350,8 @@ def run_ours(args):
     fwd_ms = phases["tube_forward"]
     fwd_gbs = tube_fused_bytes(N, esz) / (fwd_ms * 1e-3) / 1e9 if fwd_ms > 0 else None
     step_bytes = tube_fused_bytes(N, esz) + 2 * N * esz
-    value = K * world / (ms * 1e-3)
-    plain_value = K * world / (plain["ms"] * 1e-3)
+    value = job_rate(K, world, ms * 1e-3)
+    plain_value = job_rate(K, world, plain["ms"] * 1e-3)
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -388,7 +403,7 @@ def run_ours(args):
             },
             "phases_ms": {"tube_fused": fwd_ms, "slice_pass": phases["slice_pass"]},
             "step_hbm_fraction": (step_bytes / (ms / K * 1e-3) / 1e9) / hbm_peak,
-            "e2e": {"value": KE * world / e2e_s, "unit": UNIT,
+            "e2e": {"value": job_rate(KE, world, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": int(N * esz + N),
                     "d2h_bytes_per_step": int(8 * 5 + 4 + 4 * n)},
             "clocks": ch["clocks"],
