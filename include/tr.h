@@ -177,6 +177,14 @@ tr_status tr_transform_inverse(tr_handle *h, const void *src, void *dst);
 tr_status tr_slice_prox(tr_handle *h, const void *Abar, void *Gbar,
                         double tau, int t);
 
+/* Point the handle at other observed data (device buffers of the same
+ * shape, dtype and layout as at tr_init; caller-owned, valid until the next
+ * call or tr_free).  Later steps read them; the iterate is kept.  For
+ * streaming inputs: copy the next step's data into a second buffer on
+ * another stream while a step runs.  A captured step graph (tr_graph_mode)
+ * is re-captured at the next steady-state step.  Errors: TR_EINVAL (NULL).  */
+tr_status tr_set_observed(tr_handle *h, const void *observed, const uint8_t *mask);
+
 /* Per-slice singular values and kept ranks of the last slice pass (host
  * buffers: sigma n*l doubles, ranks n ints; either may be NULL).  `l` is
  * the sketch width in use.  Synchronises.                                   */
@@ -319,8 +327,8 @@ tr_status tr_mlp_train(float *params, const float *X, const float *y, int n, int
  *   handle owns, ordered after the handle's stream by events).  Results are
  *   identical to eager steps.  The learned engine plans on the host and
  *   returns TR_EUNSUPPORTED.
- * tr_set_tube_tile: tubes per block of the tube kernels (4, 8, 16 or 32;
- *   0 = the default, the largest that fits).  Every tile computes the same
+ * tr_set_tube_tile: tubes per block of the tube kernels (4, 8, 16, 32 or
+ *   64; 0 = the default, the largest of 4..32 that fits).  Every tile computes the same
  *   values.  Errors: TR_EINVAL (not a power of two in range or too large).
  * tr_set_slice_groups: split the RSVD slice pass into `groups` (1..4)
  *   contiguous slice ranges run on side streams, so that latency-bound

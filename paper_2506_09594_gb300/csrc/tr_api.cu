@@ -1019,8 +1019,8 @@ extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups)
     if (fs != TR_OK) return fs;
   }
   // tube tile
-  int cand[4];
-  const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 4);
+  int cand[5];
+  const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 5);
   if (nc == 0) return fail(h, TR_EUNSUPPORTED, "no tube tile fits");
   float best = 0.f;
   int best_tp = cand[0];
@@ -1086,11 +1086,23 @@ extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups)
   return TR_OK;
 }
 
+extern "C" tr_status tr_set_observed(tr_handle *h, const void *observed, const uint8_t *mask) {
+  if (!h || !observed || !mask) return TR_EINVAL;
+  h->M = observed;
+  h->mask = mask;
+  if (h->gexec) {   // a captured step holds the old pointers
+    TR_CUDA(h, cudaStreamSynchronize(h->gstream));
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return TR_OK;
+}
+
 extern "C" tr_status tr_set_tube_tile(tr_handle *h, int tp) {
   if (!h) return TR_EINVAL;
   if (tp != 0) {
-    int cand[4];
-    const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 4);
+    int cand[5];
+    const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 5);
     bool ok = false;
     for (int c = 0; c < nc; ++c) ok = ok || cand[c] == tp;
     if (!ok) return fail(h, TR_EINVAL, "tube tile %d does not fit", tp);

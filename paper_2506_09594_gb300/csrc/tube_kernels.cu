@@ -578,7 +578,7 @@ bool tube_geometry(int64_t P, int n, const TransformDesc &td, TubeLaunch &g) {
   g.n = n;
   g.tp = pick_tp<T>(n, td);
   if (!g.tp) return false;
-  if (td.tp > 0 && td.tp <= 32 && tube_smem_for<T>(n, td, td.tp) <= kSmemBudget) g.tp = td.tp;
+  if (td.tp > 0 && td.tp <= 64 && tube_smem_for<T>(n, td, td.tp) <= kSmemBudget) g.tp = td.tp;
   g.smem = tube_smem_for<T>(n, td, g.tp);
   g.grid = (unsigned)((P + g.tp - 1) / g.tp);
   return true;
@@ -748,7 +748,7 @@ cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc 
 // partitions the tubes among blocks: every tube's arithmetic is the same.
 int tube_tile_candidates(tr_dtype dt, int n, const TransformDesc &td, int *tps, int cap) {
   int k = 0;
-  for (int tp = 32; tp >= 4 && k < cap; tp >>= 1) {
+  for (int tp = 64; tp >= 4 && k < cap; tp >>= 1) {
     const size_t b = dt == TR_F64 ? tube_smem_for<double>(n, td, tp) : tube_smem_for<float>(n, td, tp);
     if (b <= kSmemBudget) tps[k++] = tp;
   }

@@ -106,6 +106,7 @@ _SIGS = {
                                    ctypes.c_int, _P]),
     "tr_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, _P, _P]),
+    "tr_set_observed": (ctypes.c_int, [_P, _P, _P]),
     "tr_graph_mode": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_set_tube_tile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_set_slice_groups": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -404,6 +405,11 @@ class Handle:
         w = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
         _check(load().tr_set_model(self.h, ctypes.c_void_p(w.ctypes.data), int(w.size)), self.h)
 
+    def set_observed(self, observed, mask):
+        """Point the handle at other observed data (same shape and dtype)."""
+        _check(load().tr_set_observed(self.h, _ptr(observed), _ptr(mask)), self.h)
+        self._keep = (observed, mask)
+
     def graph_mode(self, on=True):
         _check(load().tr_graph_mode(self.h, int(bool(on))), self.h)
 
@@ -520,6 +526,11 @@ class Batch:
         _check_batch(load().tr_batch_handle(self.b, int(i), ctypes.byref(h)))
         dims, dtype, prm = self.meta[i]
         return BorrowedHandle(h, dims, dtype, prm, self.stream)
+
+    def set_observed(self, observed, mask):
+        """Point the handle at other observed data (same shape and dtype)."""
+        _check(load().tr_set_observed(self.h, _ptr(observed), _ptr(mask)), self.h)
+        self._keep = (observed, mask)
 
     def graph_mode(self, on=True):
         _check_batch(load().tr_batch_graph_mode(self.b, int(bool(on))))

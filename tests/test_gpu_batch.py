@@ -120,7 +120,7 @@ def test_tube_tiles_compute_identical_steps():
     dims = (64, 40, 20, 20)
     _, M, mask = problem(dims, 4)
     outs = []
-    for tp in (0, 8, 16):
+    for tp in (0, 8, 16, 64):
         h = handle(dims, "f32", M, mask, rank=8, oversample=4)
         h.set_tube_tile(tp)
         for _ in range(3):
@@ -134,7 +134,7 @@ def test_tube_tiles_compute_identical_steps():
     h = handle(dims, "f32", M, mask, rank=8, oversample=4)
     h.step()
     tile, groups = h.autotune(3)
-    assert tile in (4, 8, 16, 32) and groups in (1, 2, 4)
+    assert tile in (4, 8, 16, 32, 64) and groups in (1, 2, 4)
     assert h.autotune(0) == (tile, groups)      # cached choice
     h.step(info=True)                            # the deferred pass was completed first
     with pytest.raises(tr.TrError):
