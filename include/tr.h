@@ -237,8 +237,10 @@ tr_status tr_slice_prox_noalloc(tr_dtype dtype, int n, int n1, int n2, const voi
  *   certificate: if the kept rank exceeds l_j - oversample and l_j < l_max,
  *     slice j is recomputed at l_max (counted in fallback_slices).
  * The first pass of a handle (and the first after tr_set_state) has no
- * history and runs every slice at l_max.  A slice pass synchronises the
- * stream twice (width plan, certificate count).
+ * history and runs every slice at l_max.  Widths are planned and grouped on
+ * the device, so a pass never synchronises the host and steady-state steps
+ * can be replayed as a graph; the panels hold every width class at once
+ * (n slices per class).
  *
  * MLP parameter vector (FP32, TR_MLP_PARAMS = 35329 values): for each layer
  * in order (16 -> 128, 128 -> 128, 128 -> 128, 128 -> 1) its weights W
@@ -325,8 +327,7 @@ tr_status tr_mlp_train(float *params, const float *X, const float *y, int n, int
  * tr_graph_mode: when on, steady-state steps of this handle replay one
  *   captured CUDA graph (captured at the first such step, on a stream the
  *   handle owns, ordered after the handle's stream by events).  Results are
- *   identical to eager steps.  The learned engine plans on the host and
- *   returns TR_EUNSUPPORTED.
+ *   identical to eager steps.
  * tr_set_tube_tile: tubes per block of the tube kernels (4, 8, 16, 32 or
  *   64; 0 = the default, the largest of 4..32 that fits).  Every tile computes the same
  *   values.  Errors: TR_EINVAL (not a power of two in range or too large).
@@ -353,9 +354,9 @@ tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups);
  * over `nstreams` internal streams (<= 0: 8); each step of the batch is one
  * CUDA graph launch covering every problem's steady-state step (captured at
  * the first such step; eager launches otherwise, or when graph mode is off).
- *   tr_batch_create: problems[i] with params[i] (any engine but
- *     TR_LR_LEARNED); `cuda_stream` is the caller's stream, which every
- *     batch step is ordered after and before.
+ *   tr_batch_create: problems[i] with params[i] (any engine);
+ *     `cuda_stream` is the caller's stream, which every batch step is
+ *     ordered after and before.
  *   tr_batch_step: one iteration of every problem; `infos` (NULL or nprob
  *     entries) requests the per-problem reports, which synchronises.
  *   tr_batch_handle: the handle of problem i (for tr_get_state and the

@@ -11,10 +11,12 @@
 //   2. a ReLU MLP (16 -> 128 -> 128 -> 128 -> 1; FP16 weights, FP32 biases
 //      and accumulation) predicts y_j ~ log(1 + rank_j);
 //   3. l_j = round_up(round(exp(y_j) - 1) + p, 8), clipped to [8, l_max];
-//      slices are grouped by width (a stable counting sort on the device),
-//      groups narrower than a few slices are merged into the next wider
-//      one, and each group runs the randomized slice prox with its own
-//      width on its own stream;
+//      slices are grouped by width on the device (a stable counting sort;
+//      classes of fewer than a few slices join the next wider one), and
+//      every width class runs the randomized slice prox at its width on a
+//      side stream, launched for all n slices and sized on the device
+//      (blocks past the class count exit), so a pass needs no host
+//      synchronisation and can be captured in a graph;
 //   4. certificate: a slice whose kept rank exceeds l_j - p may own more
 //      singular values above the threshold than its sketch could see; it
 //      is recomputed at l_max, the fixed width of the plain engine.
@@ -294,10 +296,25 @@ __global__ void gather_kernel(const float *__restrict__ X, const float *__restri
 //   f15 = clip(t / T, 0, 1)
 // A zero s1 gives f2 = f3 = -1 and f4..f9 = 0; a zero threshold counts as
 // +infinity in the logarithms' ratios (f2/f3 = 1, f14 = 0).
+// Smallest singular value the shrink keeps nonzero (the threshold of the
+// features): tau theta for l1 and for MCP with gamma > tau, theta sqrt(gamma
+// tau) otherwise.
+__device__ __forceinline__ double shrink_threshold_dev(int phi, double theta, double gamma,
+                                                       double tau) {
+  if (phi == TR_PEN_L1 || gamma > tau) return tau * theta;
+  return theta * sqrt(gamma * tau);
+}
+
 template <typename T>
 __global__ void features_kernel(int n, const T *__restrict__ sig, int ldsig,
                                 const int *__restrict__ rank, const int *__restrict__ width,
-                                float thr, float thr0, float tfrac, float *__restrict__ F) {
+                                float thr, float thr0, float tfrac, FeatSched fs,
+                                float *__restrict__ F) {
+  if (fs.d) {   // thresholds and run fraction from the device schedule
+    thr = (float)shrink_threshold_dev(fs.phi, fs.theta, fs.gamma, 1.0 / fs.d->mu);
+    thr0 = (float)shrink_threshold_dev(fs.phi, fs.theta, fs.gamma, 1.0 / fs.d->mu_prev);
+    tfrac = fs.T > 0 ? (float)((double)fs.d->t / (double)fs.T) : 0.f;
+  }
   __shared__ float sv[4][TR_MAX_L];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int j = blockIdx.x * 4 + warp;
@@ -426,6 +443,39 @@ __global__ void __launch_bounds__(1024) plan_kernel(int n, const float *__restri
 
 // Certificate: slices whose kept rank exceeds width - p (and whose width is
 // below lmax) are listed for a recomputation at lmax.
+// Width groups on the device: walking the classes from narrow to wide, a
+// class with fewer than merge_min slices (while a wider non-empty class
+// follows) joins the next one.  Group g is launched at the width of its
+// widest class c: its slice ids go to gids[c * n ...], its size to
+// gcount[c]; classes merged away get gcount 0.  One block.
+__global__ void group_kernel(int n, int C, int merge_min, const int *__restrict__ counts,
+                             const int *__restrict__ ids, int *__restrict__ gids,
+                             int *__restrict__ gcount) {
+  __shared__ int src[kMaxClasses], cnt[kMaxClasses];
+  if (threadIdx.x == 0) {
+    int start = 0, pend = 0, pstart = 0;
+    for (int c = 0; c < C; ++c) {
+      src[c] = 0;
+      cnt[c] = 0;
+      const int k = counts[c];
+      if (k == 0) continue;
+      if (pend == 0) pstart = start;
+      pend += k;
+      start += k;
+      bool later = false;
+      for (int c2 = c + 1; c2 < C; ++c2) later = later || counts[c2] > 0;
+      if (pend < merge_min && later) continue;
+      src[c] = pstart;
+      cnt[c] = pend;
+      pend = 0;
+    }
+    for (int c = 0; c < C; ++c) gcount[c] = cnt[c];
+  }
+  __syncthreads();
+  for (int c = 0; c < C; ++c)
+    for (int i = threadIdx.x; i < cnt[c]; i += blockDim.x) gids[(int64_t)c * n + i] = ids[src[c] + i];
+}
+
 __global__ void saturation_kernel(int n, const int *__restrict__ rank,
                                   const int *__restrict__ width, int p, int lmax,
                                   int *__restrict__ fb_ids, int *__restrict__ fb_count) {
@@ -509,15 +559,15 @@ cudaError_t launch_mlp_gather(const float *X, const float *y, int n, int B, int 
 
 cudaError_t launch_features(tr_dtype dt, int n, const void *sig, int ldsig, const int *rank,
                             const int *width, double thr, double thr0, double tfrac, float *F,
-                            cudaStream_t s) {
+                            cudaStream_t s, FeatSched fs) {
   if (n <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((n + 3) / 4);
   if (dt == TR_F64)
     features_kernel<double><<<grid, 128, 0, s>>>(n, (const double *)sig, ldsig, rank, width,
-                                                 (float)thr, (float)thr0, (float)tfrac, F);
+                                                 (float)thr, (float)thr0, (float)tfrac, fs, F);
   else
     features_kernel<float><<<grid, 128, 0, s>>>(n, (const float *)sig, ldsig, rank, width,
-                                                (float)thr, (float)thr0, (float)tfrac, F);
+                                                (float)thr, (float)thr0, (float)tfrac, fs, F);
   return cudaGetLastError();
 }
 
@@ -530,106 +580,85 @@ cudaError_t launch_plan(int n, const float *yhat, int p, int lmax, int *width, i
   return cudaGetLastError();
 }
 
+// Panel columns the device-planned pass reserves: every width class owns a
+// region able to hold all n slices at its width.
+int learned_panel_cols(int lmax) {
+  int cols = 0;
+  for (int c = 0; c < plan_classes(lmax); ++c) cols += 8 * (c + 1) < lmax ? 8 * (c + 1) : lmax;
+  return cols;
+}
+
 cudaError_t launch_slice_learned(tr_dtype dt, const SliceWork &w, LearnedWork &lw,
                                  const void *Abar, void *Gbar, const ShrinkScalars &sh,
-                                 double thr, int t, int T, cudaStream_t s, uint64_t *launches) {
+                                 double thr, int t, int T, FeatSched fs, cudaStream_t s,
+                                 uint64_t *launches) {
   const int n = w.n, lmax = lw.lmax, p = lw.p;
   const size_t esz = dt == TR_F64 ? 8 : 4;
-  const uint64_t per_group = 7 + 4 * (uint64_t)w.q;
   SliceWork base = w;
   base.l = lmax;
   base.ldsig = lmax;
   base.width = lw.width;
   base.sel = SliceSel{};
-  lw.last_fallback = 0;
   cudaError_t e;
   if (!lw.have_hist) {
     // no previous pass: every slice at the plain width
+    if ((e = cudaMemsetAsync(lw.fb_count, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = launch_slice_rsvd(dt, base, Abar, Gbar, sh, t, s)) != cudaSuccess) return e;
-    *launches += per_group;
-    lw.last_groups = 1;
+    *launches += 7 + 4 * (uint64_t)w.q;
     lw.have_hist = true;
     lw.thr_prev = thr;
     return cudaSuccess;
   }
-  // 1-3: features of the previous pass, predicted log-ranks, width plan
+  // 1-3: features of the previous pass, predicted log-ranks, width plan and
+  // groups, all on the device (no host synchronisation: the pass can be
+  // captured in a graph)
   const double tfrac = T > 0 ? (double)t / (double)T : 0.0;
   if ((e = launch_features(dt, n, w.sig, lmax, w.rank, lw.width, thr, lw.thr_prev, tfrac, lw.feat,
-                           s)) != cudaSuccess)
+                           s, fs)) != cudaSuccess)
     return e;
   if ((e = launch_mlp_forward(lw.params, lw.feat, n, lw.pred, nullptr, s)) != cudaSuccess) return e;
   if ((e = launch_plan(n, lw.pred, p, lmax, lw.width, lw.ids, lw.counts, s)) != cudaSuccess) return e;
-  *launches += 3;
   const int C = plan_classes(lmax);
-  if ((e = cudaMemcpyAsync(lw.h_counts, lw.counts, C * sizeof(int), cudaMemcpyDeviceToHost, s)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  // groups: consecutive classes, a class with fewer than merge_min slices
-  // joining the next non-empty wider class
-  struct Group {
-    int start, count, l;
-  } groups[(TR_MAX_L + 7) / 8];
-  int ng = 0, start = 0, pend = 0;
-  for (int c = 0; c < C; ++c) {
-    const int cnt = lw.h_counts[c];
-    if (cnt == 0) continue;
-    pend += cnt;
-    bool later = false;
-    for (int c2 = c + 1; c2 < C; ++c2) later = later || lw.h_counts[c2] > 0;
-    if (pend < lw.merge_min && later) continue;
-    const int l = 8 * (c + 1) < lmax ? 8 * (c + 1) : lmax;
-    groups[ng++] = Group{start, pend, l};
-    start += pend;
-    pend = 0;
-  }
-  // each group on its own stream, panels in disjoint regions of the workspace
+  group_kernel<<<1, 256, 0, s>>>(n, C, lw.merge_min, lw.counts, lw.ids, lw.gids, lw.gcount);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  *launches += 4;
+  // every class on a side stream, sized on the device (blocks past the
+  // class count exit at once), panels in the class's own region
   if ((e = cudaEventRecord(lw.fork, s)) != cudaSuccess) return e;
-  const int nstreams = ng < TR_LEARNED_STREAMS ? ng : TR_LEARNED_STREAMS;
+  const int nstreams = C < TR_LEARNED_STREAMS ? C : TR_LEARNED_STREAMS;
   for (int i = 0; i < nstreams; ++i)
     if ((e = cudaStreamWaitEvent(lw.aux[i], lw.fork, 0)) != cudaSuccess) return e;
   size_t o_om = 0, o_p1 = 0, o_p2 = 0;
-  auto up = [](size_t x) { return (x + 63) / 64 * 64; };
-  for (int g = 0; g < ng; ++g) {
+  for (int c = 0; c < C; ++c) {
     SliceWork gw = base;
-    gw.n = groups[g].count;
-    gw.l = groups[g].l;
-    gw.sel.ids = lw.ids + groups[g].start;
+    gw.l = 8 * (c + 1) < lmax ? 8 * (c + 1) : lmax;
+    gw.sel.ids = lw.gids + (size_t)c * n;
+    gw.sel.count = lw.gcount + c;
     gw.Om = (char *)w.Om + o_om * esz;
     gw.P1 = (char *)w.P1 + o_p1 * esz;
     gw.P2 = (char *)w.P2 + o_p2 * esz;
-    o_om += up((size_t)gw.n * w.n2 * gw.l);
-    o_p1 += up((size_t)gw.n * w.n1 * gw.l);
-    o_p2 += up((size_t)gw.n * w.n2 * gw.l);
-    if ((e = launch_slice_rsvd(dt, gw, Abar, Gbar, sh, t, lw.aux[g % TR_LEARNED_STREAMS])) !=
+    o_om += (size_t)n * w.n2 * gw.l;
+    o_p1 += (size_t)n * w.n1 * gw.l;
+    o_p2 += (size_t)n * w.n2 * gw.l;
+    if ((e = launch_slice_rsvd(dt, gw, Abar, Gbar, sh, t, lw.aux[c % TR_LEARNED_STREAMS])) !=
         cudaSuccess)
       return e;
-    *launches += per_group;
+    *launches += 7 + 4 * (uint64_t)w.q;
   }
   for (int i = 0; i < nstreams; ++i) {
     if ((e = cudaEventRecord(lw.join[i], lw.aux[i])) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, lw.join[i], 0)) != cudaSuccess) return e;
   }
-  lw.last_groups = ng;
-  // 4: certificate and fallback at the plain width
+  // 4: certificate and fallback at the plain width (sized on the device)
   if ((e = cudaMemsetAsync(lw.fb_count, 0, sizeof(int), s)) != cudaSuccess) return e;
   saturation_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, w.rank, lw.width, p, lmax, lw.fb_ids,
                                                    lw.fb_count);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *launches += 1;
-  if ((e = cudaMemcpyAsync(lw.h_counts + kMaxClasses, lw.fb_count, sizeof(int),
-                           cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  const int nfb = lw.h_counts[kMaxClasses];
-  if (nfb > 0) {
-    SliceWork fw = base;
-    fw.n = nfb;
-    fw.sel.ids = lw.fb_ids;
-    if ((e = launch_slice_rsvd(dt, fw, Abar, Gbar, sh, t, s)) != cudaSuccess) return e;
-    *launches += per_group;
-  }
-  lw.last_fallback = nfb;
+  SliceWork fw = base;
+  fw.sel.ids = lw.fb_ids;
+  fw.sel.count = lw.fb_count;
+  if ((e = launch_slice_rsvd(dt, fw, Abar, Gbar, sh, t, s)) != cudaSuccess) return e;
+  *launches += 1 + 7 + 4 * (uint64_t)w.q;
   lw.thr_prev = thr;
   return cudaSuccess;
 }

@@ -135,10 +135,10 @@ static void free_profile(tr_handle *h) {
 static void free_all(tr_handle *h) {
   free_profile(h);
   LearnedWork &lw = h->lw;
-  void *lbufs[] = {lw.params, lw.feat, lw.pred, lw.ids, lw.counts, lw.fb_ids, lw.fb_count};
+  void *lbufs[] = {lw.params, lw.feat, lw.pred, lw.ids, lw.counts, lw.fb_ids, lw.fb_count,
+                   lw.gids, lw.gcount};
   for (void *b : lbufs)
     if (b) cudaFree(b);
-  if (lw.h_counts) cudaFreeHost(lw.h_counts);
   for (int i = 0; i < TR_LEARNED_STREAMS; ++i) {
     if (lw.aux[i]) cudaStreamDestroy(lw.aux[i]);
     if (lw.join[i]) cudaEventDestroy(lw.join[i]);
@@ -358,12 +358,12 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   sw.l = l;
   sw.q = prm->power_iters;
   sw.seed = prm->seed;
-  // the learned engine packs width groups into the panels, each group's
-  // region rounded up to 64 elements
-  const size_t slack = prm->engine == TR_LR_LEARNED ? (size_t)64 * plan_classes(l) : 0;
-  INIT_CUDA(cudaMalloc(&sw.Om, ((size_t)h->n * h->n2 * l + slack) * h->esz));
-  INIT_CUDA(cudaMalloc(&sw.P1, ((size_t)h->n * h->n1 * l + slack) * h->esz));
-  INIT_CUDA(cudaMalloc(&sw.P2, ((size_t)h->n * h->n2 * l + slack) * h->esz));
+  // the learned engine gives every width class its own panel region able to
+  // hold all n slices at the class width
+  const size_t pcols = prm->engine == TR_LR_LEARNED ? (size_t)learned_panel_cols(l) : (size_t)l;
+  INIT_CUDA(cudaMalloc(&sw.Om, (size_t)h->n * h->n2 * pcols * h->esz));
+  INIT_CUDA(cudaMalloc(&sw.P1, (size_t)h->n * h->n1 * pcols * h->esz));
+  INIT_CUDA(cudaMalloc(&sw.P2, (size_t)h->n * h->n2 * pcols * h->esz));
   INIT_CUDA(cudaMalloc((void **)&h->width, (size_t)h->n * sizeof(int)));
   sw.width = h->width;
   sw.ldsig = l;
@@ -402,7 +402,8 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     INIT_CUDA(cudaMalloc((void **)&lw.counts, (size_t)C * sizeof(int)));
     INIT_CUDA(cudaMalloc((void **)&lw.fb_ids, (size_t)h->n * sizeof(int)));
     INIT_CUDA(cudaMalloc((void **)&lw.fb_count, sizeof(int)));
-    INIT_CUDA(cudaMallocHost((void **)&lw.h_counts, ((TR_MAX_L + 7) / 8 + 1) * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&lw.gids, (size_t)C * h->n * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&lw.gcount, (size_t)C * sizeof(int)));
     lw.width = h->width;
     for (int i = 0; i < TR_LEARNED_STREAMS; ++i) {
       INIT_CUDA(cudaStreamCreateWithFlags(&lw.aux[i], cudaStreamNonBlocking));
@@ -449,8 +450,16 @@ static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double t
     TR_CUDA(h, cudaMemcpyAsync(h->width, h->aw.kept, (size_t)h->n * sizeof(int),
                                cudaMemcpyDeviceToDevice, h->stream));
   } else if (h->prm.engine == TR_LR_LEARNED) {
+    FeatSched fs;
+    if (sched) {   // a step: thresholds and t from the device schedule
+      fs.d = h->sched;
+      fs.phi = (int)h->prm.phi;
+      fs.theta = h->prm.phi_theta;
+      fs.gamma = h->prm.phi_gamma;
+      fs.T = h->prm.max_iter;
+    }
     cudaError_t e = launch_slice_learned(h->dtype, h->sw, h->lw, Abar, Gbar, sh, thr, t,
-                                         h->prm.max_iter, h->stream, &h->launches);
+                                         h->prm.max_iter, fs, h->stream, &h->launches);
     if (e != cudaSuccess)
       return fail(h, TR_ECUDA, "learned slice pass: %s", cudaGetErrorString(e));
   } else if (h->slice_groups > 1) {
@@ -514,7 +523,10 @@ static tr_status read_info(tr_handle *h, double mu_used, tr_step_info *info) {
   }
   info->max_rank = mx;
   info->sum_rank = (int)sum;
-  info->fallback_slices = h->prm.engine == TR_LR_LEARNED ? h->lw.last_fallback : 0;
+  info->fallback_slices = 0;
+  if (h->prm.engine == TR_LR_LEARNED && h->lw.fb_count)
+    TR_CUDA(h, cudaMemcpy(&info->fallback_slices, h->lw.fb_count, sizeof(int),
+                          cudaMemcpyDeviceToHost));
   info->ms = ms;
   int tc_err = 0;
   TR_CUDA(h, cudaMemcpy(&tc_err, h->sw.err, sizeof tc_err, cudaMemcpyDeviceToHost));
@@ -666,8 +678,6 @@ extern "C" tr_status tr_prox_step(tr_handle *h, tr_step_info *info) {
 
 extern "C" tr_status tr_graph_mode(tr_handle *h, int on) {
   if (!h) return TR_EINVAL;
-  if (on && h->prm.engine == TR_LR_LEARNED)
-    return fail(h, TR_EUNSUPPORTED, "the learned engine plans on the host: no graph replay");
   if (on && !h->gstream) {
     TR_CUDA(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
     TR_CUDA(h, cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
@@ -1213,8 +1223,6 @@ extern "C" tr_status tr_batch_create(tr_batch **out, int nprob, const tr_problem
   BATCH_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
   BATCH_CUDA(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
   for (int i = 0; i < nprob; ++i) {
-    if (prms[i].engine == TR_LR_LEARNED)
-      return bail(batch_fail(TR_EUNSUPPORTED, "problem %d: the learned engine cannot join a batch graph", i));
     tr_handle *h = nullptr;
     tr_status st = tr_init(&h, &probs[i], &prms[i], b->pool[(size_t)i % b->pool.size()]);
     if (st != TR_OK) return bail(batch_fail(st, "problem %d: %s", i, g_init_err));

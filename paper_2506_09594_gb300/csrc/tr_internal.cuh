@@ -137,10 +137,9 @@ struct LearnedWork {
   int *width = nullptr;      // sketch width used per slice (history of the last pass)
   int *ids = nullptr, *counts = nullptr;     // plan: slice ids sorted by width class
   int *fb_ids = nullptr, *fb_count = nullptr;
-  int *h_counts = nullptr;   // pinned host mirror: class counts, then the fallback count
+  int *gids = nullptr, *gcount = nullptr;    // width groups: C x n slice ids, C sizes
   bool have_hist = false;
   double thr_prev = 0.0;
-  int last_fallback = 0, last_groups = 0;
   cudaStream_t aux[TR_LEARNED_STREAMS] = {};
   cudaEvent_t fork = nullptr, join[TR_LEARNED_STREAMS] = {};
 };
@@ -156,12 +155,22 @@ cudaError_t launch_mlp_adam(float *prm, const float *g, float *m, float *v, int6
                             double b1, double b2, double eps, int step, cudaStream_t s);
 cudaError_t launch_mlp_gather(const float *X, const float *y, int n, int B, int step,
                               uint64_t seed, float *Xb, float *yb, cudaStream_t s);
+// Optional device schedule for the features: thresholds from mu and the
+// previous mu, run fraction t / T (null d: the host values are used).
+struct FeatSched {
+  const DevSched *d = nullptr;
+  int phi = 0;
+  double theta = 1.0, gamma = 1.0;
+  int T = 0;
+};
 cudaError_t launch_features(tr_dtype dt, int n, const void *sig, int ldsig, const int *rank,
                             const int *width, double thr, double thr0, double tfrac, float *F,
-                            cudaStream_t s);
+                            cudaStream_t s, FeatSched fs = FeatSched{});
+int learned_panel_cols(int lmax);
 int plan_classes(int lmax);
 cudaError_t launch_plan(int n, const float *yhat, int p, int lmax, int *width, int *ids,
                         int *counts, cudaStream_t s);
 cudaError_t launch_slice_learned(tr_dtype dt, const SliceWork &w, LearnedWork &lw,
                                  const void *Abar, void *Gbar, const ShrinkScalars &sh,
-                                 double thr, int t, int T, cudaStream_t s, uint64_t *launches);
+                                 double thr, int t, int T, FeatSched fs, cudaStream_t s,
+                                 uint64_t *launches);

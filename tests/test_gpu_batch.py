@@ -107,13 +107,24 @@ def test_graph_steps_match_oracle():
     assert got["t"] == 5 and abs(got["mu"] - st.mu) < 1e-15
 
 
-def test_graph_mode_refuses_learned_engine():
-    dims = (32, 32, 4)
-    _, M, mask = problem(dims, 2)
-    h = handle(dims, "f32", M, mask, engine=tr.TR_LR_LEARNED, rank=8, oversample=8)
-    with pytest.raises(tr.TrError):
-        h.graph_mode(True)
-    h.close()
+def test_learned_engine_graph_steps_identical_to_eager():
+    # the learned pass plans widths on the device, so it can be replayed
+    dims = (64, 56, 6, 4)
+    _, M, mask = problem(dims, 2, rank=5, sr=0.5)
+    outs = []
+    for graph in (False, True):
+        h = handle(dims, "f32", M, mask, engine=tr.TR_LR_LEARNED, rank=24, oversample=8,
+                   model_path=tr.DEFAULT_MODEL.encode(), prec=tr.TR_PREC_BF16, mu0=0.05)
+        h.graph_mode(graph)
+        for _ in range(6):
+            h.step()
+        info = h.step(info=True)
+        outs.append((h.get_state(), h.slice_widths()))
+        h.close()
+    ok, what = states_equal(outs[0][0], outs[1][0])
+    assert ok, what
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert info["fallback_slices"] >= 0
 
 
 def test_tube_tiles_compute_identical_steps():
@@ -201,9 +212,19 @@ def test_batch_matches_individual_handles(nstreams):
     b.close()
 
 
-def test_batch_rejects_learned_and_reports():
-    dims = (32, 32, 4)
-    _, M, mask = problem(dims, 5)
-    p = tr.default_params(engine=tr.TR_LR_LEARNED, rank=8, oversample=8)
-    with pytest.raises(tr.TrError):
-        tr.Batch([(dev(M, "f32"), torch.from_numpy(mask).cuda(), dims)], p)
+def test_batch_with_a_learned_problem_matches_its_handle():
+    dims = (48, 40, 5, 4)
+    _, M, mask = problem(dims, 5, rank=4, sr=0.5)
+    p = tr.default_params(engine=tr.TR_LR_LEARNED, rank=16, oversample=8, mu0=0.05,
+                          model_path=tr.DEFAULT_MODEL.encode())
+    b = tr.Batch([(dev(M, "f32"), torch.from_numpy(mask).cuda(), dims)], p)
+    for _ in range(5):
+        b.step()
+    got = b.handle(0).get_state()
+    h = handle(dims, "f32", M, mask, params=p)
+    for _ in range(5):
+        h.step()
+    ok, what = states_equal(h.get_state(), got)
+    assert ok, what
+    h.close()
+    b.close()
