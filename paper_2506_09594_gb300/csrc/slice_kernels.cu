@@ -249,7 +249,8 @@ cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T
   return cudaGetLastError();
 }
 
-// Skinny product on the tensor cores (N <= 128, FP32 in/out): split = 1 is
+// Skinny product on the tensor cores (FP32 in/out, column tiles of up to
+// 128): split = 1 is
 // BF16 operands, split = 3 the hi/lo split (FP32-level accuracy).
 cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return cudaSuccess;

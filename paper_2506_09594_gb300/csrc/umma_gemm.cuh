@@ -1,7 +1,8 @@
 // Batched skinny GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out, N <= 128.
-// One CTA (4 warps) owns a 128-row tile of one batch entry.  K is consumed
+// C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out.  One CTA
+// (4 warps) owns a 128-row x NP-column tile of one batch entry (NP in {32,
+// 64, 128}; N above 128 takes several column tiles).  K is consumed
 // in chunks of 64: the 128 threads load the FP32 operands from global
 // memory, round them to BF16 (optionally split x = hi + lo, both BF16) and
 // store them in shared memory in the canonical K-major layout without
