@@ -116,3 +116,20 @@ def test_batch_and_graph_calls_validate_without_gpu(lib):
     assert lib.tr_set_tube_tile(None, 8) == tr.TR_EINVAL
     assert lib.tr_autotune(None, 1, None, None) == tr.TR_EINVAL
     assert lib.tr_set_slice_groups(None, 2) == tr.TR_EINVAL
+
+
+def test_init_rejects_oversized_problems_without_a_gpu(lib):
+    # slice panels beyond shared memory, sketches beyond the widest width,
+    # adaptive blocks out of range, an engine that is not built, too many
+    # slices: all refused before any device allocation
+    st, _ = _init(lib, 3, [2048, 64, 4])                              # slice rows > 1024
+    assert st == tr.TR_EUNSUPPORTED and "exceed" in lib.tr_last_error(None).decode()
+    st, _ = _init(lib, 3, [512, 512, 4], rank=120, oversample=10)     # l = 130 > 96
+    assert st == tr.TR_EUNSUPPORTED
+    st, _ = _init(lib, 3, [64, 64, 4], engine=tr.TR_LR_ADAPTIVE, adapt_block=0)
+    assert st == tr.TR_EINVAL
+    st, _ = _init(lib, 3, [64, 64, 4], engine=tr.TR_LR_FULLSVD)
+    assert st == tr.TR_EUNSUPPORTED
+    st, _ = _init(lib, 3, [64, 64, 70000])                           # slices > 65535
+    assert st == tr.TR_EUNSUPPORTED
+    assert lib.tr_set_observed(None, None, None) == tr.TR_EINVAL
