@@ -270,17 +270,12 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     return st;
   }
   td.nkpad = ((maxd + 7) / 8) * 8;
-  int stride = 1, off = 0;
+  int stride = 1;
   for (int k = 0; k < td.nt; ++k) {
     td.stride[k] = stride;
     stride *= td.dim[k];
-    td.off_fwd[k] = off;
-    off += td.dim[k] * td.nkpad;
-    td.off_inv[k] = off;
-    off += td.dim[k] * td.nkpad;
   }
-  td.mats_len = ((off + 3) / 4) * 4;
-  if (td.mats_len == 0) td.mats_len = 4;
+  const int hk = transform_mats_layout(td);
   int tp = 0;
   if (tube_smem_bytes(h->dtype, (int)h->n, td, &tp) == 0 || tp == 0) {
     tr_status st = fail(nullptr, TR_EUNSUPPORTED, "%lld slices do not fit a tube tile", (long long)h->n);
@@ -319,7 +314,9 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     for (int i = 0; i < d; ++i)
       for (int m = 0; m < d; ++m) {
         hm[(size_t)td.off_fwd[k] + (size_t)i * td.nkpad + m] = U[(size_t)i * d + m];
-        hm[(size_t)td.off_inv[k] + (size_t)i * td.nkpad + m] = U[(size_t)m * d + i];
+        // column m of U, even rows then odd rows, for the folded inverse
+        if (2 * m + 1 <= d)
+          hm[(size_t)td.off_inv[k] + (size_t)m * 2 * hk + (i & 1) * hk + i / 2] = U[(size_t)i * d + m];
       }
   }
 

@@ -18,9 +18,10 @@
 // The transformed modes 3..d of a problem as seen from the slice index j.
 // Mode k (0-based among the transformed modes) has size dim[k] and stride
 // stride[k] in j (stride[0] = 1, stride[k] = dim[0]*...*dim[k-1]).  Its
-// forward matrix U (dim x dim, rows padded to nkpad columns with zeros) is at
-// element offset off_fwd[k] of the matrix buffer, its inverse U^{-1} = U^T
-// at off_inv[k].
+// forward matrix U (the orthonormal DCT-II, dim x dim, rows padded to nkpad
+// columns with zeros) is at element offset off_fwd[k] of the matrix buffer;
+// the inverse U^{-1} = U^T, folded by the cosine symmetry of U, at
+// off_inv[k] (layout: transform_mats_layout).
 struct TransformDesc {
   int nt;
   int nkpad;
@@ -84,6 +85,12 @@ cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc 
                              const void *mats, const void *src, void *dst, bool inverse,
                              cudaStream_t s);
 int tube_tile_candidates(tr_dtype dt, int n, const TransformDesc &td, int *tps, int cap);
+// Sets off_fwd, off_inv and mats_len from nt, dim and nkpad; returns HK, the
+// padded half row length.  Forward rows: U[i][0..dim) at off_fwd + i nkpad.
+// Folded inverse rows, m < ceil(dim/2): U[0][m], U[2][m], ... at
+// off_inv + 2 HK m and U[1][m], U[3][m], ... at off_inv + 2 HK m + HK
+// (zeros beyond dim).
+int transform_mats_layout(TransformDesc &td);
 size_t tube_smem_bytes(tr_dtype dt, int n, const TransformDesc &td, int *tp_out);
 
 // ---- slice pass (slice_kernels.cu) ----

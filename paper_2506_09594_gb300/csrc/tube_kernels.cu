@@ -166,26 +166,75 @@ __device__ __forceinline__ double row_dot(const double *Ui, const double (&x)[NK
 
 // Mode products of the transform (or its inverse) on a tube tile in shared
 // memory, tile[j * TP + p].  A fibre is the n_k elements of one position p
-// that differ only in mode k; a thread loads its fibre into registers,
-// multiplies by the n_k x n_k matrix (rows zero-padded to NK) and writes the
-// result back in place.  The summation order over m is the same as a plain
-// loop m = 0..NK-1.
+// that differ only in mode k; a thread reads its fibre into registers,
+// applies the n_k x n_k matrix and writes the result back in place.
+//
+// The transform is the orthonormal DCT-II along every mode, whose matrix
+// obeys C[k][n-1-m] = (-1)^k C[k][m] (the cosines are symmetric about the
+// centre of the fibre).  With h = ceil(n/2) the forward product folds the
+// fibre into s_m = x_m + x_{n-1-m}, d_m = x_m - x_{n-1-m} (m < h; the centre
+// of an odd fibre enters both as x_m) and takes
+//   y_k = sum_{m<h} C[k][m] s_m (k even),   y_k = sum_{m<h} C[k][m] d_m (k odd),
+// the inverse x = C^T y the even-k and odd-k sums E_m, O_m of C[k][m] y_k
+// with x_m = E_m + O_m and x_{n-1-m} = E_m - O_m: half the multiply-adds of
+// the plain matrix-vector product, the same values up to rounding.
+//   Forward rows: row k of C at off_fwd + k NK (entries m >= h meet zeros).
+//   Inverse rows: row m < h at off_inv + 2 HK m holds C[0][m], C[2][m], ...
+//   (HK entries) and then C[1][m], C[3][m], ... (HK entries).
+template <int NK>
+__host__ __device__ constexpr int half_k() {
+  return ((NK / 2 + 3) / 4) * 4;
+}
+
 template <typename T, int NK>
 __device__ void tile_transform(T *tile, int n, int TP, const T *mats, const TransformDesc &td,
                                bool inverse) {
   static_assert(NK % 4 == 0, "rows padded to a multiple of 4");
+  constexpr int HK = half_k<NK>();
   for (int mi = 0; mi < td.nt; ++mi) {
     const int k = inverse ? td.nt - 1 - mi : mi;
-    const int nk = td.dim[k], stp = td.stride[k];
+    const int nk = td.dim[k], stp = td.stride[k], h = (nk + 1) / 2;
     const T *U = mats + (inverse ? td.off_inv[k] : td.off_fwd[k]);
     const int nfib = n / nk;
     for (int w = threadIdx.x; w < nfib * TP; w += blockDim.x) {
       const int p = w % TP, f = w / TP;
-      const int base = (f % stp) + (f / stp) * (stp * nk);
-      T x[NK];
+      T *fib = tile + ((f % stp) + (f / stp) * (stp * nk)) * TP + p;
+      const int step = stp * TP;
+      T a[HK], b[HK];
+      if (!inverse) {
 #pragma unroll
-      for (int m = 0; m < NK; ++m) x[m] = (m < nk) ? tile[(base + m * stp) * TP + p] : T(0);
-      for (int i = 0; i < nk; ++i) tile[(base + i * stp) * TP + p] = row_dot<NK>(U + i * NK, x);
+        for (int m = 0; m < HK; ++m) {
+          if (m < h) {
+            const T x0 = fib[m * step];
+            if (2 * m + 1 == nk) {
+              a[m] = x0;
+              b[m] = x0;
+            } else {
+              const T x1 = fib[(nk - 1 - m) * step];
+              a[m] = x0 + x1;
+              b[m] = x0 - x1;
+            }
+          } else {
+            a[m] = T(0);
+            b[m] = T(0);
+          }
+        }
+        for (int i = 0; i < nk; i += 2) {
+          fib[i * step] = row_dot<HK>(U + i * NK, a);
+          if (i + 1 < nk) fib[(i + 1) * step] = row_dot<HK>(U + (i + 1) * NK, b);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < HK; ++i) {
+          a[i] = (2 * i < nk) ? fib[2 * i * step] : T(0);
+          b[i] = (2 * i + 1 < nk) ? fib[(2 * i + 1) * step] : T(0);
+        }
+        for (int m = 0; m < h; ++m) {
+          const T e = row_dot<HK>(U + m * 2 * HK, a), o = row_dot<HK>(U + m * 2 * HK + HK, b);
+          fib[m * step] = e + o;
+          if (2 * m + 1 != nk) fib[(nk - 1 - m) * step] = e - o;
+        }
+      }
     }
     __syncthreads();
   }
@@ -760,4 +809,19 @@ size_t tube_smem_bytes(tr_dtype dt, int n, const TransformDesc &td, int *tp_out)
   if (tp_out) *tp_out = tp;
   if (!tp) return 0;
   return dt == TR_F64 ? tube_smem_for<double>(n, td, tp) : tube_smem_for<float>(n, td, tp);
+}
+
+// Elements of the matrix buffer for the transformed modes: per mode the
+// forward rows (dim x nkpad) and the folded inverse rows (ceil(dim/2) x 2 HK).
+int transform_mats_layout(TransformDesc &td) {
+  const int hk = ((td.nkpad / 2 + 3) / 4) * 4;
+  int off = 0;
+  for (int k = 0; k < td.nt; ++k) {
+    td.off_fwd[k] = off;
+    off += td.dim[k] * td.nkpad;
+    td.off_inv[k] = off;
+    off += ((td.dim[k] + 1) / 2) * 2 * hk;
+  }
+  td.mats_len = off < 4 ? 4 : ((off + 3) / 4) * 4;
+  return hk;
 }

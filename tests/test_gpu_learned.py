@@ -272,3 +272,50 @@ def test_learned_step_recovers_like_the_plain_width(model):
     assert widths["learned"].mean() < 0.5 * 74, widths["learned"].mean()
     # certificate holds on the last pass: kept rank <= width - p below l_max
     assert np.all((kept <= widths["learned"] - 10) | (widths["learned"] == 74))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("model,prec", [("previous_rank", tr.TR_PREC_FP32),
+                                        ("trained", tr.TR_PREC_BF16X3),
+                                        ("trained", tr.TR_PREC_BF16)])
+def test_learned_full_size_sampled(model, prec):
+    # the 512 x 512 x 32 x 16 power-law shape (512 slices of rank 2..64,
+    # l_max = 64 + 10) in the launch configuration of a step: the first pass
+    # runs at l_max, the second at the planned widths.  Every width above the
+    # rank gives the exact prox and the certificate catches the rest, so the
+    # kept ranks equal the slice ranks bit for bit on all 512 slices, and
+    # four sampled slices match the FP64 full-SVD prox (split BF16 at the
+    # FP32 bound, plain BF16 products at 1e-3)
+    import os
+    if model == "trained" and not os.path.exists(tr.DEFAULT_MODEL):
+        pytest.skip("no trained weights file")
+    n, n1, n2, p, lmax = 512, 512, 512, 10, 74
+    ranks = synth.powerlaw_ranks(n, np.random.default_rng(512))
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, ranks, 0.0, seed=513)
+    tau = 0.1        # the smallest nonzero singular value is above 10
+    h = _learned_handle((n1, n2, 32, 16), 64, p, prec=prec,
+                        **({} if model == "previous_rank"
+                           else {"model_path": tr.DEFAULT_MODEL.encode()}))
+    if model == "previous_rank":
+        h.set_model(previous_rank_model())
+    Ad = dev(Ab)
+    tol = 1e-3 if prec == tr.TR_PREC_BF16 else 1e-4
+    sample = (0, 129, 300, 511)
+    refs = {j: svt.slice_prox_full(Ab[j], tau, prox.L1)[0] for j in sample}
+    del Ab
+    for t in range(2):
+        G = h.slice_prox(Ad, tau, t)
+        _, kept = h.slice_stats()
+        w = h.slice_widths()
+        assert np.array_equal(kept, ranks), (t, np.flatnonzero(kept != ranks)[:8])
+        assert np.all((w == lmax) | (kept <= w - p)), t
+        if t == 0:
+            assert np.all(w == lmax)
+        elif model == "previous_rank":
+            want = np.minimum((ranks + p + 7) // 8 * 8, lmax)
+            assert np.all(w >= want) and w.mean() < lmax - 20
+        for j in sample:
+            err = relF(host(G[j]), refs[j])
+            assert err < tol, (t, j, err)
+        del G
+    h.close()
