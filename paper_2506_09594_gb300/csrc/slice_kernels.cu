@@ -545,12 +545,24 @@ __global__ void qr_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel 
 // ordering, l/2 disjoint pairs per round; each pair is handled by a group
 // of G lanes that split the rows, so its inner products need log2(G)
 // shuffle levels.
+// The FP32 form takes its square roots and reciprocals from the special
+// function unit (rsqrtf, __frcp_rn): a rotation only has to be accurate to
+// a few units in the last place (the sweeps correct the angle, and c, s
+// come from one t, so c^2 + s^2 = 1 to rounding); it sits on the latency
+// chain of every round.
+template <typename T>
+__device__ __forceinline__ bool jacobi_wants(T al, T be, T ga, T tol) {
+  if constexpr (sizeof(T) == 4) return ga != T(0) && fabsf(ga) * rsqrtf(al) * rsqrtf(be) > tol;
+  else return ga != T(0) && fabs(ga) > tol * sqrt(al * be);
+}
+
 template <typename T>
 __device__ __forceinline__ void jacobi_rotation(T al, T be, T ga, T &c, T &s) {
   if constexpr (sizeof(T) == 4) {
     const T zeta = T(0.5) * (be - al) * __frcp_rn(ga);
     const T az = fabsf(zeta);
-    const T t = az > T(1e10) ? T(0.5) / az : T(1) / (az + sqrtf(fmaf(az, az, T(1))));
+    const T r2 = fmaf(az, az, T(1));
+    const T t = az > T(1e10) ? T(0.5) * __frcp_rn(az) : __frcp_rn(az + r2 * rsqrtf(r2));
     const T ts = zeta >= T(0) ? t : -t;
     c = rsqrtf(fmaf(ts, ts, T(1)));
     s = c * ts;
@@ -571,7 +583,10 @@ __device__ __forceinline__ void named_sync(int nthr) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
 }
 
-template <typename T, int G>
+// A lane holds its rows of the pair's two columns of W and J in registers
+// between the inner products and the rotation (JR >= ceil(l / G) rows), so
+// the J loads overlap the reductions and the update needs no reloads.
+template <typename T, int G, int JR>
 __device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps, int nthr) {
   const int lp = l + (l & 1);
   if (lp < 2 || (int)threadIdx.x >= nthr) return;
@@ -596,31 +611,39 @@ __device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps
         }
         const bool valid = pi < npairs && q < l;
         T *wp = W + (size_t)p * l, *wq = W + (size_t)q * l;
+        T *jp = J + (size_t)p * l, *jq = J + (size_t)q * l;
+        T x[JR], y[JR], u[JR], v[JR];
         T al = T(0), be = T(0), ga = T(0);
-        if (valid)
-          for (int i = gl; i < l; i += G) {
-            const T x = wp[i], y = wq[i];
-            al = fma(x, x, al);
-            be = fma(y, y, be);
-            ga = fma(x, y, ga);
-          }
+#pragma unroll
+        for (int t = 0; t < JR; ++t) {
+          const int i = gl + G * t;
+          const bool in = valid && i < l;
+          x[t] = in ? wp[i] : T(0);
+          y[t] = in ? wq[i] : T(0);
+          u[t] = in ? jp[i] : T(0);
+          v[t] = in ? jq[i] : T(0);
+          al = fma(x[t], x[t], al);
+          be = fma(y[t], y[t], be);
+          ga = fma(x[t], y[t], ga);
+        }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (valid && ga != T(0) && fabs(ga) > tol * sqrt(al * be)) {
+        if (valid && jacobi_wants(al, be, ga, tol)) {
           T c, s;
           jacobi_rotation(al, be, ga, c, s);
-          T *jp = J + (size_t)p * l, *jq = J + (size_t)q * l;
-          for (int i = gl; i < l; i += G) {
-            const T x = wp[i], y = wq[i];
-            wp[i] = c * x - s * y;
-            wq[i] = s * x + c * y;
-            const T u = jp[i], w = jq[i];
-            jp[i] = c * u - s * w;
-            jq[i] = s * u + c * w;
+#pragma unroll
+          for (int t = 0; t < JR; ++t) {
+            const int i = gl + G * t;
+            if (i < l) {
+              wp[i] = c * x[t] - s * y[t];
+              wq[i] = s * x[t] + c * y[t];
+              jp[i] = c * u[t] - s * v[t];
+              jq[i] = s * u[t] + c * v[t];
+            }
           }
           if (gl == 0) *flag = 1;
         }
@@ -651,7 +674,7 @@ __device__ __forceinline__ T prox_sv(T s, const ShrinkScalars &sh) {
 
 // Per slice: QR of B^T (P2), Jacobi SVD of R, shrink, core C, then
 // P1 <- P1 C (= Q C) and P2 <- Qb, ready for Gbar = P1 P2^T.
-template <typename T, int CPW, int RPL, int G, bool REG>
+template <typename T, int CPW, int RPL, int G, int JR, bool REG>
 __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64_t sP1,
                                 T *__restrict__ P2, int64_t sP2, ShrinkScalars sh,
                                 T *__restrict__ sig_out, int ldsig,
@@ -687,7 +710,7 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     int nthr = ((lp / 2) * G + 31) / 32 * 32;
     if (nthr > (int)blockDim.x) nthr = blockDim.x;
     __syncthreads();
-    block_jacobi<T, G>(W, J, l, flag, tol, sizeof(T) == 4 ? 16 : 30, nthr);
+    block_jacobi<T, G, JR>(W, J, l, flag, tol, sizeof(T) == 4 ? 16 : 30, nthr);
     __syncthreads();
   }
 
@@ -801,11 +824,11 @@ cudaError_t run_qr_t(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) {
   return cudaGetLastError();
 }
 
-template <typename T, int CPW, int RPL, int G>
+template <typename T, int CPW, int RPL, int G, int JR>
 cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh, T *sig,
                       int ldsig, int *rank, int *width, cudaStream_t s, SliceSel sel) {
   const size_t smem = svd_smem<T>(n1, n2, l);
-  auto k = svd_core_kernel<T, CPW, RPL, G, true>;
+  auto k = svd_core_kernel<T, CPW, RPL, G, JR, true>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int lp = l + (l & 1);
@@ -816,7 +839,7 @@ cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkSc
   bool fits = false;
   if ((e = fits_one_block(k, 32 * nw, smem, fits)) != cudaSuccess) return e;
   if (!fits) {
-    auto k2 = svd_core_kernel<T, 4, 1, G, false>;
+    auto k2 = svd_core_kernel<T, 4, 1, G, JR, false>;
     if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
       return e;
@@ -851,11 +874,12 @@ cudaError_t run_svd_core(int n1, int n2, int l, T *P1, T *P2, int n, const Shrin
                          T *sig, int *rank, cudaStream_t s, SliceSel sel = SliceSel{},
                          int ldsig = 0, int *width = nullptr) {
 #define TR_SVD_ARGS n1, n2, l, P1, P2, n, sh, sig, ldsig, rank, width, s, sel
+  // eight lanes per Jacobi pair; JR = rows of a pair's columns per lane
   if (pick_cpw(l) == 2) {
-    if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 4>(TR_SVD_ARGS))) }
-    TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8>(TR_SVD_ARGS)))
+    if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8, 4>(TR_SVD_ARGS))) }
+    TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8, 8>(TR_SVD_ARGS)))
   }
-  TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8>(TR_SVD_ARGS)))
+  TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 4, RPL, 8, 16>(TR_SVD_ARGS)))
 #undef TR_SVD_ARGS
 }
 
