@@ -257,6 +257,14 @@ cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStr
   umma::Args a{g.M, g.N, g.K, (const float *)g.A, g.sAb, g.sAi, g.sAk, (const float *)g.B,
                g.sBb, g.sBk, g.sBn, (float *)g.C, g.sCb, g.sCi, g.sCn,
                g.sel.ids, g.sel.count, g.a_by_id, g.c_by_id};
+  // the operand A (Abar) is streamed from HBM; its next K chunk is prefetched
+  // into L2 when A is a plain slice-major array
+  if (g.sAk == 1 && g.sAb == (int64_t)g.M * g.sAi)
+    a.a_pf = encode_tensor_2d(&a.amap, g.A, false, g.K, (int64_t)batch * g.M, g.sAi, umma::kKC,
+                              umma::kBM);
+  else if (g.sAi == 1 && g.sAb == (int64_t)g.K * g.sAk)
+    a.a_pf = encode_tensor_2d(&a.amap, g.A, false, g.M, (int64_t)batch * g.K, g.sAk, umma::kBM,
+                              umma::kKC);
   const unsigned ntiles = g.N <= 128 ? 1u : (unsigned)((g.N + 127) / 128);
   const dim3 grid((g.M + umma::kBM - 1) / umma::kBM, ntiles, batch);
 #define TR_UMMA(NP, SP)                                                                        \

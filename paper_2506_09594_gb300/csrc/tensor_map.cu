@@ -1,0 +1,72 @@
+// Tensor maps (TMA descriptors) for 2D views of device arrays, encoded through
+// the driver entry point cuTensorMapEncodeTiled and cached by view.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tr_internal.cuh"
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+struct MapEntry {
+  const void *base;
+  int64_t cols, rows, stride;
+  int bx, by, u8;
+  CUtensorMap map;
+};
+
+constexpr int kCacheSize = 128;
+
+}  // namespace
+
+bool encode_tensor_2d(CUtensorMap *out, const void *base, bool u8, int64_t cols, int64_t rows,
+                      int64_t row_stride, int box_cols, int box_rows) {
+  static std::mutex mu;
+  static MapEntry cache[kCacheSize];
+  static int used = 0, next = 0;
+  const int esz = u8 ? 1 : 4;
+  if (!base || (uintptr_t)base % 16 != 0 || (row_stride * esz) % 16 != 0 || cols < 1 ||
+      rows < 1 || box_cols < 1 || box_cols > 256 || box_rows < 1 || box_rows > 256 ||
+      (box_cols * esz) % 16 != 0)
+    return false;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < used; ++i) {
+    const MapEntry &c = cache[i];
+    if (c.base == base && c.cols == cols && c.rows == rows && c.stride == row_stride &&
+        c.bx == box_cols && c.by == box_rows && c.u8 == (int)u8) {
+      *out = c.map;
+      return true;
+    }
+  }
+  auto fn = tmap_encoder();
+  if (!fn) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)(row_stride * esz)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  CUtensorMap m;
+  if (fn(&m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+         const_cast<void *>(base), dim, stride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  cache[next] = MapEntry{base, cols, rows, row_stride, box_cols, box_rows, (int)u8, m};
+  next = (next + 1) % kCacheSize;
+  if (used < kCacheSize) ++used;
+  *out = m;
+  return true;
+}

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libtr translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -64,6 +65,15 @@ struct ShrinkScalars {
 // Residual slots written with atomicMax on the bit pattern of a
 // non-negative double.
 enum { RES_DL = 0, RES_DE = 1, RES_LG = 2, RES_DG = 3, RES_CONS = 4, RES_COUNT = 5 };
+
+// ---- tensor maps (tensor_map.cu) ----
+// A 2D tensor map of `rows` rows of `cols` elements (FP32, or bytes when
+// u8), rows `row_stride` elements apart, with boxes of box_cols x box_rows;
+// cached by view.  False when the view breaks a tensor-copy rule (16-byte
+// aligned base and row stride, box edge <= 256, box rows of 16-byte
+// multiples) or the driver refuses it.
+bool encode_tensor_2d(CUtensorMap *out, const void *base, bool u8, int64_t cols, int64_t rows,
+                      int64_t row_stride, int box_cols, int box_rows);
 
 // ---- tube passes (tube_kernels.cu) ----
 cudaError_t launch_tube_forward(tr_dtype dt, int64_t P, int n, const TransformDesc &td,

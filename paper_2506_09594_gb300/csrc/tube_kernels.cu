@@ -18,13 +18,10 @@
 // SM before the forward pass uses them).
 // All three reduce their share of the Eq. convercon infinity norms.
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
 
 #include <initializer_list>
-#include <mutex>
 
 #include "tr_internal.cuh"
 
@@ -774,62 +771,6 @@ cudaError_t inv_t(int64_t P, int n, const TransformDesc &td, const void *mats, c
                                   flags, s);
 }
 
-// ---- tensor maps for the TMA form of the fused pass ------------------------
-PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
-// A slice-major array (n rows of P elements) as a 2D tensor with boxes of
-// bx positions x by rows.  Encoded maps are cached by (address, shape, box).
-struct MapEntry {
-  const void *base;
-  int64_t P;
-  int n, bx, by, u8;
-  CUtensorMap map;
-};
-
-bool encode_rows(CUtensorMap *out, const void *base, bool u8, int64_t P, int n, int bx, int by) {
-  static std::mutex mu;
-  static MapEntry cache[64];
-  static int used = 0, next = 0;
-  std::lock_guard<std::mutex> lock(mu);
-  for (int i = 0; i < used; ++i) {
-    const MapEntry &c = cache[i];
-    if (c.base == base && c.P == P && c.n == n && c.bx == bx && c.by == by && c.u8 == (int)u8) {
-      *out = c.map;
-      return true;
-    }
-  }
-  auto fn = tmap_encoder();
-  if (!fn) return false;
-  const cuuint64_t dim[2] = {(cuuint64_t)P, (cuuint64_t)n};
-  const cuuint64_t stride[1] = {(cuuint64_t)P * (u8 ? 1u : 4u)};
-  const cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
-  const cuuint32_t es[2] = {1, 1};
-  CUtensorMap m;
-  if (fn(&m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-         const_cast<void *>(base), dim, stride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return false;
-  MapEntry &slot = cache[next];
-  slot = MapEntry{base, P, n, bx, by, (int)u8, m};
-  next = (next + 1) % 64;
-  if (used < 64) ++used;
-  *out = m;
-  return true;
-}
-
 // Prefetch maps for an FP32 fused launch with 16-byte packs, P and the tile
 // a multiple of 16 (mask rows and tensor-copy x coordinates on 16-byte
 // boundaries).  False: the launch runs without prefetch.
@@ -844,14 +785,14 @@ bool fused_prefetch_maps(const TubeLaunch &g, const void *Gbar, const void *M, c
   pf.RBG = (g.n + pf.nbox - 1) / pf.nbox;
   const int rows = kTubeThreads * kUnroll / (g.tp / 4);
   if (rows < 1 || rows > 256) return false;
-  pf.pf = encode_rows(&pf.tm.gbar, Gbar, false, g.P, g.n, g.tp, pf.RBG) &&
-          encode_rows(&pf.tm.m, M, false, g.P, g.n, g.tp, rows) &&
-          encode_rows(&pf.tm.l, L, false, g.P, g.n, g.tp, rows) &&
-          encode_rows(&pf.tm.e, E, false, g.P, g.n, g.tp, rows) &&
-          encode_rows(&pf.tm.y, Y, false, g.P, g.n, g.tp, rows) &&
-          encode_rows(&pf.tm.g, G, false, g.P, g.n, g.tp, rows) &&
-          encode_rows(&pf.tm.lam, Lam, false, g.P, g.n, g.tp, rows) &&
-          encode_rows(&pf.tm.mask, mask, true, g.P, g.n, g.tp, rows);
+  pf.pf = encode_tensor_2d(&pf.tm.gbar, Gbar, false, g.P, g.n, g.P, g.tp, pf.RBG) &&
+          encode_tensor_2d(&pf.tm.m, M, false, g.P, g.n, g.P, g.tp, rows) &&
+          encode_tensor_2d(&pf.tm.l, L, false, g.P, g.n, g.P, g.tp, rows) &&
+          encode_tensor_2d(&pf.tm.e, E, false, g.P, g.n, g.P, g.tp, rows) &&
+          encode_tensor_2d(&pf.tm.y, Y, false, g.P, g.n, g.P, g.tp, rows) &&
+          encode_tensor_2d(&pf.tm.g, G, false, g.P, g.n, g.P, g.tp, rows) &&
+          encode_tensor_2d(&pf.tm.lam, Lam, false, g.P, g.n, g.P, g.tp, rows) &&
+          encode_tensor_2d(&pf.tm.mask, mask, true, g.P, g.n, g.P, g.tp, rows);
   return pf.pf;
 }
 

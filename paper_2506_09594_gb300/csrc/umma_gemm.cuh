@@ -24,6 +24,7 @@
 // TMEM before returning.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -136,7 +137,20 @@ struct Args {
   const int *ids = nullptr;
   const int *count = nullptr;
   int a_by_id = 0, c_by_id = 0;
+  // optional L2 prefetch of A's next K chunk (a_pf != 0) through a tensor map
+  // of A as a 2D view: slices x M rows of K elements (box 64 x 128) when k is
+  // contiguous (sAk == 1), slices x K rows of M elements (box 128 x 64) when
+  // m is (sAi == 1)
+  int a_pf = 0;
+  CUtensorMap amap;
 };
+
+__device__ __forceinline__ void l2_prefetch_2d(const CUtensorMap *map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
 
 // Round x to BF16 (hi) and, for the split form, its remainder (lo).
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
@@ -228,7 +242,8 @@ template <int NP, int SPLIT>
 constexpr int min_blocks() { return (SPLIT == 1 && NP <= 64) ? 4 : 1; }
 
 template <int NP, int SPLIT>
-__global__ void __launch_bounds__(kThreads, min_blocks<NP, SPLIT>()) gemm_kernel(Args g, int *err) {
+__global__ void __launch_bounds__(kThreads, min_blocks<NP, SPLIT>())
+    gemm_kernel(const __grid_constant__ Args g, int *err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base_s;
@@ -270,9 +285,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks<NP, SPLIT>()) gemm_kernel
   uint32_t issued[2] = {0, 0};
   Stager<kBM> sa;
   Stager<NP> sb;
+  const int64_t aslice = g.a_by_id ? jb : b;
 #pragma unroll 1
   for (int ci = 0; ci < nchunks; ++ci) {
     const int h = ci & 1;
+    if (g.a_pf && threadIdx.x == 0 && ci + 1 < nchunks) {   // warm L2 for the next chunk
+      if (g.sAk == 1) l2_prefetch_2d(&g.amap, (ci + 1) * kKC, (int)(aslice * g.M + m0));
+      else l2_prefetch_2d(&g.amap, m0, (int)(aslice * g.K + (ci + 1) * kKC));
+    }
     sa.load(A, g.sAi, g.sAk, g.M, m0, ci * kKC, g.K, a_vec);
     sb.load(B, g.sBn, g.sBk, g.N, n0, ci * kKC, g.K, b_vec);
     uint8_t *st = smem + h * Lay::stage_bytes;
