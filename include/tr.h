@@ -181,9 +181,23 @@ tr_status tr_slice_prox(tr_handle *h, const void *Abar, void *Gbar,
  * shape, dtype and layout as at tr_init; caller-owned, valid until the next
  * call or tr_free).  Later steps read them; the iterate is kept.  For
  * streaming inputs: copy the next step's data into a second buffer on
- * another stream while a step runs.  A captured step graph (tr_graph_mode)
- * is re-captured at the next steady-state step.  Errors: TR_EINVAL (NULL).  */
+ * another stream while a step runs.  Captured step graphs (tr_graph_mode)
+ * are kept per (observed, mask) pair, two at a time, so alternating between
+ * two buffer pairs replays without re-capturing.  Errors: TR_EINVAL (NULL).  */
 tr_status tr_set_observed(tr_handle *h, const void *observed, const uint8_t *mask);
+
+/* Enqueue on the handle's stream a copy of the residual maxima (Eq.
+ * convercon) of the last enqueued step into res_host[0 .. 10): host memory,
+ * caller-owned; pinned memory keeps the call asynchronous.  The values are
+ * there once the stream has passed this point.
+ *   res_host[0..5): the step's slots in tr_step_info.res_inf order.  A step
+ *     without a report defers its inverse pass to the next step, so its
+ *     ||L-G|| and ||dG|| slots are 0;
+ *   res_host[5..10): ||L-G|| and ||dG|| (entries 7 and 8) of the step before,
+ *     completed by this step's fused pass; the other entries are 0.
+ * No host synchronisation, so a graph-replayed step can be followed by it.
+ * Errors: TR_EINVAL (NULL), TR_ECUDA.                                        */
+tr_status tr_read_residuals(tr_handle *h, double *res_host);
 
 /* Per-slice singular values and kept ranks of the last slice pass (host
  * buffers: sigma n*l doubles, ranks n ints; either may be NULL).  `l` is

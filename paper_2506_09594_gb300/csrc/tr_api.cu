@@ -45,9 +45,16 @@ struct tr_handle {
   cudaStream_t side[kSideStreams] = {};
   cudaEvent_t side_fork = nullptr, side_join[kSideStreams] = {};
   // graph replay of steady-state steps (tr_graph_mode)
+  // Captured steps are kept per observed-data pair (tr_set_observed), so that
+  // double-buffered inputs replay two graphs instead of re-capturing.
   bool graph_on = false;
   cudaStream_t gstream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  struct GraphSlot {
+    const void *M = nullptr;
+    const uint8_t *mask = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  } gx[2];
+  int gx_next = 0;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   uint64_t graph_kernels = 0;                 // kernels in one replay
   unsigned long long *res = nullptr;          // RES_COUNT slots
@@ -152,7 +159,8 @@ static void free_all(tr_handle *h) {
     if (h->side_join[i]) cudaEventDestroy(h->side_join[i]);
   }
   if (h->side_fork) cudaEventDestroy(h->side_fork);
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto &g : h->gx)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
   if (h->gev_out) cudaEventDestroy(h->gev_out);
@@ -566,6 +574,8 @@ static tr_status enqueue_step(tr_handle *h, bool pending, bool with_inverse, cud
   sc.dmu = &h->sched->mu;
   sc.lambda = h->prm.lambda;
   cudaError_t e = cudaMemsetAsync(h->res, 0, RES_COUNT * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->res_prev, 0, RES_COUNT * sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[0], h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) {
@@ -626,21 +636,54 @@ static tr_status capture_step(tr_handle *h) {
   h->graph_kernels = h->launches - before;
   h->launches = before;
   if (st == TR_OK) {
-    e = cudaGraphInstantiate(&h->gexec, g, 0);
-    if (e != cudaSuccess) st = fail(h, TR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    tr_handle::GraphSlot &slot = h->gx[h->gx_next];
+    if (slot.exec) {
+      cudaGraphExecDestroy(slot.exec);
+      slot.exec = nullptr;
+    }
+    e = cudaGraphInstantiate(&slot.exec, g, 0);
+    if (e != cudaSuccess) {
+      slot.exec = nullptr;
+      st = fail(h, TR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    } else {
+      slot.M = h->M;
+      slot.mask = h->mask;
+      h->gx_next ^= 1;
+    }
   }
   if (g) cudaGraphDestroy(g);
   return st;
 }
 
+// Forget every captured step (their kernels hold settings that changed).
+static tr_status drop_graphs(tr_handle *h) {
+  bool any = false;
+  for (auto &g : h->gx) any |= g.exec != nullptr;
+  if (!any) return TR_OK;
+  TR_CUDA(h, cudaStreamSynchronize(h->gstream));
+  for (auto &g : h->gx) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = tr_handle::GraphSlot{};
+  }
+  return TR_OK;
+}
+
+static cudaGraphExec_t find_graph(tr_handle *h) {
+  for (auto &g : h->gx)
+    if (g.exec && g.M == h->M && g.mask == h->mask) return g.exec;
+  return nullptr;
+}
+
 static tr_status replay_step(tr_handle *h) {
-  if (!h->gexec) {
+  cudaGraphExec_t exec = find_graph(h);
+  if (!exec) {
     tr_status st = capture_step(h);
     if (st != TR_OK) return st;
+    exec = find_graph(h);
   }
   TR_CUDA(h, cudaEventRecord(h->gev_in, h->stream));
   TR_CUDA(h, cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
-  TR_CUDA(h, cudaGraphLaunch(h->gexec, h->gstream));
+  TR_CUDA(h, cudaGraphLaunch(exec, h->gstream));
   TR_CUDA(h, cudaEventRecord(h->gev_out, h->gstream));
   TR_CUDA(h, cudaStreamWaitEvent(h->stream, h->gev_out, 0));
   h->launches += h->graph_kernels;
@@ -1084,24 +1127,30 @@ extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups)
       }
     if (!found) g_tune_cache.push_back({key, TuneChoice{best_tp, best_g}});
   }
-  if (h->gexec) {   // a captured step holds the old choices
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
+  {   // a captured step holds the old choices
+    tr_status st = drop_graphs(h);
+    if (st != TR_OK) return st;
   }
   if (tile) *tile = best_tp;
   if (groups) *groups = best_g;
   return TR_OK;
 }
 
+extern "C" tr_status tr_read_residuals(tr_handle *h, double *res_host) {
+  if (!h || !res_host) return TR_EINVAL;
+  // the slots hold the bit patterns of non-negative doubles (atomicMax)
+  static_assert(sizeof(double) == sizeof(unsigned long long), "64-bit slots");
+  TR_CUDA(h, cudaMemcpyAsync(res_host, h->res, RES_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  TR_CUDA(h, cudaMemcpyAsync(res_host + RES_COUNT, h->res_prev, RES_COUNT * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  return TR_OK;
+}
+
 extern "C" tr_status tr_set_observed(tr_handle *h, const void *observed, const uint8_t *mask) {
   if (!h || !observed || !mask) return TR_EINVAL;
   h->M = observed;
-  h->mask = mask;
-  if (h->gexec) {   // a captured step holds the old pointers
-    TR_CUDA(h, cudaStreamSynchronize(h->gstream));
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-  }
+  h->mask = mask;   // captured steps are looked up by these pointers
   return TR_OK;
 }
 
@@ -1114,13 +1163,9 @@ extern "C" tr_status tr_set_tube_tile(tr_handle *h, int tp) {
     for (int c = 0; c < nc; ++c) ok = ok || cand[c] == tp;
     if (!ok) return fail(h, TR_EINVAL, "tube tile %d does not fit", tp);
   }
+  TR_CUDA(h, cudaStreamSynchronize(h->stream));
   h->td.tp = tp;
-  if (h->gexec) {
-    TR_CUDA(h, cudaStreamSynchronize(h->stream));
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-  }
-  return TR_OK;
+  return drop_graphs(h);
 }
 
 extern "C" tr_status tr_set_slice_groups(tr_handle *h, int groups) {
@@ -1142,11 +1187,7 @@ extern "C" tr_status tr_set_slice_groups(tr_handle *h, int groups) {
   }
   TR_CUDA(h, cudaStreamSynchronize(h->stream));
   h->slice_groups = groups;
-  if (h->gexec) {
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-  }
-  return TR_OK;
+  return drop_graphs(h);
 }
 
 // ---- batches of independent problems ----------------------------------------

@@ -107,6 +107,7 @@ _SIGS = {
     "tr_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, _P, _P]),
     "tr_set_observed": (ctypes.c_int, [_P, _P, _P]),
+    "tr_read_residuals": (ctypes.c_int, [_P, _P]),
     "tr_graph_mode": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_set_tube_tile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_set_slice_groups": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -412,6 +413,17 @@ class Handle:
 
     def graph_mode(self, on=True):
         _check(load().tr_graph_mode(self.h, int(bool(on))), self.h)
+
+    def read_residuals(self, out):
+        """tr_read_residuals: enqueue the copy of the last step's residual
+        maxima into `out`, a CPU float64 tensor of 10 entries (pinned for an
+        asynchronous copy); valid after the handle's stream reaches it."""
+        import torch
+        if out.device.type != "cpu" or out.dtype != torch.float64 or out.numel() < 10 \
+                or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CPU float64 tensor of 10 entries")
+        _check(load().tr_read_residuals(self.h, _ptr(out)), self.h)
+        return out
 
     def set_tube_tile(self, tp):
         _check(load().tr_set_tube_tile(self.h, int(tp)), self.h)

@@ -133,3 +133,4 @@ def test_init_rejects_oversized_problems_without_a_gpu(lib):
     st, _ = _init(lib, 3, [64, 64, 70000])                           # slices > 65535
     assert st == tr.TR_EUNSUPPORTED
     assert lib.tr_set_observed(None, None, None) == tr.TR_EINVAL
+    assert lib.tr_read_residuals(None, None) == tr.TR_EINVAL

@@ -228,3 +228,52 @@ def test_batch_with_a_learned_problem_matches_its_handle():
     assert ok, what
     h.close()
     b.close()
+
+
+def test_graph_replay_with_alternating_observed_buffers():
+    # double-buffered inputs: tr_set_observed alternates between two device
+    # copies of the same data, each with its own captured step; the iterate
+    # and the residuals read back asynchronously (tr_read_residuals) are bit
+    # for bit those of replaying one buffer pair
+    dims = (48, 40, 6, 3)
+    _, M, mask = problem(dims, 11)
+    outs, res = [], []
+    for alternate in (False, True):
+        h = handle(dims, "f32", M, mask, rank=8, oversample=4, seed=5, mu0=0.05)
+        bufs = [(dev(M, "f32"), torch.from_numpy(mask).cuda()) for _ in range(2)]
+        h.graph_mode(True)
+        r = torch.zeros(10 * 8, dtype=torch.float64).pin_memory()
+        for k in range(8):
+            h.set_observed(*bufs[k % 2 if alternate else 0])
+            h.step()
+            h.read_residuals(r[10 * k:10 * k + 10])
+        torch.cuda.synchronize()
+        outs.append(h.get_state())
+        res.append(r.clone())
+        h.close()
+    ok, what = states_equal(outs[0], outs[1])
+    assert ok, what
+    assert torch.equal(res[0], res[1])
+    r = res[0].view(8, 10)
+    # deferred steps: this step's ||dL||, ||dE||, ||M-L-E|| in the first half,
+    # the previous step's ||L-G||, ||dG|| (completed by the fused pass) in the second
+    assert bool((r[:, [2, 3]] == 0).all()), r
+    assert bool((r[0, 5:] == 0).all()) and bool((r[:, [5, 6, 9]] == 0).all()), r
+    assert float(r[1:, 0].max()) > 0 and float(r[1:, 7].max()) > 0, r
+    assert bool(torch.isfinite(r).all()), r
+
+
+def test_read_residuals_match_a_reported_step():
+    dims = (40, 44, 5, 4)
+    _, M, mask = problem(dims, 12)
+    h = handle(dims, "f32", M, mask, rank=8, oversample=4, seed=6)
+    for _ in range(3):
+        h.step()
+    info = h.step(info=True)                 # runs its inverse pass: all five slots
+    r = torch.zeros(10, dtype=torch.float64).pin_memory()
+    h.read_residuals(r)
+    torch.cuda.synchronize()
+    assert np.array_equal(r[:5].numpy(), np.asarray(info["res_inf"]))
+    with pytest.raises(ValueError):
+        h.read_residuals(torch.zeros(4, dtype=torch.float64))
+    h.close()
