@@ -546,6 +546,163 @@ __global__ void qr_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel 
   block_reg_qr<T, CPW, RPL>(P + (int64_t)blockIdx.x * sP, m, l, V, tau, nullptr);
 }
 
+// ------------------------------------- Gram-Schmidt QR for narrow panels
+// Classical Gram-Schmidt with reorthogonalisation ("twice is enough") for
+// panels of at most 32 columns: thread t holds rows t + r*blockDim (r < RPT)
+// of every column in registers, so a column's projection coefficients
+// against all previous columns (and its squared norm) come from one block
+// reduction per pass, and Q needs no separate formation.  A column is
+// accepted after a pass that kept more than half of its squared norm, or
+// after a second or later pass that kept a quarter (it is then orthogonal to
+// the previous columns to working precision); the final norm follows from
+// the last pass by Pythagoras.  A column that stays numerically dependent
+// after four passes restarts from the next unit vector e_u (its R entries
+// are the coefficients found so far, R_jj = 0): Q is always orthonormal and
+// Q R reproduces the panel.  Same span and R up to column signs as the
+// Householder QR, which the parity tests compare through the slice prox.
+constexpr int kCgsCols = 32;
+
+// Sum of V values over the block: `p` per thread in, every thread reads the
+// totals from coef[0..V).  Within a warp a reduce-scatter butterfly: at the
+// level of lane bit b every lane keeps half of its values (the upper half
+// when its bit b is set) and adds its partner's copy of that half, so VP
+// values (V padded to a power of two) cost VP - 1 shuffles plus one per
+// remaining level, and lane L ends with the sum of value idx(L) (the lane's
+// high log2(VP) bits).  red holds nw x 33 partials.
+template <typename T, int V>
+__device__ __forceinline__ void block_sum_vec(T (&p)[kCgsCols + 1], T *red, T *coef) {
+  constexpr int VP = V <= 1 ? 1 : V <= 2 ? 2 : V <= 4 ? 4 : V <= 8 ? 8 : V <= 16 ? 16 : 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = V; v < VP; ++v) p[v] = T(0);
+  int idx = 0;
+#pragma unroll
+  for (int h = VP / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const T give = up ? p[k] : p[k + h];
+      const T keep = up ? p[k + h] : p[k];
+      p[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+    idx += up ? h : 0;
+  }
+  constexpr int LOW = 32 / VP;   // lanes still holding partial sums of one value
+#pragma unroll
+  for (int o = LOW / 2; o > 0; o >>= 1) p[0] += __shfl_xor_sync(0xffffffffu, p[0], o);
+  if ((lane & (LOW - 1)) == 0 && idx < V) red[warp * (kCgsCols + 1) + idx] = p[0];
+  __syncthreads();
+  if (warp == 0 && lane < V) {
+    T t = T(0);
+    for (int w = 0; w < nw; ++w) t += red[w * (kCgsCols + 1) + lane];
+    coef[lane] = t;
+  }
+  __syncthreads();
+}
+
+template <typename T, int RPT, int J>
+__device__ __forceinline__ void cgs_column(T (&x)[RPT][kCgsCols], int m, int l, T *Rout, T *red,
+                                           T *coef) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const T tiny = sizeof(T) == 4 ? T(FLT_MIN) : T(DBL_MIN);
+  int pass = 0, unit = -1, restarts = 0;
+  T after = T(0);
+  while (true) {
+    T p[kCgsCols + 1];
+#pragma unroll
+    for (int i = 0; i <= J; ++i) p[i] = T(0);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+#pragma unroll
+      for (int i = 0; i < J; ++i) p[i] = fma(x[r][i], x[r][J], p[i]);
+      p[J] = fma(x[r][J], x[r][J], p[J]);
+    }
+    block_sum_vec<T, J + 1>(p, red, coef);
+    T c[kCgsCols];
+    T csq = T(0);
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      c[i] = coef[i];
+      csq = fma(c[i], c[i], csq);
+    }
+    const T s = coef[J];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int i = 0; i < J; ++i) x[r][J] = fma(-c[i], x[r][i], x[r][J]);
+    if (Rout && unit < 0 && tid < J) {
+#pragma unroll
+      for (int i = 0; i < J; ++i)
+        if (i == tid) Rout[(size_t)J * l + i] += c[i];
+    }
+    after = s - csq;
+    ++pass;
+    // accept: a pass that kept more than half the squared norm leaves the
+    // column orthogonal to working precision; after a second pass, a
+    // quarter suffices
+    if (after > tiny && (after > T(0.5) * s || (pass >= 2 && after > T(0.25) * s))) break;
+    if (pass >= 4) {   // numerically dependent: continue from a unit vector
+      if (++restarts > m) break;
+      unit = unit < 0 ? J % m : (unit + 1) % m;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) x[r][J] = (tid + r * nthr == unit) ? T(1) : T(0);
+      pass = 0;
+    }
+  }
+  const T nrm = sqrt(after > T(0) ? after : T(0));
+  const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) x[r][J] *= inv;
+  if (Rout && tid == 0) Rout[(size_t)J * l + J] = unit < 0 ? nrm : T(0);
+}
+
+template <typename T, int RPT, int J>
+__device__ __forceinline__ void cgs_columns(T (&x)[RPT][kCgsCols], int m, int l, T *Rout, T *red,
+                                            T *coef) {
+  if constexpr (J < kCgsCols) {
+    if (J >= l) return;
+    cgs_column<T, RPT, J>(x, m, l, Rout, red, coef);
+    cgs_columns<T, RPT, J + 1>(x, m, l, Rout, red, coef);
+  }
+}
+
+// QR of P (global, column-major m x l, ld m, l <= 32, m <= RPT * blockDim):
+// Q overwrites P, R (l x l, column-major, zero below the diagonal) goes to
+// Rout (shared memory) when non-null.  red: (blockDim/32) x 33, coef: 33
+// elements of shared memory.
+template <typename T, int RPT>
+__device__ void block_cgs_qr(T *P, int m, int l, T *Rout, T *red, T *coef) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  T x[RPT][kCgsCols];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int row = tid + r * nthr;
+#pragma unroll
+    for (int c = 0; c < kCgsCols; ++c) x[r][c] = (c < l && row < m) ? P[(size_t)c * m + row] : T(0);
+  }
+  if (Rout)
+    for (int e = tid; e < l * l; e += nthr) Rout[e] = T(0);
+  __syncthreads();
+  cgs_columns<T, RPT, 0>(x, m, l, Rout, red, coef);
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int row = tid + r * nthr;
+    if (row < m)
+#pragma unroll
+      for (int c = 0; c < kCgsCols; ++c)
+        if (c < l) P[(size_t)c * m + row] = x[r][c];
+  }
+}
+
+template <typename T, int RPT>
+__global__ void __launch_bounds__(256) cgs_qr_kernel(int m, int l, T *__restrict__ P, int64_t sP,
+                                                     SliceSel sel) {
+  if (sel.count && (int)blockIdx.x >= *sel.count) return;
+  __shared__ T red[8 * (kCgsCols + 1)];
+  __shared__ T coef[kCgsCols + 1];
+  block_cgs_qr<T, RPT>(P + (int64_t)blockIdx.x * sP, m, l, nullptr, red, coef);
+}
+
 // ------------------------------------------------------ one-sided Jacobi
 // Hestenes one-sided Jacobi on the l x l matrix W (column-major): rotate
 // column pairs until all are mutually orthogonal, accumulating the
@@ -871,8 +1028,20 @@ cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkSc
     default: { constexpr int RPL = 32; return CALL; } \
   }
 
+// Gram-Schmidt QR for panels of at most 32 columns and 512 rows.
+inline bool cgs_panel_ok(int m, int l) { return l <= kCgsCols && m <= 512; }
+
+template <typename T>
+cudaError_t run_cgs_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) {
+  // two rows per thread: at most 128 registers x 256 threads per block
+  const int threads = ((m + 1) / 2 + 31) / 32 * 32;
+  cgs_qr_kernel<T, 2><<<n, threads, 0, s>>>(m, l, P, (int64_t)m * l, sel);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t run_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel = SliceSel{}) {
+  if (cgs_panel_ok(m, l)) return run_cgs_qr<T>(m, l, P, n, s, sel);
   if (pick_cpw(l) == 2) { TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 2, RPL>(m, l, P, n, s, sel))) }
   TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 4, RPL>(m, l, P, n, s, sel)))
 }
