@@ -27,6 +27,7 @@ namespace {
 template <typename T>
 __global__ void sketch_kernel(int64_t per_slice, T *__restrict__ Om, uint32_t k0, uint32_t k1,
                               uint32_t t_host, const int *dt, uint32_t stream, SliceSel sel) {
+  pdl_wait();
   const uint32_t t = dt ? (uint32_t)*dt : t_host;
   const int b = blockIdx.y;
   if (sel.count && b >= *sel.count) return;
@@ -46,6 +47,7 @@ __global__ void sketch_kernel(int64_t per_slice, T *__restrict__ Om, uint32_t k0
       if (m < per_slice) dst[m] = z[i];
     }
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------ batched SIMT GEMM
@@ -68,6 +70,7 @@ struct GemmArgs {
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 bgemm_kernel(GemmArgs g) {
+  pdl_wait();
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ __align__(16) T As[BK][BM + 4];
   __shared__ __align__(16) T Bs[BK][BN + 4];
@@ -157,6 +160,7 @@ bgemm_kernel(GemmArgs g) {
       if (col < g.N) C[row * g.sCi + col * g.sCn] = acc[i][jn];
     }
   }
+  pdl_trigger();
 }
 
 template <typename T>
@@ -164,10 +168,12 @@ cudaError_t bgemm(const GemmArgs &g, int batch, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return cudaSuccess;
   if (g.N <= 32) {
     dim3 grid((g.M + 63) / 64, (g.N + 31) / 32, batch);
-    bgemm_kernel<T, 64, 32, 32, 4, 2><<<grid, 256, 0, s>>>(g);
+    cudaError_t e = launch_pdl(bgemm_kernel<T, 64, 32, 32, 4, 2>, grid, dim3(256), 0, s, g);
+    if (e != cudaSuccess) return e;
   } else {
     dim3 grid((g.M + 63) / 64, (g.N + 63) / 64, batch);
-    bgemm_kernel<T, 64, 64, 16, 4, 4><<<grid, 256, 0, s>>>(g);
+    cudaError_t e = launch_pdl(bgemm_kernel<T, 64, 64, 16, 4, 4>, grid, dim3(256), 0, s, g);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -182,6 +188,7 @@ __global__ void __launch_bounds__(256)
 rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
                    const T *__restrict__ Qb, int64_t sQ, T *__restrict__ C, int64_t sC,
                    int vec_ok, SliceSel sel) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Zs = reinterpret_cast<T *>(smem_raw);          // [l][64]
   T *Qs = Zs + (size_t)l * 64;                       // [l][64]
@@ -231,6 +238,7 @@ rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
         if (col + jj < n2) dst[jj] = acc[i][jj];
     }
   }
+  pdl_trigger();
 }
 
 template <typename T>
@@ -243,10 +251,8 @@ cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T
   const dim3 grid((n1 + 63) / 64, (n2 + 63) / 64, n);
   // 16-byte row stores need n2 % 4 == 0 and a 16-byte aligned base
   const int vec_ok = (n2 % 4 == 0) && ((uintptr_t)C % 16 == 0);
-  rank_update_kernel<T><<<grid, 256, smem, s>>>(n1, n2, l, Z, (int64_t)n1 * l, Qb,
-                                                (int64_t)n2 * l, C, (int64_t)n1 * n2, vec_ok,
-                                                sel);
-  return cudaGetLastError();
+  return launch_pdl(rank_update_kernel<T>, grid, dim3(256), smem, s, n1, n2, l, Z,
+                    (int64_t)n1 * l, Qb, (int64_t)n2 * l, C, (int64_t)n1 * n2, vec_ok, sel);
 }
 
 // Skinny product on the tensor cores (FP32 in/out, column tiles of up to
@@ -273,8 +279,7 @@ cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStr
     const int smem = umma::Layout<NP, SP>::total;                                              \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
     if (e != cudaSuccess) return e;                                                            \
-    k<<<grid, umma::kThreads, smem, s>>>(a, err);                                              \
-    return cudaGetLastError();                                                                 \
+    return launch_pdl(k, grid, dim3(umma::kThreads), smem, s, a, err);                        \
   }
   if (g.N <= 32) {
     if (split > 1) TR_UMMA(32, 3) else TR_UMMA(32, 1)
@@ -531,19 +536,23 @@ __device__ void block_smem_qr(T *P, int m, int l, T *S, T *tau, T *Rout) {
 
 template <typename T>
 __global__ void qr_smem_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel sel) {
+  pdl_wait();
   if (sel.count && (int)blockIdx.x >= *sel.count) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = reinterpret_cast<T *>(smem_raw);
   block_smem_qr<T>(P + (int64_t)blockIdx.x * sP, m, l, S, S + (size_t)m * l, nullptr);
+  pdl_trigger();
 }
 
 template <typename T, int CPW, int RPL>
 __global__ void qr_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel sel) {
+  pdl_wait();
   if (sel.count && (int)blockIdx.x >= *sel.count) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *V = reinterpret_cast<T *>(smem_raw);
   T *tau = V + (size_t)m * l;
   block_reg_qr<T, CPW, RPL>(P + (int64_t)blockIdx.x * sP, m, l, V, tau, nullptr);
+  pdl_trigger();
 }
 
 // ------------------------------------- Gram-Schmidt QR for narrow panels
@@ -697,10 +706,12 @@ __device__ void block_cgs_qr(T *P, int m, int l, T *Rout, T *red, T *coef) {
 template <typename T, int RPT>
 __global__ void __launch_bounds__(256) cgs_qr_kernel(int m, int l, T *__restrict__ P, int64_t sP,
                                                      SliceSel sel) {
+  pdl_wait();
   if (sel.count && (int)blockIdx.x >= *sel.count) return;
   __shared__ T red[8 * (kCgsCols + 1)];
   __shared__ T coef[kCgsCols + 1];
   block_cgs_qr<T, RPT>(P + (int64_t)blockIdx.x * sP, m, l, nullptr, red, coef);
+  pdl_trigger();
 }
 
 // ------------------------------------------------------ one-sided Jacobi
@@ -845,6 +856,7 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
                                 T *__restrict__ sig_out, int ldsig,
                                 int *__restrict__ rank_out, int *__restrict__ width_out,
                                 SliceSel sel) {
+  pdl_wait();
   if (sel.count && (int)blockIdx.x >= *sel.count) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int mx = n1 > n2 ? n1 : n2;
@@ -924,6 +936,7 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     for (int u = 0; u < 4; ++u)
       if (b0 + u < l) P1j[(size_t)(b0 + u) * n1 + r] = acc[u];
   }
+  pdl_trigger();
 }
 
 // Threads for the panel kernels: each warp owns at most CPW columns.
@@ -978,13 +991,15 @@ cudaError_t run_qr_t(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) {
   bool fits = false;
   if ((e = fits_one_block(k, threads, smem, fits)) != cudaSuccess) return e;
   if (fits) {
-    k<<<n, threads, smem, s>>>(m, l, P, (int64_t)m * l, sel);
+    e = launch_pdl(k, dim3(n), dim3(threads), smem, s, m, l, P, (int64_t)m * l, sel);
+    if (e != cudaSuccess) return e;
   } else {
     auto k2 = qr_smem_kernel<T>;
     if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
       return e;
-    k2<<<n, 32 * kSmemPanelWarps, smem, s>>>(m, l, P, (int64_t)m * l, sel);
+    e = launch_pdl(k2, dim3(n), dim3(32 * kSmemPanelWarps), smem, s, m, l, P, (int64_t)m * l, sel);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -1009,13 +1024,11 @@ cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkSc
         cudaSuccess)
       return e;
     nw = jw > kSmemPanelWarps ? (jw > 32 ? 32 : jw) : kSmemPanelWarps;
-    k2<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig,
-                                ldsig > l ? ldsig : l, rank, width, sel);
-    return cudaGetLastError();
+    return launch_pdl(k2, dim3(n), dim3(32 * nw), smem, s, n1, n2, l, P1, (int64_t)n1 * l, P2,
+                      (int64_t)n2 * l, sh, sig, ldsig > l ? ldsig : l, rank, width, sel);
   }
-  k<<<n, 32 * nw, smem, s>>>(n1, n2, l, P1, (int64_t)n1 * l, P2, (int64_t)n2 * l, sh, sig,
-                             ldsig > l ? ldsig : l, rank, width, sel);
-  return cudaGetLastError();
+  return launch_pdl(k, dim3(n), dim3(32 * nw), smem, s, n1, n2, l, P1, (int64_t)n1 * l, P2,
+                    (int64_t)n2 * l, sh, sig, ldsig > l ? ldsig : l, rank, width, sel);
 }
 
 #define TR_RPL_DISPATCH(RPLV, CALL) \
@@ -1035,8 +1048,8 @@ template <typename T>
 cudaError_t run_cgs_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) {
   // two rows per thread: at most 128 registers x 256 threads per block
   const int threads = ((m + 1) / 2 + 31) / 32 * 32;
-  cgs_qr_kernel<T, 2><<<n, threads, 0, s>>>(m, l, P, (int64_t)m * l, sel);
-  return cudaGetLastError();
+  return launch_pdl(cgs_qr_kernel<T, 2>, dim3(n), dim3(threads), 0, s, m, l, P, (int64_t)m * l,
+                    sel);
 }
 
 template <typename T>
@@ -1074,10 +1087,10 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
     const int64_t per = (int64_t)n2 * l;
     const int64_t groups = (per + 3) / 4;
     dim3 grid((unsigned)((groups + 255) / 256), n);
-    sketch_kernel<T><<<grid, 256, 0, s>>>(per, Om, (uint32_t)(w.seed & 0xffffffffu),
-                                          (uint32_t)(w.seed >> 32), (uint32_t)t, w.dt, 0u,
-                                          w.sel);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_pdl(sketch_kernel<T>, grid, dim3(256), 0, s, per, Om,
+                   (uint32_t)(w.seed & 0xffffffffu), (uint32_t)(w.seed >> 32), (uint32_t)t, w.dt,
+                   0u, w.sel);
+    if (e != cudaSuccess) return e;
   }
   // Precision of each skinny product: 0 = SIMT FP32, 1 = BF16, 3 = split
   // BF16.  The BF16 form keeps the sketch and the early power products in

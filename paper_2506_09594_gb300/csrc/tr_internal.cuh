@@ -66,6 +66,35 @@ struct ShrinkScalars {
 // non-negative double.
 enum { RES_DL = 0, RES_DE = 1, RES_LG = 2, RES_DG = 3, RES_CONS = 4, RES_COUNT = 5 };
 
+// ---- programmatic dependent launch ----
+// Kernels of a step launched with programmatic stream serialization may
+// start while the previous kernel in the stream drains.  Each such kernel
+// calls pdl_wait() before it touches memory (it returns once the previous
+// grid has completed and its writes are visible) and pdl_trigger() after its
+// last store; a grid is launched early only once every block of its
+// predecessor has triggered or exited, so every predecessor block is already
+// resident and nothing can wait on an unscheduled block.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---- tensor maps (tensor_map.cu) ----
 // A 2D tensor map of `rows` rows of `cols` elements (FP32, or bytes when
 // u8), rows `row_stride` elements apart, with boxes of box_cols x box_rows;

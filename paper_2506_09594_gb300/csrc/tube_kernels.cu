@@ -508,6 +508,7 @@ tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restric
                   T *__restrict__ Abar, TubeScalars sc, unsigned long long *res_prev,
                   unsigned long long *res, int *flags, const __grid_constant__ TubeMaps tm,
                   int RBG, int nbox) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *mats = reinterpret_cast<T *>(smem_raw);
   T *tile = mats + td.mats_len;
@@ -588,6 +589,7 @@ tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restric
   unsigned long long *const slots[5] = {res_prev + RES_LG, res_prev + RES_DG, res + RES_DL,
                                         res + RES_DE, res + RES_CONS};
   block_max_to_global<T, 5>(v, slots);
+  pdl_trigger();
 }
 
 template <typename T, int NK, int VEC>
@@ -727,11 +729,10 @@ struct FusedLauncher {
       if (pf.pf) k = tube_fused_kernel<T, NK, VEC, true>;
     cudaError_t e = prep(k, g.smem);
     if (e != cudaSuccess) return e;
-    k<<<g.grid, kTubeThreads, g.smem, s>>>(g.P, g.n, g.tp, td, (const T *)mats, (const T *)Gbar,
-                                          mu_prev, dmu_prev, (const T *)M, mask, (T *)L, (T *)E,
-                                          (T *)Y, (T *)G, (T *)Lam, (T *)Abar, sc, res_prev, res,
-                                          flags, pf.tm, pf.RBG, pf.nbox);
-    return cudaGetLastError();
+    return launch_pdl(k, dim3(g.grid), dim3(kTubeThreads), g.smem, s, g.P, g.n, g.tp, td,
+                      (const T *)mats, (const T *)Gbar, mu_prev, dmu_prev, (const T *)M, mask,
+                      (T *)L, (T *)E, (T *)Y, (T *)G, (T *)Lam, (T *)Abar, sc, res_prev, res,
+                      flags, pf.tm, pf.RBG, pf.nbox);
   }
 };
 
@@ -854,15 +855,16 @@ cudaError_t launch_tube_fused(tr_dtype dt, int64_t P, int n, const TransformDesc
 }
 
 __global__ void schedule_kernel(DevSched *d, double growth, double mu_max) {
+  pdl_wait();
   const double next = growth * d->mu;
   d->mu_prev = d->mu;
   d->mu = next < mu_max ? next : mu_max;
   d->t += 1;
+  pdl_trigger();
 }
 
 cudaError_t launch_schedule(DevSched *d, double growth, double mu_max, cudaStream_t s) {
-  schedule_kernel<<<1, 1, 0, s>>>(d, growth, mu_max);
-  return cudaGetLastError();
+  return launch_pdl(schedule_kernel, dim3(1), dim3(1), 0, s, d, growth, mu_max);
 }
 
 cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc &td,

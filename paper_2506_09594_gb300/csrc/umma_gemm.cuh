@@ -244,6 +244,7 @@ constexpr int min_blocks() { return (SPLIT == 1 && NP <= 64) ? 4 : 1; }
 template <int NP, int SPLIT>
 __global__ void __launch_bounds__(kThreads, min_blocks<NP, SPLIT>())
     gemm_kernel(const __grid_constant__ Args g, int *err) {
+  pdl_wait();
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base_s;
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<NP, SPLIT>())
       }
     }
   }
+  pdl_trigger();
   fence_before();
   __syncthreads();
   if (warp == 0)
