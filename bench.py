@@ -198,8 +198,8 @@ def tube_inverse_bytes(N, esz):
 # DRAM traffic of one tube_fused_kernel launch on the bench workload, from the
 # ncu capture summarised in profiles/tube_fused_kernel_tubal200x400_r10.md,
 # valid only while the kernel source is the one that was profiled.
-TUBE_FUSED_TRAFFIC = {"workload": "tubal200x400_r10", "src_sha256_prefix": "74c48f9efef142e5",
-                      "bytes": 467.186688e6 + 324.910336e6}
+TUBE_FUSED_TRAFFIC = {"workload": "tubal200x400_r10", "src_sha256_prefix": "0eda26e30eaef43f",
+                      "bytes": 467.361536e6 + 324.569088e6}
 
 
 def profiled_traffic(workload):
