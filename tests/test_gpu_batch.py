@@ -145,7 +145,8 @@ def test_tube_tiles_compute_identical_steps():
     h = handle(dims, "f32", M, mask, rank=8, oversample=4)
     h.step()
     tile, groups = h.autotune(3)
-    assert tile in (4, 8, 16, 32, 64) and groups in (1, 2, 4)
+    # FP32 with P % 16 == 0: only tiles the fused pass can prefetch with
+    assert tile in (16, 32, 64) and groups in (1, 2, 4)
     assert h.autotune(0) == (tile, groups)      # cached choice
     h.step(info=True)                            # the deferred pass was completed first
     with pytest.raises(tr.TrError):
