@@ -31,6 +31,11 @@ paper's order and notation:
 * ``learned``   the learned sketch-width engine (not in the paper): slice
                 features, width plan, certificate and the rank-predictor
                 MLP (forward, backpropagation, Adam).
+* ``tucker``    the paper's own randomized GNHTSVT: shared Tucker factors of
+                the two spatial modes by Alg. 1 (R-STHOSVD-BKI, block Krylov
+                space, orthonormal basis, top singular vectors of
+                Z^T A A^T Z, sequential truncation), then the deterministic
+                GNTSVT of the core (Alg. 4, randomized branch).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force, library routines it does not itself
@@ -38,4 +43,4 @@ call, or published known-answer vectors, except where a docstring says
 "parity unpinned".
 """
 
-from . import philox, transform, prox, svt, admm, learned  # noqa: F401
+from . import philox, transform, prox, svt, admm, learned, tucker  # noqa: F401

@@ -1,0 +1,99 @@
+"""Randomized GNHTSVT with shared Tucker factors, in float64.
+
+Test infrastructure (see the package docstring).
+
+Alg. 4, randomized branch: the tensor A is first compressed by a Tucker
+decomposition A ~ [C; F_1, F_2] computed by Alg. 1 (R-STHOSVD-BKI), the
+deterministic GNTSVT is applied to the core, and the result is mapped back
+with the factors:
+
+    D_{Phi,tau}(A, L) ~ D_{Phi,tau}(C, L) x_1 F_1 x_2 F_2.
+
+Here the processing order of Alg. 1 is rho = (1, 2): the two spatial modes
+of the face slices get shared factors, the transformed modes 3..d keep
+their full size, so L acts on the core exactly as on A.  For one mode
+(Alg. 1, loop body), with A the mode unfolding of the current core C:
+
+    K = [A G, (A A^T) A G, ..., (A A^T)^q A G]      (block Krylov space)
+    Z = orthonormal basis of K
+    M = Z^T A A^T Z,  U_r = its r top singular vectors
+    F = Z U_r,        C <- C x_mode F^T             (sequential truncation)
+
+The Gaussian block G is an input (the caller draws it), with one row per
+column of the unfolding.  Unfoldings of a slice stack X[j][i1][i2]:
+mode 1 is the n1 x (n n2) matrix with column j*n2 + i2, mode 2 the
+n2 x (n n1) matrix with column j*n1 + i1.
+"""
+
+import numpy as np
+
+from . import svt
+
+
+def unfold(X, mode):
+    """Mode-1 or mode-2 unfolding of a slice stack X (n, n1, n2)."""
+    n, n1, n2 = X.shape
+    if mode == 1:
+        return np.transpose(X, (1, 0, 2)).reshape(n1, n * n2)
+    if mode == 2:
+        return np.transpose(X, (2, 0, 1)).reshape(n2, n * n1)
+    raise ValueError(mode)
+
+
+def mode_product_t(X, F, mode):
+    """C = X x_mode F^T for a slice stack: F^T X_j (mode 1) or X_j F (mode 2)."""
+    if mode == 1:
+        return np.einsum("ia,jib->jab", F, X)
+    if mode == 2:
+        return np.einsum("jia,ab->jib", X, F)
+    raise ValueError(mode)
+
+
+def mode_product(C, F, mode):
+    """X = C x_mode F: F C_j (mode 1) or C_j F^T (mode 2)."""
+    if mode == 1:
+        return np.einsum("ia,jab->jib", F, C)
+    if mode == 2:
+        return np.einsum("jia,ba->jib", C, F)
+    raise ValueError(mode)
+
+
+def krylov_basis(A, G, q):
+    """Z: an orthonormal basis of K = [A G, (A A^T) A G, ..., (A A^T)^q A G]
+    (Alg. 1, "build the Krylov subspace", "form an orthonormal basis")."""
+    blocks = [A @ G]
+    for _ in range(q):
+        blocks.append(A @ (A.T @ blocks[-1]))
+    Z, _ = np.linalg.qr(np.concatenate(blocks, axis=1))
+    return Z
+
+
+def bki_factor(A, G, q, r):
+    """F = Z U_r for one mode (Alg. 1 loop body), with M = Z^T A A^T Z."""
+    Z = krylov_basis(A, G, q)
+    W = A.T @ Z
+    M = W.T @ W
+    U, _, _ = np.linalg.svd(M)
+    return Z @ U[:, :r], Z
+
+
+def rsthosvd_bki(X, ranks, G, q):
+    """Alg. 1 with processing order (1, 2) on a slice stack X (n, n1, n2).
+
+    ranks = (r1, r2), G = (G1, G2) with G1 (n n2, b1) and G2 (n r1, b2),
+    q = (q1, q2).  Returns the core C (n, r1, r2) and the factors F1, F2."""
+    C = X
+    F = []
+    for mode, r, Gm, qm in ((1, ranks[0], G[0], q[0]), (2, ranks[1], G[1], q[1])):
+        Fm, _ = bki_factor(unfold(C, mode), Gm, qm, r)
+        C = mode_product_t(C, Fm, mode)
+        F.append(Fm)
+    return C, F[0], F[1]
+
+
+def randomized_gnhtsvt(X, tdims, tau, kind, ranks, G, q, theta=1.0, gamma=4.0):
+    """Alg. 4, randomized branch: D(C, L) x_1 F1 x_2 F2 with [C; F1, F2]
+    from rsthosvd_bki.  Returns the result and (C, F1, F2)."""
+    C, F1, F2 = rsthosvd_bki(X, ranks, G, q)
+    Ct, _ = svt.gnhtsvt(C, tdims, tau, kind, theta, gamma)
+    return mode_product(mode_product(Ct, F1, 1), F2, 2), (C, F1, F2)

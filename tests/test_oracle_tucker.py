@@ -1,0 +1,115 @@
+"""Pins of the shared-Tucker randomized GNHTSVT oracle (Alg. 1 with
+processing order (1, 2), Alg. 4 randomized branch).
+
+The pins use what the mathematics fixes, not the oracle's own formulas:
+
+* on stacks whose slices share column and row spaces of dimensions
+  s1 <= r1, s2 <= r2, the Tucker factors capture those spaces exactly, so
+  the result equals the deterministic GNHTSVT (full SVD of every
+  transformed slice) and the Tucker reconstruction equals the input;
+* with full ranks (r1 = n1, r2 = n2) the factors are square orthogonal and
+  the result equals the deterministic GNHTSVT on any input;
+* with many Krylov steps and a spectral gap, span(F1) is the span of the r1
+  top left singular vectors of the mode-1 unfolding (numpy's SVD);
+* factors and Krylov bases are orthonormal, and the Krylov basis contains
+  its generating blocks.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import prox, svt, tucker
+
+
+def shared_stack(n, n1, n2, s1, s2, rng, scale=3.0):
+    P, _ = np.linalg.qr(rng.standard_normal((n1, s1)))
+    Q, _ = np.linalg.qr(rng.standard_normal((n2, s2)))
+    S = scale * rng.standard_normal((n, s1, s2))
+    return np.einsum("ia,jab,kb->jik", P, S, Q), P, Q
+
+
+def gaussians(n, n2, r1, b1, b2, rng):
+    return (rng.standard_normal((n * n2, b1)), rng.standard_normal((n * r1, b2)))
+
+
+@pytest.mark.parametrize("kind", [prox.L1, prox.MCP])
+def test_shared_spaces_give_the_deterministic_prox(kind):
+    rng = np.random.default_rng(1)
+    tdims, n1, n2, s1, s2 = (4, 3), 30, 22, 5, 3
+    n = int(np.prod(tdims))
+    X, _, _ = shared_stack(n, n1, n2, s1, s2, rng)
+    G = gaussians(n, n2, s1, 3, 2, rng)
+    tau = 0.7
+    got, _ = tucker.randomized_gnhtsvt(X, tdims, tau, kind, (s1, s2), G, (1, 1), gamma=50.0)
+    want, _ = svt.gnhtsvt(X, tdims, tau, kind, gamma=50.0)
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_tucker_reconstruction_is_exact_on_shared_spaces():
+    rng = np.random.default_rng(2)
+    n, n1, n2, s1, s2 = 6, 17, 25, 4, 6
+    X, P, Q = shared_stack(n, n1, n2, s1, s2, rng)
+    G = gaussians(n, n2, s1 + 1, 3, 4, rng)
+    C, F1, F2 = tucker.rsthosvd_bki(X, (s1 + 1, s2), G, (1, 1))
+    assert C.shape == (n, s1 + 1, s2)
+    back = tucker.mode_product(tucker.mode_product(C, F1, 1), F2, 2)
+    assert np.linalg.norm(back - X) <= 1e-11 * np.linalg.norm(X)
+    # the factors span the shared spaces
+    assert np.linalg.norm(P - F1 @ (F1.T @ P)) < 1e-11
+    assert np.linalg.norm(Q - F2 @ (F2.T @ Q)) < 1e-11
+
+
+def test_full_ranks_give_the_deterministic_prox_on_any_input():
+    rng = np.random.default_rng(3)
+    tdims, n1, n2 = (5,), 9, 7
+    X = rng.standard_normal((5, n1, n2))
+    G = gaussians(5, n2, n1, n1, n2, rng)
+    got, (_, F1, F2) = tucker.randomized_gnhtsvt(X, tdims, 0.9, prox.L1, (n1, n2), G, (0, 0))
+    want, _ = svt.gnhtsvt(X, tdims, 0.9, prox.L1)
+    assert np.linalg.norm(F1.T @ F1 - np.eye(n1)) < 1e-12
+    assert np.linalg.norm(F2.T @ F2 - np.eye(n2)) < 1e-12
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_factor_converges_to_the_top_singular_subspace():
+    # mode-1 unfolding with singular values 10, 9, 8 over a tail at most 1:
+    # after six Krylov steps span(F1) is the top-3 left singular space
+    rng = np.random.default_rng(4)
+    n, n1, n2, r = 8, 40, 12, 3
+    U, _ = np.linalg.qr(rng.standard_normal((n1, n1)))
+    V, _ = np.linalg.qr(rng.standard_normal((n * n2, n1)))
+    sv = np.concatenate([[10.0, 9.0, 8.0], np.linspace(1.0, 0.1, n1 - 3)])
+    A1 = (U * sv) @ V.T
+    X = np.transpose(A1.reshape(n1, n, n2), (1, 0, 2))
+    assert np.allclose(tucker.unfold(X, 1), A1)
+    F1, Z = tucker.bki_factor(tucker.unfold(X, 1), rng.standard_normal((n * n2, r)), 6, r)
+    top = U[:, :r]
+    # sines of the principal angles between span(F1) and span(top)
+    sines = np.linalg.svd(top - F1 @ (F1.T @ top), compute_uv=False)
+    assert sines.max() < 1e-8
+    assert np.linalg.norm(Z.T @ Z - np.eye(Z.shape[1])) < 1e-12
+
+
+def test_krylov_basis_contains_its_blocks():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((20, 50))
+    G = rng.standard_normal((50, 2))
+    Z = tucker.krylov_basis(A, G, 2)
+    assert Z.shape == (20, 6)
+    for Y in (A @ G, A @ (A.T @ (A @ G)), A @ A.T @ A @ A.T @ A @ G):
+        assert np.linalg.norm(Y - Z @ (Z.T @ Y)) <= 1e-10 * np.linalg.norm(Y)
+
+
+def test_unfoldings_and_mode_products_are_adjoint():
+    # <X x_k F^T, C> = <X, C x_k F>: the two mode products are adjoint, and
+    # the unfoldings hold every element once
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((3, 5, 4))
+    for mode, m, r in ((1, 5, 2), (2, 4, 3)):
+        F = rng.standard_normal((m, r))
+        C = rng.standard_normal(tucker.mode_product_t(X, F, mode).shape)
+        lhs = np.sum(tucker.mode_product_t(X, F, mode) * C)
+        rhs = np.sum(X * tucker.mode_product(C, F, mode))
+        assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+        U = tucker.unfold(X, mode)
+        assert np.array_equal(np.sort(U.ravel()), np.sort(X.ravel()))
