@@ -177,6 +177,30 @@ tr_status tr_transform_inverse(tr_handle *h, const void *src, void *dst);
 tr_status tr_slice_prox(tr_handle *h, const void *Abar, void *Gbar,
                         double tau, int t);
 
+/* The paper's own randomized GNHTSVT (Alg. 4, randomized branch) on the
+ * transformed stack Abar: shared Tucker factors F1 (n1 x r1) and F2
+ * (n2 x r2) of the two spatial modes from Alg. 1 (R-STHOSVD-BKI, processing
+ * order (1, 2)): for each mode the block Krylov space
+ * [A G, (A A^T) A G, ..., (A A^T)^q A G] of the mode unfolding A, an
+ * orthonormal basis Z of it, the r top singular vectors U_r of
+ * Z^T A A^T Z and F = Z U_r, the core truncated by F before the next mode.
+ * Then every transformed slice is replaced by F1 Prox(F1^T Abar_j F2) F2^T
+ * (the handle's Phi, theta, gamma; tau as given), written to Gbar.
+ *   Abar, Gbar: device, (n, n1, n2) of the handle's shape and dtype; no alias.
+ *   G1: device, column-major (n n2) x b1 Gaussian block of mode 1, row
+ *       j n2 + i2 for slice j (a transform-domain draw: the transform of a
+ *       spatial draw gives exactly the spatial form of Alg. 1).
+ *   G2: device, column-major (n r1) x b2 Gaussian block of mode 2, row
+ *       j r1 + a.
+ *   F1_out, F2_out: device, column-major, optional (NULL: not written).
+ * Needs 1 <= r1 <= min(n1, n2), r2 <= n2, r_k <= (q_k + 1) b_k <= 32 and
+ * (q_k + 1) b_k <= the mode size.  Workspace is taken from the stream-ordered
+ * allocator for the call.  Errors: TR_EINVAL (arguments), TR_EUNSUPPORTED
+ * (Krylov spaces above 32 columns, panels beyond shared memory), TR_ECUDA. */
+tr_status tr_slice_prox_tucker(tr_handle *h, const void *Abar, void *Gbar, double tau,
+                               int r1, int r2, int b1, int b2, int q1, int q2,
+                               const void *G1, const void *G2, void *F1_out, void *F2_out);
+
 /* Point the handle at other observed data (device buffers of the same
  * shape, dtype and layout as at tr_init; caller-owned, valid until the next
  * call or tr_free).  Later steps read them; the iterate is kept.  For

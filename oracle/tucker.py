@@ -68,13 +68,25 @@ def krylov_basis(A, G, q):
     return Z
 
 
+def canonical_signs(F):
+    """Columns scaled by +-1 so that each column's entry of largest magnitude
+    (the first one on ties) is positive.  Singular vectors are defined up to
+    sign; with processing order (1, 2) the mode-2 sketch is drawn on
+    C x_1 F1^T, which depends on the signs of F1's columns, so the factor
+    carries this fixed sign convention."""
+    idx = np.argmax(np.abs(F), axis=0)
+    sgn = np.where(F[idx, np.arange(F.shape[1])] < 0, -1.0, 1.0)
+    return F * sgn
+
+
 def bki_factor(A, G, q, r):
-    """F = Z U_r for one mode (Alg. 1 loop body), with M = Z^T A A^T Z."""
+    """F = Z U_r for one mode (Alg. 1 loop body), with M = Z^T A A^T Z, the
+    columns of U_r in decreasing order of singular value, signs canonical."""
     Z = krylov_basis(A, G, q)
     W = A.T @ Z
     M = W.T @ W
     U, _, _ = np.linalg.svd(M)
-    return Z @ U[:, :r], Z
+    return canonical_signs(Z @ U[:, :r]), Z
 
 
 def rsthosvd_bki(X, ranks, G, q):
@@ -97,3 +109,18 @@ def randomized_gnhtsvt(X, tdims, tau, kind, ranks, G, q, theta=1.0, gamma=4.0):
     C, F1, F2 = rsthosvd_bki(X, ranks, G, q)
     Ct, _ = svt.gnhtsvt(C, tdims, tau, kind, theta, gamma)
     return mode_product(mode_product(Ct, F1, 1), F2, 2), (C, F1, F2)
+
+
+def transformed_randomized_prox(Abar, tau, kind, ranks, G, q, theta=1.0, gamma=4.0):
+    """The same operator on the transformed stack Abar = L(A).
+
+    For an orthonormal L along modes 3..d the mode-1 and mode-2 unfoldings of
+    Abar are those of A times an orthogonal matrix, so with the Gaussian
+    blocks transformed the same way (each block viewed as a stack and
+    transformed along its slice index) the Krylov spaces, factors and core
+    are those of the spatial form, the core's GNTSVT is the per-slice prox of
+    its transformed slices, and the result is L of the spatial result.
+    Returns Gbar and (Cbar, F1, F2)."""
+    Cbar, F1, F2 = rsthosvd_bki(Abar, ranks, G, q)
+    Ct, _ = svt.transformed_prox(Cbar, tau, kind, theta, gamma)
+    return mode_product(mode_product(Ct, F1, 1), F2, 2), (Cbar, F1, F2)

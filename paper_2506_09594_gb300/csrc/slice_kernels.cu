@@ -1073,6 +1073,244 @@ cudaError_t run_svd_core(int n1, int n2, int l, T *P1, T *P2, int n, const Shrin
 #undef TR_SVD_ARGS
 }
 
+// ------------------------------- shared Tucker factors (Alg. 1 + Alg. 4)
+// The paper's own randomized GNHTSVT on the transformed stack: factors F1
+// (n1 x r1) and F2 (n2 x r2) shared by all slices from the block Krylov
+// spaces of the mode-1 and mode-2 unfoldings (R-STHOSVD-BKI, processing
+// order (1, 2)), then the prox of every slice restricted to them.  The
+// unfolding products are batched per-slice products with a shared operand
+// followed by a sum over the slices.
+
+// out[i] = sum_j in[j * count + i]
+template <typename T>
+__global__ void reduce_slices_kernel(T *__restrict__ out, const T *__restrict__ in, int64_t count,
+                                     int n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = T(0);
+    for (int j = 0; j < n; ++j) acc += in[(int64_t)j * count + i];
+    out[i] = acc;
+  }
+}
+
+// dst[j * count + i] = src[i]
+template <typename T>
+__global__ void bcast_slices_kernel(T *__restrict__ dst, const T *__restrict__ src, int64_t count,
+                                    int n) {
+  const int64_t total = count * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e % count];
+}
+
+// The r top singular vectors of the symmetric positive semi-definite L x L
+// matrix M (column-major), L <= 32, as the columns of Ur (L x r): one-sided
+// Jacobi M J = W (block_jacobi), sigma_i = ||W_i||, the columns of J sorted
+// by sigma.  One block of 128 threads.
+template <typename T>
+__global__ void __launch_bounds__(128) eig_top_kernel(int L, const T *__restrict__ M, int r,
+                                                     T *__restrict__ Ur) {
+  __shared__ T W[32 * 32], J[32 * 32], sg[32];
+  __shared__ int order[32];
+  __shared__ int flag;
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+    W[e] = M[e];
+    J[e] = (e % L == e / L) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const T eps = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
+  const int lp = L + (L & 1);
+  int nthr = ((lp / 2) * 8 + 31) / 32 * 32;
+  if (nthr > (int)blockDim.x) nthr = blockDim.x;
+  block_jacobi<T, 8, 4>(W, J, L, &flag, T(L > 8 ? L : 8) * eps, sizeof(T) == 4 ? 16 : 30, nthr);
+  __syncthreads();
+  if (threadIdx.x < L) {
+    T ss = T(0);
+    for (int i = 0; i < L; ++i) ss = fma(W[threadIdx.x * L + i], W[threadIdx.x * L + i], ss);
+    sg[threadIdx.x] = ss;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // selection by decreasing sigma (stable for ties)
+    bool used[32] = {};
+    for (int c = 0; c < L; ++c) {
+      int best = -1;
+      for (int i = 0; i < L; ++i)
+        if (!used[i] && (best < 0 || sg[i] > sg[best])) best = i;
+      used[best] = true;
+      order[c] = best;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < L * r; e += blockDim.x) {
+    const int i = e % L, c = e / L;
+    Ur[e] = J[order[c] * L + i];
+  }
+}
+
+// Columns of F (m x r, column-major) scaled by +-1 so that each column's
+// entry of largest magnitude (the first one on ties) is positive: the sign
+// convention of the factors (the mode-2 sketch depends on F1's signs).  One
+// warp per column; the signed winner travels with the reduction.
+template <typename T>
+__global__ void canon_sign_kernel(T *__restrict__ F, int m, int r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < r; c += nw) {
+    T *col = F + (size_t)c * m;
+    T best = T(-1), val = T(0);
+    int bi = m;
+    for (int i = lane; i < m; i += 32) {
+      const T a = fabs(col[i]);
+      if (a > best) {   // i increases within a lane: first index on ties
+        best = a;
+        val = col[i];
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const T ov = __shfl_xor_sync(0xffffffffu, val, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        val = ov;
+        bi = oi;
+      }
+    }
+    const T sgn = val < T(0) ? T(-1) : T(1);
+    for (int i = lane; i < m; i += 32) col[i] *= sgn;
+  }
+}
+
+struct TuckerDims {
+  int n, n1, n2, r1, r2, b1, b2, q1, q2;
+  int L1() const { return (q1 + 1) * b1; }
+  int L2() const { return (q2 + 1) * b2; }
+};
+
+template <typename T>
+size_t tucker_ws_elems(const TuckerDims &d) {
+  const size_t L1 = d.L1(), L2 = d.L2();
+  size_t pm = (size_t)d.n1 * L1;
+  pm = pm > (size_t)d.n2 * L2 ? pm : (size_t)d.n2 * L2;
+  pm = pm > L1 * L1 ? pm : L1 * L1;
+  pm = pm > L2 * L2 ? pm : L2 * L2;
+  size_t wm = (size_t)d.n2 * L1;
+  wm = wm > (size_t)d.r1 * L2 ? wm : (size_t)d.r1 * L2;
+  return (size_t)d.n * (pm + wm) + (size_t)d.n1 * L1 + (size_t)d.n2 * L2 + 2 * 32 * 32 +
+         (size_t)d.n1 * d.r1 + (size_t)d.n2 * d.r2 +
+         (size_t)d.n * ((size_t)d.n2 * d.r1 + (size_t)d.r2 * d.r1 + (size_t)d.n1 * d.r1 +
+                        (size_t)d.n2 * d.r1 + d.r1) +
+         (size_t)d.n + 64;   // the ranks (n ints) after the singular values
+}
+
+template <typename T>
+cudaError_t reduce_slices(T *out, const T *in, int64_t count, int n, cudaStream_t s) {
+  const int threads = 256;
+  const int blocks = (int)((count + threads - 1) / threads);
+  reduce_slices_kernel<T><<<blocks < 1 ? 1 : blocks, threads, 0, s>>>(out, in, count, n);
+  return cudaGetLastError();
+}
+
+// Block Krylov factor of one unfolding A = [A_0 ... A_{n-1}] (A_j: m x k,
+// the slice blocks of the unfolding, given by their element strides sAi,
+// sAk and slice stride sAb): K = [A G, (A A^T) A G, ..., (A A^T)^q A G],
+// Z = qr(K), M = Z^T A A^T Z, F = Z U_r (Alg. 1 loop body).  G's rows for
+// slice j start at j * k.
+template <typename T>
+cudaError_t tucker_factor(int n, int m, int k, const T *A, int64_t sAb, int64_t sAi, int64_t sAk,
+                          const T *G, int b, int q, int r, T *K, T *part, T *W, T *Mm, T *Ur,
+                          T *F, cudaStream_t s) {
+  const int L = (q + 1) * b;
+  cudaError_t e;
+  // K block 0 = sum_j A_j G_j
+  GemmArgs g0{m, b, k, A, sAb, sAi, sAk, G, k, 1, (int64_t)n * k, part, (int64_t)m * b, 1, m};
+  if ((e = bgemm<T>(g0, n, s)) != cudaSuccess) return e;
+  if ((e = reduce_slices<T>(K, part, (int64_t)m * b, n, s)) != cudaSuccess) return e;
+  for (int i = 1; i <= q; ++i) {
+    const T *X = K + (size_t)(i - 1) * b * m;
+    GemmArgs gw{k, b, m, A, sAb, sAk, sAi, X, 0, 1, m, W, (int64_t)k * b, 1, k};   // W_j = A_j^T X
+    if ((e = bgemm<T>(gw, n, s)) != cudaSuccess) return e;
+    GemmArgs gp{m, b, k, A, sAb, sAi, sAk, W, (int64_t)k * b, 1, k, part, (int64_t)m * b, 1, m};
+    if ((e = bgemm<T>(gp, n, s)) != cudaSuccess) return e;
+    if ((e = reduce_slices<T>(K + (size_t)i * b * m, part, (int64_t)m * b, n, s)) != cudaSuccess)
+      return e;
+  }
+  if ((e = run_qr<T>(m, L, K, 1, s)) != cudaSuccess) return e;                   // Z
+  GemmArgs gz{k, L, m, A, sAb, sAk, sAi, K, 0, 1, m, W, (int64_t)k * L, 1, k};      // W_j = A_j^T Z
+  if ((e = bgemm<T>(gz, n, s)) != cudaSuccess) return e;
+  GemmArgs gm{L, L, k, W, (int64_t)k * L, k, 1, W, (int64_t)k * L, 1, k, part, (int64_t)L * L, 1, L};
+  if ((e = bgemm<T>(gm, n, s)) != cudaSuccess) return e;                         // W_j^T W_j
+  if ((e = reduce_slices<T>(Mm, part, (int64_t)L * L, n, s)) != cudaSuccess) return e;
+  eig_top_kernel<T><<<1, 128, 0, s>>>(L, Mm, r, Ur);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  GemmArgs gf{m, r, L, K, 0, 1, m, Ur, 0, 1, L, F, 0, 1, m};                        // F = Z U_r
+  if ((e = bgemm<T>(gf, 1, s)) != cudaSuccess) return e;
+  canon_sign_kernel<T><<<1, 256, 0, s>>>(F, m, r);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_tucker(const TuckerDims &d, const T *Abar, T *Gbar, const T *G1, const T *G2,
+                       T *ws, const ShrinkScalars &sh, T *F1_out, T *F2_out, cudaStream_t s) {
+  const int n = d.n, n1 = d.n1, n2 = d.n2, r1 = d.r1, r2 = d.r2;
+  const int L1 = d.L1(), L2 = d.L2();
+  size_t pm = (size_t)n1 * L1;
+  pm = pm > (size_t)n2 * L2 ? pm : (size_t)n2 * L2;
+  pm = pm > (size_t)L1 * L1 ? pm : (size_t)L1 * L1;
+  pm = pm > (size_t)L2 * L2 ? pm : (size_t)L2 * L2;
+  size_t wm = (size_t)n2 * L1;
+  wm = wm > (size_t)r1 * L2 ? wm : (size_t)r1 * L2;
+  T *part = ws;
+  T *W = part + (size_t)n * pm;
+  T *K1 = W + (size_t)n * wm;
+  T *K2 = K1 + (size_t)n1 * L1;
+  T *Mm = K2 + (size_t)n2 * L2;
+  T *Ur = Mm + 32 * 32;
+  T *F1 = Ur + 32 * 32;
+  T *F2 = F1 + (size_t)n1 * r1;
+  T *Tt = F2 + (size_t)n2 * r2;       // T_j = Abar_j^T F1       (n2 x r1)
+  T *U = Tt + (size_t)n * n2 * r1;    // U_j = F2^T T_j          (r2 x r1)
+  T *P1 = U + (size_t)n * r2 * r1;    // copies of F1            (n1 x r1)
+  T *P2 = P1 + (size_t)n * n1 * r1;   // F2 F2^T Abar_j^T F1     (n2 x r1)
+  T *sig = P2 + (size_t)n * n2 * r1;
+  int *rank = reinterpret_cast<int *>(sig + (size_t)n * r1 + 1);
+  const int64_t sA = (int64_t)n1 * n2;
+  cudaError_t e;
+  // mode 1: the slice blocks of the unfolding are Abar_j (n1 x n2)
+  if ((e = tucker_factor<T>(n, n1, n2, Abar, sA, n2, 1, G1, d.b1, d.q1, r1, K1, part, W, Mm, Ur, F1,
+                            s)) != cudaSuccess)
+    return e;
+  // mode 2 of C = Abar x_1 F1^T: its slice blocks are T_j = Abar_j^T F1 (n2 x r1)
+  GemmArgs gt{n2, r1, n1, Abar, sA, 1, n2, F1, 0, 1, n1, Tt, (int64_t)n2 * r1, 1, n2};
+  if ((e = bgemm<T>(gt, n, s)) != cudaSuccess) return e;
+  if ((e = tucker_factor<T>(n, n2, r1, Tt, (int64_t)n2 * r1, 1, n2, G2, d.b2, d.q2, r2, K2, part, W,
+                            Mm, Ur, F2, s)) != cudaSuccess)
+    return e;
+  // per slice: B_j^T = F2 F2^T T_j, basis F1; the slice prox of Abar_j
+  // restricted to the factors is F1 SVT(F1^T Abar_j F2) F2^T
+  GemmArgs gu{r2, r1, n2, F2, 0, n2, 1, Tt, (int64_t)n2 * r1, 1, n2, U, (int64_t)r2 * r1, 1, r2};
+  if ((e = bgemm<T>(gu, n, s)) != cudaSuccess) return e;
+  GemmArgs gp{n2, r1, r2, F2, 0, 1, n2, U, (int64_t)r2 * r1, 1, r2, P2, (int64_t)n2 * r1, 1, n2};
+  if ((e = bgemm<T>(gp, n, s)) != cudaSuccess) return e;
+  {
+    const int64_t cnt = (int64_t)n1 * r1;
+    const int64_t tot = cnt * n;
+    const int blocks = (int)((tot + 255) / 256);
+    bcast_slices_kernel<T><<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(P1, F1, cnt, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = run_svd_core<T>(n1, n2, r1, P1, P2, n, sh, sig, rank, s)) != cudaSuccess) return e;
+  if ((e = rank_update<T>(n, n1, n2, r1, P1, P2, Gbar, s)) != cudaSuccess) return e;
+  if (F1_out && (e = cudaMemcpyAsync(F1_out, F1, sizeof(T) * n1 * r1, cudaMemcpyDeviceToDevice,
+                                     s)) != cudaSuccess)
+    return e;
+  if (F2_out && (e = cudaMemcpyAsync(F2_out, F2, sizeof(T) * n2 * r2, cudaMemcpyDeviceToDevice,
+                                     s)) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
 #include "adapt_kernels.cuh"
 
 template <typename T>
@@ -1206,4 +1444,24 @@ size_t slice_smem_limit_ok(tr_dtype dt, int n1, int n2, int l) {
   const size_t a = dt == TR_F64 ? svd_smem<double>(n1, n2, l) : svd_smem<float>(n1, n2, l);
   const size_t b = dt == TR_F64 ? qr_smem<double>(mx, l) : qr_smem<float>(mx, l);
   return (a <= kSliceSmemMax && b <= kSliceSmemMax && mx <= 1024 && l <= 128) ? 1 : 0;
+}
+
+size_t tucker_ws_bytes(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b1, int b2, int q1,
+                       int q2) {
+  const TuckerDims d{n, n1, n2, r1, r2, b1, b2, q1, q2};
+  return dt == TR_F64 ? sizeof(double) * tucker_ws_elems<double>(d)
+                      : sizeof(float) * tucker_ws_elems<float>(d);
+}
+
+cudaError_t launch_slice_tucker(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b1, int b2,
+                                int q1, int q2, const void *Abar, void *Gbar, const void *G1,
+                                const void *G2, void *ws, const ShrinkScalars &sh, void *F1_out,
+                                void *F2_out, cudaStream_t s) {
+  const TuckerDims d{n, n1, n2, r1, r2, b1, b2, q1, q2};
+  if (dt == TR_F64)
+    return run_tucker<double>(d, (const double *)Abar, (double *)Gbar, (const double *)G1,
+                              (const double *)G2, (double *)ws, sh, (double *)F1_out,
+                              (double *)F2_out, s);
+  return run_tucker<float>(d, (const float *)Abar, (float *)Gbar, (const float *)G1,
+                           (const float *)G2, (float *)ws, sh, (float *)F1_out, (float *)F2_out, s);
 }

@@ -818,6 +818,32 @@ extern "C" tr_status tr_slice_prox(tr_handle *h, const void *Abar, void *Gbar, d
   return slice_pass(h, Abar, Gbar, tau, t);
 }
 
+extern "C" tr_status tr_slice_prox_tucker(tr_handle *h, const void *Abar, void *Gbar, double tau,
+                                          int r1, int r2, int b1, int b2, int q1, int q2,
+                                          const void *G1, const void *G2, void *F1_out,
+                                          void *F2_out) {
+  if (!h || !Abar || !Gbar || !G1 || !G2) return TR_EINVAL;
+  if (Abar == Gbar) return fail(h, TR_EINVAL, "Abar and Gbar must not alias");
+  if (!(tau >= 0)) return fail(h, TR_EINVAL, "need tau >= 0");
+  const int n1 = (int)h->n1, n2 = (int)h->n2, L1 = (q1 + 1) * b1, L2 = (q2 + 1) * b2;
+  if (r1 < 1 || r2 < 1 || b1 < 1 || b2 < 1 || q1 < 0 || q2 < 0)
+    return fail(h, TR_EINVAL, "need ranks, blocks >= 1 and Krylov steps >= 0");
+  if (r1 > n1 || r1 > n2 || r2 > n2 || L1 < r1 || L2 < r2 || L1 > n1 || L2 > n2)
+    return fail(h, TR_EINVAL, "need r1 <= min(n1, n2), r2 <= n2, r <= (q+1) b <= mode size");
+  if (L1 > 32 || L2 > 32 || !slice_smem_limit_ok(h->dtype, n1, n2, r1))
+    return fail(h, TR_EUNSUPPORTED, "Krylov spaces above 32 columns are not built");
+  const size_t bytes = tucker_ws_bytes(h->dtype, (int)h->n, n1, n2, r1, r2, b1, b2, q1, q2);
+  void *ws = nullptr;
+  TR_CUDA(h, cudaMallocAsync(&ws, bytes, h->stream));
+  ShrinkScalars sh{tau, (int)h->prm.phi, h->prm.phi_theta, h->prm.phi_gamma};
+  cudaError_t e = launch_slice_tucker(h->dtype, (int)h->n, n1, n2, r1, r2, b1, b2, q1, q2, Abar,
+                                      Gbar, G1, G2, ws, sh, F1_out, F2_out, h->stream);
+  cudaError_t e2 = cudaFreeAsync(ws, h->stream);
+  if (e != cudaSuccess) return fail(h, TR_ECUDA, "tucker prox: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(h, TR_ECUDA, "tucker workspace: %s", cudaGetErrorString(e2));
+  return TR_OK;
+}
+
 extern "C" tr_status tr_last_slice_stats(tr_handle *h, double *sigma, int *ranks, int *l) {
   if (!h) return TR_EINVAL;
   const int ll = h->sw.l;

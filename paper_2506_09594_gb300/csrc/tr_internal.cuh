@@ -172,6 +172,14 @@ size_t adapt_smem_bytes(tr_dtype dt, int n1, int n2, int b, int kcap);
 cudaError_t launch_slice_rsvd(tr_dtype dt, const SliceWork &w, const void *Abar, void *Gbar,
                               const ShrinkScalars &sh, int t, cudaStream_t s);
 size_t slice_smem_limit_ok(tr_dtype dt, int n1, int n2, int l);
+// Shared-Tucker randomized prox (Alg. 1 with processing order (1, 2), Alg. 4
+// randomized branch) on a transformed stack; ws holds tucker_ws_bytes.
+size_t tucker_ws_bytes(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b1, int b2, int q1,
+                       int q2);
+cudaError_t launch_slice_tucker(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b1, int b2,
+                                int q1, int q2, const void *Abar, void *Gbar, const void *G1,
+                                const void *G2, void *ws, const ShrinkScalars &sh, void *F1_out,
+                                void *F2_out, cudaStream_t s);
 
 // ---- learned sketch widths and the rank-predictor MLP (learned.cu) ----
 struct LearnedWork {

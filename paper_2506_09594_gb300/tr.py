@@ -108,6 +108,9 @@ _SIGS = {
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, _P, _P]),
     "tr_set_observed": (ctypes.c_int, [_P, _P, _P]),
     "tr_read_residuals": (ctypes.c_int, [_P, _P]),
+    "tr_slice_prox_tucker": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "tr_graph_mode": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_set_tube_tile": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_set_slice_groups": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -375,6 +378,25 @@ class Handle:
     def slice_prox(self, Abar, tau, t, out=None):
         Gbar = self._new() if out is None else out
         _check(load().tr_slice_prox(self.h, _ptr(Abar), _ptr(Gbar), float(tau), int(t)), self.h)
+        return Gbar
+
+    def slice_prox_tucker(self, Abar, tau, ranks, blocks, krylov, G1, G2, out=None,
+                          factors=False):
+        """tr_slice_prox_tucker: the shared-Tucker randomized prox of a
+        transformed stack; returns Gbar (and F1, F2 when factors)."""
+        import torch
+        Gbar = self._new() if out is None else out
+        r1, r2 = ranks
+        F1 = F2 = None
+        if factors:
+            F1 = torch.empty((r1, self.dims[0]), dtype=Abar.dtype, device=Abar.device)
+            F2 = torch.empty((r2, self.dims[1]), dtype=Abar.dtype, device=Abar.device)
+        _check(load().tr_slice_prox_tucker(self.h, _ptr(Abar), _ptr(Gbar), float(tau), int(r1),
+                                           int(r2), int(blocks[0]), int(blocks[1]),
+                                           int(krylov[0]), int(krylov[1]), _ptr(G1), _ptr(G2),
+                                           _ptr(F1), _ptr(F2)), self.h)
+        if factors:
+            return Gbar, F1.T, F2.T      # column-major (n_k x r_k) as (r_k, n_k) row-major
         return Gbar
 
     def slice_stats(self):

@@ -113,3 +113,31 @@ def test_unfoldings_and_mode_products_are_adjoint():
         assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
         U = tucker.unfold(X, mode)
         assert np.array_equal(np.sort(U.ravel()), np.sort(X.ravel()))
+
+
+@pytest.mark.parametrize("kind", [prox.L1, prox.MCP])
+def test_transform_domain_form_equals_the_spatial_form(kind):
+    # generic (noisy) input: the spatial Alg. 4 with Gaussian blocks G equals
+    # L^{-1} of the transform-domain form run with the transformed blocks
+    from oracle import transform
+    rng = np.random.default_rng(7)
+    tdims, n1, n2, r1, r2 = (3, 4), 16, 13, 5, 4
+    n = int(np.prod(tdims))
+    X = rng.standard_normal((n, n1, n2))
+    G1 = rng.standard_normal((n * n2, 3))
+    G2 = rng.standard_normal((n * r1, 2))
+    spatial, _ = tucker.randomized_gnhtsvt(X, tdims, 0.8, kind, (r1, r2), (G1, G2), (1, 1),
+                                           gamma=40.0)
+    G1b = transform.forward(G1.reshape(n, n2, 3), tdims).reshape(n * n2, 3)
+    G2b = transform.forward(G2.reshape(n, r1, 2), tdims).reshape(n * r1, 2)
+    Gbar, _ = tucker.transformed_randomized_prox(transform.forward(X, tdims), 0.8, kind,
+                                                 (r1, r2), (G1b, G2b), (1, 1), gamma=40.0)
+    back = transform.inverse(Gbar, tdims)
+    assert np.linalg.norm(back - spatial) <= 1e-10 * np.linalg.norm(spatial)
+
+
+def test_canonical_signs():
+    F = np.array([[0.1, -0.9, 0.5], [-0.8, 0.2, -0.5], [0.3, 0.1, 0.0]])
+    G = tucker.canonical_signs(F)
+    assert np.array_equal(G, F * np.array([-1.0, -1.0, 1.0]))   # ties: the first entry
+    assert np.array_equal(tucker.canonical_signs(G), G)
