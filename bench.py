@@ -49,6 +49,8 @@ def parse():
                     help="skip the batch of 64 uneven problems")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the precision forms on the 1024x1024x64 workload")
+    ap.add_argument("--no-tucker", action="store_true",
+                    help="skip the shared-Tucker prox (Alg. 1 + Alg. 4) timing")
     ap.add_argument("--learned-iters", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=8)
     return ap.parse_args()
@@ -453,6 +455,9 @@ def run_ours(args):
         if not args.no_precision and world == 1:
             line["precision"] = precision_forms(tr, torch, 20)
             torch.cuda.empty_cache()
+        if not args.no_tucker and world == 1:
+            line["tucker"] = tucker_section(tr, torch)
+            torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -528,6 +533,58 @@ def learned_ab(tr, torch, iters, prec):
     out["speedup_per_iteration"] = {k: out[k]["iters_per_s"] / out["plain"]["iters_per_s"]
                                     for k in ("learned", "adaptive")}
     return out
+
+
+def tucker_section(tr, torch, reps=20):
+    """The paper's own randomized GNHTSVT (shared Tucker factors of the two
+    spatial modes, Alg. 1 + Alg. 4 randomized branch) beside the per-slice
+    randomized prox, on a 200x200x20x20 FP32 transformed stack whose slices
+    share column and row spaces of dimension 10 (plus 1e-3 noise): device ms
+    per prox (CUDA events; the Tucker call's workspace comes from the
+    stream-ordered allocator inside the timed region) and the relative
+    difference of the two results."""
+    dims, n, n1, n2, sdim = (200, 200, 20, 20), 400, 200, 200, 10
+    g = torch.Generator(device="cuda").manual_seed(7)
+    P = torch.linalg.qr(torch.randn(n1, sdim, device="cuda", generator=g))[0]
+    Q = torch.linalg.qr(torch.randn(n2, sdim, device="cuda", generator=g))[0]
+    S = 3.0 * torch.randn(n, sdim, sdim, device="cuda", generator=g)
+    Ab = (P @ S @ Q.T + 1e-3 * torch.randn(n, n1, n2, device="cuda", generator=g)).float()
+    # blocks at least the shared dimension (with a flat signal spectrum
+    # (A A^T) A G is nearly parallel to A G, so smaller blocks miss part of
+    # the shared spaces) and one Krylov step (the sketch of an unfolding
+    # with n n2 columns gathers the noise of every slice)
+    r, b, q = (16, 16), (16, 16), (1, 1)
+    G1 = torch.randn(b[0], n * n2, device="cuda", generator=g)   # column-major (n n2) x b1
+    G2 = torch.randn(b[1], n * r[0], device="cuda", generator=g)
+    M = torch.zeros_like(Ab)
+    mask = torch.ones(Ab.shape, dtype=torch.uint8, device="cuda")
+    h = tr.Handle(M, mask, dims, phi=tr.TR_PEN_L1, rank=r[0], oversample=0, power_iters=1)
+    tau = 1.0
+    out_t, out_r = torch.empty_like(Ab), torch.empty_like(Ab)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_t = timed(lambda: h.slice_prox_tucker(Ab, tau, r, b, q, G1, G2, out=out_t))
+    ms_r = timed(lambda: h.slice_prox(Ab, tau, 0, out=out_r))
+    diff = float(torch.linalg.norm((out_t - out_r).double())
+                 / torch.linalg.norm(out_r.double()).clamp_min(1e-300))
+    h.close()
+    return {"workload": "200x200x20x20 FP32 transformed stack, shared column/row spaces of "
+                        "dimension 10, noise 1e-3, l1 shrink tau 1",
+            "tucker": {"ranks": list(r), "blocks": list(b), "krylov": list(q),
+                       "ms_per_prox": ms_t},
+            "per_slice_rsvd": {"l": r[0], "q": 1, "ms_per_prox": ms_r},
+            "rel_diff_tucker_vs_per_slice": diff}
 
 
 def precision_forms(tr, torch, K):
