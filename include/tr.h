@@ -66,7 +66,12 @@ typedef enum {
   TR_LR_FULLSVD = 0,    /* deterministic branch: full SVD of every slice    */
   TR_LR_RSVD = 1,       /* per-slice Gaussian sketch + power iterations      */
   TR_LR_ADAPTIVE = 2,   /* per-slice fixed-accuracy block Lanczos (Alg. 3)  */
-  TR_LR_LEARNED = 3     /* per-slice sketch width predicted by an MLP        */
+  TR_LR_LEARNED = 3,    /* per-slice sketch width predicted by an MLP        */
+  TR_LR_TUCKER = 4      /* shared Tucker factors of modes 1, 2 (Alg. 1 +
+                           Alg. 4 randomized branch): r = b = l, q Krylov
+                           steps, (q + 1) l <= 32 and <= n1, n2; Gaussian
+                           blocks per transformed slice (Philox streams 2
+                           and 4, like the sketch's counters otherwise)    */
 } tr_engine;
 
 /* Operand precision of the slice contractions (accumulation is FP32).

@@ -49,7 +49,7 @@ class Params:
     growth: float = 1.1
     tol: float = 1e-4
     max_iter: int = 100
-    engine: str = "rsvd"          # "full" | "rsvd" | "adaptive"
+    engine: str = "rsvd"          # "full" | "rsvd" | "adaptive" | "tucker"
     l: int = 15                   # sketch width r + p
     q: int = 1                    # power iterations
     seed: int = 0

@@ -39,6 +39,8 @@ _SHIFT32 = np.uint64(32)
 # Stream tags (fourth counter word).
 STREAM_SKETCH = 0      # the sketch Omega of the randomized range finder
 STREAM_ADAPTIVE = 1    # the start block and refills of the adaptive engine
+STREAM_TUCKER_1 = 2    # the mode-1 Gaussian block of the shared-Tucker engine
+STREAM_TUCKER_2 = 4    # the mode-2 Gaussian block of the shared-Tucker engine
 
 
 def philox4x32_10(counter, key):

@@ -181,6 +181,21 @@ def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
     number of kept (non-zero shrunk) singular values.
     """
     n, n1, n2 = Abar.shape
+    if engine == "tucker":
+        # Alg. 4 randomized branch with shared factors of the two spatial
+        # modes (oracle.tucker): ranks, block sizes l, q Krylov steps; the
+        # Gaussian blocks are drawn per transformed slice (Philox streams 2
+        # and 4), stacked by rows
+        from . import tucker
+        ll = min(int(l), n1, n2)
+        G1 = np.concatenate([philox.gaussian_block(seed, t, j, n2, ll, philox.STREAM_TUCKER_1)
+                             for j in range(n)], axis=0)
+        G2 = np.concatenate([philox.gaussian_block(seed, t, j, ll, ll, philox.STREAM_TUCKER_2)
+                             for j in range(n)], axis=0)
+        Cbar, F1, F2 = tucker.rsthosvd_bki(np.asarray(Abar, dtype=np.float64), (ll, ll), (G1, G2),
+                                           (q, q))
+        Ct, info = transformed_prox(Cbar, tau, kind, theta, gamma)
+        return tucker.mode_product(tucker.mode_product(Ct, F1, 1), F2, 2), info
     Gbar = np.zeros_like(Abar, dtype=np.float64)
     ranks = np.zeros(n, dtype=np.int64)
     sig = []

@@ -1215,16 +1215,16 @@ cudaError_t reduce_slices(T *out, const T *in, int64_t count, int n, cudaStream_
 // Block Krylov factor of one unfolding A = [A_0 ... A_{n-1}] (A_j: m x k,
 // the slice blocks of the unfolding, given by their element strides sAi,
 // sAk and slice stride sAb): K = [A G, (A A^T) A G, ..., (A A^T)^q A G],
-// Z = qr(K), M = Z^T A A^T Z, F = Z U_r (Alg. 1 loop body).  G's rows for
-// slice j start at j * k.
+// Z = qr(K), M = Z^T A A^T Z, F = Z U_r (Alg. 1 loop body).  The block of G
+// that multiplies A_j starts at j * sGb, columns sGn apart.
 template <typename T>
 cudaError_t tucker_factor(int n, int m, int k, const T *A, int64_t sAb, int64_t sAi, int64_t sAk,
-                          const T *G, int b, int q, int r, T *K, T *part, T *W, T *Mm, T *Ur,
-                          T *F, cudaStream_t s) {
+                          const T *G, int64_t sGb, int64_t sGn, int b, int q, int r, T *K, T *part,
+                          T *W, T *Mm, T *Ur, T *F, cudaStream_t s) {
   const int L = (q + 1) * b;
   cudaError_t e;
-  // K block 0 = sum_j A_j G_j
-  GemmArgs g0{m, b, k, A, sAb, sAi, sAk, G, k, 1, (int64_t)n * k, part, (int64_t)m * b, 1, m};
+  // K block 0 = sum_j A_j G_j (G_j: k x b, slice stride sGb, column stride sGn)
+  GemmArgs g0{m, b, k, A, sAb, sAi, sAk, G, sGb, 1, sGn, part, (int64_t)m * b, 1, m};
   if ((e = bgemm<T>(g0, n, s)) != cudaSuccess) return e;
   if ((e = reduce_slices<T>(K, part, (int64_t)m * b, n, s)) != cudaSuccess) return e;
   for (int i = 1; i <= q; ++i) {
@@ -1250,9 +1250,14 @@ cudaError_t tucker_factor(int n, int m, int k, const T *A, int64_t sAb, int64_t 
   return cudaGetLastError();
 }
 
+// G1, G2: one column-major matrix each (rows j k + i for slice j), or, with
+// g_blocks, one column-major k x b block per slice (the sketch layout).
+// sig_out/rank_out (optional): per-slice singular values (row stride r1)
+// and kept ranks.
 template <typename T>
 cudaError_t run_tucker(const TuckerDims &d, const T *Abar, T *Gbar, const T *G1, const T *G2,
-                       T *ws, const ShrinkScalars &sh, T *F1_out, T *F2_out, cudaStream_t s) {
+                       T *ws, const ShrinkScalars &sh, T *F1_out, T *F2_out, cudaStream_t s,
+                       bool g_blocks = false, T *sig_out = nullptr, int *rank_out = nullptr) {
   const int n = d.n, n1 = d.n1, n2 = d.n2, r1 = d.r1, r2 = d.r2;
   const int L1 = d.L1(), L2 = d.L2();
   size_t pm = (size_t)n1 * L1;
@@ -1273,19 +1278,22 @@ cudaError_t run_tucker(const TuckerDims &d, const T *Abar, T *Gbar, const T *G1,
   T *U = Tt + (size_t)n * n2 * r1;    // U_j = F2^T T_j          (r2 x r1)
   T *P1 = U + (size_t)n * r2 * r1;    // copies of F1            (n1 x r1)
   T *P2 = P1 + (size_t)n * n1 * r1;   // F2 F2^T Abar_j^T F1     (n2 x r1)
-  T *sig = P2 + (size_t)n * n2 * r1;
-  int *rank = reinterpret_cast<int *>(sig + (size_t)n * r1 + 1);
+  T *sig = sig_out ? sig_out : P2 + (size_t)n * n2 * r1;
+  int *rank = rank_out ? rank_out
+                       : reinterpret_cast<int *>(P2 + (size_t)n * n2 * r1 + (size_t)n * r1 + 1);
   const int64_t sA = (int64_t)n1 * n2;
   cudaError_t e;
   // mode 1: the slice blocks of the unfolding are Abar_j (n1 x n2)
-  if ((e = tucker_factor<T>(n, n1, n2, Abar, sA, n2, 1, G1, d.b1, d.q1, r1, K1, part, W, Mm, Ur, F1,
-                            s)) != cudaSuccess)
+  const int64_t g1b = g_blocks ? (int64_t)n2 * d.b1 : n2, g1n = g_blocks ? n2 : (int64_t)n * n2;
+  const int64_t g2b = g_blocks ? (int64_t)r1 * d.b2 : r1, g2n = g_blocks ? r1 : (int64_t)n * r1;
+  if ((e = tucker_factor<T>(n, n1, n2, Abar, sA, n2, 1, G1, g1b, g1n, d.b1, d.q1, r1, K1, part, W,
+                            Mm, Ur, F1, s)) != cudaSuccess)
     return e;
   // mode 2 of C = Abar x_1 F1^T: its slice blocks are T_j = Abar_j^T F1 (n2 x r1)
   GemmArgs gt{n2, r1, n1, Abar, sA, 1, n2, F1, 0, 1, n1, Tt, (int64_t)n2 * r1, 1, n2};
   if ((e = bgemm<T>(gt, n, s)) != cudaSuccess) return e;
-  if ((e = tucker_factor<T>(n, n2, r1, Tt, (int64_t)n2 * r1, 1, n2, G2, d.b2, d.q2, r2, K2, part, W,
-                            Mm, Ur, F2, s)) != cudaSuccess)
+  if ((e = tucker_factor<T>(n, n2, r1, Tt, (int64_t)n2 * r1, 1, n2, G2, g2b, g2n, d.b2, d.q2, r2, K2,
+                            part, W, Mm, Ur, F2, s)) != cudaSuccess)
     return e;
   // per slice: B_j^T = F2 F2^T T_j, basis F1; the slice prox of Abar_j
   // restricted to the factors is F1 SVT(F1^T Abar_j F2) F2^T
@@ -1456,12 +1464,27 @@ size_t tucker_ws_bytes(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b
 cudaError_t launch_slice_tucker(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b1, int b2,
                                 int q1, int q2, const void *Abar, void *Gbar, const void *G1,
                                 const void *G2, void *ws, const ShrinkScalars &sh, void *F1_out,
-                                void *F2_out, cudaStream_t s) {
+                                void *F2_out, cudaStream_t s, bool g_blocks, void *sig,
+                                int *rank) {
   const TuckerDims d{n, n1, n2, r1, r2, b1, b2, q1, q2};
   if (dt == TR_F64)
     return run_tucker<double>(d, (const double *)Abar, (double *)Gbar, (const double *)G1,
                               (const double *)G2, (double *)ws, sh, (double *)F1_out,
-                              (double *)F2_out, s);
+                              (double *)F2_out, s, g_blocks, (double *)sig, rank);
   return run_tucker<float>(d, (const float *)Abar, (float *)Gbar, (const float *)G1,
-                           (const float *)G2, (float *)ws, sh, (float *)F1_out, (float *)F2_out, s);
+                           (const float *)G2, (float *)ws, sh, (float *)F1_out, (float *)F2_out, s,
+                           g_blocks, (float *)sig, rank);
+}
+
+cudaError_t launch_gaussian_blocks(tr_dtype dt, int n, int64_t per_slice, void *out, uint64_t seed,
+                                   int t, const int *dt_dev, uint32_t stream, cudaStream_t s) {
+  const int64_t groups = (per_slice + 3) / 4;
+  const dim3 grid((unsigned)((groups + 255) / 256), n);
+  if (dt == TR_F64)
+    return launch_pdl(sketch_kernel<double>, grid, dim3(256), 0, s, per_slice, (double *)out,
+                      (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)t, dt_dev,
+                      stream, SliceSel{});
+  return launch_pdl(sketch_kernel<float>, grid, dim3(256), 0, s, per_slice, (float *)out,
+                    (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)t, dt_dev,
+                    stream, SliceSel{});
 }

@@ -41,6 +41,8 @@ struct tr_handle {
   // side streams, so latency-bound kernels of one range overlap the
   // bandwidth-bound products of another (tr_set_slice_groups, tr_autotune)
   int slice_groups = 1;
+  // shared-Tucker engine (TR_LR_TUCKER): workspace and the two Gaussian blocks
+  void *tk_ws = nullptr, *tk_g1 = nullptr, *tk_g2 = nullptr;
   int *iota = nullptr;                        // 0, 1, ..., n-1 (slice ids of the ranges)
   cudaStream_t side[kSideStreams] = {};
   cudaEvent_t side_fork = nullptr, side_join[kSideStreams] = {};
@@ -153,6 +155,9 @@ static void free_all(tr_handle *h) {
   if (lw.fork) cudaEventDestroy(lw.fork);
   if (h->width) cudaFree(h->width);
   if (h->sched) cudaFree(h->sched);
+  if (h->tk_ws) cudaFree(h->tk_ws);
+  if (h->tk_g1) cudaFree(h->tk_g1);
+  if (h->tk_g2) cudaFree(h->tk_g2);
   if (h->iota) cudaFree(h->iota);
   for (int i = 0; i < kSideStreams; ++i) {
     if (h->side[i]) cudaStreamDestroy(h->side[i]);
@@ -223,7 +228,8 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   if (!p->observed || !p->mask) return fail(nullptr, TR_EINVAL, "observed/mask must be device pointers");
   for (int i = 0; i < p->order; ++i)
     if (p->dims[i] < 1) return fail(nullptr, TR_EINVAL, "dims[%d] = %lld < 1", i, (long long)p->dims[i]);
-  if (prm->engine != TR_LR_RSVD && prm->engine != TR_LR_ADAPTIVE && prm->engine != TR_LR_LEARNED)
+  if (prm->engine != TR_LR_RSVD && prm->engine != TR_LR_ADAPTIVE && prm->engine != TR_LR_LEARNED &&
+      prm->engine != TR_LR_TUCKER)
     return fail(nullptr, TR_EUNSUPPORTED, "engine %d not built", (int)prm->engine);
   if (prm->engine == TR_LR_ADAPTIVE &&
       (prm->adapt_block < 1 || prm->adapt_block > 32 || !(prm->adapt_eps > 0)))
@@ -395,6 +401,18 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     INIT_CUDA(cudaMalloc((void **)&aw.kept, (size_t)h->n * sizeof(int)));
     INIT_CUDA(cudaMalloc((void **)&aw.draws, (size_t)h->n * sizeof(int)));
   }
+  if (prm->engine == TR_LR_TUCKER) {
+    // r = b = l on both spatial modes, q = power_iters Krylov steps
+    const int q = prm->power_iters, L = (q + 1) * l;
+    if (L > 32 || L > h->n1 || L > h->n2) {
+      fail(h, TR_EUNSUPPORTED, "shared-Tucker engine: (q + 1) l = %d above 32 or a mode size", L);
+      return cleanup(TR_EUNSUPPORTED);
+    }
+    INIT_CUDA(cudaMalloc(&h->tk_ws, tucker_ws_bytes(h->dtype, (int)h->n, (int)h->n1, (int)h->n2, l,
+                                                   l, l, l, q, q)));
+    INIT_CUDA(cudaMalloc(&h->tk_g1, (size_t)h->n * h->n2 * l * h->esz));
+    INIT_CUDA(cudaMalloc(&h->tk_g2, (size_t)h->n * l * l * h->esz));
+  }
   if (prm->engine == TR_LR_LEARNED) {
     LearnedWork &lw = h->lw;
     lw.lmax = l;
@@ -467,6 +485,19 @@ static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double t
                                          h->prm.max_iter, fs, h->stream, &h->launches);
     if (e != cudaSuccess)
       return fail(h, TR_ECUDA, "learned slice pass: %s", cudaGetErrorString(e));
+  } else if (h->prm.engine == TR_LR_TUCKER) {
+    // Gaussian blocks per transformed slice (Philox streams 2 and 4), then
+    // the shared-Tucker prox with r = b = l and q Krylov steps per mode
+    const int l = h->sw.l, q = h->prm.power_iters, n = (int)h->n;
+    TR_CUDA(h, launch_gaussian_blocks(h->dtype, n, (int64_t)h->n2 * l, h->tk_g1, h->prm.seed, t,
+                                      h->sw.dt, 2u, h->stream));
+    TR_CUDA(h, launch_gaussian_blocks(h->dtype, n, (int64_t)l * l, h->tk_g2, h->prm.seed, t,
+                                      h->sw.dt, 4u, h->stream));
+    cudaError_t e = launch_slice_tucker(h->dtype, n, (int)h->n1, (int)h->n2, l, l, l, l, q, q, Abar,
+                                        Gbar, h->tk_g1, h->tk_g2, h->tk_ws, sh, nullptr, nullptr,
+                                        h->stream, true, h->sw.sig, h->sw.rank);
+    if (e != cudaSuccess) return fail(h, TR_ECUDA, "tucker slice pass: %s", cudaGetErrorString(e));
+    h->launches += 2 + 2 * (7 + 3 * (uint64_t)q) + 7;
   } else if (h->slice_groups > 1) {
     // contiguous slice ranges on side streams; each range's panels sit at
     // its own offset of the workspace (same width, so no overlap)

@@ -176,10 +176,18 @@ size_t slice_smem_limit_ok(tr_dtype dt, int n1, int n2, int l);
 // randomized branch) on a transformed stack; ws holds tucker_ws_bytes.
 size_t tucker_ws_bytes(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b1, int b2, int q1,
                        int q2);
+// g_blocks: G1, G2 are per-slice column-major blocks (k x b each) instead of
+// one stacked matrix; sig (row stride r1) and rank receive the slice
+// statistics when non-null.
 cudaError_t launch_slice_tucker(tr_dtype dt, int n, int n1, int n2, int r1, int r2, int b1, int b2,
                                 int q1, int q2, const void *Abar, void *Gbar, const void *G1,
                                 const void *G2, void *ws, const ShrinkScalars &sh, void *F1_out,
-                                void *F2_out, cudaStream_t s);
+                                void *F2_out, cudaStream_t s, bool g_blocks = false,
+                                void *sig = nullptr, int *rank = nullptr);
+// n per-slice Gaussian blocks of per_slice elements (Philox4x32-10 counter
+// (m/4, j, t, stream), Box-Muller; t from dt_dev when non-null).
+cudaError_t launch_gaussian_blocks(tr_dtype dt, int n, int64_t per_slice, void *out, uint64_t seed,
+                                   int t, const int *dt_dev, uint32_t stream, cudaStream_t s);
 
 // ---- learned sketch widths and the rank-predictor MLP (learned.cu) ----
 struct LearnedWork {

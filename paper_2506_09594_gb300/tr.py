@@ -22,7 +22,7 @@ STATUS_NAMES = ["TR_OK", "TR_EINVAL", "TR_ENOMEM", "TR_ECUDA", "TR_ENUMERIC", "T
 TR_F32, TR_F64 = 0, 1
 TR_PEN_L1, TR_PEN_MCP = 0, 1
 TR_NOISE_NONE, TR_NOISE_L1 = 0, 1
-TR_LR_FULLSVD, TR_LR_RSVD, TR_LR_ADAPTIVE, TR_LR_LEARNED = 0, 1, 2, 3
+TR_LR_FULLSVD, TR_LR_RSVD, TR_LR_ADAPTIVE, TR_LR_LEARNED, TR_LR_TUCKER = 0, 1, 2, 3, 4
 TR_PREC_FP32, TR_PREC_TF32, TR_PREC_BF16, TR_PREC_BF16X3 = 0, 1, 2, 3
 TR_MLP_FEATURES, TR_MLP_PARAMS = 16, 35329
 MODEL_MAGIC = b"TRRANK01"

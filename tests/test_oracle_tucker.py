@@ -141,3 +141,18 @@ def test_canonical_signs():
     G = tucker.canonical_signs(F)
     assert np.array_equal(G, F * np.array([-1.0, -1.0, 1.0]))   # ties: the first entry
     assert np.array_equal(tucker.canonical_signs(G), G)
+
+
+def test_tucker_engine_of_the_prox_is_exact_on_shared_spaces():
+    # the "tucker" engine of svt.transformed_prox (Philox blocks, r = b = l)
+    # on slices sharing spaces of dimensions 4 and 3 <= l: the full-SVD prox
+    rng = np.random.default_rng(8)
+    n, n1, n2 = 10, 30, 26
+    P, _ = np.linalg.qr(rng.standard_normal((n1, 4)))
+    Q, _ = np.linalg.qr(rng.standard_normal((n2, 3)))
+    Ab = np.einsum("ia,jab,kb->jik", P, 3.0 * rng.standard_normal((n, 4, 3)), Q)
+    got, info = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0, engine="tucker", l=6, q=1,
+                                     seed=5, t=2)
+    want, winfo = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0)
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+    assert np.array_equal(info["ranks"], winfo["ranks"])
