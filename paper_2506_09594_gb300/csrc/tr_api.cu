@@ -314,6 +314,16 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     h->aw.eps = prm->adapt_eps;
     h->aw.delta_rel = p->dtype == TR_F64 ? 1e-11 : 1e-5;
   }
+  if (prm->engine == TR_LR_TUCKER) {
+    const int64_t L = (int64_t)(prm->power_iters + 1) * l;
+    if (L > 32 || L > h->n1 || L > h->n2) {
+      tr_status st = fail(nullptr, TR_EUNSUPPORTED,
+                          "shared-Tucker engine: (q + 1) l = %lld above 32 or a mode size",
+                          (long long)L);
+      delete h;
+      return st;
+    }
+  }
   if (l > TR_MAX_L || !slice_smem_limit_ok(h->dtype, (int)h->n1, (int)h->n2, l)) {
     tr_status st = fail(nullptr, TR_EUNSUPPORTED, "slice panels %lld x %d exceed shared memory",
                         (long long)(h->n1 > h->n2 ? h->n1 : h->n2), l);
@@ -403,11 +413,7 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   }
   if (prm->engine == TR_LR_TUCKER) {
     // r = b = l on both spatial modes, q = power_iters Krylov steps
-    const int q = prm->power_iters, L = (q + 1) * l;
-    if (L > 32 || L > h->n1 || L > h->n2) {
-      fail(h, TR_EUNSUPPORTED, "shared-Tucker engine: (q + 1) l = %d above 32 or a mode size", L);
-      return cleanup(TR_EUNSUPPORTED);
-    }
+    const int q = prm->power_iters;
     INIT_CUDA(cudaMalloc(&h->tk_ws, tucker_ws_bytes(h->dtype, (int)h->n, (int)h->n1, (int)h->n2, l,
                                                    l, l, l, q, q)));
     INIT_CUDA(cudaMalloc(&h->tk_g1, (size_t)h->n * h->n2 * l * h->esz));

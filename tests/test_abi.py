@@ -134,3 +134,11 @@ def test_init_rejects_oversized_problems_without_a_gpu(lib):
     assert st == tr.TR_EUNSUPPORTED
     assert lib.tr_set_observed(None, None, None) == tr.TR_EINVAL
     assert lib.tr_read_residuals(None, None) == tr.TR_EINVAL
+    assert lib.tr_slice_prox_tucker(None, None, None, 0.0, 1, 1, 1, 1, 0, 0, None, None, None,
+                                    None) == tr.TR_EINVAL
+    # shared-Tucker engine: (q + 1) l above 32 (l = 20, q = 1) or a mode size
+    st, _ = _init(lib, 3, [64, 64, 4], engine=tr.TR_LR_TUCKER, rank=10, oversample=10)
+    assert st == tr.TR_EUNSUPPORTED and "Tucker" in lib.tr_last_error(None).decode()
+    st, _ = _init(lib, 3, [64, 10, 4], engine=tr.TR_LR_TUCKER, rank=4, oversample=2,
+                  power_iters=1)
+    assert st == tr.TR_EUNSUPPORTED
