@@ -41,6 +41,9 @@ STREAM_SKETCH = 0      # the sketch Omega of the randomized range finder
 STREAM_ADAPTIVE = 1    # the start block and refills of the adaptive engine
 STREAM_TUCKER_1 = 2    # the mode-1 Gaussian block of the shared-Tucker engine
 STREAM_TUCKER_2 = 4    # the mode-2 Gaussian block of the shared-Tucker engine
+STREAM_AD_TUCKER_1 = 0x10000  # mode-1 start block and refills of the fixed-accuracy
+                              # Tucker engine: stream STREAM_AD_TUCKER_1 + 2*draw
+STREAM_AD_TUCKER_2 = 0x20000  # the same for mode 2
 
 
 def philox4x32_10(counter, key):

@@ -26,6 +26,10 @@ Three engines compute the transform-domain slice map Abar^<j> -> Gbar^<j>:
                              Alg. 2, Gaussian refill on deflation, error
                              indicator E) restated for one face slice; its
                              basis U replaces Q above.
+
+Two more engines compress all slices at once with Tucker factors of the two
+spatial modes shared by every slice (oracle.tucker): ``tucker`` (Alg. 1,
+fixed ranks) and ``ad_tucker`` (Alg. AD-RSTHOSVD-BLBP, fixed accuracy).
 """
 
 import numpy as np
@@ -103,32 +107,25 @@ def defl_qr(A, delta):
     return Qt[:, :s], R, s
 
 
-def adaptive_basis(Ab, eps, b, delta_rel, seed, t, j, max_rank=None):
-    """Alg. 3 restated for one face slice: returns (U, E, history).
+def blbp_basis(A, eps, b, delta, gauss, cap):
+    """Block Lanczos bidiagonalization with deflation and an error estimate:
+    the loop of Alg. 3 (one matrix) and of Alg. "AD-RSTHOSVD-BLBP" (one mode
+    unfolding).  Returns (U, E, history) with U = U^{v} truncated to cap
+    columns and E = ||A||_F^2 - sum ||R^(i)||^2 - sum ||L^(i+1)||^2.
 
-    Readings of the printed algorithm (its indexing is garbled):
+    gauss(cols) returns the next standard Gaussian block (A.shape[1], cols);
+    delta is the absolute deflation tolerance.
+
+    Readings of the printed algorithms (their indexing is garbled):
     U^(0) = 0 and L^(1) = 0 (the first step is plain A V^(1)); U^{v} starts
     empty; when defl-QR of the new V block keeps s < b columns, the b - s
     Gaussian refill columns are appended to V^(i+1) itself (and L^(i+1)
     padded with zero columns), so every block stays b wide; the stopping
-    test is relative, E < eps^2 ||A||_F^2; delta = delta_rel * ||A||_F.
-    Gaussian draws use stream STREAM_ADAPTIVE with counter words
-    (m//4, j, t, STREAM_ADAPTIVE + 2*draw_index).
+    test is relative, E < eps^2 ||A||_F^2.
     """
-    n1, n2 = Ab.shape
-    cap = min(n1, n2) if max_rank is None else min(max_rank, n1, n2)
-    normA2 = float(np.sum(Ab * Ab))
-    delta = delta_rel * np.sqrt(normA2)
+    n1, n2 = A.shape
+    normA2 = float(np.sum(A * A))
     E = normA2
-    draw = 0
-
-    def gauss(cols):
-        nonlocal draw
-        G = philox.gaussian_block(seed, t, j, n2, cols,
-                                  stream=philox.STREAM_ADAPTIVE + 2 * draw)
-        draw += 1
-        return G
-
     V, _ = np.linalg.qr(gauss(b))
     Vcat = V.copy()
     Ucat = np.zeros((n1, 0))
@@ -138,10 +135,10 @@ def adaptive_basis(Ab, eps, b, delta_rel, seed, t, j, max_rank=None):
     if normA2 == 0.0:
         return Ucat, 0.0, hist
     while True:
-        U, R, _ = defl_qr(Ab @ V - U_prev @ L, delta)
+        U, R, _ = defl_qr(A @ V - U_prev @ L, delta)
         Ucat = np.concatenate([Ucat, U], axis=1)
         E -= float(np.sum(R * R))
-        Vn = Ab.T @ U - V @ R.T
+        Vn = A.T @ U - V @ R.T
         Vn = Vn - Vcat @ (Vcat.T @ Vn)
         Vn, Lt, s = defl_qr(Vn, delta)
         Vcat = np.concatenate([Vcat, Vn], axis=1)
@@ -159,6 +156,28 @@ def adaptive_basis(Ab, eps, b, delta_rel, seed, t, j, max_rank=None):
         if E < eps * eps * normA2 or Ucat.shape[1] >= cap or V.shape[1] == 0:
             break
     return Ucat[:, :cap], E, hist
+
+
+def adaptive_basis(Ab, eps, b, delta_rel, seed, t, j, max_rank=None):
+    """Alg. 3 restated for one face slice: returns (U, E, history).
+
+    The loop is blbp_basis with delta = delta_rel * ||A||_F and the rank cap
+    min(n1, n2) (or max_rank).  Gaussian draws use stream STREAM_ADAPTIVE
+    with counter words (m//4, j, t, STREAM_ADAPTIVE + 2*draw_index).
+    """
+    n1, n2 = Ab.shape
+    cap = min(n1, n2) if max_rank is None else min(max_rank, n1, n2)
+    delta = delta_rel * np.sqrt(float(np.sum(Ab * Ab)))
+    draw = 0
+
+    def gauss(cols):
+        nonlocal draw
+        G = philox.gaussian_block(seed, t, j, n2, cols,
+                                  stream=philox.STREAM_ADAPTIVE + 2 * draw)
+        draw += 1
+        return G
+
+    return blbp_basis(Ab, eps, b, delta, gauss, cap)
 
 
 def slice_prox_adaptive(Ab, eps, b, delta_rel, seed, t, j, tau, kind,
@@ -195,6 +214,26 @@ def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
         Cbar, F1, F2 = tucker.rsthosvd_bki(np.asarray(Abar, dtype=np.float64), (ll, ll), (G1, G2),
                                            (q, q))
         Ct, info = transformed_prox(Cbar, tau, kind, theta, gamma)
+        return tucker.mode_product(tucker.mode_product(Ct, F1, 1), F2, 2), info
+    if engine == "ad_tucker":
+        # the fixed-accuracy Tucker form (Alg. "AD-RSTHOSVD-BLBP", order
+        # (1, 2)): tolerance eps, block size b, deflation delta_rel, rank cap
+        # max_rank per mode; draw d of mode m is a Philox block per
+        # transformed slice on stream STREAM_AD_TUCKER_m + 2 d, with the
+        # slice's share of the unfolding's columns as rows, stacked by rows
+        from . import tucker
+        base = {1: philox.STREAM_AD_TUCKER_1, 2: philox.STREAM_AD_TUCKER_2}
+
+        def gauss(mode, rows, cols, draw):
+            return np.concatenate([philox.gaussian_block(seed, t, j, rows // n, cols,
+                                                         base[mode] + 2 * draw)
+                                   for j in range(n)], axis=0)
+
+        Cbar, F1, F2, E = tucker.ad_rsthosvd_blbp(np.asarray(Abar, dtype=np.float64), eps, b,
+                                                  delta_rel, gauss, (max_rank, max_rank))
+        Ct, info = transformed_prox(Cbar, tau, kind, theta, gamma)
+        info["tucker_ranks"] = (F1.shape[1], F2.shape[1])
+        info["tucker_estimates"] = E
         return tucker.mode_product(tucker.mode_product(Ct, F1, 1), F2, 2), info
     Gbar = np.zeros_like(Abar, dtype=np.float64)
     ranks = np.zeros(n, dtype=np.int64)

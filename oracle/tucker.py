@@ -23,6 +23,11 @@ The Gaussian block G is an input (the caller draws it), with one row per
 column of the unfolding.  Unfoldings of a slice stack X[j][i1][i2]:
 mode 1 is the n1 x (n n2) matrix with column j*n2 + i2, mode 2 the
 n2 x (n n1) matrix with column j*n1 + i1.
+
+When the ranks are not known, Alg. "AD-RSTHOSVD-BLBP" takes Alg. 1's place
+(ad_rsthosvd_blbp below): each mode's factor is the block Lanczos basis of
+Alg. 3 grown on the unfolding until its error estimate meets a relative
+tolerance.
 """
 
 import numpy as np
@@ -124,3 +129,65 @@ def transformed_randomized_prox(Abar, tau, kind, ranks, G, q, theta=1.0, gamma=4
     Cbar, F1, F2 = rsthosvd_bki(Abar, ranks, G, q)
     Ct, _ = svt.transformed_prox(Cbar, tau, kind, theta, gamma)
     return mode_product(mode_product(Ct, F1, 1), F2, 2), (Cbar, F1, F2)
+
+
+def ad_rsthosvd_blbp(X, eps, b, delta_rel, gauss, caps=(None, None)):
+    """Alg. "AD-RSTHOSVD-BLBP" (fixed-accuracy Tucker by block Lanczos
+    bidiagonalization) with processing order (1, 2) on a slice stack X.
+
+    For each mode: A = the mode unfolding of the current core C; the factor
+    F = U^{v} is the basis the block Lanczos loop builds (svt.blbp_basis)
+    until its error estimate E falls below eps^2 ||A||_F^2, with deflation
+    tolerance delta = delta_rel * ||A||_F and at most min(A's sizes) columns
+    (or caps[mode - 1]); then C <- C x_mode F^T.
+
+    gauss(mode, rows, cols, draw) returns the draw-th standard Gaussian
+    (rows x cols) block of the mode, rows being the number of columns of
+    that mode's unfolding.
+    Returns the core C, the factors F1, F2 and the final estimates (E1, E2).
+
+    Reading: the printed algorithm names one tolerance epsilon for every
+    mode and compares each mode's E with ||A||_F^2 of that mode's own
+    unfolding, so the total error satisfies
+    ||X - C x_1 F1 x_2 F2||_F^2 <= E1 + E2 <= 2 eps^2 ||X||_F^2."""
+    C = X
+    F, E = [], []
+    for mode in (1, 2):
+        A = unfold(C, mode)
+        cap = min(A.shape) if caps[mode - 1] is None else min(caps[mode - 1], *A.shape)
+        delta = delta_rel * np.sqrt(float(np.sum(A * A)))
+        draws = [0]
+
+        def draw_block(cols, mode=mode, rows=A.shape[1], draws=draws):
+            G = gauss(mode, rows, cols, draws[0])
+            draws[0] += 1
+            return G
+
+        Fm, Em, _ = svt.blbp_basis(A, eps, b, delta, draw_block, cap)
+        C = mode_product_t(C, Fm, mode)
+        F.append(Fm)
+        E.append(Em)
+    return C, F[0], F[1], tuple(E)
+
+
+def fixed_accuracy_gnhtsvt(X, tdims, tau, kind, eps, b, delta_rel, gauss, theta=1.0, gamma=4.0,
+                           caps=(None, None)):
+    """Alg. 4, randomized branch with the fixed-accuracy Tucker form:
+    D(C, L) x_1 F1 x_2 F2 with [C; F1, F2] from ad_rsthosvd_blbp.
+    Returns the result and (C, F1, F2, (E1, E2))."""
+    C, F1, F2, E = ad_rsthosvd_blbp(X, eps, b, delta_rel, gauss, caps)
+    Ct, _ = svt.gnhtsvt(C, tdims, tau, kind, theta, gamma)
+    return mode_product(mode_product(Ct, F1, 1), F2, 2), (C, F1, F2, E)
+
+
+def transformed_fixed_accuracy_prox(Abar, tau, kind, eps, b, delta_rel, gauss, theta=1.0,
+                                    gamma=4.0, caps=(None, None)):
+    """The same operator on the transformed stack Abar = L(A), the form an
+    ADMM step evaluates: the factors are built from the unfoldings of Abar
+    (those of A times an orthogonal matrix, so the first mode's factor spans
+    the same space as in the spatial form when its draws are transformed
+    alike), the core's GNTSVT is the per-slice prox of its transformed
+    slices.  Returns Gbar and (Cbar, F1, F2, (E1, E2))."""
+    Cbar, F1, F2, E = ad_rsthosvd_blbp(Abar, eps, b, delta_rel, gauss, caps)
+    Ct, _ = svt.transformed_prox(Cbar, tau, kind, theta, gamma)
+    return mode_product(mode_product(Ct, F1, 1), F2, 2), (Cbar, F1, F2, E)

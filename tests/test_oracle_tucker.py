@@ -156,3 +156,125 @@ def test_tucker_engine_of_the_prox_is_exact_on_shared_spaces():
     want, winfo = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0)
     assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
     assert np.array_equal(info["ranks"], winfo["ranks"])
+
+
+# ------------------------------------------------ fixed-accuracy Tucker form
+# Alg. "AD-RSTHOSVD-BLBP": per mode, block Lanczos bidiagonalization of the
+# unfolding until the estimate E < eps^2 ||A||_F^2.  Pins from the
+# mathematics: with orthonormal factors the sequential-truncation error is
+# the sum of the per-mode projection errors, and in exact arithmetic (no
+# deflation) the Lanczos relations make E equal each projection error.
+
+def gauss_source(rng):
+    return lambda mode, rows, cols, draw: rng.standard_normal((rows, cols))
+
+
+@pytest.mark.parametrize("kind", [prox.L1, prox.MCP])
+def test_fixed_accuracy_finds_the_shared_dimensions(kind):
+    rng = np.random.default_rng(11)
+    tdims, n1, n2, s1, s2 = (3, 4), 30, 22, 5, 3
+    n = int(np.prod(tdims))
+    X, P, Q = shared_stack(n, n1, n2, s1, s2, rng)
+    got, (C, F1, F2, E) = tucker.fixed_accuracy_gnhtsvt(X, tdims, 0.6, kind, 1e-8, 2, 1e-12,
+                                                        gauss_source(rng), gamma=50.0)
+    assert F1.shape == (n1, s1) and F2.shape == (n2, s2)
+    assert np.linalg.norm(P - F1 @ (F1.T @ P)) < 1e-11
+    assert np.linalg.norm(Q - F2 @ (F2.T @ Q)) < 1e-11
+    want, _ = svt.gnhtsvt(X, tdims, 0.6, kind, gamma=50.0)
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("eps,b", [(0.3, 3), (0.1, 2), (0.05, 4)])
+def test_fixed_accuracy_estimate_is_the_error(eps, b):
+    rng = np.random.default_rng(12)
+    X = shared_stack(8, 40, 30, 10, 8, rng)[0] + 0.05 * rng.standard_normal((8, 40, 30))
+    C, F1, F2, (E1, E2) = tucker.ad_rsthosvd_blbp(X, eps, b, 1e-12, gauss_source(rng))
+    nx = np.sum(X * X)
+    assert np.linalg.norm(F1.T @ F1 - np.eye(F1.shape[1])) < 1e-10
+    assert np.linalg.norm(F2.T @ F2 - np.eye(F2.shape[1])) < 1e-10
+    # per-mode projection errors computed directly
+    A1 = tucker.unfold(X, 1)
+    e1 = np.sum((A1 - F1 @ (F1.T @ A1)) ** 2)
+    C1 = tucker.mode_product_t(X, F1, 1)
+    A2 = tucker.unfold(C1, 2)
+    e2 = np.sum((A2 - F2 @ (F2.T @ A2)) ** 2)
+    assert abs(e1 - E1) < 1e-12 * nx and abs(e2 - E2) < 1e-12 * nx
+    # the reconstruction error is their sum, within the requested accuracy
+    back = tucker.mode_product(tucker.mode_product(C, F1, 1), F2, 2)
+    err = np.sum((X - back) ** 2)
+    assert abs(err - (E1 + E2)) < 1e-12 * nx
+    assert E1 < eps ** 2 * nx and E2 < eps ** 2 * np.sum(C1 * C1)
+    assert err < 2 * eps ** 2 * nx
+    # the rank found is below full: the stop rule ended the loop
+    assert F1.shape[1] < 40 and F2.shape[1] < 30
+
+
+def test_fixed_accuracy_stops_at_the_first_block_that_meets_the_bound():
+    # the loop's history: E decreases, only its last entry is below eps^2 ||A||^2
+    rng = np.random.default_rng(13)
+    A = (rng.standard_normal((50, 12)) * np.geomspace(10.0, 0.1, 12)) @ rng.standard_normal((12, 70))
+    eps = 0.02
+    U, E, hist = svt.blbp_basis(A, eps, 2, 1e-12 * np.linalg.norm(A),
+                                lambda cols: rng.standard_normal((70, cols)), 50)
+    bound = eps ** 2 * np.sum(A * A)
+    es = [h[1] for h in hist]
+    assert all(x > y for x, y in zip(es, es[1:]))
+    assert es[-1] < bound and all(x >= bound for x in es[:-1])
+    assert U.shape[1] == hist[-1][0] and abs(E - es[-1]) == 0.0
+
+
+def test_fixed_accuracy_with_tiny_tolerance_is_the_deterministic_prox():
+    rng = np.random.default_rng(14)
+    tdims, n1, n2 = (5,), 9, 7
+    X = rng.standard_normal((5, n1, n2))
+    got, (_, F1, F2, _) = tucker.fixed_accuracy_gnhtsvt(X, tdims, 0.9, prox.L1, 1e-9, 3, 1e-13,
+                                                        gauss_source(rng))
+    assert F1.shape == (n1, n1) and F2.shape == (n2, n2)
+    assert np.linalg.norm(F1.T @ F1 - np.eye(n1)) < 1e-10
+    assert np.linalg.norm(F2.T @ F2 - np.eye(n2)) < 1e-10
+    want, _ = svt.gnhtsvt(X, tdims, 0.9, prox.L1)
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+
+
+def test_fixed_accuracy_first_mode_is_transform_invariant():
+    # the mode-1 unfolding of L(X) is that of X times an orthogonal matrix:
+    # with the draws transformed alike the factor agrees up to column signs
+    # and the estimate is the same
+    from oracle import transform
+    rng = np.random.default_rng(15)
+    tdims, n1, n2 = (3, 4), 16, 13
+    n = int(np.prod(tdims))
+    X = shared_stack(n, n1, n2, 6, 5, rng)[0] + 0.02 * rng.standard_normal((n, n1, n2))
+    draws = {}
+
+    def spatial(mode, rows, cols, d):
+        if (mode, d) not in draws:
+            draws[(mode, d)] = rng.standard_normal((rows, cols))
+        return draws[(mode, d)]
+
+    def transformed(mode, rows, cols, d):
+        G = spatial(mode, rows, cols, d)
+        return transform.forward(G.reshape(n, rows // n, cols), tdims).reshape(rows, cols)
+
+    _, F1, _, E = tucker.ad_rsthosvd_blbp(X, 0.1, 3, 1e-12, spatial, (None, 1))
+    _, F1b, _, Eb = tucker.ad_rsthosvd_blbp(transform.forward(X, tdims), 0.1, 3, 1e-12,
+                                            transformed, (None, 1))
+    assert F1.shape == F1b.shape and F1.shape[1] < n1
+    sg = np.sign(np.sum(F1 * F1b, axis=0))
+    assert np.abs(F1 - F1b * sg).max() < 1e-10
+    assert abs(E[0] - Eb[0]) < 1e-12 * np.sum(X * X)
+
+
+def test_ad_tucker_engine_of_the_prox_is_exact_on_shared_spaces():
+    # engine "ad_tucker" of svt.transformed_prox (Philox draws per slice)
+    rng = np.random.default_rng(16)
+    n, n1, n2 = 10, 30, 26
+    P, _ = np.linalg.qr(rng.standard_normal((n1, 4)))
+    Q, _ = np.linalg.qr(rng.standard_normal((n2, 3)))
+    Ab = np.einsum("ia,jab,kb->jik", P, 3.0 * rng.standard_normal((n, 4, 3)), Q)
+    got, info = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0, engine="ad_tucker",
+                                     eps=1e-8, b=2, seed=5, t=2)
+    want, winfo = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0)
+    assert info["tucker_ranks"] == (4, 3)
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+    assert np.array_equal(info["ranks"], winfo["ranks"])
