@@ -17,8 +17,8 @@ paper's order and notation:
                 matrices the method draws, Alg. 1 "draw a Gaussian random
                 matrix").
 * ``transform`` the invertible transform L = x_3 U_3 ... x_d U_d with the
-                orthonormal DCT-II (Sec. 2, Eq. trans / orth), and face
-                slices X^<j> (Sec. 2).
+                orthonormal DCT-II or the DFT of the paper's experiments
+                (Sec. 2, Eq. trans / orth), and face slices X^<j> (Sec. 2).
 * ``prox``      scalar proximal maps Prox_{psi,mu} (Eq. equ_gst1) for the
                 l1 and MCP penalties, and GNHTT (Sec. 4.2.1).
 * ``svt``       GNHTSVT D_{Phi,tau}(A, L): the deterministic branch of
@@ -35,7 +35,12 @@ paper's order and notation:
                 the two spatial modes by Alg. 1 (R-STHOSVD-BKI, block Krylov
                 space, orthonormal basis, top singular vectors of
                 Z^T A A^T Z, sequential truncation), then the deterministic
-                GNTSVT of the core (Alg. 4, randomized branch).
+                GNTSVT of the core (Alg. 4, randomized branch); and the
+                fixed-accuracy form, Alg. AD-RSTHOSVD-BLBP.
+* ``ctv``       the gradient-domain prior (GNHTCTV): difference operators
+                nabla_k, the FFT-diagonalised L-update (Eq. coef-tensor,
+                Eq. gnrhtc-L) and one iteration of Alg. 5 with a set Gamma
+                of gradient directions.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force, library routines it does not itself
@@ -43,4 +48,4 @@ call, or published known-answer vectors, except where a docstring says
 "parity unpinned".
 """
 
-from . import philox, transform, prox, svt, admm, learned, tucker  # noqa: F401
+from . import philox, transform, prox, svt, admm, learned, tucker, ctv  # noqa: F401

@@ -235,12 +235,12 @@ def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
         info["tucker_ranks"] = (F1.shape[1], F2.shape[1])
         info["tucker_estimates"] = E
         return tucker.mode_product(tucker.mode_product(Ct, F1, 1), F2, 2), info
-    Gbar = np.zeros_like(Abar, dtype=np.float64)
+    Gbar = np.zeros(Abar.shape, dtype=np.result_type(Abar.dtype, np.float64))
     ranks = np.zeros(n, dtype=np.int64)
     sig = []
     adaptive_ranks = []
     for j in range(n):
-        Ab = np.asarray(Abar[j], dtype=np.float64)
+        Ab = np.asarray(Abar[j]).astype(np.result_type(Abar.dtype, np.float64))
         if engine == "full":
             Gbar[j], s, s2 = slice_prox_full(Ab, tau, kind, theta, gamma)
         elif engine == "rsvd":
@@ -258,11 +258,24 @@ def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
     return Gbar, {"ranks": ranks, "sigma": sig, "adaptive_ranks": adaptive_ranks}
 
 
-def gnhtsvt(A, tdims, tau, kind, theta=1.0, gamma=4.0, engine="full", **kw):
-    """D_{Phi,tau}(A, L) on a slice stack A (n, n1, n2) (Alg. 4)."""
-    Abar = transform.forward(A, tdims)
+def gnhtsvt(A, tdims, tau, kind, theta=1.0, gamma=4.0, engine="full", transform_kind="dct",
+            **kw):
+    """D_{Phi,tau}(A, L) on a slice stack A (n, n1, n2) (Alg. 4).
+
+    With transform_kind="fft" (U U^H = n I, rho = n3 ... nd) the objective
+    tau ||G||_{Phi,L} + ||G - A||_F^2 / 2 equals
+    (1/rho) sum_j [tau sum Phi(sigma(Gbar_j)) + ||Gbar_j - Abar_j||_F^2 / 2], so the
+    minimiser is again the per-slice prox with the same tau, on complex
+    slices (full SVD only).  Slices j and -j of a real tensor are conjugate
+    and the prox commutes with conjugation, so the result is real; its
+    imaginary part (rounding only) is dropped.
+    """
+    if transform_kind == "fft" and engine != "full":
+        raise ValueError("the DFT transform takes the full-SVD engine")
+    Abar = transform.forward(A, tdims, transform_kind)
     Gbar, info = transformed_prox(Abar, tau, kind, theta, gamma, engine, **kw)
-    return transform.inverse(Gbar, tdims), info
+    out = transform.inverse(Gbar, tdims, transform_kind)
+    return (out.real.copy() if np.iscomplexobj(out) else out), info
 
 
 def objective(G, A, tdims, tau, kind, theta=1.0, gamma=4.0):

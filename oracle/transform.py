@@ -14,6 +14,10 @@ U U^H = U^H U = alpha I (Eq. orth).  Here U_n is the orthonormal DCT-II
 matrix U[k, m] = s_k cos(pi (2m + 1) k / (2n)), s_0 = sqrt(1/n),
 s_k = sqrt(2/n) for k > 0, so alpha = 1 and U^{-1} = U^T.  The inverse
 applies U^{-1} mode by mode from d down to 3 (Sec. 2).
+
+kind="fft" takes instead the DFT matrix F_n[k, m] = exp(-2 pi i k m / n), the
+transform of the paper's experiments: F F^H = n I, so alpha = n,
+rho = n3 ... nd and F^{-1} = F^H / n; transformed slices are complex.
 """
 
 import numpy as np
@@ -26,6 +30,39 @@ def dct_matrix(n):
     s = np.full((n, 1), np.sqrt(2.0 / n))
     s[0, 0] = np.sqrt(1.0 / n)
     return s * np.cos(np.pi * (2.0 * m + 1.0) * k / (2.0 * n))
+
+
+def dft_matrix(n):
+    """DFT matrix F_n (n x n): F[k, m] = exp(-2 pi i k m / n), F F^H = n I."""
+    k = np.arange(n, dtype=np.float64)[:, None]
+    m = np.arange(n, dtype=np.float64)[None, :]
+    return np.exp(-2j * np.pi * k * m / n)
+
+
+def _matrix(kind, n):
+    if kind == "dct":
+        return dct_matrix(n)
+    if kind == "fft":
+        return dft_matrix(n)
+    raise ValueError(kind)
+
+
+def _inverse_matrix(kind, n):
+    if kind == "dct":
+        return dct_matrix(n).T
+    if kind == "fft":
+        return dft_matrix(n).conj().T / n
+    raise ValueError(kind)
+
+
+def rho(tdims, kind="dct"):
+    """rho = alpha_3 ... alpha_d: 1 for the orthonormal DCT, n3 ... nd for the DFT."""
+    return 1.0 if kind == "dct" else float(num_slices(tdims))
+
+
+def _as_array(S):
+    S = np.asarray(S)
+    return S.astype(np.complex128 if np.iscomplexobj(S) else np.float64)
 
 
 def num_slices(tdims):
@@ -47,25 +84,26 @@ def mode_product(Xv, U, axis):
     return np.moveaxis(out, 0, axis)
 
 
-def forward(S, tdims):
+def forward(S, tdims, kind="dct"):
     """L(X) on a slice stack S (n, n1, n2): x_3 U_3, then x_4 U_4, ..., x_d U_d."""
     n, n1, n2 = S.shape
     assert n == num_slices(tdims)
-    Xv = np.asarray(S, dtype=np.float64).reshape(tuple(reversed(tdims)) + (n1, n2))
+    Xv = _as_array(S).reshape(tuple(reversed(tdims)) + (n1, n2))
     for mode in range(3, 3 + len(tdims)):
-        U = dct_matrix(tdims[mode - 3])
+        U = _matrix(kind, tdims[mode - 3])
         Xv = mode_product(Xv, U, _mode_axis(tdims, mode))
     return Xv.reshape(n, n1, n2)
 
 
-def inverse(S, tdims):
-    """L^{-1}(X) = X x_d U_d^{-1} ... x_3 U_3^{-1}, with U^{-1} = U^T (alpha = 1)."""
+def inverse(S, tdims, kind="dct"):
+    """L^{-1}(X) = X x_d U_d^{-1} ... x_3 U_3^{-1}; U^{-1} = U^T for the DCT,
+    F^H / n for the DFT."""
     n, n1, n2 = S.shape
     assert n == num_slices(tdims)
-    Xv = np.asarray(S, dtype=np.float64).reshape(tuple(reversed(tdims)) + (n1, n2))
+    Xv = _as_array(S).reshape(tuple(reversed(tdims)) + (n1, n2))
     for mode in range(2 + len(tdims), 2, -1):
-        U = dct_matrix(tdims[mode - 3])
-        Xv = mode_product(Xv, U.T, _mode_axis(tdims, mode))
+        Ui = _inverse_matrix(kind, tdims[mode - 3])
+        Xv = mode_product(Xv, Ui, _mode_axis(tdims, mode))
     return Xv.reshape(n, n1, n2)
 
 
