@@ -405,7 +405,8 @@ tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups);
  *   tr_batch_handle: the handle of problem i (for tr_get_state and the
  *     other per-handle calls; do not tr_free it).
  *   tr_batch_launches: kernels launched by the batch so far.
- *   tr_batch_last_error: message of the last failed batch call.            */
+ *   tr_batch_last_error: message of the calling thread's last failed
+ *     batch call.                                                          */
 typedef struct tr_batch tr_batch;
 tr_status tr_batch_create(tr_batch **b, int nprob, const tr_problem *problems,
                           const tr_params *params, int nstreams, void *cuda_stream);
@@ -419,8 +420,9 @@ const char *tr_batch_last_error(void);
 /* Release all workspace.  Safe on NULL.                                     */
 tr_status tr_free(tr_handle *h);
 
-/* Last error message for `h` (or for the last failed tr_init when h is
- * NULL).  The string is owned by the library.                               */
+/* Last error message for `h` (or, when h is NULL, for the calling thread's
+ * last failed call that had no handle, such as tr_init).  The string is
+ * owned by the library.                                                     */
 const char *tr_last_error(const tr_handle *h);
 
 #ifdef __cplusplus

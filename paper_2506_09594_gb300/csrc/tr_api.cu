@@ -78,7 +78,8 @@ struct tr_handle {
   char err[512] = {0};
 };
 
-static char g_init_err[512] = {0};
+// Messages of failed calls that have no handle, one per calling host thread.
+static thread_local char g_init_err[512] = {0};
 
 static tr_status fail(tr_handle *h, tr_status st, const char *fmt, ...) {
   char *buf = h ? h->err : g_init_err;
@@ -1276,7 +1277,7 @@ struct tr_batch {
   bool graph_on = true;
 };
 
-static char g_batch_err[512] = {0};
+static thread_local char g_batch_err[512] = {0};
 
 static tr_status batch_fail(tr_status st, const char *fmt, ...) {
   va_list ap;

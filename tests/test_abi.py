@@ -142,3 +142,24 @@ def test_init_rejects_oversized_problems_without_a_gpu(lib):
     st, _ = _init(lib, 3, [64, 10, 4], engine=tr.TR_LR_TUCKER, rank=4, oversample=2,
                   power_iters=1)
     assert st == tr.TR_EUNSUPPORTED
+
+
+def test_handleless_error_messages_are_per_thread(lib):
+    # a failed tr_init in one host thread does not overwrite the message
+    # another thread reads for its own failed call
+    import threading
+    st, _ = _init(lib, 3, [4, 4, 100])                                # mode > 64
+    assert st == tr.TR_EUNSUPPORTED
+    mine = lib.tr_last_error(None).decode()
+    seen = {}
+
+    def other():
+        s, _ = _init(lib, 3, [2048, 64, 4])                           # slice rows > 1024
+        seen["st"] = s
+        seen["msg"] = lib.tr_last_error(None).decode()
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["st"] == tr.TR_EUNSUPPORTED and "exceed" in seen["msg"]
+    assert lib.tr_last_error(None).decode() == mine and "64" in mine
