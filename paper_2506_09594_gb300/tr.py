@@ -429,9 +429,15 @@ class Handle:
         _check(load().tr_set_model(self.h, ctypes.c_void_p(w.ctypes.data), int(w.size)), self.h)
 
     def set_observed(self, observed, mask):
-        """Point the handle at other observed data (same shape and dtype)."""
+        """Point the handle at other observed data (same shape and dtype).
+        The binding keeps the last two buffer pairs alive: a step enqueued on
+        the previous pair may still be running on the handle's stream."""
         _check(load().tr_set_observed(self.h, _ptr(observed), _ptr(mask)), self.h)
-        self._keep = (observed, mask)
+        self._remember((observed, mask))
+
+    def _remember(self, pair):
+        self._keep_prev = getattr(self, "_keep", None)
+        self._keep = pair
 
     def graph_mode(self, on=True):
         _check(load().tr_graph_mode(self.h, int(bool(on))), self.h)
@@ -497,8 +503,10 @@ def _check_batch(st):
 class BorrowedHandle(Handle):
     """The handle of one problem of a Batch (owned by the batch)."""
 
-    def __init__(self, h, dims, dtype, params, stream):
+    def __init__(self, h, dims, dtype, params, stream, owner=None, index=0):
         self.h = h
+        self._owner = owner
+        self._index = index
         self.dims = tuple(dims)
         self.dtype = dtype
         self.params = params
@@ -507,6 +515,10 @@ class BorrowedHandle(Handle):
         for d in self.dims[2:]:
             n *= d
         self.shape = (n, self.dims[0], self.dims[1])
+
+    def _remember(self, pair):
+        if self._owner is not None:
+            self._owner._remember(self._index, pair)
 
     def close(self):
         self.h = None
@@ -526,6 +538,7 @@ class Batch:
         probs = (tr_problem * n)()
         prms = (tr_params * n)()
         self._keep = []
+        self._keep_prev = [None] * len(problems)
         self.meta = []
         for i, (obs, mask, dims) in enumerate(problems):
             probs[i].order = len(dims)
@@ -559,12 +572,13 @@ class Batch:
         h = ctypes.c_void_p()
         _check_batch(load().tr_batch_handle(self.b, int(i), ctypes.byref(h)))
         dims, dtype, prm = self.meta[i]
-        return BorrowedHandle(h, dims, dtype, prm, self.stream)
+        return BorrowedHandle(h, dims, dtype, prm, self.stream, owner=self, index=int(i))
 
-    def set_observed(self, observed, mask):
-        """Point the handle at other observed data (same shape and dtype)."""
-        _check(load().tr_set_observed(self.h, _ptr(observed), _ptr(mask)), self.h)
-        self._keep = (observed, mask)
+    def _remember(self, i, pair):
+        # buffers of problem i set through its borrowed handle: keep the
+        # current and the previous pair alive as long as the batch
+        self._keep_prev[i] = self._keep[i]
+        self._keep[i] = pair
 
     def graph_mode(self, on=True):
         _check_batch(load().tr_batch_graph_mode(self.b, int(bool(on))))

@@ -163,3 +163,22 @@ def test_handleless_error_messages_are_per_thread(lib):
     t.join()
     assert seen["st"] == tr.TR_EUNSUPPORTED and "exceed" in seen["msg"]
     assert lib.tr_last_error(None).decode() == mine and "64" in mine
+
+
+def test_binding_keeps_the_current_and_previous_buffers_alive():
+    # tr_set_observed switches buffer pairs while a step enqueued on the
+    # previous pair may still run: the binding holds both, for plain handles
+    # and for the borrowed handles of a batch (whose references the batch keeps)
+    h = tr.Handle.__new__(tr.Handle)
+    h._keep = ("M0", "m0")
+    h._remember(("M1", "m1"))
+    h._remember(("M2", "m2"))
+    assert h._keep == ("M2", "m2") and h._keep_prev == ("M1", "m1")
+    b = tr.Batch.__new__(tr.Batch)
+    b._keep = [("A", "a"), ("B", "b")]
+    b._keep_prev = [None, None]
+    bh = tr.BorrowedHandle(None, (4, 4, 2), None, None, 0, owner=b, index=1)
+    bh._remember(("C", "c"))
+    del bh
+    assert b._keep == [("A", "a"), ("C", "c")] and b._keep_prev == [None, ("B", "b")]
+    assert not hasattr(tr.Batch, "set_observed")
