@@ -174,6 +174,43 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+class TrArgError(TrError, ValueError):
+    """A tensor argument refused by the binding before the C call (the C ABI
+    sees only pointers, so dtype, device, layout and size are checked here)."""
+
+    def __init__(self, msg):
+        super().__init__(TR_EINVAL, msg)
+
+
+def _need(t, name, dtype, numel, device="cuda", optional=False):
+    """Check that `t` is a contiguous tensor on `device` of `dtype` (a dtype
+    or a tuple of them) holding at least `numel` elements; None passes when
+    the C call accepts NULL (optional)."""
+    import torch
+    if t is None:
+        if optional:
+            return
+        raise TrArgError("%s: a tensor is required" % name)
+    if not isinstance(t, torch.Tensor):
+        raise TrArgError("%s: expected a torch tensor, got %s" % (name, type(t).__name__))
+    if t.device.type != device:
+        raise TrArgError("%s: expected a %s tensor, got one on %s" % (name, device, t.device))
+    ok = dtype if isinstance(dtype, tuple) else (dtype,)
+    if dtype is not None and t.dtype not in ok:
+        raise TrArgError("%s: expected %s, got %s" % (name, " or ".join(map(str, ok)), t.dtype))
+    if not t.is_contiguous():
+        raise TrArgError("%s: must be contiguous" % name)
+    if t.numel() < numel:
+        raise TrArgError("%s: holds %d elements, the call needs %d" % (name, t.numel(), numel))
+
+
+def _float_dtype(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype not in (torch.float32, torch.float64):
+        raise TrArgError("%s: expected a float32 or float64 tensor" % name)
+    return {torch.float32: TR_F32, torch.float64: TR_F64}[t.dtype]
+
+
 def slice_prox_noalloc(Abar, Gbar, l, q, tau, t, seed=0, phi=TR_PEN_MCP, theta=1.0,
                        gamma=4000.0, stream=None):
     """tr_slice_prox_noalloc: the slice pass with no device allocation.
@@ -184,8 +221,12 @@ def slice_prox_noalloc(Abar, Gbar, l, q, tau, t, seed=0, phi=TR_PEN_MCP, theta=1
     fixed array inside the library.  Raises TrError on failure.
     """
     import torch
-    dt = {torch.float32: TR_F32, torch.float64: TR_F64}[Abar.dtype]
+    dt = _float_dtype(Abar, "Abar")
+    if Abar.dim() != 3:
+        raise TrArgError("Abar: expected an (n, n1, n2) tensor")
     n, n1, n2 = Abar.shape
+    _need(Abar, "Abar", Abar.dtype, n * n1 * n2)
+    _need(Gbar, "Gbar", Abar.dtype, n * n1 * n2)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     buf = ctypes.create_string_buffer(256)
@@ -234,8 +275,13 @@ def load_model(path):
 def features(sig, rank, width, thr, thr0, tfrac, stream=None):
     """tr_features: (n, 16) float32 features from per-slice singular values."""
     import torch
+    dt = _float_dtype(sig, "sig")
+    if sig.dim() != 2:
+        raise TrArgError("sig: expected an (n, ldsig) tensor")
     n, ldsig = sig.shape
-    dt = {torch.float32: TR_F32, torch.float64: TR_F64}[sig.dtype]
+    _need(sig, "sig", sig.dtype, n * ldsig)
+    _need(rank, "rank", torch.int32, n)
+    _need(width, "width", torch.int32, n)
     out = torch.empty((n, TR_MLP_FEATURES), dtype=torch.float32, device=sig.device)
     _check(load().tr_features(dt, n, _ptr(sig), ldsig, _ptr(rank), _ptr(width), float(thr),
                               float(thr0), float(tfrac), _ptr(out), _stream(stream)))
@@ -245,7 +291,8 @@ def features(sig, rank, width, thr, thr0, tfrac, stream=None):
 def plan_widths(yhat, oversample, lmax, stream=None):
     """tr_plan_widths: (width per slice, ids sorted by class, class counts)."""
     import torch
-    n = yhat.shape[0]
+    _need(yhat, "yhat", torch.float32, 0)
+    n = yhat.numel()
     width = torch.empty(n, dtype=torch.int32, device=yhat.device)
     ids = torch.empty(n, dtype=torch.int32, device=yhat.device)
     counts = torch.empty((lmax + 7) // 8, dtype=torch.int32, device=yhat.device)
@@ -263,6 +310,9 @@ def mlp_init(seed, device="cuda", stream=None):
 
 def mlp_forward(params, X, stream=None):
     import torch
+    _need(params, "params", torch.float32, TR_MLP_PARAMS)
+    _need(X, "X", torch.float32, 0)
+    _need(X, "X", torch.float32, X.shape[0] * TR_MLP_FEATURES)
     y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
     _check(load().tr_mlp_forward(_ptr(params), _ptr(X), int(X.shape[0]), _ptr(y), _stream(stream)))
     return y
@@ -270,6 +320,10 @@ def mlp_forward(params, X, stream=None):
 
 def mlp_loss_grad(params, X, y, under_weight, stream=None):
     import torch
+    _need(params, "params", torch.float32, TR_MLP_PARAMS)
+    _need(X, "X", torch.float32, 0)
+    _need(X, "X", torch.float32, X.shape[0] * TR_MLP_FEATURES)
+    _need(y, "y", torch.float32, X.shape[0])
     grad = torch.empty_like(params)
     loss = torch.empty(1, dtype=torch.float32, device=params.device)
     _check(load().tr_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(y), int(X.shape[0]),
@@ -278,6 +332,10 @@ def mlp_loss_grad(params, X, y, under_weight, stream=None):
 
 
 def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    import torch
+    _need(params, "params", torch.float32, 0)
+    for t, name in ((grad, "grad"), (m, "m"), (v, "v")):
+        _need(t, name, torch.float32, params.numel())
     _check(load().tr_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(params.numel()),
                               float(lr), float(beta1), float(beta2), float(eps), int(step),
                               _stream(stream)))
@@ -286,6 +344,10 @@ def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, str
 def mlp_train(params, X, y, batch, steps, lr, under_weight, seed, stream=None):
     """tr_mlp_train in place on `params`; returns the per-step loss (device)."""
     import torch
+    _need(params, "params", torch.float32, TR_MLP_PARAMS)
+    _need(X, "X", torch.float32, 0)
+    _need(X, "X", torch.float32, X.shape[0] * TR_MLP_FEATURES)
+    _need(y, "y", torch.float32, X.shape[0])
     hist = torch.empty(max(int(steps), 1), dtype=torch.float32, device=params.device)
     _check(load().tr_mlp_train(_ptr(params), _ptr(X), _ptr(y), int(X.shape[0]), int(batch),
                                int(steps), float(lr), float(under_weight), int(seed), _ptr(hist),
@@ -299,13 +361,14 @@ class Handle:
     def __init__(self, observed, mask, dims, params=None, stream=None, **kw):
         import torch
         lib = load()
-        if not (observed.is_cuda and mask.is_cuda):
-            raise ValueError("observed and mask must be CUDA tensors")
-        if mask.dtype != torch.uint8:
-            raise ValueError("mask must be uint8")
+        dt = _float_dtype(observed, "observed")
         self.dtype = observed.dtype
-        dt = {torch.float32: TR_F32, torch.float64: TR_F64}[observed.dtype]
         self.dims = tuple(int(d) for d in dims)
+        N = 1
+        for d in self.dims:
+            N *= max(d, 0)
+        _need(observed, "observed", observed.dtype, N)
+        _need(mask, "mask", torch.uint8, N)
         prob = tr_problem()
         prob.order = len(self.dims)
         for i, d in enumerate(self.dims):
@@ -332,6 +395,13 @@ class Handle:
         import torch
         return torch.empty(self.shape, dtype=self.dtype, device="cuda")
 
+    def _numel(self):
+        return self.shape[0] * self.shape[1] * self.shape[2]
+
+    def _same(self, t, name, optional=False):
+        """t must hold one tensor of this problem (N elements of its dtype)."""
+        _need(t, name, self.dtype, self._numel(), optional=optional)
+
     def step(self, info=False):
         if info:
             si = tr_step_info()
@@ -342,6 +412,7 @@ class Handle:
 
     def recover(self, L_out=None, check=True):
         si = tr_step_info()
+        self._same(L_out, "L_out", optional=True)
         st = load().tr_recover(self.h, _ptr(L_out), ctypes.byref(si))
         if check:
             _check(st, self.h)
@@ -362,21 +433,27 @@ class Handle:
         return L
 
     def set_state(self, L, E, Y, Lam, G, mu, t):
+        for x, name in ((L, "L"), (E, "E"), (Y, "Y"), (Lam, "Lam"), (G, "G")):
+            self._same(x, name, optional=True)       # None: keep that tensor
         _check(load().tr_set_state(self.h, _ptr(L), _ptr(E), _ptr(Y), _ptr(Lam), _ptr(G),
                                    float(mu), int(t)), self.h)
 
     def transform_forward(self, src):
+        self._same(src, "src")
         dst = self._new()
         _check(load().tr_transform_forward(self.h, _ptr(src), _ptr(dst)), self.h)
         return dst
 
     def transform_inverse(self, src):
+        self._same(src, "src")
         dst = self._new()
         _check(load().tr_transform_inverse(self.h, _ptr(src), _ptr(dst)), self.h)
         return dst
 
     def slice_prox(self, Abar, tau, t, out=None):
+        self._same(Abar, "Abar")
         Gbar = self._new() if out is None else out
+        self._same(Gbar, "out")
         _check(load().tr_slice_prox(self.h, _ptr(Abar), _ptr(Gbar), float(tau), int(t)), self.h)
         return Gbar
 
@@ -385,8 +462,14 @@ class Handle:
         """tr_slice_prox_tucker: the shared-Tucker randomized prox of a
         transformed stack; returns Gbar (and F1, F2 when factors)."""
         import torch
+        self._same(Abar, "Abar")
         Gbar = self._new() if out is None else out
+        self._same(Gbar, "out")
         r1, r2 = ranks
+        n, n1, n2 = self.shape
+        # G1 is (n n2) x b1 and G2 (n r1) x b2, column-major
+        _need(G1, "G1", self.dtype, n * n2 * max(int(blocks[0]), 0))
+        _need(G2, "G2", self.dtype, n * max(int(r1), 0) * max(int(blocks[1]), 0))
         F1 = F2 = None
         if factors:
             F1 = torch.empty((r1, self.dims[0]), dtype=Abar.dtype, device=Abar.device)
@@ -432,6 +515,9 @@ class Handle:
         """Point the handle at other observed data (same shape and dtype).
         The binding keeps the last two buffer pairs alive: a step enqueued on
         the previous pair may still be running on the handle's stream."""
+        import torch
+        self._same(observed, "observed")
+        _need(mask, "mask", torch.uint8, self._numel())
         _check(load().tr_set_observed(self.h, _ptr(observed), _ptr(mask)), self.h)
         self._remember((observed, mask))
 
@@ -541,6 +627,12 @@ class Batch:
         self._keep_prev = [None] * len(problems)
         self.meta = []
         for i, (obs, mask, dims) in enumerate(problems):
+            N = 1
+            for d in dims:
+                N *= max(int(d), 0)
+            _float_dtype(obs, "problems[%d] observed" % i)
+            _need(obs, "problems[%d] observed" % i, obs.dtype, N)
+            _need(mask, "problems[%d] mask" % i, torch.uint8, N)
             probs[i].order = len(dims)
             for k, d in enumerate(dims):
                 probs[i].dims[k] = int(d)

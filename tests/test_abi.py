@@ -182,3 +182,38 @@ def test_binding_keeps_the_current_and_previous_buffers_alive():
     del bh
     assert b._keep == [("A", "a"), ("C", "c")] and b._keep_prev == [None, ("B", "b")]
     assert not hasattr(tr.Batch, "set_observed")
+
+
+def test_binding_refuses_bad_tensors_before_the_c_call(lib):
+    # the C ABI sees only pointers: dtype, device, layout and size are checked
+    # by the binding, with an error that is both a TrError (TR_EINVAL) and a
+    # ValueError
+    torch = pytest.importorskip("torch")
+    need = tr._need
+    x = torch.zeros((4, 6), dtype=torch.float32)
+    need(x, "x", torch.float32, 24, device="cpu")
+    need(None, "x", torch.float32, 24, device="cpu", optional=True)
+    for args, what in (((x, "x", torch.float64, 24), "float64"),
+                       ((x, "x", torch.float32, 25), "needs 25"),
+                       ((x.t(), "x", torch.float32, 24), "contiguous"),
+                       ((None, "x", torch.float32, 1), "required"),
+                       ((x.numpy(), "x", torch.float32, 1), "torch tensor")):
+        with pytest.raises(tr.TrArgError) as ei:
+            need(*args, device="cpu")
+        assert what in str(ei.value) and ei.value.status == tr.TR_EINVAL
+        assert isinstance(ei.value, ValueError)
+    with pytest.raises(tr.TrArgError, match="cuda"):
+        need(x, "x", torch.float32, 24)
+    # entry points refuse host tensors, wrong dtypes and short buffers
+    M = torch.zeros((2, 4, 4))
+    mask = torch.ones((2, 4, 4), dtype=torch.uint8)
+    with pytest.raises(tr.TrArgError):
+        tr.Handle(M, mask, (4, 4, 2))
+    with pytest.raises(tr.TrArgError):
+        tr.Handle(M.to(torch.int32), mask, (4, 4, 2))
+    with pytest.raises(tr.TrArgError):
+        tr.slice_prox_noalloc(M, M, 4, 1, 0.1, 0)
+    with pytest.raises(tr.TrArgError):
+        tr.mlp_forward(torch.zeros(tr.TR_MLP_PARAMS), torch.zeros((3, tr.TR_MLP_FEATURES)))
+    with pytest.raises(tr.TrArgError):
+        tr.Batch([(M, mask, (4, 4, 2))], tr.default_params())
