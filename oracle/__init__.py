@@ -41,6 +41,9 @@ paper's order and notation:
                 nabla_k, the FFT-diagonalised L-update (Eq. coef-tensor,
                 Eq. gnrhtc-L) and one iteration of Alg. 5 with a set Gamma
                 of gradient directions.
+* ``onebit``    the one-bit completion model GNOBHTC: one iteration of
+                Alg. 6 (box-constrained L-step derived from Eq.
+                1bittensorqqqq, FFT Z-step, GNHTSVT G-steps).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force, library routines it does not itself
@@ -48,4 +51,4 @@ call, or published known-answer vectors, except where a docstring says
 "parity unpinned".
 """
 
-from . import philox, transform, prox, svt, admm, learned, tucker, ctv  # noqa: F401
+from . import philox, transform, prox, svt, admm, learned, tucker, ctv, onebit  # noqa: F401

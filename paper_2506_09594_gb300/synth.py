@@ -170,3 +170,17 @@ def lowrank_plus_noise_stack(n, n1, n2, rank, noise, seed):
         out[j] = A @ B.T / np.sqrt(max(r, 1))
     out += noise * rng.standard_normal(out.shape)
     return out
+
+
+def one_bit_observations(Lstar, m, theta, noise_sd, rng):
+    """Dithered one-bit samples of a tensor (the observation model of the
+    one-bit completion model): m entries drawn uniformly with replacement,
+    y_k = Lstar[s_k] + eps_k with eps_k ~ N(0, noise_sd^2), and
+    q_k = sign(y_k + xi_k) with dither xi_k ~ U[-theta, theta] (sign(0) = +1).
+    Returns (s, q): flat entry indices (int64) and signs (+-1, float64)."""
+    flat = np.asarray(Lstar, dtype=np.float64).ravel()
+    s = rng.integers(0, flat.size, size=int(m))
+    y = flat[s] + noise_sd * rng.standard_normal(int(m))
+    xi = rng.uniform(-theta, theta, size=int(m))
+    q = np.where(y + xi >= 0.0, 1.0, -1.0)
+    return s.astype(np.int64), q
