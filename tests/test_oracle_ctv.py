@@ -279,3 +279,36 @@ def test_dft_transform_needs_the_full_engine():
     with pytest.raises(ValueError):
         svt.gnhtsvt(np.zeros((4, 3, 3)), (4,), 1.0, prox.L1, engine="rsvd", transform_kind="fft",
                     l=2)
+
+
+def test_hartley_basis_diagonalises_the_difference_operators():
+    # the real Hartley matrix H[k, m] = cas(2 pi k m / n)/sqrt(n) is symmetric,
+    # orthogonal and its own inverse, and diagonalises every symmetric
+    # circulant, D^T D among them (eigenvalues 2 - 2 cos(2 pi k / n)); so the
+    # FFT solve of Eq. gnrhtc-L equals real mode products with H
+    for n in (5, 8, 20):
+        a = 2 * np.pi * np.outer(np.arange(n), np.arange(n)) / n
+        H = (np.cos(a) + np.sin(a)) / np.sqrt(n)
+        D = ctv.difference_matrix(n)
+        lam = 2 - 2 * np.cos(2 * np.pi * np.arange(n) / n)
+        assert np.abs(H @ H - np.eye(n)).max() < 1e-13
+        assert np.abs(H @ D.T @ D @ H - np.diag(lam)).max() < 1e-12
+    rng = np.random.default_rng(10)
+    tdims, shape, modes = (6,), (6, 8, 10), (1, 2, 3)
+    R0 = rng.standard_normal(shape)
+    Rk = {k: rng.standard_normal(shape) for k in modes}
+    rhs = R0 + sum(roll_grad_t(Rk[k], tdims, k) for k in modes)
+
+    def hartley(n):
+        a = 2 * np.pi * np.outer(np.arange(n), np.arange(n)) / n
+        return (np.cos(a) + np.sin(a)) / np.sqrt(n)
+
+    def apply(W):
+        W = np.einsum("ab,bij->aij", hartley(6), W)
+        W = np.einsum("ia,jab->jib", hartley(8), W)
+        return np.einsum("jib,cb->jic", W, hartley(10))
+
+    lam = [2 - 2 * np.cos(2 * np.pi * np.arange(n) / n) for n in (6, 8, 10)]
+    den = 1 + lam[0][:, None, None] + lam[1][None, :, None] + lam[2][None, None, :]
+    got = apply(apply(rhs) / den)
+    assert np.abs(got - ctv.l_update(R0, Rk, tdims, modes)).max() < 1e-12
