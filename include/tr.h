@@ -267,6 +267,34 @@ tr_status tr_slice_prox_noalloc(tr_dtype dtype, int n, int n1, int n2, const voi
                                 double gamma, double tau, uint64_t seed, int t,
                                 void *cuda_stream, char *err, size_t err_len);
 
+/* ---- Gradient-domain building blocks (GNHTCTV prior) -------------------
+ * The operators of the gradient-domain model (Def. gradient tensor, Def.
+ * GNHTCTV, Eq. coef-tensor, Eq. gnrhtc-L); they need no handle.  Tensors
+ * are device buffers in the face-slice layout above, shape given by `order`
+ * (2..8) and `dims` (host array n1, n2, n3, ...), dtype elements.  Work is
+ * enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy stream); `err`
+ * (may be NULL) receives a message of at most err_len bytes on failure.
+ *   tr_grad: dst = nabla_k(src) = src x_k D_{n_k}, the periodic forward
+ *     difference (nabla_k X)[.., i_k, ..] = X[.., i_k + 1 mod n_k, ..] -
+ *     X[.., i_k, ..], for mode k = `mode` (1..order); with adjoint != 0
+ *     dst = nabla_k^T(src), the periodic backward difference.  src and dst
+ *     must not alias.
+ *   tr_gradient_solve: out = (I + sum_{k in Gamma} nabla_k^T nabla_k)^{-1} rhs,
+ *     Gamma = the modes whose bit (k - 1) is set in `modes` (empty: a
+ *     copy); the L-system of Eq. coef-tensor, solved as Eq. gnrhtc-L does by
+ *     diagonalising every nabla_k^T nabla_k, here with the real Hartley
+ *     basis (mode products with cas(2 pi a b / n)/sqrt(n)) instead of the
+ *     complex FFT.  rhs and out must not alias.  Allocates its workspace
+ *     (one tensor plus the Hartley matrices) with stream-ordered
+ *     allocation.  Each mode in Gamma may have at most 2048 entries.
+ * Errors: TR_EINVAL (dtype, shape, mode, pointers), TR_EUNSUPPORTED (mode
+ * sizes or a tensor beyond one launch per product), TR_ENOMEM, TR_ECUDA.    */
+tr_status tr_grad(tr_dtype dtype, int order, const int64_t *dims, int mode, int adjoint,
+                  const void *src, void *dst, void *cuda_stream, char *err, size_t err_len);
+tr_status tr_gradient_solve(tr_dtype dtype, int order, const int64_t *dims, uint32_t modes,
+                            const void *rhs, void *out, void *cuda_stream, char *err,
+                            size_t err_len);
+
 /* ---- Learned sketch widths (engine TR_LR_LEARNED) ----------------------
  * Not in the paper, which fixes one sketch rank (Alg. 1) or grows the basis
  * to an accuracy (Alg. 3) and leaves learned sketching to future work

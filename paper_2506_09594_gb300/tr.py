@@ -90,6 +90,12 @@ _SIGS = {
                                              ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_int, _P,
                                              ctypes.c_char_p, ctypes.c_size_t]),
+    "tr_grad": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_char_p,
+                               ctypes.c_size_t]),
+    "tr_gradient_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32, _P, _P,
+                                         _P, ctypes.c_char_p, ctypes.c_size_t]),
     "tr_mlp_param_count": (ctypes.c_int64, []),
     "tr_set_model": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "tr_last_slice_widths": (ctypes.c_int, [_P, _P]),
@@ -236,6 +242,55 @@ def slice_prox_noalloc(Abar, Gbar, l, q, tau, t, seed=0, phi=TR_PEN_MCP, theta=1
     if st != TR_OK:
         raise TrError(st, buf.value.decode())
     return Gbar
+
+
+def _dims_array(dims):
+    arr = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+    n = 1
+    for d in dims:
+        n *= max(int(d), 0)
+    return arr, n
+
+
+def grad(src, dims, mode, adjoint=False, out=None, stream=None):
+    """tr_grad: nabla_mode(src) (or its adjoint) of a face-slice stack of the
+    tensor with sizes `dims`; returns `out`."""
+    import torch
+    dt = _float_dtype(src, "src")
+    arr, N = _dims_array(dims)
+    _need(src, "src", src.dtype, N)
+    if out is None:
+        out = torch.empty_like(src)
+    _need(out, "out", src.dtype, N)
+    buf = ctypes.create_string_buffer(256)
+    st = load().tr_grad(dt, len(dims), arr, int(mode), int(bool(adjoint)), _ptr(src), _ptr(out),
+                        _stream(stream), buf, 256)
+    if st != TR_OK:
+        raise TrError(st, buf.value.decode())
+    return out
+
+
+def gradient_solve(rhs, dims, modes, out=None, stream=None):
+    """tr_gradient_solve: (I + sum_{k in modes} nabla_k^T nabla_k)^{-1} rhs for
+    the modes listed (1-based); returns `out`."""
+    import torch
+    dt = _float_dtype(rhs, "rhs")
+    arr, N = _dims_array(dims)
+    _need(rhs, "rhs", rhs.dtype, N)
+    if out is None:
+        out = torch.empty_like(rhs)
+    _need(out, "out", rhs.dtype, N)
+    mask = 0
+    for k in modes:
+        if not 1 <= int(k) <= len(dims):
+            raise TrArgError("modes: %r is not a mode of an order-%d tensor" % (k, len(dims)))
+        mask |= 1 << (int(k) - 1)
+    buf = ctypes.create_string_buffer(256)
+    st = load().tr_gradient_solve(dt, len(dims), arr, mask, _ptr(rhs), _ptr(out), _stream(stream),
+                                  buf, 256)
+    if st != TR_OK:
+        raise TrError(st, buf.value.decode())
+    return out
 
 
 def _stream(stream):

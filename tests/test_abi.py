@@ -217,3 +217,28 @@ def test_binding_refuses_bad_tensors_before_the_c_call(lib):
         tr.mlp_forward(torch.zeros(tr.TR_MLP_PARAMS), torch.zeros((3, tr.TR_MLP_FEATURES)))
     with pytest.raises(tr.TrArgError):
         tr.Batch([(M, mask, (4, 4, 2))], tr.default_params())
+
+
+def test_gradient_building_blocks_validate_without_gpu(lib):
+    # tr_grad / tr_gradient_solve refuse bad arguments before any CUDA call
+    dims = (ctypes.c_int64 * 3)(8, 6, 4)
+    buf = ctypes.create_string_buffer(128)
+    a, b = ctypes.c_void_p(256), ctypes.c_void_p(512)
+    assert lib.tr_grad(7, 3, dims, 1, 0, a, b, None, buf, 128) == tr.TR_EINVAL
+    assert lib.tr_grad(tr.TR_F32, 1, dims, 1, 0, a, b, None, buf, 128) == tr.TR_EINVAL
+    assert lib.tr_grad(tr.TR_F32, 3, dims, 4, 0, a, b, None, buf, 128) == tr.TR_EINVAL
+    assert lib.tr_grad(tr.TR_F32, 3, dims, 0, 0, a, b, None, buf, 128) == tr.TR_EINVAL
+    assert lib.tr_grad(tr.TR_F32, 3, dims, 1, 0, a, a, None, buf, 128) == tr.TR_EINVAL
+    assert b"distinct" in buf.value
+    assert lib.tr_gradient_solve(tr.TR_F32, 3, dims, 0b1000, a, b, None, buf, 128) == tr.TR_EINVAL
+    assert lib.tr_gradient_solve(tr.TR_F64, 3, dims, 0b011, a, a, None, buf, 128) == tr.TR_EINVAL
+    zero = (ctypes.c_int64 * 3)(8, 0, 4)
+    assert lib.tr_gradient_solve(tr.TR_F32, 3, zero, 0b011, a, b, None, buf, 128) == tr.TR_EINVAL
+    big = (ctypes.c_int64 * 3)(4096, 6, 4)                  # a solved mode above 2048
+    assert lib.tr_gradient_solve(tr.TR_F32, 3, big, 0b001, a, b, None, buf, 128) == \
+        tr.TR_EUNSUPPORTED
+    tall = (ctypes.c_int64 * 2)(1 << 23, 1)                 # mode-2 product rows beyond one grid
+    assert lib.tr_gradient_solve(tr.TR_F32, 2, tall, 0b010, a, b, None, buf, 128) == \
+        tr.TR_EUNSUPPORTED
+    with pytest.raises(tr.TrArgError):
+        tr.gradient_solve(pytest.importorskip("torch").zeros((4, 8, 6)), (8, 6, 4), (5,))
