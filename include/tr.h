@@ -295,6 +295,66 @@ tr_status tr_gradient_solve(tr_dtype dtype, int order, const int64_t *dims, uint
                             const void *rhs, void *out, void *cuda_stream, char *err,
                             size_t err_len);
 
+/* ---- One-bit completion, GNOBHTC (Alg. 6) --------------------------------
+ * Recovers L from m dithered one-bit samples q_k = sign(L*[s_k] + eps_k +
+ * xi_k), xi_k ~ U[-theta, theta] (Prop. one-bitequ: theta q_k stands in for
+ * the sample), by the ADMM of Alg. 6 on Eq. 1bittensorqqqq:
+ *   1. L = clip((m mu Z + J1 - m Y) / (m mu + J2), -alpha, alpha), with
+ *      J1 = sum_k theta q_k P_k and J2 = sum_k P_k (the L-subproblem is one
+ *      box-constrained quadratic per entry)                      (Eq. 1bit-L)
+ *   2. (I + sum_{i in Gamma} nabla_i^T nabla_i) Z =
+ *      L + Y/mu + sum_i nabla_i^T (G_i - Lambda_i/mu)             (Eq. 1bit-Z)
+ *   3. G_i = D_{Phi, lambda/(gamma mu)}(nabla_i Z + Lambda_i/mu, L), gamma =
+ *      |Gamma|, by the per-slice randomized engine (sketch width rank +
+ *      oversample, power_iters, Philox key seed, counter word t)  (Eq. 1bit-g)
+ *   4. Y += mu (L - Z); Lambda_i += mu (nabla_i Z - G_i);
+ *      mu = min(mu_max, growth mu)                          (Eq. 1bit-Y..MU)
+ * L is the orthonormal DCT-II along modes 3..d, as for tr_init.
+ *   tr_onebit_create: a problem of order 3..8 with sizes `dims` (host) and
+ *     dtype; `idx` (device, m int64) holds the flat face-slice index of each
+ *     sample, `sign` (device, m int8) its sign (> 0: +1, else -1); both are
+ *     read once (J1, J2 are formed here) and may be freed afterwards.
+ *     Initialises L = Z = Y = G_i = Lambda_i = 0, mu = mu0, t = 0 (Alg. 6).
+ *     Allocates about (9 + 2 |Gamma|) tensors plus an internal tr_init
+ *     handle.  An index outside the tensor gives TR_EINVAL.
+ *   tr_onebit_step: one iteration on the stream; with rel_change non-NULL
+ *     it synchronises and returns ||L^{t+1} - L^t||_F / ||L^t||_F (the stop
+ *     quantity of Alg. 6; +inf when L^t = 0).
+ *   tr_onebit_get_state / tr_onebit_set_state: copy L, Z, Y (N elements
+ *     each) and G, Lambda (|Gamma| tensors back to back, modes ascending)
+ *     out of / into the object (device buffers; NULL skips one); both
+ *     synchronise.
+ * Errors: TR_EINVAL, TR_EUNSUPPORTED (shapes the internal handle refuses,
+ * more than 2^31 - 1 entries or samples), TR_ENOMEM, TR_ECUDA.              */
+typedef struct tr_onebit tr_onebit;
+typedef struct {
+  uint32_t modes;                  /* Gamma: bit k - 1 set for mode k        */
+  double lambda, theta, alpha;     /* lambda, dither half-width, ||L||_inf   */
+  double mu0, mu_max, growth;      /* mu^0, mu^max, vartheta                 */
+  double tol;                      /* varpi of the stop test                 */
+  int max_iter;
+  tr_penalty phi;  double phi_theta, phi_gamma;
+  int rank, oversample, power_iters;
+  uint64_t seed;
+  tr_prec prec;
+} tr_onebit_params;
+
+/* Defaults: Gamma = {1, 2}, lambda = theta = alpha = 1, mu0 = 1e-6,
+ * mu_max = 1e3, growth 1.05 (Alg. 6), tol 1e-5, max_iter 200, Phi = MCP
+ * (theta 1, gamma 4000), rank 10 + oversample 10, q = 1, seed 0, FP32.      */
+void tr_onebit_default_params(tr_onebit_params *p);
+tr_status tr_onebit_create(tr_onebit **ob, tr_dtype dtype, int order, const int64_t *dims,
+                           int64_t m, const int64_t *idx, const int8_t *sign,
+                           const tr_onebit_params *prm, void *cuda_stream, char *err,
+                           size_t err_len);
+tr_status tr_onebit_step(tr_onebit *ob, double *rel_change);
+tr_status tr_onebit_get_state(tr_onebit *ob, void *L, void *Z, void *Y, void *G, void *Lam,
+                              double *mu, int *t);
+tr_status tr_onebit_set_state(tr_onebit *ob, const void *L, const void *Z, const void *Y,
+                              const void *G, const void *Lam, double mu, int t);
+const char *tr_onebit_last_error(const tr_onebit *ob);
+tr_status tr_onebit_free(tr_onebit *ob);
+
 /* ---- Learned sketch widths (engine TR_LR_LEARNED) ----------------------
  * Not in the paper, which fixes one sketch rank (Alg. 1) or grows the basis
  * to an accuracy (Alg. 3) and leaves learned sketching to future work

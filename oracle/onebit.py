@@ -56,6 +56,10 @@ class Params:
     growth: float = 1.05
     tol: float = 1e-5              # varpi
     max_iter: int = 200
+    engine: str = "full"           # GNHTSVT engine: "full" or "rsvd" (oracle.svt)
+    l: int = 15                    # rsvd: sketch width
+    q: int = 1                     # rsvd: power iterations
+    seed: int = 0                  # rsvd: Philox key; the draws of step t use counter t
 
 
 @dataclass
@@ -106,7 +110,8 @@ def step(st, J1, J2, m, tdims, p):
     for i in modes:
         gradZ[i] = ctv.grad(Z, tdims, i)
         G[i], info[i] = svt.gnhtsvt(gradZ[i] + st.Lam[i] / mu, tdims, tau, p.phi, p.phi_theta,
-                                    p.phi_gamma, transform_kind=p.transform)
+                                    p.phi_gamma, engine=p.engine, transform_kind=p.transform,
+                                    l=p.l, q=p.q, seed=p.seed, t=st.t)
     # 4. multipliers and penalty (Eq. 1bit-Y .. 1bit-MU)
     Y = st.Y + mu * (L - Z)
     Lam = {i: st.Lam[i] + mu * (gradZ[i] - G[i]) for i in modes}

@@ -53,6 +53,17 @@ class tr_params(ctypes.Structure):
                 ("model_path", ctypes.c_char_p)]
 
 
+class tr_onebit_params(ctypes.Structure):
+    _fields_ = [("modes", ctypes.c_uint32), ("lambda_", ctypes.c_double),
+                ("theta", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("mu0", ctypes.c_double), ("mu_max", ctypes.c_double), ("growth", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("phi", ctypes.c_int), ("phi_theta", ctypes.c_double),
+                ("phi_gamma", ctypes.c_double), ("rank", ctypes.c_int),
+                ("oversample", ctypes.c_int), ("power_iters", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int)]
+
+
 class tr_step_info(ctypes.Structure):
     _fields_ = [("iter", ctypes.c_int), ("mu", ctypes.c_double), ("tau", ctypes.c_double),
                 ("res_inf", ctypes.c_double * 5), ("max_rank", ctypes.c_int),
@@ -96,6 +107,16 @@ _SIGS = {
     "tr_gradient_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32, _P, _P,
                                          _P, ctypes.c_char_p, ctypes.c_size_t]),
+    "tr_onebit_default_params": (None, [_P]),
+    "tr_onebit_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _P, _P,
+                                        _P, _P, ctypes.c_char_p, ctypes.c_size_t]),
+    "tr_onebit_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "tr_onebit_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int)]),
+    "tr_onebit_set_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int]),
+    "tr_onebit_last_error": (ctypes.c_char_p, [_P]),
+    "tr_onebit_free": (ctypes.c_int, [_P]),
     "tr_mlp_param_count": (ctypes.c_int64, []),
     "tr_set_model": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "tr_last_slice_widths": (ctypes.c_int, [_P, _P]),
@@ -739,6 +760,103 @@ class Batch:
         if getattr(self, "b", None):
             load().tr_batch_free(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def onebit_params(**kw):
+    """tr_onebit_params with the defaults of tr_onebit_default_params, then `kw`
+    (`modes` may be a list of 1-based modes; `lambda` stands for lambda_)."""
+    p = tr_onebit_params()
+    load().tr_onebit_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "lambda":
+            k = "lambda_"
+        if k == "modes" and not isinstance(v, int):
+            bits = 0
+            for i in v:
+                bits |= 1 << (int(i) - 1)
+            v = bits
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class OneBit:
+    """One-bit completion (tr_onebit_*): Alg. 6 on dithered one-bit samples."""
+
+    def __init__(self, dims, idx, sign, params=None, dtype=None, stream=None, **kw):
+        """dims: tensor sizes (order 3..8); idx: CUDA int64 flat face-slice
+        indices of the m samples; sign: CUDA int8 signs (> 0: +1)."""
+        import torch
+        self.dtype = torch.float32 if dtype is None else dtype
+        if self.dtype not in (torch.float32, torch.float64):
+            raise TrArgError("dtype must be float32 or float64")
+        m = idx.numel() if isinstance(idx, torch.Tensor) else 0
+        _need(idx, "idx", torch.int64, max(m, 1))
+        _need(sign, "sign", torch.int8, max(m, 1))
+        self.dims = tuple(int(d) for d in dims)
+        arr, self.N = _dims_array(self.dims)
+        self.params = params if params is not None else onebit_params(**kw)
+        self.nmodes = bin(int(self.params.modes)).count("1")
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        n = 1
+        for d in self.dims[2:]:
+            n *= d
+        self.shape = (n, self.dims[0], self.dims[1])
+        ob = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(256)
+        dt = TR_F32 if self.dtype == torch.float32 else TR_F64
+        st = load().tr_onebit_create(ctypes.byref(ob), dt, len(self.dims), arr, int(m), _ptr(idx),
+                                     _ptr(sign), ctypes.byref(self.params),
+                                     ctypes.c_void_p(self.stream), buf, 256)
+        if st != TR_OK:
+            raise TrError(st, buf.value.decode())
+        self.ob = ob
+
+    def _check(self, st):
+        if st != TR_OK:
+            msg = load().tr_onebit_last_error(self.ob)
+            raise TrError(st, msg.decode() if msg else "")
+
+    def step(self, rel=False):
+        """One iteration; with rel=True returns the stop quantity (synchronises)."""
+        if rel:
+            r = ctypes.c_double()
+            self._check(load().tr_onebit_step(self.ob, ctypes.byref(r)))
+            return r.value
+        self._check(load().tr_onebit_step(self.ob, None))
+        return None
+
+    def get_state(self):
+        import torch
+        L, Z, Y = (torch.empty(self.shape, dtype=self.dtype, device="cuda") for _ in range(3))
+        G = torch.empty((self.nmodes,) + self.shape, dtype=self.dtype, device="cuda")
+        Lam = torch.empty_like(G)
+        mu = ctypes.c_double()
+        t = ctypes.c_int()
+        self._check(load().tr_onebit_get_state(self.ob, _ptr(L), _ptr(Z), _ptr(Y), _ptr(G),
+                                               _ptr(Lam), ctypes.byref(mu), ctypes.byref(t)))
+        return {"L": L, "Z": Z, "Y": Y, "G": G, "Lam": Lam, "mu": mu.value, "t": t.value}
+
+    def set_state(self, L, Z, Y, G, Lam, mu, t):
+        """G, Lam: (|Gamma|, n, n1, n2) tensors, modes ascending; None keeps one."""
+        for x, name in ((L, "L"), (Z, "Z"), (Y, "Y")):
+            _need(x, name, self.dtype, self.N, optional=True)
+        for x, name in ((G, "G"), (Lam, "Lam")):
+            _need(x, name, self.dtype, self.N * self.nmodes, optional=True)
+        self._check(load().tr_onebit_set_state(self.ob, _ptr(L), _ptr(Z), _ptr(Y), _ptr(G),
+                                               _ptr(Lam), float(mu), int(t)))
+
+    def close(self):
+        if getattr(self, "ob", None):
+            load().tr_onebit_free(self.ob)
+            self.ob = None
 
     def __del__(self):
         try:

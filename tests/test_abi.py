@@ -242,3 +242,29 @@ def test_gradient_building_blocks_validate_without_gpu(lib):
         tr.TR_EUNSUPPORTED
     with pytest.raises(tr.TrArgError):
         tr.gradient_solve(pytest.importorskip("torch").zeros((4, 8, 6)), (8, 6, 4), (5,))
+
+
+def test_onebit_create_validates_without_gpu(lib):
+    dims = (ctypes.c_int64 * 3)(8, 6, 4)
+    buf = ctypes.create_string_buffer(128)
+    p = tr.onebit_params()
+    a, b = ctypes.c_void_p(256), ctypes.c_void_p(512)
+    ob = ctypes.c_void_p()
+
+    def create(dt=tr.TR_F32, order=3, d=dims, m=10, idx=a, sgn=b, prm=p):
+        return lib.tr_onebit_create(ctypes.byref(ob), dt, order, d, m, idx, sgn,
+                                    ctypes.byref(prm), None, buf, 128)
+
+    assert create(idx=None) == tr.TR_EINVAL
+    assert create(m=0) == tr.TR_EINVAL
+    assert create(dt=5) == tr.TR_EINVAL
+    assert create(order=2) == tr.TR_EINVAL
+    assert create(prm=tr.onebit_params(modes=0)) == tr.TR_EINVAL
+    assert create(prm=tr.onebit_params(modes=[4])) == tr.TR_EINVAL
+    assert create(prm=tr.onebit_params(mu0=0.0)) == tr.TR_EINVAL
+    assert create(prm=tr.onebit_params(alpha=-1.0)) == tr.TR_EINVAL
+    assert create(d=(ctypes.c_int64 * 3)(8, 0, 4)) == tr.TR_EINVAL
+    assert create(d=(ctypes.c_int64 * 3)(1 << 16, 1 << 16, 4)) == tr.TR_EUNSUPPORTED
+    assert b"entries" in buf.value
+    assert lib.tr_onebit_step(None, None) == tr.TR_EINVAL
+    assert lib.tr_onebit_free(None) == tr.TR_OK
