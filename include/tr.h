@@ -295,6 +295,59 @@ tr_status tr_gradient_solve(tr_dtype dtype, int order, const int64_t *dims, uint
                             const void *rhs, void *out, void *cuda_stream, char *err,
                             size_t err_len);
 
+/* ---- Gradient-domain prior, GNHTCTV (Alg. 5 with Gamma) -----------------
+ * Alg. 5 on the model of Eq. equ_nonconvex with a set Gamma of gradient
+ * directions (Def. GNHTCTV), gamma = |Gamma|.  One step:
+ *   1. (I + sum_k nabla_k^T nabla_k) L = (M - E + Y/mu) + sum_k nabla_k^T (G_k - Lambda_k/mu)
+ *      solved as tr_gradient_solve does          (Eq. coef-tensor, Eq. gnrhtc-L)
+ *   2. G_k = D_{Phi, 1/(gamma mu)}(nabla_k L + Lambda_k/mu, L) by the
+ *      per-slice randomized engine (sketch width rank + oversample,
+ *      power_iters, Philox key seed, counter word t)            (Eq. L_prox)
+ *   3. H = M - L + Y/mu; E = Prox_{psi, lambda/mu}(H) on Omega (0 with
+ *      TR_NOISE_NONE), E = H off Omega              (Eq. E_prox_ome, E_prox_ome1)
+ *   4. Y += mu (M - L - E); Lambda_k += mu (nabla_k L - G_k);
+ *      mu = min(mu_max, growth mu)                        (Eq. lagrange11-22)
+ *   5. res_inf = the infinity norms of L - L^t, E - E^t, nabla_k L - G_k and
+ *      G_k - G_k^t (each the maximum over k), M - L - E      (Eq. convercon)
+ * L is the orthonormal DCT-II along modes 3..d.
+ *   tr_ctv_create: `problem` as for tr_init (order 3..8; observed and mask
+ *     caller-owned, valid until tr_ctv_free); lambda <= 0 selects
+ *     1/sqrt(max(n1, n2)).  Initialises L = E = Y = G_k = Lambda_k = 0,
+ *     mu = mu0, t = 0.  Allocates about (7 + 2 |Gamma|) tensors plus an
+ *     internal tr_init handle.
+ *   tr_ctv_step: one iteration on the stream; with res_inf non-NULL (5
+ *     doubles) it synchronises and returns the residuals of step 5.
+ *   tr_ctv_get_state / tr_ctv_set_state: copy L, E, Y (N elements each) and
+ *     G, Lambda (|Gamma| tensors back to back, modes ascending) out of /
+ *     into the object (device buffers; NULL skips one); both synchronise.
+ * Errors: TR_EINVAL, TR_EUNSUPPORTED (shapes the internal handle refuses),
+ * TR_ENOMEM, TR_ECUDA.                                                      */
+typedef struct tr_ctv tr_ctv;
+typedef struct {
+  uint32_t modes;                  /* Gamma: bit k - 1 set for mode k        */
+  tr_penalty phi;  double phi_theta, phi_gamma;
+  tr_penalty psi;  double psi_theta, psi_gamma;
+  tr_noise noise;  double lambda;
+  double mu0, mu_max, growth;
+  int rank, oversample, power_iters;
+  uint64_t seed;
+  tr_prec prec;
+} tr_ctv_params;
+
+/* Defaults: Gamma = {1, 2}, Phi = psi = MCP (theta 1, gamma 4000), l1 noise,
+ * lambda = 0 (automatic), mu0 = 1e-3, mu_max = 1e10, growth 1.1, rank 10 +
+ * oversample 10, q = 1, seed 0, FP32 (Sec. 6 parameter settings).           */
+void tr_ctv_default_params(tr_ctv_params *p);
+tr_status tr_ctv_create(tr_ctv **c, const tr_problem *problem, const tr_ctv_params *prm,
+                        void *cuda_stream, char *err, size_t err_len);
+tr_status tr_ctv_step(tr_ctv *c, double *res_inf);
+tr_status tr_ctv_get_state(tr_ctv *c, void *L, void *E, void *Y, void *G, void *Lam, double *mu,
+                           int *t);
+tr_status tr_ctv_set_state(tr_ctv *c, const void *L, const void *E, const void *Y, const void *G,
+                           const void *Lam, double mu, int t);
+const char *tr_ctv_last_error(const tr_ctv *c);
+tr_status tr_ctv_free(tr_ctv *c);
+
 /* ---- One-bit completion, GNOBHTC (Alg. 6) --------------------------------
  * Recovers L from m dithered one-bit samples q_k = sign(L*[s_k] + eps_k +
  * xi_k), xi_k ~ U[-theta, theta] (Prop. one-bitequ: theta q_k stands in for

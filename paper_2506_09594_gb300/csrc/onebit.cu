@@ -30,6 +30,7 @@
 #include <new>
 #include <vector>
 
+#include "ew_kernels.cuh"
 #include "tr_internal.cuh"
 
 struct tr_onebit {
@@ -133,23 +134,6 @@ __global__ void onebit_l_kernel(T *L, const T *__restrict__ Z, const T *__restri
   }
 }
 
-// out = a X + b Y (out may be X or Y).
-template <typename T>
-__global__ void axpby_kernel(T *out, T a, const T *X, T b, const T *Y, int64_t N) {
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < N; f += step)
-    out[f] = a * X[f] + b * Y[f];
-}
-
-// Lam += mu (A - B).
-template <typename T>
-__global__ void multiplier_kernel(T *Lam, T mu, const T *__restrict__ A, const T *__restrict__ B,
-                                  int64_t N) {
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < N; f += step)
-    Lam[f] += mu * (A[f] - B[f]);
-}
-
 void free_onebit(tr_onebit *ob) {
   if (ob->prox) tr_free(ob->prox);
   void *bufs[] = {ob->L, ob->Z, ob->Y, ob->J1, ob->J2, ob->G, ob->Lam,
@@ -188,17 +172,17 @@ tr_status onebit_step(tr_onebit *ob, double *rel) {
                                        ob->acc);
   OB_CUDA(cudaGetLastError());
   // 2. Z-update: R = L + Y/mu + sum_i nabla_i^T (G_i - Lambda_i/mu); Z = solve(R)
-  axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), L, (T)(1.0 / mu), Y, N);
+  ew::axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), L, (T)(1.0 / mu), Y, N);
   OB_CUDA(cudaGetLastError());
   uint32_t mask = 0;
   for (int q = 0; q < ob->nmodes; ++q) {
     const int k = ob->modes[q];
     mask |= 1u << (k - 1);
     T *Gi = (T *)tensor(ob, ob->G, q), *Li = (T *)tensor(ob, ob->Lam, q);
-    axpby_kernel<T><<<g, 256, 0, s>>>(W, T(1), Gi, (T)(-1.0 / mu), Li, N);
+    ew::axpby_kernel<T><<<g, 256, 0, s>>>(W, T(1), Gi, (T)(-1.0 / mu), Li, N);
     OB_CUDA(cudaGetLastError());
     OB_TR(tr_grad(ob->dtype, ob->order, ob->dims, k, 1, W, ob->Abar, s, buf, sizeof buf));
-    axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), R, T(1), (const T *)ob->Abar, N);
+    ew::axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), R, T(1), (const T *)ob->Abar, N);
     OB_CUDA(cudaGetLastError());
   }
   OB_TR(tr_gradient_solve(ob->dtype, ob->order, ob->dims, mask, R, Z, s, buf, sizeof buf));
@@ -208,15 +192,15 @@ tr_status onebit_step(tr_onebit *ob, double *rel) {
     const int k = ob->modes[q];
     T *Gi = (T *)tensor(ob, ob->G, q), *Li = (T *)tensor(ob, ob->Lam, q);
     OB_TR(tr_grad(ob->dtype, ob->order, ob->dims, k, 0, Z, W, s, buf, sizeof buf));
-    axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), W, (T)(1.0 / mu), Li, N);   // R: prox input
+    ew::axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), W, (T)(1.0 / mu), Li, N);   // R: prox input
     OB_CUDA(cudaGetLastError());
     OB_TR(tr_transform_forward(ob->prox, R, ob->Abar));
     OB_TR(tr_slice_prox(ob->prox, ob->Abar, ob->Gbar, tau, ob->t));
     OB_TR(tr_transform_inverse(ob->prox, ob->Gbar, Gi));
-    multiplier_kernel<T><<<g, 256, 0, s>>>(Li, (T)mu, W, Gi, N);          // W = nabla_i Z
+    ew::multiplier_kernel<T><<<g, 256, 0, s>>>(Li, (T)mu, W, Gi, N);          // W = nabla_i Z
     OB_CUDA(cudaGetLastError());
   }
-  multiplier_kernel<T><<<g, 256, 0, s>>>(Y, (T)mu, L, Z, N);
+  ew::multiplier_kernel<T><<<g, 256, 0, s>>>(Y, (T)mu, L, Z, N);
   OB_CUDA(cudaGetLastError());
 #undef OB_CUDA
 #undef OB_TR

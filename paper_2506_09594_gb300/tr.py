@@ -53,6 +53,16 @@ class tr_params(ctypes.Structure):
                 ("model_path", ctypes.c_char_p)]
 
 
+class tr_ctv_params(ctypes.Structure):
+    _fields_ = [("modes", ctypes.c_uint32), ("phi", ctypes.c_int), ("phi_theta", ctypes.c_double),
+                ("phi_gamma", ctypes.c_double), ("psi", ctypes.c_int),
+                ("psi_theta", ctypes.c_double), ("psi_gamma", ctypes.c_double),
+                ("noise", ctypes.c_int), ("lambda_", ctypes.c_double),
+                ("mu0", ctypes.c_double), ("mu_max", ctypes.c_double), ("growth", ctypes.c_double),
+                ("rank", ctypes.c_int), ("oversample", ctypes.c_int), ("power_iters", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int)]
+
+
 class tr_onebit_params(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_uint32), ("lambda_", ctypes.c_double),
                 ("theta", ctypes.c_double), ("alpha", ctypes.c_double),
@@ -107,6 +117,15 @@ _SIGS = {
     "tr_gradient_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32, _P, _P,
                                          _P, ctypes.c_char_p, ctypes.c_size_t]),
+    "tr_ctv_default_params": (None, [_P]),
+    "tr_ctv_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, _P, ctypes.c_char_p,
+                                     ctypes.c_size_t]),
+    "tr_ctv_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "tr_ctv_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "tr_ctv_set_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int]),
+    "tr_ctv_last_error": (ctypes.c_char_p, [_P]),
+    "tr_ctv_free": (ctypes.c_int, [_P]),
     "tr_onebit_default_params": (None, [_P]),
     "tr_onebit_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _P, _P,
@@ -857,6 +876,106 @@ class OneBit:
         if getattr(self, "ob", None):
             load().tr_onebit_free(self.ob)
             self.ob = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ctv_params(**kw):
+    """tr_ctv_params with the defaults of tr_ctv_default_params, then `kw`
+    (`modes` may be a list of 1-based modes; `lambda` stands for lambda_)."""
+    p = tr_ctv_params()
+    load().tr_ctv_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "lambda":
+            k = "lambda_"
+        if k == "modes" and not isinstance(v, int):
+            bits = 0
+            for i in v:
+                bits |= 1 << (int(i) - 1)
+            v = bits
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Ctv:
+    """The gradient-domain prior (tr_ctv_*): Alg. 5 with a set of gradient
+    directions on observed data M and mask (caller-owned CUDA tensors)."""
+
+    def __init__(self, observed, mask, dims, params=None, stream=None, **kw):
+        import torch
+        dt = _float_dtype(observed, "observed")
+        self.dtype = observed.dtype
+        self.dims = tuple(int(d) for d in dims)
+        arr, self.N = _dims_array(self.dims)
+        _need(observed, "observed", observed.dtype, self.N)
+        _need(mask, "mask", torch.uint8, self.N)
+        self.params = params if params is not None else ctv_params(**kw)
+        self.nmodes = bin(int(self.params.modes)).count("1")
+        prob = tr_problem()
+        prob.order = len(self.dims)
+        for i, d in enumerate(self.dims):
+            prob.dims[i] = d
+        prob.dtype = dt
+        prob.observed = observed.data_ptr()
+        prob.mask = mask.data_ptr()
+        self._keep = (observed, mask)
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        n = 1
+        for d in self.dims[2:]:
+            n *= d
+        self.shape = (n, self.dims[0], self.dims[1])
+        c = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(256)
+        st = load().tr_ctv_create(ctypes.byref(c), ctypes.byref(prob), ctypes.byref(self.params),
+                                  ctypes.c_void_p(self.stream), buf, 256)
+        if st != TR_OK:
+            raise TrError(st, buf.value.decode())
+        self.c = c
+
+    def _check(self, st):
+        if st != TR_OK:
+            msg = load().tr_ctv_last_error(self.c)
+            raise TrError(st, msg.decode() if msg else "")
+
+    def step(self, info=False):
+        """One iteration; with info=True returns the five residuals (synchronises)."""
+        if info:
+            r = (ctypes.c_double * 5)()
+            self._check(load().tr_ctv_step(self.c, r))
+            return list(r)
+        self._check(load().tr_ctv_step(self.c, None))
+        return None
+
+    def get_state(self):
+        import torch
+        L, E, Y = (torch.empty(self.shape, dtype=self.dtype, device="cuda") for _ in range(3))
+        G = torch.empty((self.nmodes,) + self.shape, dtype=self.dtype, device="cuda")
+        Lam = torch.empty_like(G)
+        mu = ctypes.c_double()
+        t = ctypes.c_int()
+        self._check(load().tr_ctv_get_state(self.c, _ptr(L), _ptr(E), _ptr(Y), _ptr(G), _ptr(Lam),
+                                            ctypes.byref(mu), ctypes.byref(t)))
+        return {"L": L, "E": E, "Y": Y, "G": G, "Lam": Lam, "mu": mu.value, "t": t.value}
+
+    def set_state(self, L, E, Y, G, Lam, mu, t):
+        """G, Lam: (|Gamma|, n, n1, n2) tensors, modes ascending; None keeps one."""
+        for x, name in ((L, "L"), (E, "E"), (Y, "Y")):
+            _need(x, name, self.dtype, self.N, optional=True)
+        for x, name in ((G, "G"), (Lam, "Lam")):
+            _need(x, name, self.dtype, self.N * self.nmodes, optional=True)
+        self._check(load().tr_ctv_set_state(self.c, _ptr(L), _ptr(E), _ptr(Y), _ptr(G), _ptr(Lam),
+                                            float(mu), int(t)))
+
+    def close(self):
+        if getattr(self, "c", None):
+            load().tr_ctv_free(self.c)
+            self.c = None
 
     def __del__(self):
         try:

@@ -268,3 +268,31 @@ def test_onebit_create_validates_without_gpu(lib):
     assert b"entries" in buf.value
     assert lib.tr_onebit_step(None, None) == tr.TR_EINVAL
     assert lib.tr_onebit_free(None) == tr.TR_OK
+
+
+def test_ctv_create_validates_without_gpu(lib):
+    buf = ctypes.create_string_buffer(128)
+    c = ctypes.c_void_p()
+
+    def create(order=3, dims=(8, 6, 4), dtype=tr.TR_F32, obs=256, mask=512, **kw):
+        pb = tr.tr_problem()
+        pb.order = order
+        for i, d in enumerate(dims):
+            pb.dims[i] = d
+        pb.dtype = dtype
+        pb.observed = obs
+        pb.mask = mask
+        prm = tr.ctv_params(**kw)
+        return lib.tr_ctv_create(ctypes.byref(c), ctypes.byref(pb), ctypes.byref(prm), None, buf,
+                                 128)
+
+    assert create(order=2, dims=(8, 6)) == tr.TR_EINVAL
+    assert create(dtype=9) == tr.TR_EINVAL
+    assert create(obs=None) == tr.TR_EINVAL
+    assert create(modes=0) == tr.TR_EINVAL
+    assert create(modes=[4]) == tr.TR_EINVAL
+    assert create(mu0=-1.0) == tr.TR_EINVAL
+    assert create(noise=7) == tr.TR_EINVAL
+    assert create(dims=(8, 0, 4)) == tr.TR_EINVAL
+    assert lib.tr_ctv_step(None, None) == tr.TR_EINVAL
+    assert lib.tr_ctv_free(None) == tr.TR_OK
