@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<NP, SPLIT>())
     uint8_t *st = smem + h * Lay::stage_bytes;
     uint8_t *a_hi = st, *b_hi = st + Lay::a_bytes;
     uint8_t *a_lo = st + Lay::a_bytes + Lay::b_bytes, *b_lo = a_lo + Lay::a_bytes;
-    // the MMAs that read this stage two chunks ago must be done; the verdict
-    // is made block-uniform so that no thread skips a barrier
+    // the MMAs that read this stage two chunks ago must be done; the wait's
+    // outcome is made block-uniform so that no thread skips a barrier
     const bool w = ci >= 2 ? mbar_wait(&bar[h], (issued[h] - 1) & 1) : true;
     if (!__syncthreads_and(w)) { ok = false; break; }
     sa.template store<SPLIT>(a_hi, a_lo, g.sAk == 1);
