@@ -51,6 +51,9 @@ def parse():
                     help="skip the precision forms on the 1024x1024x64 workload")
     ap.add_argument("--no-tucker", action="store_true",
                     help="skip the shared-Tucker prox (Alg. 1 + Alg. 4) timing")
+    ap.add_argument("--models", action="store_true",
+                    help="also time the gradient-domain and one-bit ADMM steps (off by "
+                         "default until their kernels have run on a GPU)")
     ap.add_argument("--learned-iters", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=8)
     return ap.parse_args()
@@ -458,6 +461,9 @@ def run_ours(args):
         if not args.no_tucker and world == 1:
             line["tucker"] = tucker_section(tr, torch)
             torch.cuda.empty_cache()
+        if args.models and world == 1:
+            line["models"] = models_section(tr, torch, 20)
+            torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -585,6 +591,54 @@ def tucker_section(tr, torch, reps=20):
                        "ms_per_prox": ms_t},
             "per_slice_rsvd": {"l": r[0], "q": 1, "ms_per_prox": ms_r},
             "rel_diff_tucker_vs_per_slice": diff}
+
+
+def models_section(tr, torch, K):
+    """The two other models of the paper on the headline shape, 200x200x20x20
+    FP32 (400 slices), Gamma = {1, 2}, per-slice randomized prox with l = 20
+    and q = 1: device ms per ADMM step (CUDA events over K steps after 3
+    warm-up steps).  The gradient-domain prior (Alg. 5 with Gamma) runs on the
+    headline observed data; the one-bit model (Alg. 6) on 2N dithered signs
+    of its ground truth (theta = 1.2 max |X*|)."""
+    import numpy as np
+
+    from paper_2506_09594_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    X, M, mask, _ = synth.make_problem(w)
+    out = {"workload": w.name, "modes": [1, 2],
+           "sketch_width": 20, "power_iters": 1, "steps": K}
+
+    def timed(step):
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    Md = torch.from_numpy(M).float().cuda()
+    maskd = torch.from_numpy(mask).cuda()
+    c = tr.Ctv(Md, maskd, w.dims, modes=[1, 2], rank=10, oversample=10, power_iters=1,
+               stream=torch.cuda.current_stream().cuda_stream)
+    ms = timed(c.step)
+    out["ctv"] = {"ms_per_step": ms, "iters_per_s": 1e3 / ms}
+    c.close()
+    del Md, maskd
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(11)
+    theta = 1.2 * float(np.abs(X).max())
+    s, q = synth.one_bit_observations(X, 2 * X.size, theta, 0.0, rng)
+    ob = tr.OneBit(w.dims, torch.from_numpy(s).cuda(), torch.from_numpy(q.astype(np.int8)).cuda(),
+                   modes=[1, 2], rank=10, oversample=10, power_iters=1, theta=theta,
+                   alpha=float(np.abs(X).max()), stream=torch.cuda.current_stream().cuda_stream)
+    ms = timed(ob.step)
+    out["onebit"] = {"ms_per_step": ms, "iters_per_s": 1e3 / ms, "samples": int(len(s))}
+    ob.close()
+    return out
 
 
 def precision_forms(tr, torch, K):
