@@ -26,6 +26,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <mutex>
 #include <vector>
 
 #include "tr_internal.cuh"
@@ -160,17 +161,68 @@ __global__ void __launch_bounds__(kGemmThreads) strided_gemm_kernel(GemmArgs g) 
 // X[f] /= 1 + sum over the modes in Gamma of lambda_k[i_k].
 struct ScaleModes {
   int count;
-  int64_t S[8], n[8], off[8];   // stride, size, offset of the mode's lambda table
+  int64_t S[8], n[8];           // stride and size of each mode
+  const void *lam[8];           // its eigenvalue table (n entries)
 };
 
 template <typename T>
-__global__ void eig_scale_kernel(T *X, int64_t N, const T *__restrict__ lam, ScaleModes m) {
+__global__ void eig_scale_kernel(T *X, int64_t N, ScaleModes m) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < N; f += step) {
     T den = T(1);
-    for (int q = 0; q < m.count; ++q) den += lam[m.off[q] + (f / m.S[q]) % m.n[q]];
+    for (int q = 0; q < m.count; ++q) den += ((const T *)m.lam[q])[(f / m.S[q]) % m.n[q]];
     X[f] = X[f] / den;
   }
+}
+
+// The Hartley matrix H_n (n x n, row-major) followed by the eigenvalues
+// 2 - 2 cos(2 pi a / n) of D_n^T D_n, computed in double, stored as T.
+template <typename T>
+void hartley_tables(int64_t n, T *out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const double inv_sqrt = 1.0 / sqrt((double)n);
+  for (int64_t a = 0; a < n; ++a) {
+    for (int64_t b = 0; b < n; ++b) {
+      const double ang = two_pi * (double)((a * b) % n) / (double)n;
+      out[a * n + b] = (T)((cos(ang) + sin(ang)) * inv_sqrt);
+    }
+    out[n * n + a] = (T)(2.0 - 2.0 * cos(two_pi * (double)a / (double)n));
+  }
+}
+
+// Device copies of the tables, built once per (device, element size, n) and
+// kept until the process exits (at most kTableCacheEntries of them; later
+// sizes are built per call).
+struct TableEntry {
+  int dev;
+  size_t esz;
+  int64_t n;
+  void *ptr;
+};
+constexpr int kTableCacheEntries = 32;
+std::mutex g_table_mu;
+TableEntry g_tables[kTableCacheEntries];
+int g_table_count = 0;
+
+template <typename T>
+const T *cached_tables(int64_t n) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(g_table_mu);
+  for (int i = 0; i < g_table_count; ++i)
+    if (g_tables[i].dev == dev && g_tables[i].esz == sizeof(T) && g_tables[i].n == n)
+      return (const T *)g_tables[i].ptr;
+  if (g_table_count == kTableCacheEntries) return nullptr;
+  std::vector<T> host((size_t)(n * n + n));
+  hartley_tables<T>(n, host.data());
+  void *d = nullptr;
+  if (cudaMalloc(&d, host.size() * sizeof(T)) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  g_tables[g_table_count++] = TableEntry{dev, sizeof(T), n, d};
+  return (const T *)d;
 }
 
 int grid_for(int64_t N) {
@@ -223,46 +275,37 @@ tr_status gradient_solve(const Shape &s, uint32_t modes, const T *rhs, T *out, c
     const cudaError_t e = cudaMemcpyAsync(out, rhs, (size_t)s.N * esz, cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? TR_OK : gfail(err, err_len, TR_ECUDA, "%s", cudaGetErrorString(e));
   }
-  // Hartley matrices and eigenvalue tables, built on the host in double
-  size_t hoff[8], loff[8], total = 0;
+  // per mode: its cached tables, or tables built for this call
+  const T *tab[8];
+  size_t own_off[8], own_total = 0;
   for (int q = 0; q < nm; ++q) {
     const int64_t n = s.n[ks[q]];
-    hoff[q] = total;
-    total += (size_t)(n * n);
+    tab[q] = cached_tables<T>(n);
+    own_off[q] = own_total;
+    if (!tab[q]) own_total += (size_t)(n * n + n);
   }
-  for (int q = 0; q < nm; ++q) {
-    loff[q] = total;
-    total += (size_t)s.n[ks[q]];
-  }
-  std::vector<T> host(total);
-  const double two_pi = 6.283185307179586476925286766559;
-  for (int q = 0; q < nm; ++q) {
-    const int64_t n = s.n[ks[q]];
-    const double inv_sqrt = 1.0 / sqrt((double)n);
-    for (int64_t a = 0; a < n; ++a) {
-      for (int64_t b = 0; b < n; ++b) {
-        const double ang = two_pi * (double)((a * b) % n) / (double)n;
-        host[hoff[q] + (size_t)(a * n + b)] = (T)((cos(ang) + sin(ang)) * inv_sqrt);
-      }
-      host[loff[q] + (size_t)a] = (T)(2.0 - 2.0 * cos(two_pi * (double)a / (double)n));
-    }
-  }
-  void *tables = nullptr, *tmp = nullptr;
-  cudaError_t e = cudaMallocAsync(&tables, total * esz, st);
+  void *own = nullptr, *tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (own_total) e = cudaMallocAsync(&own, own_total * esz, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&tmp, (size_t)s.N * esz, st);
   if (e != cudaSuccess) {
-    if (tables) cudaFreeAsync(tables, st);
+    if (own) cudaFreeAsync(own, st);
     return gfail(err, err_len, e == cudaErrorMemoryAllocation ? TR_ENOMEM : TR_ECUDA,
                  "workspace: %s", cudaGetErrorString(e));
   }
+  std::vector<T> host(own_total);
+  for (int q = 0; q < nm; ++q) {
+    if (tab[q]) continue;
+    hartley_tables<T>(s.n[ks[q]], host.data() + own_off[q]);
+    tab[q] = (const T *)own + own_off[q];
+  }
   // pageable source: the call returns once the host buffer has been staged
-  e = cudaMemcpyAsync(tables, host.data(), total * esz, cudaMemcpyHostToDevice, st);
-  const T *T0 = (const T *)tables;
+  if (own_total) e = cudaMemcpyAsync(own, host.data(), own_total * esz, cudaMemcpyHostToDevice, st);
   T *buf[2] = {(T *)tmp, out};    // product p (0-based) writes buf[p % 2]; 2 nm products end in out
   const T *cur = rhs;
   int p = 0;
   for (int q = 0; q < nm && e == cudaSuccess; ++q, ++p) {
-    e = hartley_product<T>(s, ks[q], T0 + hoff[q], cur, buf[p % 2], st);
+    e = hartley_product<T>(s, ks[q], tab[q], cur, buf[p % 2], st);
     cur = buf[p % 2];
   }
   if (e == cudaSuccess) {
@@ -271,17 +314,17 @@ tr_status gradient_solve(const Shape &s, uint32_t modes, const T *rhs, T *out, c
     for (int q = 0; q < nm; ++q) {
       sm.S[q] = s.S[ks[q]];
       sm.n[q] = s.n[ks[q]];
-      sm.off[q] = (int64_t)(loff[q]);
+      sm.lam[q] = tab[q] + s.n[ks[q]] * s.n[ks[q]];
     }
-    eig_scale_kernel<T><<<grid_for(s.N), 256, 0, st>>>((T *)cur, s.N, T0, sm);
+    eig_scale_kernel<T><<<grid_for(s.N), 256, 0, st>>>((T *)cur, s.N, sm);
     e = cudaGetLastError();
   }
   for (int q = 0; q < nm && e == cudaSuccess; ++q, ++p) {
-    e = hartley_product<T>(s, ks[q], T0 + hoff[q], cur, buf[p % 2], st);
+    e = hartley_product<T>(s, ks[q], tab[q], cur, buf[p % 2], st);
     cur = buf[p % 2];
   }
   cudaFreeAsync(tmp, st);
-  cudaFreeAsync(tables, st);
+  if (own) cudaFreeAsync(own, st);
   if (e != cudaSuccess) return gfail(err, err_len, TR_ECUDA, "%s", cudaGetErrorString(e));
   return TR_OK;
 }
