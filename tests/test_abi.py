@@ -296,3 +296,24 @@ def test_ctv_create_validates_without_gpu(lib):
     assert create(dims=(8, 0, 4)) == tr.TR_EINVAL
     assert lib.tr_ctv_step(None, None) == tr.TR_EINVAL
     assert lib.tr_ctv_free(None) == tr.TR_OK
+
+
+def test_model_bindings_refuse_bad_tensors(lib):
+    torch = pytest.importorskip("torch")
+    M = torch.zeros((4, 8, 6))
+    mask = torch.ones((4, 8, 6), dtype=torch.uint8)
+    with pytest.raises(tr.TrArgError):                 # host tensors
+        tr.Ctv(M, mask, (8, 6, 4))
+    with pytest.raises(tr.TrArgError):                 # integer observations
+        tr.Ctv(M.to(torch.int32), mask, (8, 6, 4))
+    idx = torch.zeros(10, dtype=torch.int64)
+    sgn = torch.ones(10, dtype=torch.int8)
+    with pytest.raises(tr.TrArgError):                 # host samples
+        tr.OneBit((8, 6, 4), idx, sgn)
+    with pytest.raises(tr.TrArgError):                 # signs as float
+        tr.OneBit((8, 6, 4), idx, sgn.float())
+    with pytest.raises(tr.TrArgError):
+        tr.OneBit((8, 6, 4), idx, sgn, dtype=torch.float16)
+    with pytest.raises(KeyError):
+        tr.ctv_params(no_such_field=1)
+    assert tr.onebit_params(modes=[2, 3]).modes == 0b110
