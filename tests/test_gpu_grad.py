@@ -7,6 +7,8 @@ Tolerances: differences exact in FP64 and to FP32 rounding; the solve 1e-12
 (FP64) and 1e-5 (FP32) relative to the largest entry.
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -14,8 +16,11 @@ from oracle import ctv
 from paper_2506_09594_gb300 import tr
 
 torch = pytest.importorskip("torch")
+# these kernels have not run on a GPU yet: the tests run only when asked
+# for (TR_RUN_PENDING=1) until that first run has passed
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="first GPU run of these kernels pending")]
+              pytest.mark.skipif(os.environ.get("TR_RUN_PENDING") != "1",
+                                 reason="first GPU run of these kernels pending")]
 
 TDT = {"f64": torch.float64, "f32": torch.float32}
 SHAPES = [(37, 29, 5, 3), (70, 66, 4), (130, 9), (16, 80, 1, 6)]
