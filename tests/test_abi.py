@@ -317,3 +317,34 @@ def test_model_bindings_refuse_bad_tensors(lib):
     with pytest.raises(KeyError):
         tr.ctv_params(no_such_field=1)
     assert tr.onebit_params(modes=[2, 3]).modes == 0b110
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    # every field offset of the ABI structs, as the C compiler lays them out,
+    # equals the ctypes binding's
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [("tr_problem", tr.tr_problem, {}), ("tr_params", tr.tr_params, {"lambda_": "lambda"}),
+               ("tr_step_info", tr.tr_step_info, {}),
+               ("tr_onebit_params", tr.tr_onebit_params, {"lambda_": "lambda"}),
+               ("tr_ctv_params", tr.tr_ctv_params, {"lambda_": "lambda"})]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tr.h"', "int main(void) {"]
+    for cname, cls, rename in structs:
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            c = rename.get(fname, fname)
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, c))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                      text=True).stdout.splitlines())
+    for cname, cls, _ in structs:
+        assert int(out[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(out["%s.%s" % (cname, fname)]) == getattr(cls, fname).offset, (cname, fname)
