@@ -24,23 +24,7 @@ import numpy as np
 import pytest
 
 from oracle import admm, ctv, prox, svt, transform
-
-
-def roll_grad(S, tdims, k):
-    """(nabla_k S)[i] = S[i + e_k] - S[i], written as a shift of the array."""
-    n, n1, n2 = S.shape
-    V = S.reshape(tuple(reversed(tdims)) + (n1, n2))
-    d = 2 + len(tdims)
-    ax = {1: d - 2, 2: d - 1}.get(k, d - k)
-    return (np.roll(V, -1, axis=ax) - V).reshape(S.shape)
-
-
-def roll_grad_t(S, tdims, k):
-    n, n1, n2 = S.shape
-    V = S.reshape(tuple(reversed(tdims)) + (n1, n2))
-    d = 2 + len(tdims)
-    ax = {1: d - 2, 2: d - 1}.get(k, d - k)
-    return (np.roll(V, 1, axis=ax) - V).reshape(S.shape)
+from shifts import roll_grad, roll_grad_t
 
 
 # ------------------------------------------------------------ gradient

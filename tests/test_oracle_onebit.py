@@ -20,22 +20,7 @@ import scipy.optimize
 
 from oracle import onebit, prox, transform
 from paper_2506_09594_gb300 import synth
-
-
-def roll_grad(S, tdims, k):
-    n, n1, n2 = S.shape
-    V = S.reshape(tuple(reversed(tdims)) + (n1, n2))
-    d = 2 + len(tdims)
-    ax = {1: d - 2, 2: d - 1}.get(k, d - k)
-    return (np.roll(V, -1, axis=ax) - V).reshape(S.shape)
-
-
-def roll_grad_t(S, tdims, k):
-    n, n1, n2 = S.shape
-    V = S.reshape(tuple(reversed(tdims)) + (n1, n2))
-    d = 2 + len(tdims)
-    ax = {1: d - 2, 2: d - 1}.get(k, d - k)
-    return (np.roll(V, 1, axis=ax) - V).reshape(S.shape)
+from shifts import roll_grad_t
 
 
 def smooth_tensor(n1, n2, n3, rng):
