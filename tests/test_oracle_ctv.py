@@ -296,3 +296,47 @@ def test_hartley_basis_diagonalises_the_difference_operators():
     den = 1 + lam[0][:, None, None] + lam[1][None, :, None] + lam[2][None, None, :]
     got = apply(apply(rhs) / den)
     assert np.abs(got - ctv.l_update(R0, Rk, tdims, modes)).max() < 1e-12
+
+
+def test_multipliers_are_subgradients_and_the_loop_reaches_feasibility():
+    # convex case (l1 Phi and psi): after every step
+    #   Y = 0 off Omega; |Y| <= lambda on Omega, Y = lambda sign(E) where E != 0
+    #     (Y' = mu (H - E') with E' the l1 prox of H);
+    #   every transformed slice of gamma Lambda_k has spectral norm <= 1 and
+    #   <gamma Lambda_k, G_k> equals the transformed nuclear norm of G_k
+    #     (Lambda_k' = mu (A - G_k') with G_k' the prox of A, tau = 1/(gamma mu));
+    # and the loop ends at a point with nabla_k L = G_k and L + E = M
+    rng = np.random.default_rng(3)
+    tdims, shape, modes, lam = (6,), (6, 10, 8), (1, 2), 0.3
+    X = rng.standard_normal(shape)
+    mask = rng.random(shape) < 0.7
+    M = np.where(mask, X, 0.0)
+    p = ctv.Params(modes=modes, transform="dct", engine="full", phi=prox.L1, psi=prox.L1,
+                   noise=admm.NOISE_L1, lam=lam, mu0=0.05, growth=1.1, mu_max=1e6, tol=1e-10,
+                   max_iter=600)
+    gam = len(modes)
+    checked = []
+
+    def check(st, res):
+        Y = st.Y
+        assert np.abs(Y[~mask]).max() == 0.0
+        # Y is formed as Y + mu (M - L - E) with mu up to 1e6, so it carries
+        # rounding of order eps * mu: the bounds are 1e-8 relative
+        assert np.abs(Y[mask]).max() <= lam * (1 + 1e-8)
+        nz = mask & (np.abs(st.E) > 1e-8)
+        if nz.any():
+            assert np.abs(Y[nz] - lam * np.sign(st.E[nz])).max() <= 1e-8 * lam
+        for k in modes:
+            W = transform.forward(gam * st.Lam[k], tdims)
+            Gb = transform.forward(st.G[k], tdims)
+            assert max(np.linalg.norm(W[j], 2) for j in range(W.shape[0])) <= 1 + 1e-8
+            inner = sum(np.sum(W[j] * Gb[j]) for j in range(W.shape[0]))
+            nuc = sum(np.linalg.svd(Gb[j], compute_uv=False).sum() for j in range(W.shape[0]))
+            assert abs(inner - nuc) <= 1e-8 * max(1.0, nuc)
+        checked.append(st.t)
+
+    st, hist = ctv.run(M, mask, tdims, p, callback=check)
+    assert len(checked) == len(hist) and hist[-1].max() <= 1e-8
+    for k in modes:
+        assert np.abs(ctv.grad(st.L, tdims, k) - st.G[k]).max() <= 1e-8
+    assert np.abs(M - st.L - st.E).max() <= 1e-8
