@@ -122,6 +122,11 @@ def test_g_step_threshold_is_lambda_over_gamma_mu():
         norms = np.array([np.linalg.norm(Wb[j], 2) for j in range(Wb.shape[0])])
         assert norms.max() <= tau * (1 + 1e-10)
         assert abs(norms.max() - tau) < 1e-10 * tau
+        # and Lambda_i' / mu is a subgradient of tau ||.||_* at G_i': aligned with it
+        Gb = transform.forward(new.G[i], tdims)
+        inner = sum(np.sum(Wb[j] * Gb[j]) for j in range(Wb.shape[0]))
+        nuc = sum(np.linalg.svd(Gb[j], compute_uv=False).sum() for j in range(Gb.shape[0]))
+        assert nuc > 0 and abs(inner - tau * nuc) <= 1e-9 * tau * nuc
 
 
 def test_recovery_improves_with_samples_and_beats_the_sample_average():
