@@ -340,3 +340,34 @@ def test_multipliers_are_subgradients_and_the_loop_reaches_feasibility():
     for k in modes:
         assert np.abs(ctv.grad(st.L, tdims, k) - st.G[k]).max() <= 1e-8
     assert np.abs(M - st.L - st.E).max() <= 1e-8
+
+
+def test_gradient_solve_property_over_random_shapes():
+    # any order 2..5, sizes 1..7 (size-1 modes included), any subset of modes:
+    # nabla_k is the roll difference, nabla_k^T its adjoint, and the FFT solve
+    # satisfies its linear system
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(st.lists(st.integers(1, 7), min_size=2, max_size=5), st.data())
+    def check(dims, data):
+        tdims = tuple(dims[2:])
+        n = int(np.prod(tdims)) if tdims else 1
+        shape = (n, dims[0], dims[1])
+        modes = tuple(sorted(data.draw(st.sets(st.integers(1, len(dims)), min_size=1))))
+        rng = np.random.default_rng(len(dims) * 100 + sum(dims))
+        X = rng.standard_normal(shape)
+        Y = rng.standard_normal(shape)
+        for k in range(1, len(dims) + 1):
+            assert np.array_equal(ctv.grad(X, tdims, k), roll_grad(X, tdims, k))
+            assert abs(np.sum(ctv.grad(X, tdims, k) * Y) - np.sum(X * ctv.grad_t(Y, tdims, k))) \
+                < 1e-12 * (1 + np.abs(X).sum() * np.abs(Y).max())
+        R0 = rng.standard_normal(shape)
+        Rk = {k: rng.standard_normal(shape) for k in modes}
+        L = ctv.l_update(R0, Rk, tdims, modes)
+        lhs = L + sum(roll_grad_t(roll_grad(L, tdims, k), tdims, k) for k in modes)
+        rhs = R0 + sum(roll_grad_t(Rk[k], tdims, k) for k in modes)
+        assert np.abs(lhs - rhs).max() < 1e-11 * (1 + np.abs(rhs).max())
+
+    check()

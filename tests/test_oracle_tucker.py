@@ -278,3 +278,31 @@ def test_ad_tucker_engine_of_the_prox_is_exact_on_shared_spaces():
     assert info["tucker_ranks"] == (4, 3)
     assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
     assert np.array_equal(info["ranks"], winfo["ranks"])
+
+
+def test_fixed_accuracy_property_over_random_shapes():
+    # any stack shape, shared dimensions and block size: the ranks found are
+    # those of the unfoldings (mode 1: min(s1, n s2), as [P S_1 Q^T ... P S_n Q^T]
+    # = P [S_1 Q^T ... S_n Q^T]; mode 2 on the truncated core: min(s2, n r1)),
+    # the reconstruction is exact, and each estimate is the projection error
+    # (zero)
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None)
+    @hyp.given(st.integers(1, 6), st.integers(4, 20), st.integers(4, 20), st.data())
+    def check(n, n1, n2, data):
+        s1 = data.draw(st.integers(1, n1 - 1))
+        s2 = data.draw(st.integers(1, n2 - 1))
+        b = data.draw(st.integers(1, 6))
+        rng = np.random.default_rng(n * 1000 + n1 * 30 + n2)
+        X, P, Q = shared_stack(n, n1, n2, s1, s2, rng)
+        C, F1, F2, (E1, E2) = tucker.ad_rsthosvd_blbp(X, 1e-8, b, 1e-10, gauss_source(rng))
+        r1 = min(s1, n * s2)
+        assert F1.shape[1] == r1 and F2.shape[1] == min(s2, n * r1)
+        back = tucker.mode_product(tucker.mode_product(C, F1, 1), F2, 2)
+        nx = np.sum(X * X)
+        assert np.sum((back - X) ** 2) <= 1e-16 * nx
+        assert abs(E1) <= 1e-12 * nx and abs(E2) <= 1e-12 * nx
+
+    check()
