@@ -371,3 +371,38 @@ def test_gradient_solve_property_over_random_shapes():
         assert np.abs(lhs - rhs).max() < 1e-11 * (1 + np.abs(rhs).max())
 
     check()
+
+
+def test_transforms_and_l1_prox_property_over_random_shapes():
+    # random slice sizes and transformed modes, DCT and DFT: the inverse undoes
+    # the transform, the DFT is numpy's FFT, and the l1 GNHTSVT output G of A
+    # satisfies the per-slice optimality of the nuclear-norm prox: every
+    # transformed slice of (A - G)/tau has spectral norm <= 1 and is aligned
+    # with G's (inner product = nuclear norm)
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None)
+    @hyp.given(st.integers(1, 6), st.integers(1, 6),
+               st.lists(st.integers(1, 5), min_size=1, max_size=3),
+               st.sampled_from(["dct", "fft"]), st.floats(0.05, 3.0))
+    def check(n1, n2, tdims, kind, tau):
+        tdims = tuple(tdims)
+        n = int(np.prod(tdims))
+        rng = np.random.default_rng(n1 * 7 + n2 * 11 + n)
+        A = rng.standard_normal((n, n1, n2))
+        Ab = transform.forward(A, tdims, kind)
+        assert np.abs(transform.inverse(Ab, tdims, kind) - A).max() < 1e-12
+        if kind == "fft":
+            V = A.reshape(tuple(reversed(tdims)) + (n1, n2))
+            ref = np.fft.fftn(V, axes=tuple(range(len(tdims)))).reshape(n, n1, n2)
+            assert np.abs(Ab - ref).max() < 1e-11
+        G, _ = svt.gnhtsvt(A, tdims, tau, prox.L1, transform_kind=kind)
+        Gb = transform.forward(G, tdims, kind)
+        Wb = (Ab - Gb) / tau
+        for j in range(n):
+            assert np.linalg.norm(Wb[j], 2) <= 1 + 1e-9
+            nuc = np.linalg.svd(Gb[j], compute_uv=False).sum()
+            assert abs(np.vdot(Wb[j], Gb[j]).real - nuc) <= 1e-9 * max(1.0, nuc)
+
+    check()
