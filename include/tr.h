@@ -368,7 +368,7 @@ tr_status tr_ctv_free(tr_ctv *c);
  *     sample, `sign` (device, m int8) its sign (> 0: +1, else -1); both are
  *     read once (J1, J2 are formed here) and may be freed afterwards.
  *     Initialises L = Z = Y = G_i = Lambda_i = 0, mu = mu0, t = 0 (Alg. 6).
- *     Allocates about (9 + 2 |Gamma|) tensors plus an internal tr_init
+ *     Allocates about (8 + 2 |Gamma|) tensors plus an internal tr_init
  *     handle.  An index outside the tensor gives TR_EINVAL.
  *   tr_onebit_step: one iteration on the stream; with rel_change non-NULL
  *     it synchronises and returns ||L^{t+1} - L^t||_F / ||L^t||_F (the stop

@@ -13,7 +13,8 @@
 //      mu = min(mu_max, vartheta mu)                      (Eq. lagrange11-22)
 //   5. the infinity norms of L - L^t, E - E^t, nabla_k L - G_k and G_k - G_k^t
 //      (each the maximum over k) and M - L - E               (Eq. convercon)
-// Step 1 runs through tr_grad and tr_gradient_solve; step 2 through the
+// The periodic differences are applied on the fly inside fused stencil
+// kernels; the linear solve runs through tr_gradient_solve; step 2 through the
 // public entry points tr_transform_forward, tr_slice_prox (the randomized
 // per-slice engine with the Philox sketches of iteration t) and
 // tr_transform_inverse of an internal handle.
@@ -32,6 +33,7 @@ struct tr_ctv {
   tr_dtype dtype = TR_F32;
   int order = 0;
   int64_t dims[8] = {0};
+  int64_t S[8] = {0};              // flat stride of each mode
   int64_t N = 0;
   int nmodes = 0;
   int modes[8] = {0};              // 1-based modes of Gamma, ascending
@@ -102,15 +104,15 @@ __global__ void ctv_commit_l_kernel(T *L, const T *__restrict__ Lnew, int64_t N,
   ew::block_max_to(m, res);
 }
 
-// G_k = Gnew and Lambda_k += mu (D - Gnew), D = nabla_k L; max |Gnew - G_k|
-// into res[3] and max |D - Gnew| into res[2].
+// G_k = Gnew and Lambda_k += mu (D - Gnew), D = nabla_k L computed on the
+// fly; max |Gnew - G_k| into res[3] and max |D - Gnew| into res[2].
 template <typename T>
-__global__ void ctv_commit_g_kernel(T *G, T *Lam, const T *__restrict__ Gnew, const T *__restrict__ D,
-                                    T mu, int64_t N, unsigned long long *res) {
+__global__ void ctv_commit_g_kernel(T *G, T *Lam, const T *__restrict__ Gnew, const T *__restrict__ L,
+                                    T mu, int64_t N, int64_t S, int64_t nk, unsigned long long *res) {
   double m2 = 0.0, m3 = 0.0;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < N; f += step) {
-    const T g = Gnew[f], d = D[f];
+    const T g = Gnew[f], d = L[ew::fwd_neighbour(f, S, nk)] - L[f];
     m3 = fmax(m3, fabs((double)g - (double)G[f]));
     m2 = fmax(m2, fabs((double)d - (double)g));
     G[f] = g;
@@ -182,11 +184,9 @@ tr_status ctv_step(tr_ctv *c, double *res_out) {
   for (int q = 0; q < c->nmodes; ++q) {
     const int k = c->modes[q];
     bits |= 1u << (k - 1);
-    T *Gk = (T *)slot(c, c->G, q), *Lk = (T *)slot(c, c->Lam, q);
-    ew::axpby_kernel<T><<<g, 256, 0, s>>>(W, T(1), Gk, (T)(-1.0 / mu), Lk, N);
-    CV_CUDA(cudaGetLastError());
-    CV_TR(tr_grad(c->dtype, c->order, c->dims, k, 1, W, c->Abar, s, buf, sizeof buf));
-    ew::axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), R, T(1), (const T *)c->Abar, N);
+    const T *Gk = (const T *)slot(c, c->G, q), *Lk = (const T *)slot(c, c->Lam, q);
+    ew::adj_grad_accum_kernel<T><<<g, 256, 0, s>>>(R, Gk, Lk, (T)(1.0 / mu), N, c->S[k - 1],
+                                                  c->dims[k - 1]);
     CV_CUDA(cudaGetLastError());
   }
   CV_TR(tr_gradient_solve(c->dtype, c->order, c->dims, bits, R, W, s, buf, sizeof buf));
@@ -197,13 +197,13 @@ tr_status ctv_step(tr_ctv *c, double *res_out) {
   for (int q = 0; q < c->nmodes; ++q) {
     const int k = c->modes[q];
     T *Gk = (T *)slot(c, c->G, q), *Lk = (T *)slot(c, c->Lam, q);
-    CV_TR(tr_grad(c->dtype, c->order, c->dims, k, 0, L, W, s, buf, sizeof buf));   // W = nabla_k L
-    ew::axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), W, (T)(1.0 / mu), Lk, N);
+    const int64_t S = c->S[k - 1], nk = c->dims[k - 1];
+    ew::grad_plus_kernel<T><<<g, 256, 0, s>>>(R, L, Lk, (T)(1.0 / mu), N, S, nk);   // nabla_k L + Lambda_k/mu
     CV_CUDA(cudaGetLastError());
     CV_TR(tr_transform_forward(c->prox, R, c->Abar));
     CV_TR(tr_slice_prox(c->prox, c->Abar, c->Gbar, tau, c->t));
     CV_TR(tr_transform_inverse(c->prox, c->Gbar, R));                             // R = G_k new
-    ctv_commit_g_kernel<T><<<g, 256, 0, s>>>(Gk, Lk, R, W, (T)mu, N, c->res);
+    ctv_commit_g_kernel<T><<<g, 256, 0, s>>>(Gk, Lk, R, L, (T)mu, N, S, nk, c->res);
     CV_CUDA(cudaGetLastError());
   }
   // 3. E-update and 4. Y-update
@@ -285,8 +285,10 @@ extern "C" tr_status tr_ctv_create(tr_ctv **out, const tr_problem *pb, const tr_
     c->dims[k] = pb->dims[k];
     c->N *= pb->dims[k];
   }
-  for (int k = 1; k <= pb->order; ++k)
+  for (int k = 1; k <= pb->order; ++k) {
+    c->S[k - 1] = ew::mode_stride(c->dims, k);
     if (prm->modes & (1u << (k - 1))) c->modes[c->nmodes++] = k;
+  }
   c->prm = *prm;
   if (c->prm.lambda <= 0.0) {   // lambda = 1/sqrt(max(n1, n2)), as tr_init's default
     const double mx = (double)(c->dims[0] > c->dims[1] ? c->dims[0] : c->dims[1]);

@@ -18,7 +18,7 @@
 // Step 3 runs through the public entry points tr_transform_forward,
 // tr_slice_prox and tr_transform_inverse of an internal handle (the
 // randomized per-slice engine with its Philox sketches for iteration t);
-// step 2 through tr_grad and tr_gradient_solve.  J1 and J2 come from exact
+// step 2 through fused stencil kernels and tr_gradient_solve.  J1 and J2 come from exact
 // integer counts of the +1 and -1 samples per entry, so they do not depend
 // on the order of the atomic updates.
 
@@ -37,6 +37,7 @@ struct tr_onebit {
   tr_dtype dtype = TR_F32;
   int order = 0;
   int64_t dims[8] = {0};
+  int64_t S[8] = {0};             // flat stride of each mode
   int64_t N = 0, m = 0;
   int nmodes = 0;
   int modes[8] = {0};             // 1-based modes of Gamma, ascending
@@ -46,7 +47,7 @@ struct tr_onebit {
   size_t esz = 4;
   void *L = nullptr, *Z = nullptr, *Y = nullptr, *J1 = nullptr, *J2 = nullptr;
   void *G = nullptr, *Lam = nullptr;                 // nmodes tensors each, back to back
-  void *R = nullptr, *W = nullptr, *Abar = nullptr, *Gbar = nullptr;
+  void *R = nullptr, *Abar = nullptr, *Gbar = nullptr;
   uint8_t *mask = nullptr;        // the internal handle's (unread) mask
   double *acc = nullptr;          // device: sum (L' - L)^2, sum L^2
   double mu = 0.0;
@@ -137,7 +138,7 @@ __global__ void onebit_l_kernel(T *L, const T *__restrict__ Z, const T *__restri
 void free_onebit(tr_onebit *ob) {
   if (ob->prox) tr_free(ob->prox);
   void *bufs[] = {ob->L, ob->Z, ob->Y, ob->J1, ob->J2, ob->G, ob->Lam,
-                  ob->R, ob->W, ob->Abar, ob->Gbar, ob->mask, ob->acc};
+                  ob->R, ob->Abar, ob->Gbar, ob->mask, ob->acc};
   for (void *p : bufs)
     if (p) cudaFree(p);
 }
@@ -152,7 +153,7 @@ tr_status onebit_step(tr_onebit *ob, double *rel) {
   const int g = ob_grid(ob->N);
   const int64_t N = ob->N;
   const double mu = ob->mu;
-  T *L = (T *)ob->L, *Z = (T *)ob->Z, *Y = (T *)ob->Y, *R = (T *)ob->R, *W = (T *)ob->W;
+  T *L = (T *)ob->L, *Z = (T *)ob->Z, *Y = (T *)ob->Y, *R = (T *)ob->R;
   char buf[256];
 #define OB_CUDA(call)                                                                        \
   do {                                                                                       \
@@ -178,11 +179,9 @@ tr_status onebit_step(tr_onebit *ob, double *rel) {
   for (int q = 0; q < ob->nmodes; ++q) {
     const int k = ob->modes[q];
     mask |= 1u << (k - 1);
-    T *Gi = (T *)tensor(ob, ob->G, q), *Li = (T *)tensor(ob, ob->Lam, q);
-    ew::axpby_kernel<T><<<g, 256, 0, s>>>(W, T(1), Gi, (T)(-1.0 / mu), Li, N);
-    OB_CUDA(cudaGetLastError());
-    OB_TR(tr_grad(ob->dtype, ob->order, ob->dims, k, 1, W, ob->Abar, s, buf, sizeof buf));
-    ew::axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), R, T(1), (const T *)ob->Abar, N);
+    const T *Gi = (const T *)tensor(ob, ob->G, q), *Li = (const T *)tensor(ob, ob->Lam, q);
+    ew::adj_grad_accum_kernel<T><<<g, 256, 0, s>>>(R, Gi, Li, (T)(1.0 / mu), N, ob->S[k - 1],
+                                                  ob->dims[k - 1]);
     OB_CUDA(cudaGetLastError());
   }
   OB_TR(tr_gradient_solve(ob->dtype, ob->order, ob->dims, mask, R, Z, s, buf, sizeof buf));
@@ -191,13 +190,13 @@ tr_status onebit_step(tr_onebit *ob, double *rel) {
   for (int q = 0; q < ob->nmodes; ++q) {
     const int k = ob->modes[q];
     T *Gi = (T *)tensor(ob, ob->G, q), *Li = (T *)tensor(ob, ob->Lam, q);
-    OB_TR(tr_grad(ob->dtype, ob->order, ob->dims, k, 0, Z, W, s, buf, sizeof buf));
-    ew::axpby_kernel<T><<<g, 256, 0, s>>>(R, T(1), W, (T)(1.0 / mu), Li, N);   // R: prox input
+    const int64_t S = ob->S[k - 1], nk = ob->dims[k - 1];
+    ew::grad_plus_kernel<T><<<g, 256, 0, s>>>(R, Z, Li, (T)(1.0 / mu), N, S, nk);   // prox input
     OB_CUDA(cudaGetLastError());
     OB_TR(tr_transform_forward(ob->prox, R, ob->Abar));
     OB_TR(tr_slice_prox(ob->prox, ob->Abar, ob->Gbar, tau, ob->t));
     OB_TR(tr_transform_inverse(ob->prox, ob->Gbar, Gi));
-    ew::multiplier_kernel<T><<<g, 256, 0, s>>>(Li, (T)mu, W, Gi, N);          // W = nabla_i Z
+    ew::grad_multiplier_kernel<T><<<g, 256, 0, s>>>(Li, (T)mu, Z, Gi, N, S, nk);
     OB_CUDA(cudaGetLastError());
   }
   ew::multiplier_kernel<T><<<g, 256, 0, s>>>(Y, (T)mu, L, Z, N);
@@ -277,15 +276,17 @@ extern "C" tr_status tr_onebit_create(tr_onebit **out, tr_dtype dtype, int order
     return ofail(nullptr, err, err_len, TR_EUNSUPPORTED, "at most 2^31 - 1 entries (int counts)");
   }
   ob->m = m;
-  for (int k = 1; k <= order; ++k)
+  for (int k = 1; k <= order; ++k) {
+    ob->S[k - 1] = ew::mode_stride(ob->dims, k);
     if (prm->modes & (1u << (k - 1))) ob->modes[ob->nmodes++] = k;
+  }
   ob->prm = *prm;
   ob->stream = (cudaStream_t)cuda_stream;
   ob->esz = dtype == TR_F64 ? 8 : 4;
   ob->mu = prm->mu0;
   const size_t T = (size_t)ob->N * ob->esz;
   cudaError_t e = cudaSuccess;
-  void **single[] = {&ob->L, &ob->Z, &ob->Y, &ob->J1, &ob->J2, &ob->R, &ob->W, &ob->Abar, &ob->Gbar};
+  void **single[] = {&ob->L, &ob->Z, &ob->Y, &ob->J1, &ob->J2, &ob->R, &ob->Abar, &ob->Gbar};
   for (void **p : single)
     if (e == cudaSuccess) e = cudaMalloc(p, T);
   if (e == cudaSuccess) e = cudaMalloc(&ob->G, T * ob->nmodes);
