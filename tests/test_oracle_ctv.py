@@ -349,7 +349,7 @@ def test_gradient_solve_property_over_random_shapes():
     hyp = pytest.importorskip("hypothesis")
     st = hyp.strategies
 
-    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
     @hyp.given(st.lists(st.integers(1, 7), min_size=2, max_size=5), st.data())
     def check(dims, data):
         tdims = tuple(dims[2:])
@@ -382,7 +382,7 @@ def test_transforms_and_l1_prox_property_over_random_shapes():
     hyp = pytest.importorskip("hypothesis")
     st = hyp.strategies
 
-    @hyp.settings(max_examples=40, deadline=None)
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
     @hyp.given(st.integers(1, 6), st.integers(1, 6),
                st.lists(st.integers(1, 5), min_size=1, max_size=3),
                st.sampled_from(["dct", "fft"]), st.floats(0.05, 3.0))
