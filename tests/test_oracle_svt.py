@@ -165,3 +165,30 @@ def test_adaptive_deflation_refills_block():
     U, E, hist = svt.adaptive_basis(Ab, 1e-8, 5, 1e-12, seed=1, t=0, j=0)
     assert U.shape[1] >= 2
     assert np.sum((Ab - U @ (U.T @ Ab)) ** 2) < 1e-20 * max(1.0, np.sum(Ab ** 2)) + 1e-18
+
+
+def test_randomized_prox_is_exact_when_the_sketch_covers_the_rank_property():
+    # any slice shape, slice ranks from 0 (a zero slice) to the sketch width,
+    # widths above min(n1, n2) (clamped), q = 0..2, l1 and MCP: the randomized
+    # prox equals the full-SVD prox, slice by slice
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=50, deadline=None, derandomize=True)
+    @hyp.given(st.integers(1, 4), st.integers(1, 12), st.integers(1, 12), st.data())
+    def check(n, n1, n2, data):
+        l = data.draw(st.integers(1, 14))
+        q = data.draw(st.integers(0, 2))
+        kind = data.draw(st.sampled_from([prox.L1, prox.MCP]))
+        ll = min(l, n1, n2)
+        rng = np.random.default_rng(n * 400 + n1 * 20 + n2 + l)
+        Ab = np.zeros((n, n1, n2))
+        for j in range(n):
+            r = int(rng.integers(0, ll + 1))
+            Ab[j] = rng.standard_normal((n1, r)) @ rng.standard_normal((r, n2))
+        got, _ = svt.transformed_prox(Ab, 0.7, kind, gamma=20.0, engine="rsvd", l=l, q=q, seed=3,
+                                      t=1)
+        want, _ = svt.transformed_prox(Ab, 0.7, kind, gamma=20.0)
+        assert np.abs(got - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
+
+    check()
