@@ -192,3 +192,28 @@ def test_randomized_prox_is_exact_when_the_sketch_covers_the_rank_property():
         assert np.abs(got - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
 
     check()
+
+
+def test_adaptive_basis_finds_the_rank_property():
+    # Alg. 3 per slice on any shape, rank (0 included) and block size: with
+    # eps = 1e-6 the basis has exactly the slice's rank, captures the slice,
+    # and the prox through it is the full-SVD prox
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
+    @hyp.given(st.integers(2, 30), st.integers(2, 30), st.data())
+    def check(n1, n2, data):
+        r = data.draw(st.integers(0, min(n1, n2) - 1))
+        b = data.draw(st.integers(1, 8))
+        rng = np.random.default_rng(n1 * 40 + n2 + 1000 * r + b)
+        A = rng.standard_normal((n1, r)) @ rng.standard_normal((r, n2))
+        U, E, _ = svt.adaptive_basis(A, 1e-6, b, 1e-12, seed=5, t=1, j=0)
+        assert U.shape[1] == r
+        if r:
+            assert np.linalg.norm(A - U @ (U.T @ A)) <= 1e-9 * np.linalg.norm(A)
+        G, _, _, _, _ = svt.slice_prox_adaptive(A, 1e-6, b, 1e-12, 5, 1, 0, 0.5, prox.L1)
+        want, _, _ = svt.slice_prox_full(A, 0.5, prox.L1)
+        assert np.abs(G - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
+
+    check()
