@@ -126,3 +126,37 @@ def test_first_step_from_zero_state_closed_form():
     E = np.where(mask == 1, np.sign(M / 2) * np.maximum(np.abs(M / 2) - 0.6, 0), 0)
     assert np.max(np.abs(st.E - E)) < 1e-15
     assert np.max(np.abs(st.Y - 0.5 * (M - M / 2 - E))) < 1e-15
+
+
+def test_every_step_satisfies_the_dual_identities_property():
+    # Alg. 5 with nabla = I on random shapes, both engines, both noise models:
+    # from the L-update 2L = (M - E + Y/mu) + (G - Lam/mu) and the multiplier
+    # updates, every step gives Y' - Lam' = mu (E - E') + mu (G' - G), and
+    # Y' = 0 off Omega (E = H there)
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=30, deadline=None, derandomize=True)
+    @hyp.given(st.integers(2, 9), st.integers(2, 9), st.lists(st.integers(1, 4), min_size=1,
+                                                                max_size=2), st.data())
+    def check(n1, n2, tdims, data):
+        tdims = tuple(tdims)
+        n = int(np.prod(tdims))
+        engine = data.draw(st.sampled_from(["full", "rsvd"]))
+        noise = data.draw(st.sampled_from([admm.NOISE_L1, admm.NOISE_NONE]))
+        rng = np.random.default_rng(n1 * 31 + n2 * 7 + n)
+        X = rng.standard_normal((n, n1, n2))
+        mask = rng.random(X.shape) < 0.6
+        M = np.where(mask, X, 0.0)
+        p = admm.Params(engine=engine, l=3, q=1, seed=4, noise=noise, lam=0.3, mu0=0.2,
+                        phi=prox.MCP, phi_gamma=20.0, psi=prox.MCP, psi_gamma=20.0)
+        s = admm.init_state(M.shape, p.mu0)
+        for _ in range(4):
+            new, _ = admm.step(s, M, mask, tdims, p)
+            lhs = new.Y - new.Lam
+            rhs = s.mu * (s.E - new.E) + s.mu * (new.G - s.G)
+            assert np.abs(lhs - rhs).max() <= 1e-10 * max(1.0, np.abs(new.Y).max())
+            assert np.abs(new.Y[~mask]).max() <= 1e-12 * max(1.0, np.abs(new.Y).max())
+            s = new
+
+    check()
