@@ -180,3 +180,50 @@ def test_threshold_and_certificate():
     # 7 <= 14 is not, and a slice already at lmax never is
     sat = lo.saturated([7, 7, 20, 3], [16, 24, 24, 40], 10, 40)
     assert sat.tolist() == [0, 2]
+
+
+def test_width_plan_and_feature_invariants_property():
+    # widths: within [min(8, lmax), lmax], a multiple of 8 or lmax itself, at
+    # least min(rank + p, lmax) for the predicted rank, non-decreasing in the
+    # prediction, lmax for NaN; the plan: ids a permutation stably sorted by
+    # class, counts per class; features within their stated ranges
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(st.lists(st.floats(-30, 30, allow_nan=False, width=32), min_size=1, max_size=40),
+               st.integers(0, 20), st.integers(1, 96))
+    def check(ys, p, lmax):
+        w = [lo.width_of(y, p, lmax) for y in ys]
+        for y, wi in zip(ys, w):
+            assert min(8, lmax) <= wi <= lmax and (wi % 8 == 0 or wi == lmax)
+            r = min(max(float(np.floor(np.expm1(np.clip(np.float32(y), -20, 20)) + 0.5)), 0.0), lmax)
+            assert wi >= min(int(r) + p, lmax)
+        order = np.argsort(np.asarray(ys, dtype=np.float32), kind="stable")
+        assert all(w[a] <= w[b] for a, b in zip(order, order[1:]))
+        assert lo.width_of(np.float32("nan"), p, lmax) == lmax
+        width, ids, counts = lo.plan_widths(np.asarray(ys, dtype=np.float32), p, lmax)
+        assert sorted(ids.tolist()) == list(range(len(ys)))
+        cls = (width - 1) // 8
+        assert all(cls[a] < cls[b] or (cls[a] == cls[b] and a < b) for a, b in zip(ids, ids[1:]))
+        assert counts.sum() == len(ys) and len(counts) == (lmax + 7) // 8
+        assert all(counts[c] == np.sum(cls == c) for c in range(len(counts)))
+
+    check()
+
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
+    @hyp.given(st.integers(1, 12), st.integers(1, 20), st.data())
+    def features(n, ld, data):
+        rng = np.random.default_rng(n * 50 + ld)
+        sig = rng.lognormal(0.0, 2.0, (n, ld)) * (rng.random((n, ld)) < 0.8)
+        width = rng.integers(1, ld + 1, n)
+        rank = rng.integers(0, 100, n)
+        pos = st.one_of(st.just(0.0), st.floats(1e-6, 5.0))
+        thr, thr0 = data.draw(pos), data.draw(pos)
+        F = lo.features(sig, rank, width, thr, thr0, data.draw(st.floats(-1.0, 2.0)))
+        lower = np.array([0, 0, -1, -1] + [0] * 6 + [0, 0, 0, 0, -1, 0], dtype=float)
+        upper = np.array([1, 1, 1, 1] + [1] * 6 + [1, 1, 1, 1, 1, 1], dtype=float)
+        upper[0] = np.log1p(99) / np.log(129)
+        assert np.all(F >= lower - 1e-12) and np.all(F <= upper + 1e-12)
+
+    features()
