@@ -1,0 +1,221 @@
+"""CPU emulation of the index arithmetic and launch sequences of the
+gradient-domain and one-bit CUDA code (csrc/grad_kernels.cu, csrc/ctv.cu,
+csrc/onebit.cu, csrc/ew_kernels.cuh), checked against the FP64 oracle.
+
+Each kernel is restated as one numpy operation on flat buffers, with the
+kernels' own formulas:
+* flat stride of mode k: S_1 = n2, S_2 = 1, S_k = n1 n2 n3 ... n_{k-1};
+* periodic neighbours f +- S_k with the wrap at i_k = (f / S_k) mod n_k;
+* the strided batched GEMM C[o][x][y] = sum_b A[o][x][b] B[o][b][y] with the
+  operand strides the host code passes for each mode (left product for
+  k != 2, right product for the contiguous mode 2);
+* the ping-pong of the Hartley solve between the scratch and the output;
+* the fused stencils and their order in the two ADMM steps.
+Numpy's fancy indexing raises on any out-of-range index, so these runs also
+show every access stays inside its buffer.  This checks the arithmetic the
+kernels encode, not the compiled kernels: their parity tests against the
+oracle are tests/test_gpu_grad.py, test_gpu_ctv.py and test_gpu_onebit.py.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import admm, ctv, onebit, prox, svt, transform
+from paper_2506_09594_gb300 import synth
+
+
+def mode_stride(dims, k):
+    if k == 1:
+        return dims[1]
+    if k == 2:
+        return 1
+    s = dims[0] * dims[1]
+    for m in range(3, k):
+        s *= dims[m - 1]
+    return s
+
+
+def fwd(N, S, nk):
+    f = np.arange(N)
+    return np.where((f // S) % nk == nk - 1, f - (nk - 1) * S, f + S)
+
+
+def bwd(N, S, nk):
+    f = np.arange(N)
+    return np.where((f // S) % nk == 0, f + (nk - 1) * S, f - S)
+
+
+def gemm(A, ao, ax, ab, B, bo, bb, by, C, co, cx, cy, X, Y, K, batch):
+    o = np.arange(batch)[:, None, None, None]
+    x = np.arange(X)[None, :, None, None]
+    y = np.arange(Y)[None, None, :, None]
+    b = np.arange(K)[None, None, None, :]
+    vals = (A[o * ao + x * ax + b * ab] * B[o * bo + b * bb + y * by]).sum(-1)
+    oo, xx, yy = np.meshgrid(np.arange(batch), np.arange(X), np.arange(Y), indexing="ij")
+    C[oo * co + xx * cx + yy * cy] = vals
+
+
+def hartley(n):
+    a = 2 * np.pi * (np.outer(np.arange(n), np.arange(n)) % n) / n
+    return (np.cos(a) + np.sin(a)) / np.sqrt(n)
+
+
+def mode_product(src, dst, dims, k):
+    N, m, S = src.size, dims[k - 1], mode_stride(dims, k)
+    H = hartley(m).ravel()
+    if k == 2:
+        gemm(src, 0, m, 1, H, 0, m, 1, dst, 0, m, 1, N // m, m, m, 1)
+    else:
+        gemm(H, 0, m, 1, src, m * S, S, 1, dst, m * S, S, 1, m, S, m, N // (m * S))
+
+
+def gradient_solve(rhs, dims, modes):
+    N = rhs.size
+    bufs = [np.zeros(N), np.zeros(N)]          # [scratch, out]: product p writes bufs[p % 2]
+    cur, p = rhs.ravel(), 0
+    for k in modes:
+        mode_product(cur, bufs[p % 2], dims, k)
+        cur, p = bufs[p % 2], p + 1
+    f = np.arange(N)
+    den = np.ones(N)
+    for k in modes:
+        nk = dims[k - 1]
+        den += 2 - 2 * np.cos(2 * np.pi * ((f // mode_stride(dims, k)) % nk) / nk)
+    cur /= den
+    for k in modes:
+        mode_product(cur, bufs[p % 2], dims, k)
+        cur, p = bufs[p % 2], p + 1
+    assert cur is bufs[1]                      # the last product lands in `out`
+    return cur
+
+
+@pytest.mark.parametrize("dims,modes", [((7, 5, 4, 3), (1, 2, 3, 4)), ((6, 9, 5), (1, 3)),
+                                        ((8, 8), (1, 2)), ((4, 6, 1, 3), (3, 4)),
+                                        ((37, 29, 5, 3), (2, 4))])
+def test_gradient_kernels_and_solve(dims, modes):
+    tdims = tuple(dims[2:])
+    n = int(np.prod(tdims)) if tdims else 1
+    rng = np.random.default_rng(sum(dims))
+    X = rng.standard_normal((n, dims[0], dims[1]))
+    N = X.size
+    for k in range(1, len(dims) + 1):
+        S, nk = mode_stride(dims, k), dims[k - 1]
+        got = (X.ravel()[fwd(N, S, nk)] - X.ravel()).reshape(X.shape)
+        assert np.abs(got - ctv.grad(X, tdims, k)).max() < 1e-14
+        got = (X.ravel()[bwd(N, S, nk)] - X.ravel()).reshape(X.shape)
+        assert np.abs(got - ctv.grad_t(X, tdims, k)).max() < 1e-14
+    got = gradient_solve(X, dims, modes).reshape(X.shape)
+    want = ctv.l_update(X, {k: np.zeros_like(X) for k in modes}, tdims, modes)
+    assert np.abs(got - want).max() < 1e-13
+
+
+def prox_through_handle(Rin, tau, t, p, tdims):
+    Ab = transform.forward(Rin, tdims)
+    Gb, _ = svt.transformed_prox(Ab, tau, p.phi, p.phi_theta, p.phi_gamma, engine="rsvd", l=p.l,
+                                 q=p.q, seed=p.seed, t=t)
+    return transform.inverse(Gb, tdims).ravel()
+
+
+@pytest.mark.parametrize("dims,modes,noise", [((12, 10, 5, 4), (1, 2), admm.NOISE_L1),
+                                              ((12, 10, 5, 4), (1, 2, 4), admm.NOISE_NONE),
+                                              ((9, 7, 6), (1, 3), admm.NOISE_L1)])
+def test_gradient_step_sequence(dims, modes, noise):
+    tdims = tuple(dims[2:])
+    shape = (int(np.prod(tdims)), dims[0], dims[1])
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(5)
+    draw = lambda s: s * rng.standard_normal(shape)
+    mask = (rng.random(shape) < 0.6).astype(np.uint8)
+    M = np.where(mask == 1, draw(1.0), 0.0)
+    st = ctv.State(L=draw(0.5), E=draw(0.1), Y=draw(0.05), G={k: draw(0.3) for k in modes},
+                   Lam={k: draw(0.05) for k in modes}, mu=0.4, t=2)
+    p = ctv.Params(modes=modes, transform="dct", engine="rsvd", l=6, q=1, seed=8, phi=prox.MCP,
+                   phi_gamma=30.0, psi=prox.MCP, psi_gamma=30.0, noise=noise, lam=0.2)
+    ref, res_ref = ctv.step(st, M, mask, tdims, p)
+    # the launch sequence of ctv_step
+    mu = st.mu
+    L, E, Y, Mf = st.L.ravel().copy(), st.E.ravel().copy(), st.Y.ravel().copy(), M.ravel()
+    G = {k: st.G[k].ravel().copy() for k in modes}
+    Lam = {k: st.Lam[k].ravel().copy() for k in modes}
+    res = np.zeros(5)
+    R = Mf - E + Y * (1 / mu)                                     # ctv_rhs_kernel
+    for k in modes:                                               # adj_grad_accum_kernel
+        b = bwd(N, mode_stride(dims, k), dims[k - 1])
+        W = G[k] - (1 / mu) * Lam[k]
+        R = R + (W[b] - W)
+    W = gradient_solve(R.reshape(shape), dims, modes)            # tr_gradient_solve
+    res[0] = np.abs(W - L).max()                                  # ctv_commit_l_kernel
+    L = W.copy()
+    tau = 1.0 / (len(modes) * mu)
+    for k in modes:
+        fw = fwd(N, mode_stride(dims, k), dims[k - 1])
+        R = (L[fw] - L) + (1 / mu) * Lam[k]                       # grad_plus_kernel
+        Gn = prox_through_handle(R.reshape(shape), tau, st.t, p, tdims)
+        d = L[fw] - L                                             # ctv_commit_g_kernel
+        res[3] = max(res[3], np.abs(Gn - G[k]).max())
+        res[2] = max(res[2], np.abs(d - Gn).max())
+        G[k], Lam[k] = Gn, Lam[k] + mu * (d - Gn)
+    H = Mf - L + Y / mu                                           # ctv_e_kernel
+    on = np.zeros(N) if noise == admm.NOISE_NONE else prox.prox_scalar(H, p.lam / mu, p.psi,
+                                                                        p.psi_theta, p.psi_gamma)
+    e = np.where(mask.ravel() == 1, on, H)
+    res[1] = np.abs(e - E).max()
+    r = Mf - L - e
+    res[4] = np.abs(r).max()
+    Y = Y + mu * r
+    assert np.abs(L.reshape(shape) - ref.L).max() < 1e-13
+    assert np.abs(Y.reshape(shape) - ref.Y).max() < 1e-13
+    for k in modes:
+        assert np.abs(G[k].reshape(shape) - ref.G[k]).max() < 1e-13
+        assert np.abs(Lam[k].reshape(shape) - ref.Lam[k]).max() < 1e-13
+    assert np.abs(res - res_ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("dims,modes", [((12, 10, 6), (1, 2)), ((12, 10, 6), (1, 2, 3)),
+                                        ((8, 9, 3, 2), (2, 4))])
+def test_onebit_step_sequence(dims, modes):
+    tdims = tuple(dims[2:])
+    shape = (int(np.prod(tdims)), dims[0], dims[1])
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(6)
+    S = 0.3 * rng.standard_normal(shape)
+    s, q = synth.one_bit_observations(S, 3 * S.size, 1.2, 0.05, rng)
+    p = onebit.Params(modes=modes, engine="rsvd", l=6, q=1, seed=7, mu0=0.05, lam=2e-3, theta=1.2,
+                      alpha=0.9, phi=prox.MCP, phi_gamma=50.0)
+    m = len(s)
+    # J1, J2 from integer counts (onebit_count_kernel, onebit_j_kernel)
+    pos = np.bincount(s[q > 0], minlength=N)
+    neg = np.bincount(s[q <= 0], minlength=N)
+    J1, J2 = (p.theta * (pos - neg)).reshape(shape), (pos + neg).reshape(shape).astype(float)
+    J1o, J2o = onebit.sample_tensors(shape, s, q, p.theta)
+    assert np.abs(J1 - J1o).max() < 1e-12 and np.array_equal(J2, J2o)
+    st = onebit.State(L=0.3 * rng.standard_normal(shape), Z=0.3 * rng.standard_normal(shape),
+                      Y=0.01 * rng.standard_normal(shape),
+                      G={i: 0.1 * rng.standard_normal(shape) for i in modes},
+                      Lam={i: 0.01 * rng.standard_normal(shape) for i in modes}, mu=0.05, t=4)
+    ref, rel_ref = onebit.step(st, J1o, J2o, m, tdims, p)
+    mu = st.mu
+    L = np.clip((m * mu * st.Z + J1 - m * st.Y) / (m * mu + J2), -p.alpha, p.alpha).ravel()
+    rel = np.sqrt(np.sum((L - st.L.ravel()) ** 2) / np.sum(st.L ** 2))   # onebit_l_kernel sums
+    Y = st.Y.ravel().copy()
+    G = {k: st.G[k].ravel().copy() for k in modes}
+    Lam = {k: st.Lam[k].ravel().copy() for k in modes}
+    R = L + (1 / mu) * Y                                          # axpby_kernel
+    for k in modes:                                               # adj_grad_accum_kernel
+        b = bwd(N, mode_stride(dims, k), dims[k - 1])
+        W = G[k] - (1 / mu) * Lam[k]
+        R = R + (W[b] - W)
+    Z = gradient_solve(R.reshape(shape), dims, modes)
+    tau = p.lam / (len(modes) * mu)
+    for k in modes:
+        fw = fwd(N, mode_stride(dims, k), dims[k - 1])
+        R = (Z[fw] - Z) + (1 / mu) * Lam[k]                       # grad_plus_kernel
+        G[k] = prox_through_handle(R.reshape(shape), tau, st.t, p, tdims)
+        Lam[k] = Lam[k] + mu * ((Z[fw] - Z) - G[k])               # grad_multiplier_kernel
+    Y = Y + mu * (L - Z)                                          # multiplier_kernel
+    for name, got in (("L", L), ("Z", Z), ("Y", Y)):
+        assert np.abs(got.reshape(shape) - getattr(ref, name)).max() < 1e-13, name
+    for k in modes:
+        assert np.abs(G[k].reshape(shape) - ref.G[k]).max() < 1e-13
+        assert np.abs(Lam[k].reshape(shape) - ref.Lam[k]).max() < 1e-13
+    assert abs(rel - rel_ref) < 1e-13
