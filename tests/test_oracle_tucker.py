@@ -309,3 +309,69 @@ def test_fixed_accuracy_property_over_random_shapes():
         assert abs(E1) <= 1e-12 * nx and abs(E2) <= 1e-12 * nx
 
     check()
+
+
+def pivoted_cgs2_defl_qr(A, delta):
+    """Alg. 2 in the form a GPU panel kernel takes: column-pivoted classical
+    Gram-Schmidt with one reorthogonalisation pass.  Each step picks the
+    column with the largest residual norm (the pivot rule of the pivoted
+    Householder QR), stops once that norm is below delta, and R = Q^T A."""
+    rows, k = A.shape
+    Q = np.zeros((rows, 0))
+    Rres = A.copy()
+    left = list(range(k))
+    while left:
+        norms = [np.linalg.norm(Rres[:, j]) for j in left]
+        i = int(np.argmax(norms))
+        if norms[i] < delta:
+            break
+        j = left.pop(i)
+        v = Rres[:, j] - Q @ (Q.T @ Rres[:, j])          # second pass
+        q = v / np.linalg.norm(v)
+        Q = np.concatenate([Q, q[:, None]], axis=1)
+        for c in left:
+            Rres[:, c] -= q * (q @ Rres[:, c])
+    return Q, Q.T @ A, Q.shape[1]
+
+
+def test_pivoted_gram_schmidt_defl_qr_matches_householder_defl_qr():
+    # the GPU design's defl-QR keeps the same number of columns as Alg. 2's
+    # pivoted Householder form and spans the same space, on panels of any
+    # rank, both the short U-side and the tall V-side shapes
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(st.integers(2, 400), st.integers(1, 12), st.data())
+    def check(rows, k, data):
+        r = data.draw(st.integers(0, min(rows, k)))
+        rng = np.random.default_rng(rows * 13 + k * 7 + r)
+        A = rng.standard_normal((rows, r)) @ rng.standard_normal((r, k))
+        delta = 1e-10 * max(np.linalg.norm(A), 1e-300)
+        Qh, Rh, sh = svt.defl_qr(A, delta)
+        Qg, Rg, sg = pivoted_cgs2_defl_qr(A, delta)
+        assert sg == sh == r
+        assert np.linalg.norm(Qg.T @ Qg - np.eye(sg)) < 1e-12
+        if r:
+            sines = np.linalg.svd(Qh - Qg @ (Qg.T @ Qh), compute_uv=False)
+            assert sines.max() < 1e-9
+            assert np.linalg.norm(Qg @ Rg - A) <= 1e-10 * np.linalg.norm(A)
+
+    check()
+
+
+def test_lanczos_loop_with_gram_schmidt_defl_qr_finds_the_same_ranks():
+    # the whole fixed-accuracy Tucker loop with the Gram-Schmidt defl-QR in
+    # place of Householder: same ranks, exact reconstruction on shared spaces
+    import oracle.svt as svt_mod
+    rng = np.random.default_rng(21)
+    X, P, Q = shared_stack(6, 30, 22, 5, 3, rng)
+    saved = svt_mod.defl_qr
+    try:
+        svt_mod.defl_qr = pivoted_cgs2_defl_qr
+        C, F1, F2, E = tucker.ad_rsthosvd_blbp(X, 1e-6, 2, 1e-10, gauss_source(rng))
+    finally:
+        svt_mod.defl_qr = saved
+    assert F1.shape[1] == 5 and F2.shape[1] == 3
+    back = tucker.mode_product(tucker.mode_product(C, F1, 1), F2, 2)
+    assert np.linalg.norm(back - X) <= 1e-10 * np.linalg.norm(X)
