@@ -11,6 +11,9 @@ kernels' own formulas:
   k != 2, right product for the contiguous mode 2);
 * the ping-pong of the Hartley solve between the scratch and the output;
 * the fused stencils and their order in the two ADMM steps.
+* for the fixed-accuracy Tucker loop still to be built on the GPU: A V and
+  A^T U on a mode unfolding as per-slice strided GEMMs (plus a sum over
+  slices for A V), without forming the unfolding.
 Numpy's fancy indexing raises on any out-of-range index, so these runs also
 show every access stays inside its buffer.  This checks the arithmetic the
 kernels encode, not the compiled kernels: their parity tests against the
@@ -219,3 +222,50 @@ def test_onebit_step_sequence(dims, modes):
         assert np.abs(G[k].reshape(shape) - ref.G[k]).max() < 1e-13
         assert np.abs(Lam[k].reshape(shape) - ref.Lam[k]).max() < 1e-13
     assert abs(rel - rel_ref) < 1e-13
+
+
+def unfold_times(C, mode, V):
+    """A V for the mode unfolding A of the slice stack C (n, p1, p2), with V
+    column-major (n p_other) x k (rows j p_other + i): one strided GEMM per
+    slice into a (n, rows, k) buffer, then the sum over slices."""
+    n, p1, p2 = C.shape
+    k = V.shape[1]
+    Cf, Vf = C.ravel(), V.ravel(order="F")
+    ldv = V.shape[0]
+    out = np.zeros(n * (p1 if mode == 1 else p2) * k)
+    if mode == 1:   # sum_j C_j V_j, V_j = rows j p2 ..: x = i1, b = i2
+        gemm(Cf, p1 * p2, p2, 1, Vf, p2, 1, ldv, out, p1 * k, k, 1, p1, k, p2, n)
+        return out.reshape(n, p1, k).sum(axis=0)
+    # mode 2: sum_j C_j^T V_j, V_j = rows j p1 ..: x = i2, b = i1
+    gemm(Cf, p1 * p2, 1, p2, Vf, p1, 1, ldv, out, p2 * k, k, 1, p2, k, p1, n)
+    return out.reshape(n, p2, k).sum(axis=0)
+
+
+def unfold_t_times(C, mode, U):
+    """A^T U for the mode unfolding, U column-major rows x k: one strided GEMM
+    per slice writing rows j p_other + i of a column-major result."""
+    n, p1, p2 = C.shape
+    k = U.shape[1]
+    Cf, Uf = C.ravel(), U.ravel(order="F")
+    other = p2 if mode == 1 else p1
+    ldo = n * other
+    out = np.zeros(ldo * k)
+    if mode == 1:   # (C_j^T U)[i2][c]: x = i2, b = i1
+        gemm(Cf, p1 * p2, 1, p2, Uf, 0, 1, p1, out, p2, 1, ldo, p2, k, p1, n)
+    else:           # (C_j U)[i1][c]: x = i1, b = i2
+        gemm(Cf, p1 * p2, p2, 1, Uf, 0, 1, p2, out, p1, 1, ldo, p1, k, p2, n)
+    return out.reshape(k, ldo).T
+
+
+@pytest.mark.parametrize("n,p1,p2,k", [(1, 5, 7, 3), (6, 12, 9, 4), (4, 20, 31, 1), (3, 1, 6, 2)])
+def test_unfolding_products_without_forming_the_unfolding(n, p1, p2, k):
+    # the planned GPU form of the fixed-accuracy Tucker loop's products
+    from oracle import tucker
+    rng = np.random.default_rng(n + p1 + p2 + k)
+    C = rng.standard_normal((n, p1, p2))
+    for mode, rows, cols in ((1, p1, n * p2), (2, p2, n * p1)):
+        A = tucker.unfold(C, mode)
+        V = rng.standard_normal((cols, k))
+        U = rng.standard_normal((rows, k))
+        assert np.abs(unfold_times(C, mode, V) - A @ V).max() < 1e-12
+        assert np.abs(unfold_t_times(C, mode, U) - A.T @ U).max() < 1e-12
