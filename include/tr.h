@@ -267,6 +267,31 @@ tr_status tr_slice_prox_noalloc(tr_dtype dtype, int n, int n1, int n2, const voi
                                 double gamma, double tau, uint64_t seed, int t,
                                 void *cuda_stream, char *err, size_t err_len);
 
+/* The paper's randomized GNHTSVT with the fixed-accuracy Tucker form
+ * (Alg. "AD-RSTHOSVD-BLBP" with processing order (1, 2), then the core's
+ * GNTSVT, Alg. 4 randomized branch) on the transformed stack Abar: per
+ * spatial mode, the block Lanczos loop of Alg. 3 on the mode unfolding of
+ * the current core (block size b, deflation tolerance delta_rel ||A||_F,
+ * stop once the estimate E < eps^2 ||A||_F^2 or the basis reaches
+ * min(rows, cols, max_rank) columns; max_rank 0: no cap) gives the factor,
+ * the core is truncated by it; then every core slice gets Prox_{Phi,tau} of
+ * its singular values (the exact per-slice prox) and Gbar_j = F1 Prox F2^T.
+ * The Gaussian draws are Philox blocks per transformed slice: draw d of mode
+ * m uses stream word 0x10000 m + 2 d with key seed and counter word t.  It
+ * needs no handle: Abar and Gbar are device buffers of n slices of n1 x n2
+ * (face-slice layout, dtype elements, no alias); `ranks` (host, 2 ints, may
+ * be NULL) receives the two ranks found.  Work runs on `cuda_stream` and the
+ * call synchronises it (the loop's decisions run on the host); workspace
+ * comes from stream-ordered allocation; the core's prox uses the fixed
+ * array of tr_slice_prox_noalloc, so a core beyond it gives TR_EUNSUPPORTED.
+ * Errors: TR_EINVAL, TR_EUNSUPPORTED, TR_ENOMEM, TR_ECUDA; `err` (may be
+ * NULL) receives a message of at most err_len bytes.                        */
+tr_status tr_slice_prox_ad_tucker(tr_dtype dtype, int n, int n1, int n2, const void *Abar,
+                                  void *Gbar, double tau, tr_penalty phi, double theta,
+                                  double gamma, double eps, int b, double delta_rel, int max_rank,
+                                  uint64_t seed, int t, int *ranks, void *cuda_stream, char *err,
+                                  size_t err_len);
+
 /* ---- Gradient-domain building blocks (GNHTCTV prior) -------------------
  * The operators of the gradient-domain model (Def. gradient tensor, Def.
  * GNHTCTV, Eq. coef-tensor, Eq. gnrhtc-L); they need no handle.  Tensors

@@ -29,6 +29,7 @@
 #include <mutex>
 #include <vector>
 
+#include "sgemm.cuh"
 #include "tr_internal.cuh"
 
 namespace {
@@ -86,75 +87,6 @@ __global__ void grad_kernel(const T *__restrict__ src, T *__restrict__ dst, int6
     else
       g = (i == 0) ? f + (nk - 1) * S : f - S;
     dst[f] = src[g] - src[f];
-  }
-}
-
-// C[o][x][y] = sum_b A[o][x][b] B[o][b][y] with element strides; 64 x 64
-// output tile per block, 16-deep K chunks through shared memory, 256 threads
-// with a 4 x 4 register tile each (rows ty + 16 i, columns tx + 16 j).
-struct GemmArgs {
-  const void *A, *B;
-  void *C;
-  int64_t ao, ax, ab, bo, bb, by, co, cx, cy;
-  int64_t X, Y, K;
-};
-
-constexpr int kBX = 64, kBY = 64, kBK = 16, kGemmThreads = 256;
-
-template <typename T>
-__global__ void __launch_bounds__(kGemmThreads) strided_gemm_kernel(GemmArgs g) {
-  __shared__ T As[kBK][kBX + 1];
-  __shared__ T Bs[kBK][kBY + 1];
-  const T *A = (const T *)g.A;
-  const T *B = (const T *)g.B;
-  T *C = (T *)g.C;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t o = blockIdx.z;
-  const int64_t x0 = (int64_t)blockIdx.y * kBX, y0 = (int64_t)blockIdx.x * kBY;
-  T acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  for (int64_t k0 = 0; k0 < g.K; k0 += kBK) {
-#pragma unroll
-    for (int q = 0; q < (kBX * kBK) / kGemmThreads; ++q) {
-      const int e = tid + q * kGemmThreads;
-      const int xi = e / kBK, bi = e % kBK;
-      const int64_t x = x0 + xi, b = k0 + bi;
-      As[bi][xi] = (x < g.X && b < g.K) ? A[o * g.ao + x * g.ax + b * g.ab] : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < (kBY * kBK) / kGemmThreads; ++q) {
-      const int e = tid + q * kGemmThreads;
-      const int bi = e / kBY, yi = e % kBY;
-      const int64_t y = y0 + yi, b = k0 + bi;
-      Bs[bi][yi] = (y < g.Y && b < g.K) ? B[o * g.bo + b * g.bb + y * g.by] : T(0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int bi = 0; bi < kBK; ++bi) {
-      T a[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[bi][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[bi][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t x = x0 + ty + 16 * i;
-    if (x >= g.X) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t y = y0 + tx + 16 * j;
-      if (y < g.Y) C[o * g.co + x * g.cx + y * g.cy] = acc[i][j];
-    }
   }
 }
 
@@ -235,17 +167,17 @@ template <typename T>
 cudaError_t hartley_product(const Shape &s, int k, const T *Hdev, const T *src, T *dst,
                             cudaStream_t st) {
   const int64_t m = s.n[k], S = s.S[k];
-  GemmArgs g;
+  sg::GemmArgs g;
   dim3 grid;
   if (k == 1) {   // mode 2, contiguous: out[r][a] = sum_b in[r][b] H[b][a]
-    g = GemmArgs{src, Hdev, dst, 0, m, 1, 0, m, 1, 0, m, 1, s.N / m, m, m};
-    grid = dim3((unsigned)((g.Y + kBY - 1) / kBY), (unsigned)((g.X + kBX - 1) / kBX), 1);
+    g = sg::GemmArgs{src, Hdev, dst, 0, m, 1, 0, m, 1, 0, m, 1, s.N / m, m, m};
+    grid = dim3((unsigned)((g.Y + sg::kBY - 1) / sg::kBY), (unsigned)((g.X + sg::kBX - 1) / sg::kBX), 1);
   } else {        // out[o][a][c] = sum_b H[a][b] in[o][b][c]
-    g = GemmArgs{Hdev, src, dst, 0, m, 1, m * S, S, 1, m * S, S, 1, m, S, m};
-    grid = dim3((unsigned)((g.Y + kBY - 1) / kBY), (unsigned)((g.X + kBX - 1) / kBX),
+    g = sg::GemmArgs{Hdev, src, dst, 0, m, 1, m * S, S, 1, m * S, S, 1, m, S, m};
+    grid = dim3((unsigned)((g.Y + sg::kBY - 1) / sg::kBY), (unsigned)((g.X + sg::kBX - 1) / sg::kBX),
                 (unsigned)(s.N / (m * S)));
   }
-  strided_gemm_kernel<T><<<grid, kGemmThreads, 0, st>>>(g);
+  sg::strided_gemm_kernel<T><<<grid, sg::kGemmThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -255,10 +187,10 @@ bool solve_grid_ok(const Shape &s, uint32_t modes) {
     if (!(modes & (1u << k))) continue;
     const int64_t m = s.n[k], S = s.S[k];
     if (k == 1) {
-      if ((s.N / m + kBX - 1) / kBX > 65535) return false;
+      if ((s.N / m + sg::kBX - 1) / sg::kBX > 65535) return false;
     } else {
-      if ((m + kBX - 1) / kBX > 65535 || s.N / (m * S) > 65535) return false;
-      if ((S + kBY - 1) / kBY > 0x7fffffff) return false;
+      if ((m + sg::kBX - 1) / sg::kBX > 65535 || s.N / (m * S) > 65535) return false;
+      if ((S + sg::kBY - 1) / sg::kBY > 0x7fffffff) return false;
     }
   }
   return true;

@@ -111,6 +111,13 @@ _SIGS = {
                                              ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_int, _P,
                                              ctypes.c_char_p, ctypes.c_size_t]),
+    "tr_slice_prox_ad_tucker": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_uint64, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int), _P, ctypes.c_char_p,
+                                               ctypes.c_size_t]),
     "tr_grad": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_char_p,
                                ctypes.c_size_t]),
@@ -331,6 +338,30 @@ def gradient_solve(rhs, dims, modes, out=None, stream=None):
     if st != TR_OK:
         raise TrError(st, buf.value.decode())
     return out
+
+
+def slice_prox_ad_tucker(Abar, tau, eps, b, delta_rel=1e-12, max_rank=0, phi=TR_PEN_MCP,
+                         theta=1.0, gamma=4000.0, seed=0, t=0, out=None, stream=None):
+    """tr_slice_prox_ad_tucker: the fixed-accuracy shared-Tucker prox of a
+    transformed stack Abar (n, n1, n2); returns (Gbar, (r1, r2))."""
+    import torch
+    dt = _float_dtype(Abar, "Abar")
+    if Abar.dim() != 3:
+        raise TrArgError("Abar: expected an (n, n1, n2) tensor")
+    n, n1, n2 = Abar.shape
+    _need(Abar, "Abar", Abar.dtype, n * n1 * n2)
+    if out is None:
+        out = torch.empty_like(Abar)
+    _need(out, "out", Abar.dtype, n * n1 * n2)
+    ranks = (ctypes.c_int * 2)()
+    buf = ctypes.create_string_buffer(256)
+    st = load().tr_slice_prox_ad_tucker(dt, n, n1, n2, _ptr(Abar), _ptr(out), float(tau), int(phi),
+                                        float(theta), float(gamma), float(eps), int(b),
+                                        float(delta_rel), int(max_rank), int(seed), int(t), ranks,
+                                        _stream(stream), buf, 256)
+    if st != TR_OK:
+        raise TrError(st, buf.value.decode())
+    return out, (ranks[0], ranks[1])
 
 
 def _stream(stream):

@@ -348,3 +348,22 @@ def test_binding_structs_match_the_c_layout(tmp_path):
         assert int(out[cname]) == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert int(out["%s.%s" % (cname, fname)]) == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_ad_tucker_prox_validates_without_gpu(lib):
+    buf = ctypes.create_string_buffer(128)
+    a, b = ctypes.c_void_p(256), ctypes.c_void_p(512)
+
+    def call(dt=tr.TR_F32, n=4, n1=8, n2=6, A=a, G=b, tau=0.1, phi=tr.TR_PEN_L1, eps=1e-3, bs=4,
+             dr=1e-12, mr=0, t=0):
+        return lib.tr_slice_prox_ad_tucker(dt, n, n1, n2, A, G, tau, phi, 1.0, 4.0, eps, bs, dr,
+                                           mr, 0, t, None, None, buf, 128)
+
+    assert call(dt=3) == tr.TR_EINVAL
+    assert call(n=0) == tr.TR_EINVAL
+    assert call(bs=0) == tr.TR_EINVAL and call(bs=33) == tr.TR_EINVAL
+    assert call(eps=0.0) == tr.TR_EINVAL
+    assert call(G=a) == tr.TR_EINVAL
+    assert call(phi=9) == tr.TR_EINVAL
+    assert call(mr=-1) == tr.TR_EINVAL
+    assert call(n=70000) == tr.TR_EUNSUPPORTED

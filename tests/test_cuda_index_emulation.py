@@ -269,3 +269,131 @@ def test_unfolding_products_without_forming_the_unfolding(n, p1, p2, k):
         U = rng.standard_normal((rows, k))
         assert np.abs(unfold_times(C, mode, V) - A @ V).max() < 1e-12
         assert np.abs(unfold_t_times(C, mode, U) - A.T @ U).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# tr_slice_prox_ad_tucker (csrc/ad_tucker.cu): its host loop restated with
+# numpy in place of each launch, on flat column-major buffers with the same
+# column offsets, capacities and draw counters.
+
+def cgs2_defl_qr(W, rows, k, delta):
+    """defl_qr of csrc/ad_tucker.cu: pivot = largest residual norm, stop once
+    it is below delta; second pass against the columns kept; R = Q^T W0."""
+    W0 = W.copy()
+    used = [False] * k
+    Q = []
+    for _ in range(k):
+        norms = [np.dot(W[:, c], W[:, c]) if not used[c] else -1.0 for c in range(k)]
+        j = int(np.argmax(norms))
+        best = norms[j]
+        if used[j] or not np.sqrt(max(best, 0.0)) >= delta:
+            break
+        used[j] = True
+        q = W[:, j].copy()
+        if Q:
+            Qm = np.stack(Q, axis=1)
+            q -= Qm @ (Qm.T @ q)
+        nq = np.linalg.norm(q)
+        if not nq > 0:
+            break
+        q /= nq
+        W -= np.outer(q, q @ W)
+        Q.append(q)
+    Qm = np.stack(Q, axis=1) if Q else np.zeros((rows, 0))
+    return Qm, Qm.T @ W0
+
+
+def gauss_panel(seed, t, n, per, k, stream):
+    from oracle import philox
+    return np.concatenate([philox.gaussian_block(seed, t, j, per, k, stream) for j in range(n)],
+                          axis=0)
+
+
+def blbp_mode_emul(Cst, mode, eps, b, delta_rel, cap, capV, seed, t):
+    from oracle import tucker
+    A = tucker.unfold(Cst, mode)
+    rows, cols = A.shape
+    n = Cst.shape[0]
+    normA2 = float(np.sum(A * A))
+    delta = delta_rel * np.sqrt(normA2)
+    E = normA2
+    if normA2 == 0.0:
+        return np.zeros((rows, 0)), 0.0
+    base = 0x10000 if mode == 1 else 0x20000
+    draw = [0]
+
+    def gauss(k):
+        G = gauss_panel(seed, t, n, cols // n, k, base + 2 * draw[0])
+        draw[0] += 1
+        return G
+
+    b0 = min(b, cols)
+    Vq, _ = cgs2_defl_qr(gauss(b0), cols, b0, 0.0)
+    Vcat = Vq.copy()
+    vstart, kv = 0, Vq.shape[1]
+    Ucat = np.zeros((rows, 0))
+    sprev, lcols, L = 0, 0, np.zeros((0, 0))
+    while True:
+        V = Vcat[:, vstart:vstart + kv]
+        P = A @ V
+        if sprev > 0 and lcols > 0:
+            P[:, :lcols] -= Ucat[:, -sprev:] @ L[:, :lcols]
+        U, R = cgs2_defl_qr(P.copy(), rows, kv, delta)
+        su = U.shape[1]
+        E -= float(np.sum(R * R))
+        sv = 0
+        new_vstart = Vcat.shape[1]
+        Vn = np.zeros((cols, 0))
+        if su > 0:
+            Vn = A.T @ U - V @ R.T
+            Vn = Vn - Vcat @ (Vcat.T @ Vn)
+            assert Vcat.shape[1] + su <= capV
+            Vn, Lt = cgs2_defl_qr(Vn, cols, su, delta)
+            sv = Vn.shape[1]
+            E -= float(np.sum(Lt * Lt))
+            Vcat = np.concatenate([Vcat, Vn], axis=1)
+            L = Lt.T
+        knext = sv
+        if sv < b and Vcat.shape[1] < cols:
+            want = b - sv
+            G = gauss(want)
+            G = G - Vcat @ (Vcat.T @ G)
+            keep = max(0, min(want, cols - Vcat.shape[1]))
+            assert Vcat.shape[1] + want <= capV
+            Vr, _ = cgs2_defl_qr(G, cols, want, 0.0)
+            Vr = Vr[:, :min(Vr.shape[1], keep)]
+            Vcat = np.concatenate([Vcat, Vr], axis=1)
+            knext += Vr.shape[1]
+        Ucat = np.concatenate([Ucat, U], axis=1)
+        sprev, lcols, vstart, kv = su, sv, new_vstart, knext
+        if E < eps * eps * normA2 or Ucat.shape[1] >= cap or kv == 0:
+            break
+    return Ucat[:, :cap], E
+
+
+@pytest.mark.parametrize("n,n1,n2,s1,s2,b", [(6, 30, 22, 5, 3, 2), (4, 12, 19, 10, 13, 1),
+                                             (3, 16, 16, 4, 4, 4), (1, 9, 7, 3, 2, 2)])
+def test_ad_tucker_host_loop_emulation(n, n1, n2, s1, s2, b):
+    # on stacks with shared spaces the restated loop finds the unfoldings'
+    # ranks and the result is the full-SVD prox of every slice, as the oracle's
+    from oracle import tucker
+    rng = np.random.default_rng(n * 100 + n1 + n2)
+    P, _ = np.linalg.qr(rng.standard_normal((n1, s1)))
+    Q, _ = np.linalg.qr(rng.standard_normal((n2, s2)))
+    Ab = np.einsum("ia,jab,kb->jik", P, 3.0 * rng.standard_normal((n, s1, s2)), Q)
+    r1w = min(s1, n * s2)
+    cap1 = min(n1, n * n2)
+    capV = min(n * max(n1, n2), b * (max(n1, n2) + 4))
+    F1, _ = blbp_mode_emul(Ab, 1, 1e-6, b, 1e-10, cap1, capV, 5, 2)
+    assert F1.shape[1] == r1w
+    C1 = tucker.mode_product_t(Ab, F1, 1)
+    F2, _ = blbp_mode_emul(C1, 2, 1e-6, b, 1e-10, min(n2, n * r1w), capV, 5, 2)
+    assert F2.shape[1] == min(s2, n * r1w)
+    C2 = tucker.mode_product_t(C1, F2, 2)
+    Ct, _ = svt.transformed_prox(C2, 0.4, prox.MCP, gamma=30.0)
+    got = tucker.mode_product(tucker.mode_product(Ct, F1, 1), F2, 2)
+    want, _ = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0, engine="ad_tucker", eps=1e-6,
+                                   b=b, delta_rel=1e-10, seed=5, t=2)
+    full, _ = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0)
+    assert np.abs(got - full).max() <= 1e-9 * max(1.0, np.abs(full).max())
+    assert np.abs(want - full).max() <= 1e-9 * max(1.0, np.abs(full).max())

@@ -1,0 +1,74 @@
+"""GPU parity of the fixed-accuracy shared-Tucker prox (tr_slice_prox_ad_tucker,
+Alg. AD-RSTHOSVD-BLBP + Alg. 4 randomized branch) against the FP64 oracle
+(engine "ad_tucker" of oracle.svt.transformed_prox, the same Philox draws).
+
+The GPU's defl-QR is pivoted Gram-Schmidt, the oracle's pivoted Householder:
+both keep the same columns and span the same spaces (pinned on the CPU), but
+the factor bases differ by a rotation, which the mode-2 draws see.  So the
+result is compared where it does not depend on the basis: on stacks whose
+slices share column and row spaces, where both equal the full-SVD prox and
+find the unfoldings' ranks.  Tolerances: FP64 1e-9, FP32 1e-4.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import prox, svt
+from paper_2506_09594_gb300 import tr
+
+torch = pytest.importorskip("torch")
+# these kernels have not run on a GPU yet: the tests run only when asked
+# for (TR_RUN_PENDING=1) until that first run has passed
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("TR_RUN_PENDING") != "1",
+                                 reason="first GPU run of these kernels pending")]
+
+TDT = {"f64": torch.float64, "f32": torch.float32}
+TOL = {"f64": 1e-9, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    tr.load()
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n,n1,n2,s1,s2,b", [(6, 30, 22, 5, 3, 2), (4, 12, 19, 10, 13, 1),
+                                             (20, 40, 36, 6, 5, 4), (3, 16, 16, 4, 4, 4)])
+def test_ad_tucker_prox_on_shared_spaces(dt, n, n1, n2, s1, s2, b):
+    rng = np.random.default_rng(n * 100 + n1 + n2)
+    P, _ = np.linalg.qr(rng.standard_normal((n1, s1)))
+    Q, _ = np.linalg.qr(rng.standard_normal((n2, s2)))
+    Ab = np.einsum("ia,jab,kb->jik", P, 3.0 * rng.standard_normal((n, s1, s2)), Q)
+    if dt == "f32":
+        Ab = Ab.astype(np.float32).astype(np.float64)
+    # the estimate E carries the arithmetic's rounding (about 1e-16 ||A||^2 in
+    # FP64, 1e-7 ||A||^2 in FP32), so eps^2 sits above it; every shared
+    # direction of these stacks carries a few percent of the energy, far
+    # above eps^2, so the loop captures all of them before it stops
+    if dt == "f32" and b == 1:
+        # single-vector Lanczos at eps = 1e-2 stops one direction short of
+        # exact, and U's drift then adds a mode-2 column (the oracle does the
+        # same); FP32 needs eps that large, so this case runs in FP64 only
+        pytest.skip("block size 1 at the FP32 tolerance")
+    eps, dr = (1e-6, 1e-10) if dt == "f64" else (1e-2, 1e-5)
+    full, _ = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0)
+    ref, info = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0, engine="ad_tucker", eps=eps,
+                                     b=b, delta_rel=dr, seed=5, t=2)
+    got, ranks = tr.slice_prox_ad_tucker(torch.from_numpy(Ab).to("cuda", TDT[dt]), 0.4, eps, b,
+                                         delta_rel=dr, phi=tr.TR_PEN_MCP, gamma=30.0, seed=5,
+                                         t=2)
+    got = got.double().cpu().numpy()
+    r1 = min(s1, n * s2)
+    assert ranks == (r1, min(s2, n * r1)) == info["tucker_ranks"]
+    scale = max(1.0, np.abs(full).max())
+    assert np.abs(got - full).max() <= TOL[dt] * scale
+    assert np.abs(ref - full).max() <= 1e-9 * scale
+
+
+def test_ad_tucker_prox_zero_input():
+    A = torch.zeros((3, 8, 6), dtype=torch.float64, device="cuda")
+    got, ranks = tr.slice_prox_ad_tucker(A, 0.1, 1e-3, 2)
+    assert ranks == (0, 0) and float(got.abs().max()) == 0.0
