@@ -638,6 +638,20 @@ def models_section(tr, torch, K):
     ms = timed(ob.step)
     out["onebit"] = {"ms_per_step": ms, "iters_per_s": 1e3 / ms, "samples": int(len(s))}
     ob.close()
+    # the fixed-accuracy shared-Tucker prox (Alg. AD-RSTHOSVD-BLBP + Alg. 4) on
+    # a 200x200x20x20 FP32 transformed stack sharing spaces of dimension 10
+    g = torch.Generator(device="cuda").manual_seed(7)
+    n, n1, n2, sdim = 400, 200, 200, 10
+    P = torch.linalg.qr(torch.randn(n1, sdim, device="cuda", generator=g))[0]
+    Q = torch.linalg.qr(torch.randn(n2, sdim, device="cuda", generator=g))[0]
+    Ab = torch.einsum("ia,jab,kb->jik", P, 3.0 * torch.randn(n, sdim, sdim, device="cuda",
+                                                             generator=g), Q).contiguous()
+    Ab += 1e-3 * torch.randn(Ab.shape, device="cuda", generator=g)
+    res = {}
+    ms = timed(lambda: res.__setitem__("r", tr.slice_prox_ad_tucker(Ab, 1.0, 1e-2, 10,
+                                                                    delta_rel=1e-5,
+                                                                    phi=tr.TR_PEN_L1)[1]))
+    out["ad_tucker"] = {"ms_per_prox": ms, "eps": 1e-2, "block": 10, "ranks": list(res["r"])}
     return out
 
 
