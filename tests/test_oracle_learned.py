@@ -97,6 +97,23 @@ def test_adam_without_moments_is_sign_descent():
         p = p2
 
 
+def test_adam_bias_correction_makes_constant_gradient_steps_exactly_lr():
+    # Kingma & Ba (2015), Sec. 2-3: with the bias corrections, a gradient that
+    # stays constant gives m_hat = g and v_hat = g^2 at every step, so each
+    # update is -lr g / (|g| + eps) whatever beta1 and beta2 are; without
+    # either correction the early steps are off by (1 - beta^t) factors (rtol
+    # 1e-6 covers eps against the smallest |g| and the cancellation in p2 - p)
+    rng = np.random.default_rng(8)
+    p = rng.standard_normal(40)
+    g = rng.standard_normal(40)
+    m = np.zeros(40)
+    v = np.zeros(40)
+    for step in range(1, 6):
+        p2, m, v = lo.adam_step(p, g, m, v, lr=0.02, step=step, beta1=0.9, beta2=0.999, eps=1e-12)
+        np.testing.assert_allclose(p2 - p, -0.02 * np.sign(g), rtol=1e-6)
+        p = p2
+
+
 def test_adam_minimises_a_quadratic():
     c = np.linspace(-1, 1, 20)
     p = np.zeros(20)

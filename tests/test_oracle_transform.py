@@ -65,3 +65,30 @@ def test_transform_preserves_frobenius_norm():
     rng = np.random.default_rng(3)
     S = rng.standard_normal((24, 7, 3))
     assert abs(np.linalg.norm(transform.forward(S, (4, 6))) - np.linalg.norm(S)) < 1e-12
+
+
+def test_dft_forward_matches_numpy_fft_along_modes():
+    # kind="fft": x_3 F_{n3} x_4 F_{n4} is numpy's unnormalised FFT along
+    # modes 3 and 4 (Eq. trans with the DFT); F F^H = n I (Eq. orth, alpha = n)
+    rng = np.random.default_rng(4)
+    dims = (4, 3, 5, 6)
+    X = rng.standard_normal(dims)
+    S = transform.slices_from_tensor(X)
+    Sb = transform.forward(S, dims[2:], kind="fft")
+    ref = np.fft.fftn(X, axes=(2, 3))
+    assert np.max(np.abs(transform.tensor_from_slices(Sb, dims[2:]) - ref)) < 1e-12
+    for n in [1, 3, 8]:
+        F = transform.dft_matrix(n)
+        assert np.max(np.abs(F @ F.conj().T - n * np.eye(n))) < 1e-12
+    assert transform.rho(dims[2:], "fft") == 30.0 and transform.rho(dims[2:]) == 1.0
+
+
+def test_dft_inverse_matches_numpy_ifft_and_undoes_forward():
+    rng = np.random.default_rng(5)
+    dims = (3, 4, 2, 5, 3)
+    S = rng.standard_normal((30, 3, 4)) + 1j * rng.standard_normal((30, 3, 4))
+    X = transform.tensor_from_slices(S, dims[2:])
+    got = transform.tensor_from_slices(transform.inverse(S, dims[2:], kind="fft"), dims[2:])
+    assert np.max(np.abs(got - np.fft.ifftn(X, axes=(2, 3, 4)))) < 1e-13
+    back = transform.inverse(transform.forward(S, dims[2:], kind="fft"), dims[2:], kind="fft")
+    assert np.linalg.norm(back - S) / np.linalg.norm(S) < 1e-14
