@@ -139,7 +139,9 @@ def ad_rsthosvd_blbp(X, eps, b, delta_rel, gauss, caps=(None, None)):
     F = U^{v} is the basis the block Lanczos loop builds (svt.blbp_basis)
     until its error estimate E falls below eps^2 ||A||_F^2, with deflation
     tolerance delta = delta_rel * ||A||_F and at most min(A's sizes) columns
-    (or caps[mode - 1]); then C <- C x_mode F^T.
+    (or caps[mode - 1]), with the sign convention of canonical_signs (the
+    mode-2 draws act on C x_1 F1^T, so under a rank cap F2 depends on F1's
+    signs, which the paper leaves free); then C <- C x_mode F^T.
 
     gauss(mode, rows, cols, draw) returns the draw-th standard Gaussian
     (rows x cols) block of the mode, rows being the number of columns of
@@ -164,6 +166,7 @@ def ad_rsthosvd_blbp(X, eps, b, delta_rel, gauss, caps=(None, None)):
             return G
 
         Fm, Em, _ = svt.blbp_basis(A, eps, b, delta, draw_block, cap)
+        Fm = canonical_signs(Fm)
         C = mode_product_t(C, Fm, mode)
         F.append(Fm)
         E.append(Em)

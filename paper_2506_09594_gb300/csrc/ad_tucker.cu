@@ -12,7 +12,10 @@
 //           refill V' with Gaussian columns (orthogonalised against V^{v})
 //           when deflation kept fewer than b;
 //   until E < eps^2 ||A||_F^2, the basis reaches its cap, or V' is empty;
-// then F = U^{v} and C <- C x_mode F^T.  Finally every slice of the core gets
+// then F = U^{v} with the sign convention of the shared-Tucker form (each
+// column's entry of largest magnitude positive: mode 2's draws act on
+// C x_1 F1^T, so under a rank cap F2 depends on F1's signs) and
+// C <- C x_mode F^T.  Finally every slice of the core gets
 // the per-slice prox, and Gbar_j = F1 Prox(C_j) F2^T.
 //
 // GPU form.  A V and A^T U never form the unfolding: they are per-slice
@@ -21,7 +24,10 @@
 // column of largest residual norm, the rule of the pivoted Householder QR;
 // stop once that norm is below delta; R = Q^T A): column norms and dot
 // products are multi-CTA reductions in double, the pivot choice runs on the
-// host.  Gaussian draws are the per-slice Philox blocks of the sketch kernel
+// host.  orth() of a Gaussian draw (the first V block and the refills) is
+// the same Gram-Schmidt taking the columns in order, which gives the columns
+// of the unpivoted Householder QR up to sign, so a rank cap keeps the same
+// directions as that form.  Gaussian draws are the per-slice Philox blocks of the sketch kernel
 // (stream 0x10000 m + 2 d for draw d of mode m), gathered into a stacked
 // column-major panel.  The core's prox is tr_slice_prox_noalloc at full
 // width (exact).  Panels are column-major.
@@ -194,25 +200,32 @@ dim3 red_grid(int64_t rows, int k) {
 }
 
 // defl-QR of the panel W (rows x k, ld rows; overwritten with residuals),
-// whose original is Worig: the pivoted Gram-Schmidt columns go to Q (ld
-// rows, columns 0..s-1) and R = Q^T Worig (s x k, ld k) to Rout.  Returns s.
+// whose original is Worig: the Gram-Schmidt columns go to Q (ld rows,
+// columns 0..s-1) and R = Q^T Worig (s x k, ld s) to Rout.  pivot: the next
+// column is the one of largest residual norm and the loop stops once that
+// norm is below delta; otherwise the columns are taken in order (orth()),
+// stopping at a zero residual.  Returns s.
 template <typename T>
-int defl_qr(Ctx &x, T *W, const T *Worig, int64_t rows, int k, double delta, T *Q, T *Rout) {
+int defl_qr(Ctx &x, T *W, const T *Worig, int64_t rows, int k, double delta, bool pivot, T *Q,
+            T *Rout) {
   std::vector<char> used(k, 0);
   int s = 0;
   for (int step = 0; step < k && x.e == cudaSuccess; ++step) {
-    x.e = cudaMemsetAsync(x.dscr, 0, k * sizeof(double), x.s);
-    col_dots_kernel<T><<<red_grid(rows, k), 256, 0, x.s>>>(W, rows, W, rows, rows, k, x.dscr);
-    if (x.e == cudaSuccess) x.e = cudaGetLastError();
-    if (!fetch(x, k)) break;
-    int j = -1;
-    double best = -1.0;
-    for (int c = 0; c < k; ++c)
-      if (!used[c] && x.hscr[c] > best) {
-        best = x.hscr[c];
-        j = c;
-      }
-    if (j < 0 || !(sqrt(std::max(best, 0.0)) >= delta)) break;
+    int j = step;
+    if (pivot) {
+      x.e = cudaMemsetAsync(x.dscr, 0, k * sizeof(double), x.s);
+      col_dots_kernel<T><<<red_grid(rows, k), 256, 0, x.s>>>(W, rows, W, rows, rows, k, x.dscr);
+      if (x.e == cudaSuccess) x.e = cudaGetLastError();
+      if (!fetch(x, k)) break;
+      j = -1;
+      double best = -1.0;
+      for (int c = 0; c < k; ++c)
+        if (!used[c] && x.hscr[c] > best) {
+          best = x.hscr[c];
+          j = c;
+        }
+      if (j < 0 || !(sqrt(std::max(best, 0.0)) >= delta)) break;
+    }
     used[j] = 1;
     T *q = Q + (int64_t)s * rows;
     x.e = cudaMemcpyAsync(q, W + (int64_t)j * rows, rows * sizeof(T), cudaMemcpyDeviceToDevice, x.s);
@@ -378,7 +391,7 @@ int blbp_mode(Ctx &x, const Mode &m, const T *C, double eps, int b, double delta
   const int b0 = (int)std::min<int64_t>(b, cols);
   if (!gauss(b0, G)) return -1;
   x.e = cudaMemcpyAsync(Vn0, G, cols * b0 * sizeof(T), cudaMemcpyDeviceToDevice, s);
-  int kv = defl_qr<T>(x, G, Vn0, cols, b0, 0.0, Vcat, R);
+  int kv = defl_qr<T>(x, G, Vn0, cols, b0, 0.0, false, Vcat, R);
   if (x.e != cudaSuccess) return -1;
   int64_t vcols = kv, vstart = 0, ucols = 0, ustart = 0;
   int sprev = 0;       // columns of U_prev
@@ -395,7 +408,7 @@ int blbp_mode(Ctx &x, const Mode &m, const T *C, double eps, int b, double delta
     }
     if (x.e != cudaSuccess) return -1;
     x.e = cudaMemcpyAsync(P0, P, rows * kv * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    const int su = defl_qr<T>(x, P, P0, rows, kv, delta, Ucat + ucols * rows, R);
+    const int su = defl_qr<T>(x, P, P0, rows, kv, delta, true, Ucat + ucols * rows, R);
     if (x.e != cudaSuccess) return -1;
     const int64_t uadd = su;
     E -= sumsq_host<T>(x, R, (int64_t)su * kv);
@@ -430,7 +443,7 @@ int blbp_mode(Ctx &x, const Mode &m, const T *C, double eps, int b, double delta
       if (vcols + su > capV)
         return afail(err, err_len, TR_EUNSUPPORTED, "V basis above %lld columns", (long long)capV),
                -2;
-      sv = defl_qr<T>(x, Vn, Vn0, cols, su, delta, Vcat + vcols * cols, Lt);   // Lt: sv x su
+      sv = defl_qr<T>(x, Vn, Vn0, cols, su, delta, true, Vcat + vcols * cols, Lt);   // Lt: sv x su
       if (x.e != cudaSuccess) return -1;
       E -= sumsq_host<T>(x, Lt, (int64_t)sv * su);
     }
@@ -465,7 +478,7 @@ int blbp_mode(Ctx &x, const Mode &m, const T *C, double eps, int b, double delta
       if (vcols + want > capV)
         return afail(err, err_len, TR_EUNSUPPORTED, "V basis above %lld columns", (long long)capV),
                -2;
-      int sr = defl_qr<T>(x, G, Vn0, cols, want, 0.0, Vcat + vcols * cols, X);
+      int sr = defl_qr<T>(x, G, Vn0, cols, want, 0.0, false, Vcat + vcols * cols, X);
       if (x.e != cudaSuccess) return -1;
       sr = std::min(sr, keep);
       vcols += sr;
@@ -514,7 +527,10 @@ tr_status ad_tucker(tr_dtype dt, int n, int n1, int n2, const T *Abar, T *Gbar, 
   const int64_t rows_max = std::max<int64_t>(n1, n2);
   const int64_t cols_max = (int64_t)n * std::max<int64_t>(n1, n2);
   const int64_t cap_max = std::min<int64_t>(rows_max, max_rank > 0 ? max_rank : rows_max);
-  const int64_t capV = std::min<int64_t>(cols_max, (int64_t)b * (cap_max + 4));
+  // V basis columns: the loop keeps at most about cols of them (a capped run
+  // about b (cap + 4)), and the block being appended may pass that by b
+  // before deflation trims it
+  const int64_t capV = std::min<int64_t>(cols_max, (int64_t)b * (cap_max + 4)) + b;
   std::vector<void *> allocs;
   cudaError_t e = cudaSuccess;
   auto alloc = [&](size_t bytes) -> void * {
@@ -565,6 +581,7 @@ tr_status ad_tucker(tr_dtype dt, int n, int n1, int n2, const T *Abar, T *Gbar, 
     return finish(e == cudaSuccess ? TR_OK : TR_ECUDA);
   }
   e = cudaMemcpyAsync(F1, pn.Ucat, n1 * r1 * esz, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = launch_canon_signs(dt, F1, n1, r1, s);
   if (e == cudaSuccess) e = truncate_core<T>(m1, Abar, (const T *)F1, r1, (T *)C1, s);
   // mode 2 on the core (n x r1 x n2)
   Mode m2{2, n, r1, n2, n2, (int64_t)n * r1};
@@ -586,7 +603,8 @@ tr_status ad_tucker(tr_dtype dt, int n, int n1, int n2, const T *Abar, T *Gbar, 
     return finish(e == cudaSuccess ? TR_OK : TR_ECUDA);
   }
   const T *F2 = (const T *)pn.Ucat;
-  e = truncate_core<T>(m2, (const T *)C1, F2, r2, (T *)C2, s);
+  e = launch_canon_signs(dt, pn.Ucat, n2, r2, s);
+  if (e == cudaSuccess) e = truncate_core<T>(m2, (const T *)C1, F2, r2, (T *)C2, s);
   // the core's prox at full width (exact): slices r1 x r2
   if (e == cudaSuccess) {
     const int l = std::min(r1, r2);

@@ -1476,6 +1476,15 @@ cudaError_t launch_slice_tucker(tr_dtype dt, int n, int n1, int n2, int r1, int 
                            g_blocks, (float *)sig, rank);
 }
 
+cudaError_t launch_canon_signs(tr_dtype dt, void *F, int m, int r, cudaStream_t s) {
+  if (m < 1 || r < 1) return cudaSuccess;
+  if (dt == TR_F64)
+    canon_sign_kernel<double><<<1, 256, 0, s>>>((double *)F, m, r);
+  else
+    canon_sign_kernel<float><<<1, 256, 0, s>>>((float *)F, m, r);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gaussian_blocks(tr_dtype dt, int n, int64_t per_slice, void *out, uint64_t seed,
                                    int t, const int *dt_dev, uint32_t stream, cudaStream_t s) {
   const int64_t groups = (per_slice + 3) / 4;

@@ -184,6 +184,10 @@ cudaError_t launch_slice_tucker(tr_dtype dt, int n, int n1, int n2, int r1, int 
                                 const void *G2, void *ws, const ShrinkScalars &sh, void *F1_out,
                                 void *F2_out, cudaStream_t s, bool g_blocks = false,
                                 void *sig = nullptr, int *rank = nullptr);
+// Columns of F (m x r, column-major) scaled by +-1 so that each column's
+// entry of largest magnitude (the first one on ties) is positive: the sign
+// convention of both Tucker forms' factors.
+cudaError_t launch_canon_signs(tr_dtype dt, void *F, int m, int r, cudaStream_t s);
 // n per-slice Gaussian blocks of per_slice elements (Philox4x32-10 counter
 // (m/4, j, t, stream), Box-Muller; t from dt_dev when non-null).
 cudaError_t launch_gaussian_blocks(tr_dtype dt, int n, int64_t per_slice, void *out, uint64_t seed,

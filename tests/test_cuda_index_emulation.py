@@ -276,18 +276,20 @@ def test_unfolding_products_without_forming_the_unfolding(n, p1, p2, k):
 # numpy in place of each launch, on flat column-major buffers with the same
 # column offsets, capacities and draw counters.
 
-def cgs2_defl_qr(W, rows, k, delta):
+def cgs2_defl_qr(W, rows, k, delta, pivot=True):
     """defl_qr of csrc/ad_tucker.cu: pivot = largest residual norm, stop once
-    it is below delta; second pass against the columns kept; R = Q^T W0."""
+    it is below delta (pivot=False, orth(): columns in order); second pass
+    against the columns kept; R = Q^T W0."""
     W0 = W.copy()
     used = [False] * k
     Q = []
-    for _ in range(k):
-        norms = [np.dot(W[:, c], W[:, c]) if not used[c] else -1.0 for c in range(k)]
-        j = int(np.argmax(norms))
-        best = norms[j]
-        if used[j] or not np.sqrt(max(best, 0.0)) >= delta:
-            break
+    for step in range(k):
+        j = step
+        if pivot:
+            norms = [np.dot(W[:, c], W[:, c]) if not used[c] else -1.0 for c in range(k)]
+            j = int(np.argmax(norms))
+            if used[j] or not np.sqrt(max(norms[j], 0.0)) >= delta:
+                break
         used[j] = True
         q = W[:, j].copy()
         if Q:
@@ -328,7 +330,7 @@ def blbp_mode_emul(Cst, mode, eps, b, delta_rel, cap, capV, seed, t):
         return G
 
     b0 = min(b, cols)
-    Vq, _ = cgs2_defl_qr(gauss(b0), cols, b0, 0.0)
+    Vq, _ = cgs2_defl_qr(gauss(b0), cols, b0, 0.0, pivot=False)
     Vcat = Vq.copy()
     vstart, kv = 0, Vq.shape[1]
     Ucat = np.zeros((rows, 0))
@@ -360,7 +362,7 @@ def blbp_mode_emul(Cst, mode, eps, b, delta_rel, cap, capV, seed, t):
             G = G - Vcat @ (Vcat.T @ G)
             keep = max(0, min(want, cols - Vcat.shape[1]))
             assert Vcat.shape[1] + want <= capV
-            Vr, _ = cgs2_defl_qr(G, cols, want, 0.0)
+            Vr, _ = cgs2_defl_qr(G, cols, want, 0.0, pivot=False)
             Vr = Vr[:, :min(Vr.shape[1], keep)]
             Vcat = np.concatenate([Vcat, Vr], axis=1)
             knext += Vr.shape[1]
@@ -383,11 +385,13 @@ def test_ad_tucker_host_loop_emulation(n, n1, n2, s1, s2, b):
     Ab = np.einsum("ia,jab,kb->jik", P, 3.0 * rng.standard_normal((n, s1, s2)), Q)
     r1w = min(s1, n * s2)
     cap1 = min(n1, n * n2)
-    capV = min(n * max(n1, n2), b * (max(n1, n2) + 4))
+    capV = min(n * max(n1, n2), b * (max(n1, n2) + 4)) + b
     F1, _ = blbp_mode_emul(Ab, 1, 1e-6, b, 1e-10, cap1, capV, 5, 2)
     assert F1.shape[1] == r1w
+    F1 = tucker.canonical_signs(F1)
     C1 = tucker.mode_product_t(Ab, F1, 1)
     F2, _ = blbp_mode_emul(C1, 2, 1e-6, b, 1e-10, min(n2, n * r1w), capV, 5, 2)
+    F2 = tucker.canonical_signs(F2)
     assert F2.shape[1] == min(s2, n * r1w)
     C2 = tucker.mode_product_t(C1, F2, 2)
     Ct, _ = svt.transformed_prox(C2, 0.4, prox.MCP, gamma=30.0)
@@ -397,3 +401,239 @@ def test_ad_tucker_host_loop_emulation(n, n1, n2, s1, s2, b):
     full, _ = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0)
     assert np.abs(got - full).max() <= 1e-9 * max(1.0, np.abs(full).max())
     assert np.abs(want - full).max() <= 1e-9 * max(1.0, np.abs(full).max())
+
+
+# ---------------------------------------------------------------------------
+# tr_slice_prox_ad_tucker on the flat buffers of csrc/ad_tucker.cu: every
+# strided GEMM with the element strides the host code passes (not a plain
+# matrix product), every panel at the element count the host code allocates,
+# every panel pointer at the host code's offset.  Numpy raises on an index
+# past a panel's end, so a run also shows the capacities hold.
+
+def sgemm(A, B, C, X, Y, K, batch=1, ao=0, ax=0, ab=0, bo=0, bb=0, by=0, co=0, cx=0, cy=0):
+    if X < 1 or Y < 1 or batch < 1:       # sg::gemm launches nothing
+        return
+    gemm(A, ao, ax, ab, B, bo, bb, by, C, co, cx, cy, X, Y, K, batch)
+
+
+def col(rows, c, ld):
+    return np.arange(rows) + c * ld
+
+
+def canon_signs_flat(F, m, r):
+    # canon_sign_kernel: each column's first entry of largest magnitude positive
+    for c in range(r):
+        v = F[col(m, c, m)]
+        if v[int(np.argmax(np.abs(v)))] < 0:
+            F[col(m, c, m)] = -v
+
+
+def defl_qr_flat(W, Worig, rows, k, delta, pivot, Q, Rout):
+    used = [False] * k
+    s = 0
+    for step in range(k):
+        j = step
+        if pivot:
+            norms = [float(np.sum(W[col(rows, c, rows)] ** 2)) for c in range(k)]   # col_dots_kernel
+            j, best = -1, -1.0
+            for c in range(k):
+                if not used[c] and norms[c] > best:
+                    j, best = c, norms[c]
+            if j < 0 or not np.sqrt(max(best, 0.0)) >= delta:
+                break
+        used[j] = True
+        qi = col(rows, s, rows)
+        Q[qi] = W[col(rows, j, rows)]
+        if s > 0:                        # col_dot_vec_kernel, gemv_sub_kernel
+            coef = np.array([np.dot(Q[col(rows, i, rows)], Q[qi]) for i in range(s)])
+            Q[qi] = Q[qi] - sum(Q[col(rows, i, rows)] * coef[i] for i in range(s))
+        nq = np.sqrt(np.sum(Q[qi] ** 2))
+        if not nq > 0:
+            break
+        Q[qi] = Q[qi] * (1.0 / nq)       # scale_kernel
+        coef = [np.dot(W[col(rows, c, rows)], Q[qi]) for c in range(k)]
+        for c in range(k):               # rank1_kernel
+            W[col(rows, c, rows)] -= Q[qi] * coef[c]
+        s += 1
+    if s > 0:                            # R = Q^T Worig, s x k, ld s
+        sgemm(Q, Worig, Rout, s, k, rows, ax=rows, ab=1, bb=1, by=rows, cx=1, cy=s)
+    return s
+
+
+def blbp_mode_flat(C, mode, n, p1, p2, eps, b, delta_rel, cap, capV, seed, t, pn):
+    from oracle import philox
+    rows, cols = (p1, n * p2) if mode == 1 else (p2, n * p1)
+    Ucat, Vcat, P, P0, Vn, Vn0 = pn["Ucat"], pn["Vcat"], pn["P"], pn["P0"], pn["Vn"], pn["Vn0"]
+    tmp, X, R, Lt, L, G, Gs = pn["tmp"], pn["X"], pn["R"], pn["Lt"], pn["L"], pn["G"], pn["Gs"]
+    normA2 = float(np.sum(C[np.arange(n * p1 * p2)] ** 2))
+    delta = delta_rel * np.sqrt(normA2)
+    E = normA2
+    if normA2 == 0.0:
+        return 0, 0.0
+    base = 0x10000 if mode == 1 else 0x20000
+    per = cols // n
+    draw = [0]
+
+    def gauss(k, dst):                   # launch_gaussian_blocks + gather_slices_kernel
+        blocks = [philox.gaussian_block(seed, t, j, per, k, base + 2 * draw[0]).ravel(order="F")
+                  for j in range(n)]
+        draw[0] += 1
+        Gs[np.arange(n * per * k)] = np.concatenate(blocks)
+        e = np.arange(n * per * k)
+        i, c, j = e % per, (e // per) % k, e // (per * k)
+        dst[(j * per + i) + c * cols] = Gs[e]
+
+    def unfold_times(V, ldv, k):         # P = A V: per-slice GEMMs into tmp, then batch_sum_kernel
+        if mode == 1:
+            sgemm(C, V, tmp, p1, k, p2, n, ao=p1 * p2, ax=p2, ab=1, bo=p2, bb=1, by=ldv,
+                  co=p1 * k, cx=1, cy=p1)
+        else:
+            sgemm(C, V, tmp, p2, k, p1, n, ao=p1 * p2, ax=1, ab=p2, bo=p1, bb=1, by=ldv,
+                  co=p2 * k, cx=1, cy=p2)
+        M = rows * k
+        P[np.arange(M)] = sum(tmp[o * M + np.arange(M)] for o in range(n))
+
+    def unfold_t_times(U, k):            # Vn = A^T U
+        if mode == 1:
+            sgemm(C, U, Vn, p2, k, p1, n, ao=p1 * p2, ax=1, ab=p2, bb=1, by=rows, co=p2, cx=1,
+                  cy=cols)
+        else:
+            sgemm(C, U, Vn, p1, k, p2, n, ao=p1 * p2, ax=p2, ab=1, bb=1, by=rows, co=p1, cx=1,
+                  cy=cols)
+
+    def matmul(A, la, B, lb, Cm, lc, M, N_, K, transA):
+        if transA:
+            sgemm(A, B, Cm, M, N_, K, ax=la, ab=1, bb=1, by=lb, cx=1, cy=lc)
+        else:
+            sgemm(A, B, Cm, M, N_, K, ax=1, ab=la, bb=1, by=lb, cx=1, cy=lc)
+
+    def sub(Xd, Ys, r, k, ldx, ldy):     # sub_kernel
+        for c in range(k):
+            Xd[col(r, c, ldx)] -= Ys[col(r, c, ldy)]
+
+    def copy(dst, src, count):           # cudaMemcpyAsync device to device
+        dst[np.arange(count)] = src[np.arange(count)]
+
+    b0 = min(b, cols)
+    gauss(b0, G)
+    copy(Vn0, G, cols * b0)
+    kv = defl_qr_flat(G, Vn0, cols, b0, 0.0, False, Vcat, R)
+    vcols, vstart, ucols, ustart, sprev, lcols = kv, 0, 0, 0, 0, 0
+    while True:
+        unfold_times(Vcat[vstart * cols:], cols, kv)
+        if sprev > 0 and lcols > 0:
+            matmul(Ucat[ustart * rows:], rows, L, sprev, X, rows, rows, lcols, sprev, False)
+            sub(P, X, rows, lcols, rows, rows)
+        copy(P0, P, rows * kv)
+        su = defl_qr_flat(P, P0, rows, kv, delta, True, Ucat[ucols * rows:], R)
+        E -= float(np.sum(R[np.arange(su * kv)] ** 2))
+        sv = 0
+        if su > 0:
+            unfold_t_times(Ucat[ucols * rows:], su)
+            sgemm(Vcat[vstart * cols:], R, X, cols, su, kv, ax=1, ab=cols, bb=su, by=1, cx=1,
+                  cy=cols)                                     # X = V R^T
+            sub(Vn, X, cols, su, cols, cols)
+            matmul(Vcat, cols, Vn, cols, Lt, vcols, vcols, su, cols, True)
+            matmul(Vcat, cols, Lt, vcols, X, cols, cols, su, vcols, False)
+            sub(Vn, X, cols, su, cols, cols)
+            copy(Vn0, Vn, cols * su)
+            assert vcols + su <= capV
+            sv = defl_qr_flat(Vn, Vn0, cols, su, delta, True, Vcat[vcols * cols:], Lt)
+            E -= float(np.sum(Lt[np.arange(sv * su)] ** 2))
+        new_vstart = vcols
+        vcols += sv
+        if sv > 0:                       # L = Lt^T (su x sv, ld su), through the host
+            h = Lt[np.arange(sv * su)].copy()
+            i, c = np.meshgrid(np.arange(sv), np.arange(su), indexing="ij")
+            L[(c + i * su).ravel()] = h[(i + c * sv).ravel()]
+        knext = sv
+        if sv < b and vcols < cols:
+            want = b - sv
+            gauss(want, G)
+            matmul(Vcat, cols, G, cols, X, vcols, vcols, want, cols, True)
+            matmul(Vcat, cols, X, vcols, Vn, cols, cols, want, vcols, False)
+            sub(G, Vn, cols, want, cols, cols)
+            copy(Vn0, G, cols * want)
+            keep = max(0, min(want, cols - vcols))
+            assert vcols + want <= capV
+            sr = min(defl_qr_flat(G, Vn0, cols, want, 0.0, False, Vcat[vcols * cols:], X), keep)
+            vcols += sr
+            knext += sr
+        ucols += su
+        ustart, sprev, lcols, vstart, kv = ucols - su, su, sv, new_vstart, knext
+        if E < eps * eps * normA2 or ucols >= cap or kv == 0:
+            break
+    return min(ucols, cap), E
+
+
+def ad_tucker_flat(Ab, tau, kind, gamma, eps, b, delta_rel, max_rank, seed, t):
+    n, n1, n2 = Ab.shape
+    N = n * n1 * n2
+    rows_max, cols_max = max(n1, n2), n * max(n1, n2)
+    cap_max = min(rows_max, max_rank if max_rank > 0 else rows_max)
+    capV = min(cols_max, b * (cap_max + 4)) + b
+    sizes = dict(Ucat=rows_max * (cap_max + b), Vcat=cols_max * capV, P=rows_max * b,
+                 P0=rows_max * b, Vn=cols_max * b, Vn0=cols_max * b, tmp=n * rows_max * b,
+                 X=max(cols_max, rows_max) * max(b, capV), R=b * b, Lt=max(b * b, capV * b),
+                 L=b * b, G=cols_max * b, Gs=cols_max * b)
+    pn = {k: np.full(max(v, 2), np.nan) for k, v in sizes.items()}   # unwritten reads show as NaN
+    F1, C1, C2, Ct, Tb = (np.full(v, np.nan) for v in (n1 * cap_max, N, N, N, N))
+    A = Ab.ravel().copy()
+    Gbar = np.full(N, np.nan)
+    cap1 = min(n1, n * n2, max_rank if max_rank > 0 else n1)
+    r1, _ = blbp_mode_flat(A, 1, n, n1, n2, eps, b, delta_rel, cap1, capV, seed, t, pn)
+    if r1 == 0:
+        return np.zeros(Ab.shape), (0, 0)
+    F1[np.arange(n1 * r1)] = pn["Ucat"][np.arange(n1 * r1)]
+    canon_signs_flat(F1, n1, r1)
+    # truncate_core, mode 1: C1_j = F1^T A_j (r1 x n2)
+    sgemm(F1, A, C1, r1, n2, n1, n, ax=n1, ab=1, bo=n1 * n2, bb=n2, by=1, co=r1 * n2, cx=n2, cy=1)
+    cap2 = min(n2, n * r1, max_rank if max_rank > 0 else n2)
+    r2, _ = blbp_mode_flat(C1, 2, n, r1, n2, eps, b, delta_rel, cap2, capV, seed, t, pn)
+    if r2 == 0:
+        return np.zeros(Ab.shape), (r1, 0)
+    F2 = pn["Ucat"]
+    canon_signs_flat(F2, n2, r2)
+    # truncate_core, mode 2: C2_j = C1_j F2 (r1 x r2)
+    sgemm(C1, F2, C2, r1, r2, n2, n, ao=r1 * n2, ax=n2, ab=1, bb=1, by=n2, co=r1 * r2, cx=r2, cy=1)
+    # the core's prox at full width is exact: the full-SVD prox of each slice
+    core = C2[np.arange(n * r1 * r2)].reshape(n, r1, r2)
+    Ct[np.arange(n * r1 * r2)] = svt.transformed_prox(core, tau, kind, gamma=gamma)[0].ravel()
+    # T_j = Ct_j F2^T (r1 x n2), then Gbar_j = F1 T_j
+    sgemm(Ct, F2, Tb, r1, n2, r2, n, ao=r1 * r2, ax=r2, ab=1, bb=n2, by=1, co=r1 * n2, cx=n2, cy=1)
+    sgemm(F1, Tb, Gbar, n1, n2, r1, n, ax=1, ab=n1, bo=r1 * n2, bb=n2, by=1, co=n1 * n2, cx=n2,
+          cy=1)
+    return Gbar.reshape(Ab.shape), (r1, r2)
+
+
+@pytest.mark.parametrize("n,n1,n2,s1,s2,b,max_rank",
+                         [(6, 30, 22, 5, 3, 2, 0), (4, 12, 19, 10, 13, 1, 0),
+                          (3, 16, 16, 4, 4, 4, 0), (1, 9, 7, 3, 2, 2, 0),
+                          (5, 14, 11, 6, 5, 3, 4), (1, 3, 2, 3, 2, 4, 0),
+                          (2, 8, 20, 3, 6, 32, 0)])
+def test_ad_tucker_flat_buffers_and_strides(n, n1, n2, s1, s2, b, max_rank):
+    # the launch sequence with the host code's strides, offsets and panel
+    # sizes gives the oracle's fixed-accuracy Tucker prox and its ranks
+    rng = np.random.default_rng(7 * n + n1 + 3 * n2 + b)
+    P, _ = np.linalg.qr(rng.standard_normal((n1, s1)))
+    Q, _ = np.linalg.qr(rng.standard_normal((n2, s2)))
+    Ab = np.einsum("ia,jab,kb->jik", P, 3.0 * rng.standard_normal((n, s1, s2)), Q)
+    got, ranks = ad_tucker_flat(Ab, 0.4, prox.MCP, 30.0, 1e-6, b, 1e-10, max_rank, 5, 2)
+    want, info = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0, engine="ad_tucker", eps=1e-6,
+                                      b=b, delta_rel=1e-10, seed=5, t=2,
+                                      max_rank=max_rank if max_rank > 0 else None)
+    assert ranks == tuple(info["tucker_ranks"])
+    assert np.isfinite(got).all()
+    # the two loops round differently (the oracle's Householder QR, Gram-Schmidt
+    # here) and keep U orthogonal only between adjacent blocks, so the gap
+    # grows with the number of blocks: ten one-column blocks reach ~1e-10
+    scale = max(1.0, np.abs(want).max())
+    assert np.abs(got - want).max() <= 1e-9 * scale
+    if max_rank == 0:   # uncapped on exact low-rank stacks: the full-SVD prox
+        full, _ = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0)
+        assert np.abs(got - full).max() <= 1e-9 * scale
+
+
+def test_ad_tucker_flat_zero_stack():
+    got, ranks = ad_tucker_flat(np.zeros((3, 5, 4)), 0.4, prox.L1, 4.0, 1e-6, 2, 1e-10, 0, 1, 0)
+    assert ranks == (0, 0) and not got.any()

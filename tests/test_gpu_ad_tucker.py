@@ -68,6 +68,44 @@ def test_ad_tucker_prox_on_shared_spaces(dt, n, n1, n2, s1, s2, b):
     assert np.abs(ref - full).max() <= 1e-9 * scale
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_ad_tucker_prox_under_a_rank_cap(dt):
+    # a cap below the shared dimensions truncates each basis inside a block,
+    # so the result depends on which directions the loop found first and on
+    # the factors' signs (mode 2's draws act on the mode-1 core): the oracle
+    # with the same cap, not the full-SVD prox, is the reference
+    n, n1, n2, s1, s2, b, cap = 5, 14, 11, 6, 5, 3, 4
+    rng = np.random.default_rng(n + n1 + n2)
+    P, _ = np.linalg.qr(rng.standard_normal((n1, s1)))
+    Q, _ = np.linalg.qr(rng.standard_normal((n2, s2)))
+    Ab = np.einsum("ia,jab,kb->jik", P, 3.0 * rng.standard_normal((n, s1, s2)), Q)
+    if dt == "f32":
+        Ab = Ab.astype(np.float32).astype(np.float64)
+    eps, dr = (1e-6, 1e-10) if dt == "f64" else (1e-2, 1e-5)
+    ref, info = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0, engine="ad_tucker", eps=eps,
+                                     b=b, delta_rel=dr, seed=5, t=2, max_rank=cap)
+    got, ranks = tr.slice_prox_ad_tucker(torch.from_numpy(Ab).to("cuda", TDT[dt]), 0.4, eps, b,
+                                         delta_rel=dr, max_rank=cap, phi=tr.TR_PEN_MCP,
+                                         gamma=30.0, seed=5, t=2)
+    assert ranks == (cap, cap) == info["tucker_ranks"]
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got.double().cpu().numpy() - ref).max() <= TOL[dt] * scale
+
+
+def test_ad_tucker_prox_smallest_stack():
+    # a 3 x 2 slice: the first block spans all of V's columns, so the next
+    # block is appended past them before deflation trims it
+    rng = np.random.default_rng(11)
+    Ab = rng.standard_normal((1, 3, 2))
+    ref, info = svt.transformed_prox(Ab, 0.4, prox.MCP, gamma=30.0, engine="ad_tucker", eps=1e-6,
+                                     b=4, delta_rel=1e-10, seed=5, t=2)
+    got, ranks = tr.slice_prox_ad_tucker(torch.from_numpy(Ab).to("cuda"), 0.4, 1e-6, 4,
+                                         delta_rel=1e-10, phi=tr.TR_PEN_MCP, gamma=30.0, seed=5,
+                                         t=2)
+    assert ranks == info["tucker_ranks"]
+    assert np.abs(got.cpu().numpy() - ref).max() <= 1e-9 * max(1.0, np.abs(ref).max())
+
+
 def test_ad_tucker_prox_zero_input():
     A = torch.zeros((3, 8, 6), dtype=torch.float64, device="cuda")
     got, ranks = tr.slice_prox_ad_tucker(A, 0.1, 1e-3, 2)

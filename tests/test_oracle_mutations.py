@@ -80,6 +80,7 @@ MUTANTS = [
     ("tucker-krylov-block", "tucker", "blocks.append(A @ (A.T @ blocks[-1]))",
      "blocks.append(A @ (A.T @ blocks[0]))"),
     ("svt-eps-not-squared", "svt", "if E < eps * eps * normA2", "if E < eps * normA2"),
+    ("tucker-ad-factor-signs-free", "tucker", "        Fm = canonical_signs(Fm)\n", "\n"),
     # the gradient-domain step (Eq. coef-tensor, Eq. gnrhtc-L, Alg. 5)
     ("ctv-missing-conjugate", "ctv", "num = num + np.conj(FD) * np.fft.fftn",
      "num = num + FD * np.fft.fftn"),

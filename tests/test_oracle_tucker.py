@@ -375,3 +375,22 @@ def test_lanczos_loop_with_gram_schmidt_defl_qr_finds_the_same_ranks():
     assert F1.shape[1] == 5 and F2.shape[1] == 3
     back = tucker.mode_product(tucker.mode_product(C, F1, 1), F2, 2)
     assert np.linalg.norm(back - X) <= 1e-10 * np.linalg.norm(X)
+
+
+def test_fixed_accuracy_factors_carry_the_sign_convention():
+    # both factors of Alg. AD-RSTHOSVD-BLBP come out with each column's entry
+    # of largest magnitude positive; under a rank cap mode 2's draws act on
+    # the mode-1 core, so the capped result would otherwise depend on the
+    # sign choices of the QR routine
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((4, 12, 9))
+
+    def gauss(mode, rows, cols, draw):
+        return np.random.default_rng(100 * mode + draw).standard_normal((rows, cols))
+
+    for caps in ((None, None), (3, 2)):
+        _, F1, F2, _ = tucker.ad_rsthosvd_blbp(X, 1e-3, 2, 1e-10, gauss, caps)
+        for F in (F1, F2):
+            assert F.shape[1] > 0
+            top = F[np.argmax(np.abs(F), axis=0), np.arange(F.shape[1])]
+            assert (top > 0).all()
