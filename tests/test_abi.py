@@ -27,6 +27,22 @@ def test_every_declared_function_is_exported(lib):
         assert name in tr._SIGS, "binding lacks " + name
 
 
+def test_library_leaves_no_internal_symbol_undefined(lib):
+    # a shared library links with undefined symbols and binds functions
+    # lazily, so a helper declared in one translation unit and defined in none
+    # would load here and fail only at its first call; every undefined symbol
+    # must come from the C or C++ runtime (versioned) or be weak
+    import shutil
+    import subprocess
+    if shutil.which("nm") is None:
+        pytest.skip("nm not installed")
+    out = subprocess.run(["nm", "-u", "-D", tr.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    bad = [ln.split()[-1] for ln in out.splitlines()
+           if ln.split() and ln.split()[0] != "w" and "@" not in ln.split()[-1]]
+    assert not bad, bad
+
+
 def test_binding_struct_sizes_match_header_layout():
     # tr_params: 5 ints/enums, 12 doubles, 1 uint64, 1 pointer, with C padding
     assert ctypes.sizeof(tr.tr_problem) == 4 + 4 + 8 * 8 + 4 + 4 + 8 + 8
