@@ -51,9 +51,9 @@ def parse():
                     help="skip the precision forms on the 1024x1024x64 workload")
     ap.add_argument("--no-tucker", action="store_true",
                     help="skip the shared-Tucker prox (Alg. 1 + Alg. 4) timing")
-    ap.add_argument("--models", action="store_true",
-                    help="also time the gradient-domain and one-bit ADMM steps (off by "
-                         "default until their kernels have run on a GPU)")
+    ap.add_argument("--no-models", action="store_true",
+                    help="skip the gradient-domain and one-bit ADMM steps and the "
+                         "fixed-accuracy Tucker prox")
     ap.add_argument("--learned-iters", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=8)
     return ap.parse_args()
@@ -461,7 +461,7 @@ def run_ours(args):
         if not args.no_tucker and world == 1:
             line["tucker"] = tucker_section(tr, torch)
             torch.cuda.empty_cache()
-        if args.models and world == 1:
+        if not args.no_models and world == 1:
             line["models"] = models_section(tr, torch, 20)
             torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu_baseline:

@@ -10,8 +10,6 @@ slices share column and row spaces, where both equal the full-SVD prox and
 find the unfoldings' ranks.  Tolerances: FP64 1e-9, FP32 1e-4.
 """
 
-import os
-
 import numpy as np
 import pytest
 
@@ -19,11 +17,7 @@ from oracle import prox, svt
 from paper_2506_09594_gb300 import tr
 
 torch = pytest.importorskip("torch")
-# these kernels have not run on a GPU yet: the tests run only when asked
-# for (TR_RUN_PENDING=1) until that first run has passed
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("TR_RUN_PENDING") != "1",
-                                 reason="first GPU run of these kernels pending")]
+pytestmark = pytest.mark.gpu
 
 TDT = {"f64": torch.float64, "f32": torch.float32}
 TOL = {"f64": 1e-9, "f32": 1e-4}
@@ -65,7 +59,12 @@ def test_ad_tucker_prox_on_shared_spaces(dt, n, n1, n2, s1, s2, b):
     assert ranks == (r1, min(s2, n * r1)) == info["tucker_ranks"]
     scale = max(1.0, np.abs(full).max())
     assert np.abs(got - full).max() <= TOL[dt] * scale
-    assert np.abs(ref - full).max() <= 1e-9 * scale
+    # the oracle on the same parameters: exact up to its deflation tolerance.
+    # Directions whose residual falls below delta_rel ||A||_F are dropped
+    # (Alg. 2), so at the FP32 form's delta_rel = 1e-5 the oracle sits a few
+    # 1e-7 of the scale from the full-SVD prox (measured 1.1e-7 .. 2.4e-7),
+    # and at 1e-10 (FP64 form) within 1e-9
+    assert np.abs(ref - full).max() <= (1e-9 if dt == "f64" else 1e-5) * scale
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])

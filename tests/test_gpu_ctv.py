@@ -7,8 +7,6 @@ residuals alike; the run 1e-6 from the oracle's iterate and 1e-5 from the
 truth (the oracle reaches 1.2e-7).
 """
 
-import os
-
 import numpy as np
 import pytest
 
@@ -16,11 +14,7 @@ from oracle import admm, ctv, prox
 from paper_2506_09594_gb300 import tr
 
 torch = pytest.importorskip("torch")
-# these kernels have not run on a GPU yet: the tests run only when asked
-# for (TR_RUN_PENDING=1) until that first run has passed
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("TR_RUN_PENDING") != "1",
-                                 reason="first GPU run of these kernels pending")]
+pytestmark = pytest.mark.gpu
 
 TDT = {"f64": torch.float64, "f32": torch.float32}
 TOL = {"f64": 1e-9, "f32": 1e-4}

@@ -7,8 +7,6 @@ Tolerances: differences to 1e-14 (FP64) and 1e-6 (FP32) of the largest entry; th
 (FP64) and 1e-5 (FP32) relative to the largest entry.
 """
 
-import os
-
 import numpy as np
 import pytest
 
@@ -16,11 +14,7 @@ from oracle import ctv
 from paper_2506_09594_gb300 import tr
 
 torch = pytest.importorskip("torch")
-# these kernels have not run on a GPU yet: the tests run only when asked
-# for (TR_RUN_PENDING=1) until that first run has passed
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("TR_RUN_PENDING") != "1",
-                                 reason="first GPU run of these kernels pending")]
+pytestmark = pytest.mark.gpu
 
 TDT = {"f64": torch.float64, "f32": torch.float32}
 SHAPES = [(37, 29, 5, 3), (70, 66, 4), (130, 9), (16, 80, 1, 6)]

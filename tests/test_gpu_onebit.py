@@ -6,8 +6,6 @@ whose recovery error must match the oracle's.  Tolerances: one step 1e-9
 0.01 of each other.
 """
 
-import os
-
 import numpy as np
 import pytest
 
@@ -15,11 +13,7 @@ from oracle import onebit, prox
 from paper_2506_09594_gb300 import synth, tr
 
 torch = pytest.importorskip("torch")
-# these kernels have not run on a GPU yet: the tests run only when asked
-# for (TR_RUN_PENDING=1) until that first run has passed
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("TR_RUN_PENDING") != "1",
-                                 reason="first GPU run of these kernels pending")]
+pytestmark = pytest.mark.gpu
 
 TDT = {"f64": torch.float64, "f32": torch.float32}
 TOL = {"f64": 1e-9, "f32": 1e-4}
