@@ -245,6 +245,22 @@ tr_status tr_profile_enable(tr_handle *h, int max_steps);
 tr_status tr_profile_read(tr_handle *h, double ms[3], int *steps);
 tr_status tr_kernel_launches(const tr_handle *h, uint64_t *count);
 
+/* Per-kernel device times of the fixed-width slice pass (the randomized
+ * prox of Alg. 4 on every slice: sketch, 2 + 2q skinny products, 1 + 2q
+ * panel QRs, the small SVD with the shrinkage of Def. gNtsvt, the rank-l
+ * rebuild).  Instrumentation, not in the paper.  Runs `reps` eager passes of
+ * the handle's engine settings (TR_LR_RSVD only, else TR_EUNSUPPORTED) on
+ * the caller's device buffers Abar -> Gbar (n slices of n1 x n2, face-slice
+ * layout, no alias) with threshold tau and Philox counter word t, all
+ * kernels in order on the handle's stream (slice groups ignored), with a
+ * CUDA event after every kernel; synchronises.  ms[k] (host, max_kernels
+ * entries) receives the mean milliseconds of kernel k, names[k] (may be
+ * NULL) a static label, *count the number of kernels.  Errors: TR_EINVAL,
+ * TR_EUNSUPPORTED, TR_ECUDA.                                                */
+tr_status tr_profile_slice_pass(tr_handle *h, const void *Abar, void *Gbar, double tau, int t,
+                                int reps, double *ms, const char **names, int max_kernels,
+                                int *count);
+
 /* The slice pass of tr_slice_prox without any device allocation.  The paper
  * has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- a host thread on a latency-critical loop (allocation
@@ -259,8 +275,9 @@ tr_status tr_kernel_launches(const tr_handle *h, uint64_t *count);
  * Scratch comes from one fixed 16 MiB array compiled into the library and
  * kept on every GPU that loads it until exit; calls needing more return
  * TR_EUNSUPPORTED with the size in `err`.  The first call on a device looks
- * up that array's address (make it before any stream capture).  All calls
- * share the array: calls that overlap on the GPU race.  `err` (may be NULL)
+ * up that array's address (make it before any stream capture); later calls
+ * look it up again, so the address stays valid across a device reset.  All
+ * calls share the array: calls that overlap on the GPU race.  `err` (may be NULL)
  * receives a message of at most err_len bytes on failure.                  */
 tr_status tr_slice_prox_noalloc(tr_dtype dtype, int n, int n1, int n2, const void *Abar,
                                 void *Gbar, int l, int q, tr_penalty phi, double theta,
@@ -282,8 +299,9 @@ tr_status tr_slice_prox_noalloc(tr_dtype dtype, int n, int n1, int n2, const voi
  * (face-slice layout, dtype elements, no alias); `ranks` (host, 2 ints, may
  * be NULL) receives the two ranks found.  Work runs on `cuda_stream` and the
  * call synchronises it (the loop's decisions run on the host); workspace
- * comes from stream-ordered allocation; the core's prox uses the fixed
- * array of tr_slice_prox_noalloc, so a core beyond it gives TR_EUNSUPPORTED.
+ * comes from stream-ordered allocation (the core's prox included); a core
+ * whose r1 x r2 slices exceed the slice kernels' shared memory, or with
+ * min(r1, r2) > 96, gives TR_EUNSUPPORTED.
  * Errors: TR_EINVAL, TR_EUNSUPPORTED, TR_ENOMEM, TR_ECUDA; `err` (may be
  * NULL) receives a message of at most err_len bytes.                        */
 tr_status tr_slice_prox_ad_tucker(tr_dtype dtype, int n, int n1, int n2, const void *Abar,

@@ -605,12 +605,30 @@ tr_status ad_tucker(tr_dtype dt, int n, int n1, int n2, const T *Abar, T *Gbar, 
   const T *F2 = (const T *)pn.Ucat;
   e = launch_canon_signs(dt, pn.Ucat, n2, r2, s);
   if (e == cudaSuccess) e = truncate_core<T>(m2, (const T *)C1, F2, r2, (T *)C2, s);
-  // the core's prox at full width (exact): slices r1 x r2
+  // the core's prox at full width (exact): slices r1 x r2, on workspace of
+  // this call's own (sketch, two panels, singular values, ranks)
   if (e == cudaSuccess) {
     const int l = std::min(r1, r2);
-    st = tr_slice_prox_noalloc(dt, n, r1, r2, C2, Ct, l, 1, phi, theta, gamma, tau, seed, t, s,
-                               err, err_len);
-    if (st != TR_OK) return finish(st);
+    if (l > TR_MAX_L || !slice_smem_limit_ok(dt, r1, r2, l))
+      return finish(afail(err, err_len, TR_EUNSUPPORTED,
+                          "core slices of %dx%d exceed the slice kernels' shared memory", r1, r2));
+    SliceWork w{};
+    w.n = n;
+    w.n1 = r1;
+    w.n2 = r2;
+    w.l = l;
+    w.q = 1;
+    w.seed = seed;
+    w.Om = alloc((size_t)n * r2 * l * esz);
+    w.P1 = alloc((size_t)n * r1 * l * esz);
+    w.P2 = alloc((size_t)n * r2 * l * esz);
+    w.sig = alloc((size_t)n * l * esz);
+    w.rank = (int *)alloc((size_t)n * sizeof(int));
+    if (e != cudaSuccess)
+      return finish(afail(err, err_len, e == cudaErrorMemoryAllocation ? TR_ENOMEM : TR_ECUDA,
+                          "core workspace: %s", cudaGetErrorString(e)));
+    ShrinkScalars sh{tau, (int)phi, theta, gamma};
+    e = launch_slice_rsvd(dt, w, C2, Ct, sh, t, s);
   }
   // Gbar_j = F1 Ct_j F2^T: T_j = Ct_j F2^T (r1 x n2), then F1 T_j
   if (e == cudaSuccess) {

@@ -1328,6 +1328,9 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   const int64_t sA = (int64_t)n1 * n2;
   T *Om = (T *)w.Om, *P1 = (T *)w.P1, *P2 = (T *)w.P2;
   cudaError_t e;
+  auto mark = [&](const char *nm) {
+    if (w.prof) w.prof->mark(s, nm);
+  };
   // Omega for every slice
   {
     const int64_t per = (int64_t)n2 * l;
@@ -1337,6 +1340,7 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
                    (uint32_t)(w.seed & 0xffffffffu), (uint32_t)(w.seed >> 32), (uint32_t)t, w.dt,
                    0u, w.sel);
     if (e != cudaSuccess) return e;
+    mark("sketch");
   }
   // Precision of each skinny product: 0 = SIMT FP32, 1 = BF16, 3 = split
   // BF16.  The BF16 form keeps the sketch and the early power products in
@@ -1361,24 +1365,39 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
                w.sel, 1, 0};
     return run_gemm(g, mode);
   };
-  if ((e = AX(Om, P1, w.q > 0 ? early : late)) != cudaSuccess) return e;
+  static const char *kAX[4] = {"product A*X fp32 simt", "product A*X bf16 tcgen05", "",
+                               "product A*X split-bf16 tcgen05"};
+  static const char *kAtX[4] = {"product A^T*Q fp32 simt", "product A^T*Q bf16 tcgen05", "",
+                                "product A^T*Q split-bf16 tcgen05"};
+  const int m0 = w.q > 0 ? early : late;
+  if ((e = AX(Om, P1, m0)) != cudaSuccess) return e;
+  mark(kAX[m0]);
   for (int it = 0; it < w.q; ++it) {
     const bool last = it == w.q - 1;
     if ((e = run_qr<T>(n1, l, P1, n, s, w.sel)) != cudaSuccess) return e;
+    mark("qr");
     if ((e = AtX(P1, P2, early)) != cudaSuccess) return e;
+    mark(kAtX[early]);
     if ((e = run_qr<T>(n2, l, P2, n, s, w.sel)) != cudaSuccess) return e;
+    mark("qr");
     if ((e = AX(P2, P1, last ? late : early)) != cudaSuccess) return e;
+    mark(kAX[last ? late : early]);
   }
   if ((e = run_qr<T>(n1, l, P1, n, s, w.sel)) != cudaSuccess) return e;
+  mark("qr");
   if ((e = AtX(P1, P2, late)) != cudaSuccess) return e;
+  mark(kAtX[late]);
   if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s, w.sel, w.ldsig,
                            w.width)) != cudaSuccess)
     return e;
+  mark("svd_core");
   // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output.  It stays on FP32
   // FMA in every form: with K = l the product is short, both operands are
   // k-strided panels and the output is row-major, and the tcgen05 kernel
   // measured 109 us against 38 us here on 400 slices of 200 x 200, l = 20.
-  return rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s, w.sel);
+  if ((e = rank_update<T>(n, n1, n2, l, P1, P2, Gbar, s, w.sel)) != cudaSuccess) return e;
+  mark("rank_update");
+  return cudaSuccess;
 }
 
 template <typename T>

@@ -934,6 +934,57 @@ extern "C" tr_status tr_profile_read(tr_handle *h, double ms[3], int *steps) {
   return TR_OK;
 }
 
+extern "C" tr_status tr_profile_slice_pass(tr_handle *h, const void *Abar, void *Gbar, double tau,
+                                           int t, int reps, double *ms, const char **names,
+                                           int max_kernels, int *count) {
+  if (!h || !Abar || !Gbar || !ms || !count || reps < 1 || max_kernels < 1) return TR_EINVAL;
+  if (Abar == Gbar) return fail(h, TR_EINVAL, "Abar and Gbar must not alias");
+  if (!(tau >= 0) || t < 0) return fail(h, TR_EINVAL, "need tau >= 0, t >= 0");
+  if (h->prm.engine != TR_LR_RSVD)
+    return fail(h, TR_EUNSUPPORTED, "per-kernel profile of the fixed-width engine only");
+  SliceProf prof;
+  for (int i = 0; i < SliceProf::kMax; ++i) {
+    if (cudaEventCreate(&prof.ev[i]) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(prof.ev[k]);
+      return fail(h, TR_ECUDA, "event creation failed");
+    }
+  }
+  ShrinkScalars sh{tau, (int)h->prm.phi, h->prm.phi_theta, h->prm.phi_gamma};
+  SliceWork w = h->sw;
+  w.dt = nullptr;
+  w.prof = &prof;
+  std::vector<double> acc(SliceProf::kMax, 0.0);
+  int nk = 0;
+  tr_status st = TR_OK;
+  for (int r = 0; r < reps && st == TR_OK; ++r) {
+    prof.k = 0;
+    prof.mark(h->stream, "start");
+    cudaError_t e = launch_slice_rsvd(h->dtype, w, Abar, Gbar, sh, t, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      st = fail(h, TR_ECUDA, "profiled slice pass: %s", cudaGetErrorString(e));
+      break;
+    }
+    h->launches += (uint64_t)(prof.k - 1);
+    nk = prof.k - 1;
+    for (int k = 1; k < prof.k; ++k) {
+      float v = 0.f;
+      cudaEventElapsedTime(&v, prof.ev[k - 1], prof.ev[k]);
+      acc[k] += v;
+    }
+  }
+  if (st == TR_OK) {
+    const int m = nk < max_kernels ? nk : max_kernels;
+    for (int k = 0; k < m; ++k) {
+      ms[k] = acc[k + 1] / reps;
+      if (names) names[k] = prof.name[k + 1];
+    }
+    *count = m;
+  }
+  for (int i = 0; i < SliceProf::kMax; ++i) cudaEventDestroy(prof.ev[i]);
+  return st;
+}
+
 extern "C" tr_status tr_kernel_launches(const tr_handle *h, uint64_t *count) {
   if (!h || !count) return TR_EINVAL;
   *count = h->launches;

@@ -142,6 +142,22 @@ struct SliceSel {
   const int *count = nullptr;
 };
 
+// Optional per-kernel timing of one slice pass: mark() records an event
+// after a kernel and labels it, so kernel k's device time is the interval
+// between events k-1 and k (event 0 is recorded before the first kernel).
+struct SliceProf {
+  static constexpr int kMax = 40;
+  cudaEvent_t ev[kMax] = {};
+  const char *name[kMax] = {};
+  int k = 0;
+  void mark(cudaStream_t s, const char *nm) {
+    if (k < kMax && ev[k]) {
+      cudaEventRecord(ev[k], s);
+      name[k++] = nm;
+    }
+  }
+};
+
 struct SliceWork {
   int n, n1, n2, l, q;
   uint64_t seed;
@@ -156,6 +172,7 @@ struct SliceWork {
   int ldsig;    // row stride of sig (0: l); entries l..ldsig-1 are zeroed
   int *width;   // optional: sketch width used, per slice id
   const int *dt;  // optional: iteration index of the Philox counters (device)
+  SliceProf *prof = nullptr;  // optional: per-kernel events (eager passes only)
 };
 // Workspace of the fixed-accuracy engine (Alg. 3 per slice).
 struct AdaptWork {

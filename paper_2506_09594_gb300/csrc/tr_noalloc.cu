@@ -22,19 +22,13 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "tr_internal.cuh"
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 16u << 20;   // 16 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Copy a message into the caller's buffer (if any) and return `st`.
 tr_status report(char *buf, size_t len, tr_status st, const char *fmt, ...) {
@@ -51,22 +45,17 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-// Device address of the static scratch array for the current device, set up
-// on the first call made on that device.
+// Device address of the static scratch array on the current device.  It is
+// looked up on every call (cheap next to the slice pass): after a device
+// reset the module is loaded again and the array may sit elsewhere.  The
+// first call on a device also loads the module there, so that call should
+// come before any stream capture.
 static tr_status noalloc_scratch(void **out, char *err, size_t err_len) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return report(err, err_len, TR_ECUDA, "cudaGetDevice failed");
-  if (dev < 0 || dev >= kMaxDevices)
-    return report(err, err_len, TR_EUNSUPPORTED, "device index %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return report(err, err_len, TR_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return report(err, err_len, TR_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  *out = p;
   return TR_OK;
 }
 

@@ -106,6 +106,10 @@ _SIGS = {
     "tr_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "tr_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "tr_profile_slice_pass": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int)]),
     "tr_slice_prox_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -688,6 +692,21 @@ class Handle:
         _check(load().tr_profile_read(self.h, ms, ctypes.byref(steps)), self.h)
         return {"tube_forward": ms[0], "slice_pass": ms[1], "tube_inverse": ms[2],
                 "steps": steps.value}
+
+    def profile_slice_pass(self, Abar, tau, t, reps=5, out=None):
+        """Mean device ms of every kernel of one eager slice pass
+        (tr_profile_slice_pass): a list of (label, ms) in launch order."""
+        self._same(Abar, "Abar")
+        out = self._new() if out is None else out
+        self._same(out, "out")
+        cap = 40
+        ms = (ctypes.c_double * cap)()
+        names = (ctypes.c_char_p * cap)()
+        cnt = ctypes.c_int()
+        _check(load().tr_profile_slice_pass(self.h, _ptr(Abar), _ptr(out), float(tau), int(t),
+                                            int(reps), ms, names, cap, ctypes.byref(cnt)),
+               self.h)
+        return [(names[k].decode(), ms[k]) for k in range(cnt.value)]
 
     def kernel_launches(self):
         c = ctypes.c_uint64()

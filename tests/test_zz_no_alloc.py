@@ -4,8 +4,12 @@ The no-allocation entry point serves callers that cannot call cudaMalloc
 (latency-critical host loops, code inside another framework's memory pool).
 It must produce what the handle-based slice pass produces, on two calls in
 a row (its fixed scratch array keeps the previous call's contents), and must
-refuse a problem whose scratch exceeds the fixed array.  This file sorts last
-so that a run stopping at the first failure has run every other test first.
+refuse a problem whose scratch exceeds the fixed array.  Before the checked
+calls, one call of a larger shape with a wider sketch on an all-NaN stack
+leaves NaN across the array at other offsets than the checked shape uses,
+so a read of anything the checked call did not write itself shows up.
+This file sorts last so that a run stopping at the first failure has run
+every other test first.
 """
 
 import numpy as np
@@ -35,6 +39,10 @@ def test_noalloc_matches_handle_slice_prox_twice(dtype, tol):
     ref = h.slice_prox(Ab, tau, t=7)
     torch.cuda.synchronize()
     h.close()
+    # leave NaN in the shared array: 24 slices of 96 x 96 at sketch width 48
+    junk = torch.full((24, 96, 96), float("nan"), dtype=dtype, device="cuda")
+    tr.slice_prox_noalloc(junk, torch.empty_like(junk), 48, 1, tau, 3, seed=5)
+    torch.cuda.synchronize()
     for call in range(2):
         out = torch.full_like(Ab, float("nan"))
         tr.slice_prox_noalloc(Ab, out, l, q, tau, 7, seed=99, phi=tr.TR_PEN_MCP, theta=1.0,
