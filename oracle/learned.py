@@ -26,7 +26,13 @@ per-slice sketch width from the previous slice pass:
                     [min(8, lmax), lmax], decided in float32 like the device;
                     slice ids stably sorted by width class (l - 1) // 8.
 * ``threshold``     the smallest singular value the shrink keeps.
-* ``saturated``     the certificate: kept rank > l - p with l < lmax.
+* ``judge``         which learned sketches the plain adaptive method
+                    (Alg. 3 per slice) recomputes: a sketch is kept when it
+                    meets Alg. 3's stop test (the energy its basis misses,
+                    E = ||A||^2 - ||Q^T A||^2 with Q^T A's singular values
+                    sig, below eps^2 ||A||^2), or its kept rank is at most
+                    l - p (p directions seen beyond every singular value the
+                    prox keeps), or l reaches the adaptive basis cap.
 
 Parameter vector: per layer W (out x in, row-major) then b (out), layers in
 order 16 -> 128, 128 -> 128, 128 -> 128, 128 -> 1 (35329 values).
@@ -186,8 +192,22 @@ def plan_widths(yhat, p, lmax):
     return width, ids, counts
 
 
-def saturated(rank, width, p, lmax):
-    """Certificate: slices whose kept rank may exceed what the sketch saw."""
-    rank = np.asarray(rank)
-    width = np.asarray(width)
-    return np.nonzero((width < lmax) & (rank > width - p))[0]
+def judge(anorm2, sig, eps, rank, width, p, kcap):
+    """Indices of the slices whose learned sketch is rejected.
+
+    anorm2[j] = ||A_j||_F^2; sig[j] = the singular values of B_j = Q_j^T A_j
+    (zero padding counts nothing); rank[j] the kept rank after the shrink,
+    width[j] the sketch width.  The basis Q_j misses
+    E_j = ||A_j||^2 - sum sig_j^2 = ||A_j - Q_j Q_j^T A_j||^2 of the energy
+    (Pythagoras).  Kept: E_j < eps^2 ||A_j||^2 (Alg. 3's relative stop rule)
+    or A_j = 0, or rank[j] <= width[j] - p, or width[j] >= kcap.
+    """
+    out = []
+    for j, a2 in enumerate(np.asarray(anorm2, dtype=np.float64)):
+        cap = float(np.sum(np.asarray(sig[j], dtype=np.float64) ** 2))
+        alg3 = not (a2 > 0.0) or a2 - cap < eps * eps * a2
+        margin = rank[j] <= width[j] - p
+        wide = width[j] >= kcap
+        if not (alg3 or margin or wide):
+            out.append(j)
+    return np.asarray(out, dtype=np.int64)

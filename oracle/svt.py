@@ -193,13 +193,45 @@ def slice_prox_adaptive(Ab, eps, b, delta_rel, seed, t, j, tau, kind,
 # ------------------------------------------------------ whole-tensor maps
 def transformed_prox(Abar, tau, kind, theta=1.0, gamma=4.0, engine="full",
                      l=None, q=1, seed=0, t=0, eps=0.01, b=10, delta_rel=1e-12,
-                     max_rank=None):
+                     max_rank=None, widths=None, p=0):
     """Apply the chosen slice engine to every transformed face slice.
 
     Returns (Gbar, info) where info holds per-slice singular values and the
     number of kept (non-zero shrunk) singular values.
+
+    engine "learned": slice j is sketched at its own width widths[j] (the
+    randomized engine with q power steps and the Philox block of width
+    widths[j]); learned.judge (eps, oversampling p, adaptive cap max_rank)
+    decides which sketches the adaptive engine (eps, b, delta_rel, cap
+    max_rank) recomputes.  info["fallback"] lists those slices; info["widths"]
+    holds each slice's width: the sketch's, or the adaptive basis size.
     """
     n, n1, n2 = Abar.shape
+    if engine == "learned":
+        from . import learned
+        Gbar = np.zeros(Abar.shape, dtype=np.result_type(Abar.dtype, np.float64))
+        sig, a2 = [], []
+        for j in range(n):
+            Ab = np.asarray(Abar[j]).astype(np.result_type(Abar.dtype, np.float64))
+            ll = min(int(widths[j]), n1, n2)
+            Om = philox.gaussian_block(seed, t, j, n2, ll)
+            Gbar[j], s, _ = slice_prox_randomized(Ab, Om, q, tau, kind, theta, gamma)
+            sig.append(s)
+            a2.append(float(np.sum(Ab * Ab)))
+        kept = np.array([min(int(w), n1, n2) for w in widths], dtype=np.int64)
+        shrunk = [int(np.count_nonzero(_shrink(sig[j], tau, kind, theta, gamma)))
+                  for j in range(n)]
+        fb = learned.judge(a2, sig, eps, shrunk, kept, p, max_rank)
+        ranks = np.zeros(n, dtype=np.int64)
+        for j in range(n):
+            if j in set(fb.tolist()):
+                Ab = np.asarray(Abar[j]).astype(np.result_type(Abar.dtype, np.float64))
+                Gbar[j], s, s2, kept[j], _ = slice_prox_adaptive(Ab, eps, b, delta_rel, seed, t,
+                                                                 j, tau, kind, theta, gamma,
+                                                                 max_rank)
+                sig[j] = s
+            ranks[j] = int(np.count_nonzero(_shrink(sig[j], tau, kind, theta, gamma)))
+        return Gbar, {"ranks": ranks, "sigma": sig, "fallback": fb, "widths": kept}
     if engine == "tucker":
         # Alg. 4 randomized branch with shared factors of the two spatial
         # modes (oracle.tucker): ranks, block sizes l, q Krylov steps; the

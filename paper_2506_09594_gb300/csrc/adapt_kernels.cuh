@@ -13,7 +13,10 @@
 //   stop when E < eps^2 ||A||_F^2, the cap is reached or nothing is left.
 // Blocks have a fixed width b in the workspace (deflated columns are zero),
 // so every slice's products have the same shape and run as one batched
-// GEMM; a slice that has stopped skips its per-slice kernels.
+// GEMM; a slice that has stopped skips its per-slice kernels.  With a slice
+// selection (SliceSel) batch entry e works on slice ids[e]: the transformed
+// slice, the Philox counters and the slice statistics are the slice's, the
+// panels and the loop state (E, norms, flags, counts) the entry's.
 //
 // defl-QR: Householder QR with column pivoting (largest remaining column
 // norm first); s = number of pivots whose norm is at least delta; R = Rt(1:s,
@@ -210,7 +213,7 @@ size_t adapt_smem(int m, int b, int kcap) {
 template <typename T>
 __global__ void adapt_init_kernel(int n1, int n2, int b, int kcap, const T *__restrict__ Abar,
                                   AdaptPtrs<T> w, uint32_t k0, uint32_t k1, uint32_t t_host,
-                                  const int *dt) {
+                                  const int *dt, SliceSel sel) {
   const uint32_t t = dt ? (uint32_t)*dt : t_host;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *P = reinterpret_cast<T *>(smem_raw);
@@ -220,7 +223,9 @@ __global__ void adapt_init_kernel(int n1, int n2, int b, int kcap, const T *__re
   T *red = cn + b;
   int *perm = reinterpret_cast<int *>(red + 64);
   int *pick = perm + b;
-  const int j = blockIdx.x;
+  const int e0 = blockIdx.x;   // batch entry
+  if (sel.count && e0 >= *sel.count) return;
+  const int j = sel.ids ? sel.ids[e0] : e0;   // slice id
   const T *A = Abar + (int64_t)j * n1 * n2;
   double part = 0.0;
   for (int64_t e = threadIdx.x; e < (int64_t)n1 * n2; e += blockDim.x) part += (double)A[e] * A[e];
@@ -236,18 +241,18 @@ __global__ void adapt_init_kernel(int n1, int n2, int b, int kcap, const T *__re
     if (threadIdx.x == 0) {
       double tot = 0.0;
       for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += dred[q];
-      w.nrm2[j] = tot;
-      w.E[j] = tot;
-      w.active[j] = tot > 0.0;
-      w.kept[j] = 0;
-      w.draws[j] = 1;
+      w.nrm2[e0] = tot;
+      w.E[e0] = tot;
+      w.active[e0] = tot > 0.0;
+      w.kept[e0] = 0;
+      w.draws[e0] = 1;
     }
   }
   gaussian_block_smem(P, n2, b, k0, k1, (uint32_t)j, t, 0u);
   __syncthreads();
   const int s = block_pivoted_qr(P, n2, b, n2, tau, perm, cn, pick, T(0));
   block_form_q_cols(P, n2, b, n2, tau, s, Q);
-  T *V0 = w.Vcat + (int64_t)j * n2 * (kcap + b);
+  T *V0 = w.Vcat + (int64_t)e0 * n2 * (kcap + b);
   for (int e = threadIdx.x; e < n2 * b; e += blockDim.x) V0[e] = Q[e];
   (void)red;
 }
@@ -256,9 +261,10 @@ __global__ void adapt_init_kernel(int n1, int n2, int b, int kcap, const T *__re
 // defl-QR, U_i into Ucat block i, R_i (original column order) into Rm.
 template <typename T>
 __global__ void adapt_u_kernel(int i, int n1, int b, int kcap, int64_t xs, AdaptPtrs<T> w,
-                               double delta_rel) {
+                               double delta_rel, SliceSel sel) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int j = blockIdx.x;
+  const int j = blockIdx.x;   // batch entry (the slice itself is not read here)
+  if (sel.count && j >= *sel.count) return;
   if (!w.active[j]) return;
   T *P = reinterpret_cast<T *>(smem_raw);
   T *Q = P + (size_t)n1 * b;
@@ -309,10 +315,12 @@ __global__ void adapt_u_kernel(int i, int n1, int b, int kcap, int64_t xs, Adapt
 template <typename T>
 __global__ void adapt_v_kernel(int i, int n2, int b, int kcap, int64_t xs, AdaptPtrs<T> w,
                                double delta_rel, double eps, uint32_t k0, uint32_t k1,
-                               uint32_t t_host, const int *dt) {
+                               uint32_t t_host, const int *dt, SliceSel sel) {
   const uint32_t t = dt ? (uint32_t)*dt : t_host;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int j = blockIdx.x;
+  const int j = blockIdx.x;   // batch entry; the Philox draws use the slice id
+  if (sel.count && j >= *sel.count) return;
+  const uint32_t slice = sel.ids ? (uint32_t)sel.ids[j] : (uint32_t)j;
   if (!w.active[j]) return;
   T *P = reinterpret_cast<T *>(smem_raw);
   T *Q = P + (size_t)n2 * b;
@@ -354,7 +362,7 @@ __global__ void adapt_v_kernel(int i, int n2, int b, int kcap, int64_t xs, Adapt
   if (nref < 0) nref = 0;
   if (nref > 0) {
     T *G = P;                                        // the factored panel is no longer needed
-    gaussian_block_smem(G, n2, nref, k0, k1, (uint32_t)j, t, (uint32_t)w.draws[j]);
+    gaussian_block_smem(G, n2, nref, k0, k1, slice, t, (uint32_t)w.draws[j]);
     __syncthreads();
     block_project_out(G, n2, nref, Vc, i + 1, b, Q, s, coef);
     const int s2 = block_pivoted_qr(G, n2, nref, n2, tau, perm, cn, pick, T(0));
@@ -373,4 +381,12 @@ __global__ void adapt_v_kernel(int i, int n2, int b, int kcap, int64_t xs, Adapt
                       (s + nref) == 0;
     if (done) w.active[j] = 0;
   }
+}
+
+// Width of a selected slice after an adaptive pass: its basis size.
+__global__ void adapt_width_kernel(const int *__restrict__ ids, const int *__restrict__ count,
+                                   const int *__restrict__ kept, int *__restrict__ width, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n || (count && e >= *count)) return;
+  width[ids[e]] = kept[e];
 }

@@ -17,9 +17,14 @@
 //      side stream, launched for all n slices and sized on the device
 //      (blocks past the class count exit), so a pass needs no host
 //      synchronisation and can be captured in a graph;
-//   4. certificate: a slice whose kept rank exceeds l_j - p may own more
-//      singular values above the threshold than its sketch could see; it
-//      is recomputed at l_max, the fixed width of the plain engine.
+//   4. judge and fallback: a sketch is kept when it meets Alg. 3's stop
+//      test (the energy its basis misses, E_j = ||Abar_j||^2 -
+//      ||Q_j^T Abar_j||^2, below eps^2 ||Abar_j||^2), or when it saw p
+//      directions beyond every singular value the prox keeps (kept rank <=
+//      l_j - p), or when it is as wide as the adaptive basis cap; the
+//      other slices are recomputed by the plain adaptive method (Alg. 3 per
+//      slice).  The first pass of a handle has no history and is the
+//      adaptive method on every slice.
 //
 // Training uses the same MLP kernels: forward with stored activations,
 // backward deltas per 32-row tile, weight gradients by a deterministic
@@ -441,8 +446,6 @@ __global__ void __launch_bounds__(1024) plan_kernel(int n, const float *__restri
   }
 }
 
-// Certificate: slices whose kept rank exceeds width - p (and whose width is
-// below lmax) are listed for a recomputation at lmax.
 // Width groups on the device: walking the classes from narrow to wide, a
 // class with fewer than merge_min slices (while a wider non-empty class
 // follows) joins the next one.  Group g is launched at the width of its
@@ -476,12 +479,58 @@ __global__ void group_kernel(int n, int C, int merge_min, const int *__restrict_
     for (int i = threadIdx.x; i < cnt[c]; i += blockDim.x) gids[(int64_t)c * n + i] = ids[src[c] + i];
 }
 
-__global__ void saturation_kernel(int n, const int *__restrict__ rank,
-                                  const int *__restrict__ width, int p, int lmax,
-                                  int *__restrict__ fb_ids, int *__restrict__ fb_count) {
+// ||Abar_j||_F^2 per slice: one block per slice, four FP32 partial sums per
+// thread (at most a few thousand terms each), folded and reduced in double.
+template <typename T>
+__global__ void slice_norm2_kernel(int64_t per, const T *__restrict__ A,
+                                   double *__restrict__ out) {
+  const T *a = A + (int64_t)blockIdx.x * per;
+  double acc = 0.0;
+  for (int64_t base = 0; base < per; base += (int64_t)blockDim.x * 1024) {
+    T p[4] = {T(0), T(0), T(0), T(0)};
+    const int64_t end = base + (int64_t)blockDim.x * 1024 < per ? base + (int64_t)blockDim.x * 1024
+                                                                  : per;
+    int u = 0;
+    for (int64_t e = base + threadIdx.x; e < end; e += blockDim.x, u = (u + 1) & 3)
+      p[u] = fma(a[e], a[e], p[u]);
+    acc += ((double)p[0] + (double)p[1]) + ((double)p[2] + (double)p[3]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    out[blockIdx.x] = tot;
+  }
+}
+
+// The judge of a learned width.  Slice j's sketch (width l_j, kept rank k_j
+// after the shrink) is kept when
+//   (a) it meets Alg. 3's stop test: the energy its basis misses,
+//       E_j = ||Abar_j||^2 - ||B_j||^2 (B_j = Q_j^T Abar_j, whose squared
+//       singular values are row j of sig), is below eps^2 ||Abar_j||^2; or
+//   (b) it saw p directions beyond every singular value the prox keeps
+//       (k_j <= l_j - p, the oversampling of the plain width); or
+//   (c) it is at least as wide as the adaptive engine's basis cap;
+// otherwise it is listed for the adaptive engine (Alg. 3 per slice).
+template <typename T>
+__global__ void judge_kernel(int n, const T *__restrict__ sig, int ldsig,
+                             const double *__restrict__ anorm2, double eps2,
+                             const int *__restrict__ rank, const int *__restrict__ width, int p,
+                             int kcap, int *__restrict__ fb_ids, int *__restrict__ fb_count) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  if (width[j] < lmax && rank[j] > width[j] - p) fb_ids[atomicAdd(fb_count, 1)] = j;
+  const T *s = sig + (int64_t)j * ldsig;
+  double cap = 0.0;
+  for (int i = 0; i < ldsig; ++i) cap += (double)s[i] * (double)s[i];
+  const double a2 = anorm2[j];
+  const bool alg3 = !(a2 > 0.0) || a2 - cap < eps2 * a2;
+  const bool margin = rank[j] <= width[j] - p;
+  const bool wide = width[j] >= kcap;
+  if (!(alg3 || margin || wide)) fb_ids[atomicAdd(fb_count, 1)] = j;
 }
 
 }  // namespace
@@ -600,11 +649,14 @@ cudaError_t launch_slice_learned(tr_dtype dt, const SliceWork &w, LearnedWork &l
   base.width = lw.width;
   base.sel = SliceSel{};
   cudaError_t e;
+  const uint64_t adapt_launches = 4 * (uint64_t)(lw.aw.kcap / lw.aw.b) + 3;
   if (!lw.have_hist) {
-    // no previous pass: every slice at the plain width
+    // no previous pass: the plain adaptive method on every slice
     if ((e = cudaMemsetAsync(lw.fb_count, 0, sizeof(int), s)) != cudaSuccess) return e;
-    if ((e = launch_slice_rsvd(dt, base, Abar, Gbar, sh, t, s)) != cudaSuccess) return e;
-    *launches += 7 + 4 * (uint64_t)w.q;
+    SliceWork aw0 = base;
+    aw0.sel.ids = lw.iota;
+    if ((e = launch_slice_adaptive(dt, aw0, lw.aw, Abar, Gbar, sh, t, s)) != cudaSuccess) return e;
+    *launches += adapt_launches;
     lw.have_hist = true;
     lw.thr_prev = thr;
     return cudaSuccess;
@@ -621,7 +673,15 @@ cudaError_t launch_slice_learned(tr_dtype dt, const SliceWork &w, LearnedWork &l
   const int C = plan_classes(lmax);
   group_kernel<<<1, 256, 0, s>>>(n, C, lw.merge_min, lw.counts, lw.ids, lw.gids, lw.gcount);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *launches += 4;
+  // ||Abar_j||^2 for the judge
+  if (dt == TR_F64)
+    slice_norm2_kernel<double><<<n, 256, 0, s>>>((int64_t)w.n1 * w.n2, (const double *)Abar,
+                                                 lw.anorm2);
+  else
+    slice_norm2_kernel<float><<<n, 256, 0, s>>>((int64_t)w.n1 * w.n2, (const float *)Abar,
+                                                lw.anorm2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  *launches += 5;
   // every class on a side stream, sized on the device (blocks past the
   // class count exit at once), panels in the class's own region
   if ((e = cudaEventRecord(lw.fork, s)) != cudaSuccess) return e;
@@ -649,16 +709,24 @@ cudaError_t launch_slice_learned(tr_dtype dt, const SliceWork &w, LearnedWork &l
     if ((e = cudaEventRecord(lw.join[i], lw.aux[i])) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, lw.join[i], 0)) != cudaSuccess) return e;
   }
-  // 4: certificate and fallback at the plain width (sized on the device)
+  // 4: Alg. 3's judge, and the adaptive engine on the slices it rejects
+  // (sized on the device)
   if ((e = cudaMemsetAsync(lw.fb_count, 0, sizeof(int), s)) != cudaSuccess) return e;
-  saturation_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, w.rank, lw.width, p, lmax, lw.fb_ids,
-                                                   lw.fb_count);
+  const double eps2 = lw.aw.eps * lw.aw.eps;
+  if (dt == TR_F64)
+    judge_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(n, (const double *)w.sig, lmax,
+                                                        lw.anorm2, eps2, w.rank, lw.width, p,
+                                                        lw.aw.kcap, lw.fb_ids, lw.fb_count);
+  else
+    judge_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(n, (const float *)w.sig, lmax, lw.anorm2,
+                                                       eps2, w.rank, lw.width, p, lw.aw.kcap,
+                                                       lw.fb_ids, lw.fb_count);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   SliceWork fw = base;
   fw.sel.ids = lw.fb_ids;
   fw.sel.count = lw.fb_count;
-  if ((e = launch_slice_rsvd(dt, fw, Abar, Gbar, sh, t, s)) != cudaSuccess) return e;
-  *launches += 1 + 7 + 4 * (uint64_t)w.q;
+  if ((e = launch_slice_adaptive(dt, fw, lw.aw, Abar, Gbar, sh, t, s)) != cudaSuccess) return e;
+  *launches += 1 + adapt_launches;
   lw.thr_prev = thr;
   return cudaSuccess;
 }

@@ -21,6 +21,7 @@
 #include "tr_internal.cuh"
 #include "tr_rng.cuh"
 #include "umma_gemm.cuh"
+#include "umma_tma.cuh"
 
 namespace {
 
@@ -289,6 +290,58 @@ cudaError_t umma_gemm(const GemmArgs &g, int batch, int split, int *err, cudaStr
   }
   if (split > 1) TR_UMMA(128, 3) else TR_UMMA(128, 1)
 #undef TR_UMMA
+}
+
+// The same product with TMA-fed operands (tmag::gemm_kernel) when the views
+// allow 3D tensor copies: N <= 64, B with k contiguous, A with k or m
+// contiguous, 16-byte strides.  *used is false (and nothing is launched)
+// otherwise.  nA: slices in A's array when A is addressed by slice id.
+cudaError_t tma_gemm(const GemmArgs &g, int batch, int nA, int split, int *err, cudaStream_t s,
+                     bool *used) {
+  *used = false;
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || batch <= 0 || g.N > 64 || g.sBk != 1) return cudaSuccess;
+  tmag::Args a{};
+  const int64_t za = g.a_by_id ? (int64_t)nA : (int64_t)batch;
+  bool ok;
+  if (g.sAk == 1) {
+    a.a_kcontig = 1;
+    ok = encode_tensor_3d_f32(&a.amap, g.A, g.K, g.M, za, g.sAi, g.sAb, tmag::kKC, tmag::kBM, true);
+  } else if (g.sAi == 1) {
+    a.a_kcontig = 0;
+    ok = encode_tensor_3d_f32(&a.amap, g.A, g.M, g.K, za, g.sAk, g.sAb, tmag::kBM, tmag::kKC, false);
+  } else {
+    return cudaSuccess;
+  }
+  const int np = g.N <= 32 ? 32 : 64;
+  ok = ok && encode_tensor_3d_f32(&a.bmap, g.B, g.K, g.N, batch, g.sBn,
+                                  g.sBb > 0 ? g.sBb : (int64_t)g.N * g.sBn, tmag::kKC, np, true);
+  if (!ok) return cudaSuccess;
+  a.M = g.M;
+  a.N = g.N;
+  a.K = g.K;
+  a.C = (float *)g.C;
+  a.sCb = g.sCb;
+  a.sCi = g.sCi;
+  a.sCn = g.sCn;
+  a.ids = g.sel.ids;
+  a.count = g.sel.count;
+  a.a_by_id = g.a_by_id;
+  a.c_by_id = g.c_by_id;
+  const dim3 grid((g.M + tmag::kBM - 1) / tmag::kBM, 1, batch);
+  *used = true;
+#define TR_TMAG(NP, ST, SP)                                                                    \
+  {                                                                                            \
+    auto k = tmag::gemm_kernel<NP, ST, SP>;                                                    \
+    const int smem = tmag::Layout<NP, ST, SP>::total + 1024;                                   \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    if (e != cudaSuccess) return e;                                                            \
+    return launch_pdl(k, grid, dim3(tmag::kThreads), smem, s, a, err);                        \
+  }
+  if (np == 32) {
+    if (split > 1) TR_TMAG(32, 3, 3) else TR_TMAG(32, 3, 1)
+  }
+  if (split > 1) TR_TMAG(64, 2, 3) else TR_TMAG(64, 2, 1)
+#undef TR_TMAG
 }
 
 // -------------------------------------------------- block Householder QR
@@ -1352,6 +1405,9 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   const int late = !tc ? 0 : 3;
   auto run_gemm = [&](const GemmArgs &g, int mode) {
     if (mode == 0) return bgemm<T>(g, n, s);
+    bool used = false;
+    cudaError_t e2 = tma_gemm(g, n, w.nA > 0 ? w.nA : n, mode, w.err, s, &used);
+    if (e2 != cudaSuccess || used) return e2;
     return umma_gemm(g, n, mode, w.err, s);
   };
   // Abar is indexed by slice id, the panels by batch entry
@@ -1416,33 +1472,41 @@ cudaError_t run_adaptive(const SliceWork &sw, const AdaptWork &aw, const T *Abar
   if ((e = cudaFuncSetAttribute(adapt_init_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(adapt_u_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(adapt_v_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
-  adapt_init_kernel<T><<<n, 256, sm2, s>>>(n1, n2, b, kcap, Abar, w, k0, k1, (uint32_t)t, sw.dt);
+  const SliceSel sel = sw.sel;
+  adapt_init_kernel<T><<<n, 256, sm2, s>>>(n1, n2, b, kcap, Abar, w, k0, k1, (uint32_t)t, sw.dt,
+                                          sel);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nblk = kcap / b;
   for (int i = 0; i < nblk; ++i) {
     // X = Abar V_i
     GemmArgs g1{n1, b, n2, Abar, sA, n2, 1, w.Vcat + (int64_t)i * b * n2,
-                (int64_t)n2 * (kcap + b), 1, n2, w.X, xs, 1, n1};
+                (int64_t)n2 * (kcap + b), 1, n2, w.X, xs, 1, n1, sel, 1, 0};
     if ((e = bgemm<T>(g1, n, s)) != cudaSuccess) return e;
-    adapt_u_kernel<T><<<n, 256, sm1, s>>>(i, n1, b, kcap, xs, w, aw.delta_rel);
+    adapt_u_kernel<T><<<n, 256, sm1, s>>>(i, n1, b, kcap, xs, w, aw.delta_rel, sel);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (i + 1 == nblk) break;
     // X = Abar^T U_i
     GemmArgs g2{n2, b, n1, Abar, sA, 1, n2, w.Ucat + (int64_t)i * b * n1, (int64_t)n1 * kcap, 1,
-                n1, w.X, xs, 1, n2};
+                n1, w.X, xs, 1, n2, sel, 1, 0};
     if ((e = bgemm<T>(g2, n, s)) != cudaSuccess) return e;
     adapt_v_kernel<T><<<n, 256, sm2, s>>>(i, n2, b, kcap, xs, w, aw.delta_rel, aw.eps, k0, k1,
-                                         (uint32_t)t, sw.dt);
+                                         (uint32_t)t, sw.dt, sel);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // B^T = Abar^T U (U zero-padded to kcap columns), SVD core, rebuild
   T *P2 = (T *)sw.P2;
   GemmArgs g3{n2, kcap, n1, Abar, sA, 1, n2, w.Ucat, (int64_t)n1 * kcap, 1, n1, P2,
-              (int64_t)n2 * kcap, 1, n2};
+              (int64_t)n2 * kcap, 1, n2, sel, 1, 0};
   if ((e = bgemm<T>(g3, n, s)) != cudaSuccess) return e;
-  if ((e = run_svd_core<T>(n1, n2, kcap, w.Ucat, P2, n, sh, (T *)sw.sig, sw.rank, s)) != cudaSuccess)
+  if ((e = run_svd_core<T>(n1, n2, kcap, w.Ucat, P2, n, sh, (T *)sw.sig, sw.rank, s, sel,
+                           sw.ldsig)) != cudaSuccess)
     return e;
-  return rank_update<T>(n, n1, n2, kcap, w.Ucat, P2, Gbar, s);
+  if ((e = rank_update<T>(n, n1, n2, kcap, w.Ucat, P2, Gbar, s, sel)) != cudaSuccess) return e;
+  if (sel.ids && sw.width) {
+    adapt_width_kernel<<<(n + 255) / 256, 256, 0, s>>>(sel.ids, sel.count, aw.kept, sw.width, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace

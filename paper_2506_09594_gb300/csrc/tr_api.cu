@@ -146,7 +146,7 @@ static void free_all(tr_handle *h) {
   free_profile(h);
   LearnedWork &lw = h->lw;
   void *lbufs[] = {lw.params, lw.feat, lw.pred, lw.ids, lw.counts, lw.fb_ids, lw.fb_count,
-                   lw.gids, lw.gcount};
+                   lw.gids, lw.gcount, lw.anorm2, lw.iota};
   for (void *b : lbufs)
     if (b) cudaFree(b);
   for (int i = 0; i < TR_LEARNED_STREAMS; ++i) {
@@ -232,9 +232,10 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   if (prm->engine != TR_LR_RSVD && prm->engine != TR_LR_ADAPTIVE && prm->engine != TR_LR_LEARNED &&
       prm->engine != TR_LR_TUCKER)
     return fail(nullptr, TR_EUNSUPPORTED, "engine %d not built", (int)prm->engine);
-  if (prm->engine == TR_LR_ADAPTIVE &&
+  if ((prm->engine == TR_LR_ADAPTIVE || prm->engine == TR_LR_LEARNED) &&
       (prm->adapt_block < 1 || prm->adapt_block > 32 || !(prm->adapt_eps > 0)))
-    return fail(nullptr, TR_EINVAL, "adaptive engine: need 1 <= adapt_block <= 32, adapt_eps > 0");
+    return fail(nullptr, TR_EINVAL,
+                "adaptive and learned engines: need 1 <= adapt_block <= 32, adapt_eps > 0");
   if (prm->prec != TR_PREC_FP32 && prm->prec != TR_PREC_BF16 && prm->prec != TR_PREC_BF16X3)
     return fail(nullptr, TR_EUNSUPPORTED, "precision %d not built", (int)prm->prec);
   if (prm->prec != TR_PREC_FP32 && p->dtype != TR_F32)
@@ -310,6 +311,24 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
       return st;
     }
     l = kcap;
+    h->aw.b = b;
+    h->aw.kcap = kcap;
+    h->aw.eps = prm->adapt_eps;
+    h->aw.delta_rel = p->dtype == TR_F64 ? 1e-11 : 1e-5;
+  }
+  if (prm->engine == TR_LR_LEARNED) {
+    // the adaptive judge and fallback: cap = the plain width rounded down to
+    // whole blocks (so its singular values fit the rows of l_max)
+    const int b = prm->adapt_block;
+    const int mn = (int)(h->n1 < h->n2 ? h->n1 : h->n2);
+    int kcap = (l / b) * b;
+    if (kcap > (mn / b) * b) kcap = (mn / b) * b;
+    if (kcap < b || adapt_smem_bytes(h->dtype, (int)h->n1, (int)h->n2, b, kcap) > 227 * 1024) {
+      tr_status st = fail(nullptr, TR_EUNSUPPORTED,
+                          "learned engine: adaptive fallback block %d does not fit width %d", b, l);
+      delete h;
+      return st;
+    }
     h->aw.b = b;
     h->aw.kcap = kcap;
     h->aw.eps = prm->adapt_eps;
@@ -398,7 +417,7 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   INIT_CUDA(cudaMemsetAsync(sw.err, 0, sizeof(int), h->stream));
   sw.prec = (int)prm->prec;
   INIT_CUDA(cudaMemsetAsync(sw.rank, 0, (size_t)h->n * sizeof(int), h->stream));
-  if (prm->engine == TR_LR_ADAPTIVE) {
+  if (prm->engine == TR_LR_ADAPTIVE || prm->engine == TR_LR_LEARNED) {
     AdaptWork &aw = h->aw;
     const size_t mx = (size_t)(h->n1 > h->n2 ? h->n1 : h->n2);
     INIT_CUDA(cudaMalloc(&aw.Ucat, (size_t)h->n * h->n1 * aw.kcap * h->esz));
@@ -434,6 +453,14 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     INIT_CUDA(cudaMalloc((void **)&lw.fb_count, sizeof(int)));
     INIT_CUDA(cudaMalloc((void **)&lw.gids, (size_t)C * h->n * sizeof(int)));
     INIT_CUDA(cudaMalloc((void **)&lw.gcount, (size_t)C * sizeof(int)));
+    INIT_CUDA(cudaMalloc((void **)&lw.anorm2, (size_t)h->n * sizeof(double)));
+    INIT_CUDA(cudaMalloc((void **)&lw.iota, (size_t)h->n * sizeof(int)));
+    {
+      std::vector<int> ids((size_t)h->n);
+      for (size_t i = 0; i < ids.size(); ++i) ids[i] = (int)i;
+      INIT_CUDA(cudaMemcpy(lw.iota, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    lw.aw = h->aw;
     lw.width = h->width;
     for (int i = 0; i < TR_LEARNED_STREAMS; ++i) {
       INIT_CUDA(cudaStreamCreateWithFlags(&lw.aux[i], cudaStreamNonBlocking));
@@ -520,6 +547,7 @@ static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double t
       gw.Om = (char *)h->sw.Om + (size_t)start * h->n2 * h->sw.l * h->esz;
       gw.P1 = (char *)h->sw.P1 + (size_t)start * h->n1 * h->sw.l * h->esz;
       gw.P2 = (char *)h->sw.P2 + (size_t)start * h->n2 * h->sw.l * h->esz;
+      gw.nA = (int)h->n;
       if (cnt > 0) {
         TR_CUDA(h, launch_slice_rsvd(h->dtype, gw, Abar, Gbar, sh, t, h->side[g]));
         h->launches += 7 + 4 * (uint64_t)h->sw.q;

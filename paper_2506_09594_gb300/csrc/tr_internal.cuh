@@ -104,6 +104,14 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 bool encode_tensor_2d(CUtensorMap *out, const void *base, bool u8, int64_t cols, int64_t rows,
                       int64_t row_stride, int box_cols, int box_rows);
 
+// A 3D tensor map of FP32 elements (d0 contiguous, then d1 with element
+// stride s1, then d2 with stride s2) with boxes of box0 x box1 x 1, the
+// 128-byte swizzle when swizzle128 (then box0 * 4 must be 128); cached by
+// view.  Elements past a dimension read as zeros.  False when the view
+// breaks a tensor-copy rule or the driver refuses it.
+bool encode_tensor_3d_f32(CUtensorMap *out, const void *base, int64_t d0, int64_t d1, int64_t d2,
+                          int64_t s1, int64_t s2, int box0, int box1, bool swizzle128);
+
 // ---- tube passes (tube_kernels.cu) ----
 cudaError_t launch_tube_forward(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
                                 const void *mats, const void *M, const uint8_t *mask,
@@ -173,6 +181,7 @@ struct SliceWork {
   int *width;   // optional: sketch width used, per slice id
   const int *dt;  // optional: iteration index of the Philox counters (device)
   SliceProf *prof = nullptr;  // optional: per-kernel events (eager passes only)
+  int nA = 0;   // slices in the Abar/Gbar arrays (0: n), the range of slice ids
 };
 // Workspace of the fixed-accuracy engine (Alg. 3 per slice).
 struct AdaptWork {
@@ -223,6 +232,14 @@ struct LearnedWork {
   int *gids = nullptr, *gcount = nullptr;    // width groups: C x n slice ids, C sizes
   bool have_hist = false;
   double thr_prev = 0.0;
+  // the plain adaptive method (Alg. 3 per slice) as judge and fallback of
+  // the learned widths: a sketch is kept when it meets Alg. 3's stop test
+  // E_j = ||Abar_j||^2 - ||B_j||^2 < eps^2 ||Abar_j||^2, or kept rank <=
+  // width - p, or width >= aw.kcap; else the adaptive engine recomputes the
+  // slice (workspace aw, cap aw.kcap <= lmax)
+  AdaptWork aw{};
+  double *anorm2 = nullptr;  // ||Abar_j||_F^2 per slice
+  int *iota = nullptr;       // 0, 1, ..., n-1
   cudaStream_t aux[TR_LEARNED_STREAMS] = {};
   cudaEvent_t fork = nullptr, join[TR_LEARNED_STREAMS] = {};
 };

@@ -1,0 +1,267 @@
+// Batched skinny GEMM on the tcgen05 tensor cores with operands fed by tensor
+// copies (TMA), for the products of the slice pass with the transformed
+// slices (Y = Abar X, W = Abar^T Q; Alg. 1's sketch and power steps).
+//
+// C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out, N <= 64.  One
+// CTA (4 warps) owns a 128-row tile of one batch entry.  K is consumed in
+// chunks of 32: one thread keeps STAGES chunks of both operands in flight
+// as 3D tensor copies (cp.async.bulk.tensor.3d, completion counted on an
+// mbarrier) into FP32 staging tiles, so the HBM latency of a chunk overlaps
+// the work on the chunks before it.  The 128 threads convert a landed chunk
+// to BF16 (x = hi + lo, both BF16, for the split form) in the canonical
+// K-major core-matrix layout without swizzle (8-row x 16-byte core
+// matrices, leading byte offset 128, stride byte offset 512), and one
+// elected thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into
+// a TMEM accumulator of 128 lanes x NP columns, committing to an mbarrier
+// per conversion buffer (two buffers).  The epilogue reads TMEM with
+// tcgen05.ld and writes C with element strides.
+//
+// Staging layouts.  A with k contiguous (A = Abar): box {32 k, 128 m, 1},
+// 128-byte rows with the 128-byte swizzle (16-byte chunk c of row r sits at
+// chunk c ^ (r mod 8)), so that threads taking consecutive rows read
+// distinct banks.  A with m contiguous (A = Abar^T): box {128 m, 32 k, 1},
+// rows of 128 m without swizzle (a thread reads one column).  B (k
+// contiguous): box {32 k, NP n, 1} with the 128-byte swizzle.  Every box
+// is a 3D view (inner, middle, batch), so rows past M, columns past N and
+// k past K read as zeros.
+//
+// SPLIT = 3: A_hi B_hi + A_hi B_lo + A_lo B_hi (products carry about 16
+// significant bits, FP32-form accuracy); SPLIT = 1: the plain BF16 form.
+//
+// Every mbarrier wait is bounded; on time-out the CTA records the failure
+// in *err, stops issuing work, waits (bounded) for its own copies and MMAs
+// and frees its TMEM before returning.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "umma_gemm.cuh"
+
+namespace tmag {
+
+constexpr int kThreads = 128;
+constexpr int kBM = 128;
+constexpr int kKC = 32;   // K elements per chunk: two MMAs of K = 16
+
+struct Args {
+  CUtensorMap amap;   // FP32 3D view of A: {K, M, nA} (k contiguous) or {M, K, nA}
+  CUtensorMap bmap;   // FP32 3D view of B: {K, N, batch}
+  int M, N, K;
+  int a_kcontig;      // 1: A's k is contiguous (A = Abar), 0: A's m is (A = Abar^T)
+  float *C;
+  int64_t sCb, sCi, sCn;
+  const int *ids = nullptr;    // optional batch indirection (as umma::Args)
+  const int *count = nullptr;
+  int a_by_id = 0, c_by_id = 0;
+};
+
+template <int NP, int STAGES, int SPLIT>
+struct Layout {
+  static constexpr int a_stage = kBM * kKC * 4;           // FP32 staging of A
+  static constexpr int b_stage = NP * kKC * 4;            // FP32 staging of B
+  static constexpr int stage = a_stage + b_stage;         // a multiple of 1024
+  static constexpr int a_conv = kBM * kKC * 2;            // one BF16 copy of A
+  static constexpr int b_conv = NP * kKC * 2;
+  static constexpr int conv = (a_conv + b_conv) * (SPLIT > 1 ? 2 : 1);
+  static constexpr int total = STAGES * stage + 2 * conv;
+  static_assert(stage % 1024 == 0, "swizzled staging tiles need 1024-byte alignment");
+};
+
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   umma::smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(umma::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(umma::smem_u32(bar))
+      : "memory");
+}
+
+// Eight FP32 values -> one 16-byte BF16 core-matrix row (hi) and its
+// remainder (lo).
+template <int SPLIT>
+__device__ __forceinline__ void put8(const float (&x)[8], uint8_t *hi, uint8_t *lo, int off) {
+  __align__(16) __nv_bfloat16 h[8];
+  __align__(16) __nv_bfloat16 l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) umma::split_bf16(x[e], h[e], l[e]);
+  *reinterpret_cast<uint4 *>(hi + off) = *reinterpret_cast<const uint4 *>(h);
+  if (SPLIT > 1) *reinterpret_cast<uint4 *>(lo + off) = *reinterpret_cast<const uint4 *>(l);
+}
+
+// Byte offset of row r, k-core c in a K-major core-matrix tile with kKC = 32
+// (four k-cores per 8-row group).
+__device__ __forceinline__ int core_off(int r, int c) { return ((r >> 3) * 4 + c) * 128 + (r & 7) * 16; }
+
+// Eight consecutive k (k-core c) of row r of a 128-byte-swizzled staging
+// tile (rows of 32 FP32).
+__device__ __forceinline__ void get8_swz(const uint8_t *tile, int r, int c, float (&x)[8]) {
+  const uint8_t *row = tile + r * 128;
+  const float4 v0 = *reinterpret_cast<const float4 *>(row + (((2 * c) ^ (r & 7)) << 4));
+  const float4 v1 = *reinterpret_cast<const float4 *>(row + (((2 * c + 1) ^ (r & 7)) << 4));
+  x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+  x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+}
+
+template <int NP, int STAGES, int SPLIT>
+__global__ void __launch_bounds__(kThreads)
+    gemm_kernel(const __grid_constant__ Args g, int *err) {
+  pdl_wait();
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t mdone[2];
+  __shared__ uint32_t tmem_base_s;
+  using Lay = Layout<NP, STAGES, SPLIT>;
+  constexpr int TMEM_COLS = NP < 32 ? 32 : NP;
+  // the dynamic window is aligned up to 1024 bytes (the launch reserves it)
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kBM;
+  const int b = blockIdx.z;
+  if (g.count && b >= *g.count) return;   // block-uniform, before any TMEM use
+  const int jb = g.ids ? g.ids[b] : b;
+  const int za = g.a_by_id ? jb : b;
+  float *C = g.C + (int64_t)(g.c_by_id ? jb : b) * g.sCb;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     umma::smem_u32(&tmem_base_s)),
+                 "r"((uint32_t)TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) umma::mbar_init(&full[s], 1);
+    umma::mbar_init(&mdone[0], 1);
+    umma::mbar_init(&mdone[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  const int nchunks = (g.K + kKC - 1) / kKC;
+  auto issue = [&](int c) {   // one thread: chunk c into staging stage c % STAGES
+    const int s = c % STAGES;
+    uint8_t *st = smem + s * Lay::stage;
+    expect_tx(&full[s], (uint32_t)Lay::stage);
+    if (g.a_kcontig) tma_load_3d(st, &g.amap, c * kKC, m0, za, &full[s]);
+    else tma_load_3d(st, &g.amap, m0, c * kKC, za, &full[s]);
+    tma_load_3d(st + Lay::a_stage, &g.bmap, c * kKC, 0, b, &full[s]);
+  };
+  if (tid == 0)
+    for (int c = 0; c < STAGES && c < nchunks; ++c) issue(c);
+  int issued = STAGES < nchunks ? STAGES : nchunks;   // meaningful in thread 0 only
+
+  constexpr uint32_t idesc = umma::idesc_bf16(kBM, NP);
+  constexpr uint32_t LBO = 128, SBO = (kKC / 8) * 128;
+  bool ok = true;
+  int done_chunks = 0;   // chunks whose MMAs were committed
+#pragma unroll 1
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c % STAGES, h = c & 1;
+    const bool wf = umma::mbar_wait(&full[s], (uint32_t)((c / STAGES) & 1));
+    // the MMAs that read conversion buffer h two chunks ago must be done
+    const bool wm = c >= 2 ? umma::mbar_wait(&mdone[h], (uint32_t)(((c - 2) >> 1) & 1)) : true;
+    if (!__syncthreads_and(wf && wm)) { ok = false; break; }
+    const uint8_t *sa = smem + s * Lay::stage;
+    const uint8_t *sb = sa + Lay::a_stage;
+    uint8_t *cv = smem + STAGES * Lay::stage + h * Lay::conv;
+    uint8_t *a_hi = cv, *b_hi = cv + Lay::a_conv;
+    uint8_t *a_lo = cv + Lay::a_conv + Lay::b_conv, *b_lo = a_lo + Lay::a_conv;
+    // A: thread t converts row t (four k-cores)
+    {
+      const int r = tid;
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        float x[8];
+        if (g.a_kcontig) {
+          get8_swz(sa, r, kc, x);
+        } else {
+          const float *col = reinterpret_cast<const float *>(sa) + r;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[e] = col[(kc * 8 + e) * kBM];
+        }
+        put8<SPLIT>(x, a_hi, a_lo, core_off(r, kc));
+      }
+    }
+    // B: NP rows x four k-cores
+#pragma unroll
+    for (int u = tid; u < NP * 4; u += kThreads) {
+      const int r = u % NP, kc = u / NP;
+      float x[8];
+      get8_swz(sb, r, kc, x);
+      put8<SPLIT>(x, b_hi, b_lo, core_off(r, kc));
+    }
+    umma::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      // staging stage s has been read by every thread: refill it
+      if (issued < nchunks) {
+        issue(issued);
+        ++issued;
+      }
+      umma::fence_after();
+#pragma unroll
+      for (int ks = 0; ks < kKC / 16; ++ks) {
+        const uint32_t off = ks * 2 * 128;   // two k-cores per MMA (K = 16)
+        const uint64_t dah = umma::smem_desc(umma::smem_u32(a_hi) + off, LBO, SBO);
+        const uint64_t dbh = umma::smem_desc(umma::smem_u32(b_hi) + off, LBO, SBO);
+        umma::mma_bf16(tmem, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        if (SPLIT > 1) {
+          const uint64_t dal = umma::smem_desc(umma::smem_u32(a_lo) + off, LBO, SBO);
+          const uint64_t dbl = umma::smem_desc(umma::smem_u32(b_lo) + off, LBO, SBO);
+          umma::mma_bf16(tmem, dah, dbl, idesc, 1u);
+          umma::mma_bf16(tmem, dal, dbh, idesc, 1u);
+        }
+      }
+      umma::mma_commit(&mdone[h]);
+    }
+    done_chunks = c + 1;
+  }
+  // wait for the last commit of each conversion buffer
+  bool fin = true;
+  for (int h = 0; h < 2; ++h) {
+    const int used = done_chunks > h ? (done_chunks - 1 - h) / 2 + 1 : 0;   // commits on buffer h
+    if (used > 0 && !umma::mbar_wait(&mdone[h], (uint32_t)((used - 1) & 1))) fin = false;
+  }
+  fin = __syncthreads_and(fin);
+  if (!ok || !fin) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // copies issued but never consumed: let them land before the CTA exits
+      for (int c = done_chunks; c < issued; ++c)
+        umma::mbar_wait(&full[c % STAGES], (uint32_t)((c / STAGES) & 1));
+    }
+  } else {
+    umma::fence_after();
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 32) {
+      float v[32];
+      umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < g.M) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c0 + c < g.N) C[(int64_t)row * g.sCi + (int64_t)(c0 + c) * g.sCn] = v[c];
+      }
+    }
+  }
+  pdl_trigger();
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)TMEM_COLS));
+}
+
+}  // namespace tmag

@@ -401,6 +401,34 @@ def test_slice_prox_tensor_core_forms(case, prec):
 
 
 @pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
+@pytest.mark.parametrize("case", [(4, 200, 196, 10, 1e-3, 20, 1, "mcp"),   # M tail 72, K tail 4
+                                  (3, 132, 100, 8, 1e-2, 48, 1, "l1"),     # 64-column tile
+                                  (2, 256, 64, 12, 1e-3, 32, 2, "l1"),     # whole tiles, q = 2
+                                  (5, 40, 36, 3, 0.0, 12, 1, "l1"),        # M < 128, K < 64
+                                  (3, 96, 320, 6, 1e-2, 24, 1, "mcp")])    # n2 > n1
+def test_slice_prox_tensor_core_tma_shapes(case, prec):
+    # shapes whose strides allow 3D tensor copies of Abar (n2 a multiple of
+    # 4) and of the panels (n1 a multiple of 4), with N <= 64: the products
+    # take the TMA-fed tcgen05 kernel, with zero-filled tails in M, N and K
+    n, n1, n2, r, noise, l, q, phi = case
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 * 5 + n2 + 3)
+    s1 = np.linalg.svd(Ab[0], compute_uv=False)[0]
+    tau = 0.2 * s1
+    kind = prox.L1 if phi == "l1" else prox.MCP
+    gamma = 3.0 * tau + 1.0
+    pen = tr.TR_PEN_L1 if phi == "l1" else tr.TR_PEN_MCP
+    A32 = as_dtype(Ab, "f32")
+    ref, _ = svt.transformed_prox(A32, tau, kind, 1.0, gamma, engine="rsvd", l=l, q=q, seed=41, t=6)
+    h = make_handle((n1, n2, n), "f32", rank=l, oversample=0, power_iters=q, phi=pen,
+                    phi_gamma=gamma, seed=41, prec=prec)
+    G = host(h.slice_prox(dev(Ab, "f32"), tau, t=6))
+    h.close()
+    err = relF(G, ref)
+    assert err < PREC_TOL[prec], err
+    assert np.abs(G - ref).max() < PREC_TOL[prec] * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
 def test_step_tensor_core_forms(prec):
     # The BF16 form keeps the sketch in BF16: its subspace matches the FP32
     # one only where the transformed slices' spectra decay beyond the sketch

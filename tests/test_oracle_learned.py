@@ -189,14 +189,52 @@ def test_plan_widths_edge_values():
     assert c.tolist() == [2]
 
 
-def test_threshold_and_certificate():
+def test_threshold():
     assert lo.threshold(0.5, "l1", 2.0) == 1.0
     assert lo.threshold(0.5, "mcp", 2.0, 4.0) == 1.0
     assert lo.threshold(9.0, "mcp", 1.0, 4.0) == 6.0
-    # kept rank > width - p below lmax: 7 > 6 and 20 > 14 are saturated,
-    # 7 <= 14 is not, and a slice already at lmax never is
-    sat = lo.saturated([7, 7, 20, 3], [16, 24, 24, 40], 10, 40)
-    assert sat.tolist() == [0, 2]
+
+
+def test_judge_worked_example():
+    # A = diag(3, 4): ||A||^2 = 25.  A basis that captures the 4 misses
+    # E = 9: rejected at eps = 0.5 (9 >= 0.25 * 25), kept at eps = 0.7
+    # (9 < 0.49 * 25); a basis capturing both misses nothing; A = 0 is kept;
+    # here the shrink kept 1 of width 1 (no margin at p = 1), cap 4
+    def J(a2, sig, eps, rank=(1,), width=(1,), p=1, kcap=4):
+        return lo.judge(a2, sig, eps, rank, width, p, kcap).tolist()
+
+    assert J([25.0], [[4.0]], 0.5) == [0]
+    assert J([25.0], [[4.0]], 0.7) == []
+    assert J([25.0, 0.0], [[4.0, 3.0], [0.0]], 1e-3, (1, 0), (1, 1)) == []
+    # the boundary itself fails the strict test: E = eps^2 ||A||^2
+    assert J([25.0], [[4.0]], 0.6) == [0]
+    # the oversampling margin (kept rank <= width - p) or a width at the
+    # adaptive cap keeps a sketch that misses energy
+    assert J([25.0], [[4.0]], 0.5, (1,), (2,)) == []
+    assert J([25.0], [[4.0]], 0.5, (1,), (1,), 1, 1) == []
+    assert J([25.0], [[4.0]], 0.5, (2,), (2,)) == [0]
+
+
+def test_judge_is_the_projection_error_test():
+    # E = ||A||^2 - ||Q^T A||^2 equals ||A - Q Q^T A||^2 for orthonormal Q
+    # (Pythagoras), so the judge takes Alg. 3's decision computed directly
+    rng = np.random.default_rng(7)
+    eps = 0.1
+    a2, sig, direct = [], [], []
+    for j in range(40):
+        n1, n2, r, l = 30, 24, int(rng.integers(1, 12)), int(rng.integers(1, 14))
+        A = rng.standard_normal((n1, r)) @ rng.standard_normal((r, n2))
+        A += 10.0 ** rng.uniform(-4, -1) * rng.standard_normal((n1, n2))
+        Q, _ = np.linalg.qr(A @ rng.standard_normal((n2, l)))
+        res = np.linalg.norm(A - Q @ (Q.T @ A)) ** 2
+        a2.append(np.linalg.norm(A) ** 2)
+        sig.append(np.linalg.svd(Q.T @ A, compute_uv=False))
+        direct.append(not (res < eps * eps * a2[-1]))
+    n = len(a2)
+    # no margin (kept rank = width) and no cap: Alg. 3's test alone decides
+    got = set(lo.judge(a2, sig, eps, [9] * n, [9] * n, 1, 10 ** 9).tolist())
+    assert got == {j for j, d in enumerate(direct) if d}
+    assert 0 < len(got) < 40
 
 
 def test_width_plan_and_feature_invariants_property():

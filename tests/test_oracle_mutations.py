@@ -56,6 +56,8 @@ MUTANTS = [
      "E -= 0.0 * float(np.sum(Lt * Lt))"),
     ("svt-blbp-sign-of-U-L", "svt", "defl_qr(A @ V - U_prev @ L, delta)",
      "defl_qr(A @ V + U_prev @ L, delta)"),
+    ("svt-learned-no-fallback", "svt", "            if j in set(fb.tolist()):",
+     "            if j in set():"),
     ("svt-forward-for-inverse", "svt", "out = transform.inverse(Gbar, tdims, transform_kind)",
      "out = transform.forward(Gbar, tdims, transform_kind)"),
     # the pure-L ADMM step (Alg. 5)
@@ -71,8 +73,12 @@ MUTANTS = [
     ("learned-adam-no-v-bias-correction", "learned", "vhat = v / (1.0 - beta2 ** step)",
      "vhat = v"),
     ("learned-width-rounded-down", "learned", "l = (r + p + 7) // 8 * 8", "l = (r + p) // 8 * 8"),
-    ("learned-certificate-ignores-oversampling", "learned", "(rank > width - p)",
-     "(rank > width)"),
+    ("learned-judge-eps-not-squared", "learned", "a2 - cap < eps * eps * a2",
+     "a2 - cap < eps * a2"),
+    ("learned-judge-missed-energy-sign", "learned", "a2 - cap < eps * eps * a2",
+     "a2 + cap < eps * eps * a2"),
+    ("learned-judge-margin-ignores-oversampling", "learned", "margin = rank[j] <= width[j] - p",
+     "margin = rank[j] <= width[j]"),
     # shared and fixed-accuracy Tucker forms (Alg. 1, Alg. AD-RSTHOSVD-BLBP)
     ("tucker-transposed-mode-product", "tucker", '"jia,ba->jib", C, F', '"jia,ab->jib", C, F'),
     ("tucker-trailing-singular-vectors", "tucker", "return canonical_signs(Z @ U[:, :r]), Z",

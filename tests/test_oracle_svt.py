@@ -217,3 +217,30 @@ def test_adaptive_basis_finds_the_rank_property():
         assert np.abs(G - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
 
     check()
+
+
+@pytest.mark.parametrize("kind", [prox.L1, prox.MCP])
+def test_learned_engine_exact_for_any_widths_on_low_rank_slices(kind):
+    # Exactly low-rank slices: a sketch at least as wide as the rank captures
+    # the slice (E = 0, kept by Alg. 3's test), a narrower one misses energy
+    # and keeps its whole width (no oversampling margin, below the cap), so
+    # it is rejected and the adaptive engine finds the exact rank.  Either
+    # way each slice's prox is the deterministic one, and the rejected
+    # slices are exactly those sketched below their rank.
+    ranks = [3, 9, 5, 12, 1, 7]
+    Ab = synth.lowrank_plus_noise_stack(6, 40, 32, ranks, 0.0, seed=31)
+    widths = [8, 8, 16, 8, 8, 16]
+    tau = 0.3
+    full, _ = svt.transformed_prox(Ab, tau, kind, 1.0, 5.0, engine="full")
+    got, info = svt.transformed_prox(Ab, tau, kind, 1.0, 5.0, engine="learned", widths=widths,
+                                     q=1, seed=4, t=2, eps=1e-3, b=4, delta_rel=1e-11,
+                                     max_rank=24, p=4)
+    assert np.linalg.norm(got - full) <= 1e-10 * np.linalg.norm(full)
+    assert info["fallback"].tolist() == [1, 3]
+    # rejected slices take the adaptive basis (the rank), kept ones the sketch
+    assert info["widths"].tolist() == [8, 9, 16, 12, 8, 16]
+    # a cap at the narrowest width keeps every sketch
+    _, info = svt.transformed_prox(Ab, tau, kind, 1.0, 5.0, engine="learned", widths=widths,
+                                   q=1, seed=4, t=2, eps=1e-3, b=4, delta_rel=1e-11,
+                                   max_rank=8, p=4)
+    assert info["fallback"].tolist() == []
