@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-models", action="store_true",
                     help="skip the gradient-domain and one-bit ADMM steps and the "
                          "fixed-accuracy Tucker prox")
+    ap.add_argument("--slice-kernels", action="store_true",
+                    help="take --warmup eager steps of the workload, time every kernel of one "
+                         "slice pass on the iterate, print them and exit (a small, short case "
+                         "for kernel profilers)")
     ap.add_argument("--learned-iters", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=8)
     return ap.parse_args()
@@ -970,10 +974,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def slice_kernels(args):
+    """Per-kernel device times of one slice pass of the workload's iterate
+    after `warmup` eager steps (few launches, one handle: a case for ncu)."""
+    import torch
+    from paper_2506_09594_gb300 import synth, tr
+    tr.load()
+    w = synth.WORKLOADS[args.workload]
+    _, M, mask, _ = synth.make_problem(w)
+    dt = torch.float64 if w.dtype == "f64" else torch.float32
+    Md = torch.from_numpy(M).to("cuda", dt)
+    maskd = torch.from_numpy(mask).cuda()
+    prec = PREC[args.prec] if w.dtype != "f64" else 0
+    stream = torch.cuda.Stream()
+    h = make_handle(tr, torch, w, Md, maskd, stream, 0, prec)
+    for _ in range(args.warmup):
+        h.step()
+    s = h.get_state()
+    X = (s["L"] + s["Lam"] / s["mu"]).contiguous()
+    torch.cuda.synchronize()
+    Ab = h.transform_forward(X)
+    kern = h.profile_slice_pass(Ab, 1.0 / s["mu"], s["t"], reps=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "iteration": s["t"], "prec": args.prec,
+                      "kernels_us": [[k, ms * 1e3] for k, ms in kern]}))
+    h.close()
+
+
 def main():
     args = parse()
     if args.cpu_child:
         cpu_child(args)
+        return
+    if args.slice_kernels:
+        slice_kernels(args)
         return
     if args.impl == "reference":
         run_reference(args)
