@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-engine", default="rsvd", choices=["rsvd", "full"],
+                    help=argparse.SUPPRESS)
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16", "bf16x3"],
                     help="precision of the chosen form's slice products (default: split "
                          "BF16, the form whose stated bound is the metric's 1e-4)")
@@ -50,6 +52,8 @@ def parse():
                     help="skip the batch of 64 uneven problems")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the precision forms on the 1024x1024x64 workload")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the 64x64x16 FP64 workload")
     ap.add_argument("--no-tucker", action="store_true",
                     help="skip the shared-Tucker prox (Alg. 1 + Alg. 4) timing")
     ap.add_argument("--no-models", action="store_true",
@@ -91,15 +95,18 @@ def dist_env():
 
 
 # ------------------------------------------------------------ CPU oracle leg
-def oracle_steps(workload, budget_s, max_steps, warmup=0):
-    """Time the FP64 oracle's ADMM iteration on the workload (host cores)."""
+def oracle_steps(workload, budget_s, max_steps, warmup=0, engine="rsvd"):
+    """Time the FP64 oracle's ADMM iteration on the workload (host cores);
+    engine "rsvd" is the randomized prox of the GPU path, "full" the
+    deterministic GNHTSVT (a full SVD of every transformed slice)."""
     import numpy as np
     from oracle import admm
     from paper_2506_09594_gb300 import synth
     w = synth.WORKLOADS[workload]
     _, M, mask, _ = synth.make_problem(w)
-    p = admm.Params(lam=admm.default_lambda(w.n1, w.n2, w.tdims), engine="rsvd", l=w.l, q=w.q,
-                    seed=w.seed)
+    p = admm.Params(lam=admm.default_lambda(w.n1, w.n2, w.tdims), engine=engine, l=w.l, q=w.q,
+                    seed=w.seed, noise=admm.NOISE_NONE if w.noise_model == "none"
+                    else admm.NOISE_L1)
     st = admm.init_state(M.shape, p.mu0)
     for _ in range(warmup):
         st, _ = admm.step(st, M, mask, w.tdims, p)
@@ -114,28 +121,33 @@ def oracle_steps(workload, budget_s, max_steps, warmup=0):
 
 
 def cpu_child(args):
-    done, el = oracle_steps(args.workload, args.cpu_seconds, 1000)
+    done, el = oracle_steps(args.workload, args.cpu_seconds, 1000, engine=args.cpu_engine)
     print(json.dumps({"steps": done, "seconds": el}))
 
 
-def cpu_baseline(workload, seconds):
-    """Run the oracle in a child process with every host core available."""
-    cores = os.cpu_count() or 1
+def cpu_baseline(workload, seconds, cores=None, engine="rsvd"):
+    """Run the oracle in a child process with `cores` BLAS threads (default:
+    every host core)."""
+    from paper_2506_09594_gb300 import synth
+    w = synth.WORKLOADS[workload]
+    cores = cores or os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
     env["CUDA_VISIBLE_DEVICES"] = ""
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", "--workload",
-                          workload, "--cpu-seconds", str(seconds)],
+                          workload, "--cpu-seconds", str(seconds), "--cpu-engine", engine],
                          capture_output=True, text=True, env=env, timeout=600)
     line = [l for l in out.stdout.splitlines() if l.startswith("{")]
     if out.returncode != 0 or not line:
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": "failed: " + out.stderr[-300:]}
     r = json.loads(line[-1])
+    what = ("randomized engine l=%d q=%d" % (w.l, w.q) if engine == "rsvd"
+            else "deterministic engine: full SVD of every transformed slice")
     return {"value": r["steps"] / r["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d full ADMM iterations of %s (numpy float64, randomized engine "
-                      "l=20 q=1), %.1f s" % (r["steps"], workload, r["seconds"])}
+            "sample": "%d full ADMM iterations of %s (numpy float64, %s), %.1f s"
+                      % (r["steps"], workload, what, r["seconds"])}
 
 
 # ------------------------------------------------------------ clock sampler
@@ -609,8 +621,18 @@ def run_ours(args):
         if not args.no_models and world == 1:
             line["models"] = models_section(tr, torch, 20)
             torch.cuda.empty_cache()
+        if not args.no_small and world == 1:
+            line["small"] = small_section(tr, torch, K, W, args.no_cpu_baseline)
+            torch.cuda.empty_cache()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+            # the rest of the CPU plan: the same oracle on one core, and the
+            # deterministic (full-SVD) oracle, on bounded samples
+            line["cpu_baseline"]["one_core"] = cpu_baseline(args.workload,
+                                                            args.cpu_seconds / 2, cores=1)
+            line["cpu_baseline"]["deterministic"] = cpu_baseline(args.workload,
+                                                                 args.cpu_seconds / 2,
+                                                                 engine="full")
             # the timed forms against the FP64 oracle on the same two steps
             line["oracle_parity"] = oracle_parity(w, M, mask, ch["parity"], 1e-4)
             if alt is not None:
@@ -619,6 +641,34 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def small_section(tr, torch, K, W, no_cpu):
+    """The small workload (64x64x16 FP64, tubal rank 5, 50% observed,
+    noise-free, l = 15, q = 1): the graph-replayed FP64 form timed like the
+    headline, its oracle parity (two steps from the state after the timed
+    steps, stated bound 1e-10 for FP64), and the oracle's own rate on all
+    cores and on one, randomized and deterministic (these runs are short)."""
+    import numpy as np
+    from paper_2506_09594_gb300 import synth
+    w = synth.WORKLOADS["tubal64_r5"]
+    X, M, mask, _ = synth.make_problem(w)
+    Md = torch.from_numpy(M).to("cuda", torch.float64)
+    maskd = torch.from_numpy(mask).cuda()
+    Xd = torch.from_numpy(X).to("cuda", torch.float64)
+    stream = torch.cuda.Stream()
+    h, r = time_form(tr, torch, None, w, Md, maskd, Xd, stream, 0, 1, 0, K, W, chosen=True)
+    h.close()
+    out = {"workload": w.name, "dims": list(w.dims), "dtype": "f64",
+           "value": K / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / K,
+           "form": "fp64 simt, graph replay, autotuned tube tile and slice split",
+           "recovery_rel_err": r["recovery_rel_err"], "gpu_launches": int(r["launches"])}
+    if not no_cpu:
+        out["oracle_parity"] = oracle_parity(w, M, mask, r["parity"], 1e-10)
+        out["cpu_baseline"] = cpu_baseline(w.name, 5.0)
+        out["cpu_baseline"]["one_core"] = cpu_baseline(w.name, 5.0, cores=1)
+        out["cpu_baseline"]["deterministic"] = cpu_baseline(w.name, 5.0, engine="full")
+    return out
 
 
 def learned_ab(tr, torch, iters, prec):
@@ -847,9 +897,16 @@ def precision_forms(tr, torch, K):
             h.step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        # phases of a few eager steps (tube pass, slice pass)
+        h.profile_enable(3)
+        for _ in range(3):
+            h.step()
+        ph = h.profile_read()
         L = h.get_L()
         Ls[name] = L
         out[name] = {"ms_per_step": ev0.elapsed_time(ev1) / K,
+                     "phases_ms": {"tube_forward": ph["tube_forward"],
+                                   "slice_pass": ph["slice_pass"]},
                      "recovery_rel_err": float(torch.linalg.norm((L - Xd).double())
                                                / torch.linalg.norm(Xd.double()))}
         h.close()

@@ -151,13 +151,24 @@ tr_status tr_init(tr_handle **h, const tr_problem *p, const tr_params *prm,
 
 /* One ADMM iteration (steps 1-5 above) on the handle's state.  Asynchronous
  * unless `info` is non-NULL.  Errors: TR_EINVAL (poisoned), TR_ENUMERIC
- * (NaN/Inf, only detectable when info != NULL), TR_ECUDA.                   */
+ * (NaN/Inf in the tube pass's reduction: reported by this call when info is
+ * non-NULL; a step without a report, graph replays included, copies its flag
+ * to pinned host memory without synchronising, and a later call returns
+ * TR_ENUMERIC once the copy has landed -- at the latest the first call after
+ * the step has completed), TR_ECUDA.                                        */
 tr_status tr_prox_step(tr_handle *h, tr_step_info *info);
 
-/* Alg. 5 loop: steps until max(res_inf) <= tol (checked every step when
- * tol > 0, which synchronises each step) or max_iter steps were taken, then
- * copies L to `L_out` (device, N elements, caller-owned; may be NULL).
- * Returns TR_ENOTCONV when tol > 0 and max_iter was reached.                */
+/* Alg. 5 loop, stop test of Eq. convercon.  tol <= 0: max_iter steps (graph
+ * replays when tr_graph_mode is on).  tol > 0: steps are enqueued without a
+ * report and their residual maxima read back asynchronously; step k's five
+ * maxima are complete after step k + 1 (its deferred inverse pass), so the
+ * host checks step k after enqueuing step k + 2 and waits only for step
+ * k + 1: the GPU never idles.  The loop stops at the first step whose maxima
+ * are all <= tol; the iterate returned is at most two steps past it.  Then L
+ * is copied to `L_out` (device, N elements, caller-owned; may be NULL) and
+ * `last` (may be NULL) receives the returned iterate's residual maxima and
+ * iteration count.  Returns TR_ENOTCONV when tol > 0 and neither a checked
+ * step nor the returned iterate met tol within max_iter steps.             */
 tr_status tr_recover(tr_handle *h, void *L_out, tr_step_info *last);
 
 /* Copy the iterate out of / into the handle.  Each pointer is a device

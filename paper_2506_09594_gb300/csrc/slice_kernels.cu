@@ -327,7 +327,18 @@ cudaError_t tma_gemm(const GemmArgs &g, int batch, int nA, int split, int *err, 
   a.count = g.sel.count;
   a.a_by_id = g.a_by_id;
   a.c_by_id = g.c_by_id;
-  const dim3 grid((g.M + tmag::kBM - 1) / tmag::kBM, 1, batch);
+  a.batch = batch;
+  // persistent: two CTAs per SM (their shared memory allows two), or one per
+  // tile when there are fewer tiles
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  const int64_t tiles = (int64_t)((g.M + tmag::kBM - 1) / tmag::kBM) * batch;
+  const dim3 grid((unsigned)(tiles < 2 * sms ? tiles : 2 * sms), 1, 1);
   *used = true;
 #define TR_TMAG(NP, ST, SP)                                                                    \
   {                                                                                            \
@@ -466,7 +477,8 @@ struct RegPanel {
 
 // QR of the panel P (global, column-major m x l, ld m): R (l x l, column-
 // major, zero below the diagonal) to Rout when non-null, Q overwrites P.
-template <typename T, int CPW, int RPL>
+// FORM_Q = false stops after R (P is left as it was).
+template <typename T, int CPW, int RPL, bool FORM_Q = true>
 __device__ void block_reg_qr(T *P, int m, int l, T *V, T *tau, T *Rout) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   RegPanel<T, CPW, RPL> pn;
@@ -496,6 +508,7 @@ __device__ void block_reg_qr(T *P, int m, int l, T *V, T *tau, T *Rout) {
       }
     }
   }
+  if (!FORM_Q) return;
   // form Q in registers: start from [I; 0] on the owned columns
 #pragma unroll
   for (int q = 0; q < CPW; ++q) {
@@ -551,7 +564,7 @@ __device__ __forceinline__ void smem_apply(const T *v, T tk, T *col, int k, int 
 
 // QR of P (global, column-major m x l, ld m) through the shared panel S
 // (m * l) and tau (l): R to Rout when non-null, Q overwrites P.
-template <typename T>
+template <typename T, bool FORM_Q = true>
 __device__ void block_smem_qr(T *P, int m, int l, T *S, T *tau, T *Rout) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < m * l; e += blockDim.x) S[e] = P[e];
@@ -573,6 +586,7 @@ __device__ void block_smem_qr(T *P, int m, int l, T *S, T *tau, T *Rout) {
       const int i = e % l, c = e / l;
       Rout[e] = i <= c ? S[(size_t)c * m + i] : T(0);
     }
+  if (!FORM_Q) return;
   for (int k = l - 1; k >= 0; --k) {
     const T tk = tau[k];
     const T *v = S + (size_t)k * m;
@@ -901,8 +915,13 @@ __device__ __forceinline__ T prox_sv(T s, const ShrinkScalars &sh) {
   return s > th * sqrt(ga * tau) ? s : T(0);
 }
 
-// Per slice: QR of B^T (P2), Jacobi SVD of R, shrink, core C, then
-// P1 <- P1 C (= Q C) and P2 <- Qb, ready for Gbar = P1 P2^T.
+// Per slice: R of B^T = Qb R (P2 holds B^T = Abar^T Q), one-sided Jacobi of
+// R (R J = W with orthogonal columns: B = J Sigma W_n^T Qb^T, so B's left
+// singular vectors are the columns of J and sigma the column norms of W),
+// the shrink, the core C = J diag(shrunk sigma / sigma) J^T, and P1 <- P1 C
+// (= Q C).  Since J diag(sigma~) V_B^T = J diag(sigma~/sigma) J^T B, the
+// rebuild is Gbar = (Q C) B = P1 P2^T with P2 left as B^T: Qb is never
+// formed.  A singular value shrunk to zero drops out (ratio 0).
 template <typename T, int CPW, int RPL, int G, int JR, bool REG>
 __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64_t sP1,
                                 T *__restrict__ P2, int64_t sP2, ShrinkScalars sh,
@@ -928,9 +947,9 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   T *P2j = P2 + (int64_t)bb * sP2;
 
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) J[e] = (e % l == e / l) ? T(1) : T(0);
-  // B^T = Qb R: Qb overwrites P2, R lands in W
-  if constexpr (REG) block_reg_qr<T, CPW, RPL>(P2j, n2, l, panel, tau, W);
-  else block_smem_qr<T>(P2j, n2, l, panel, tau, W);
+  // B^T = Qb R: R lands in W, P2 keeps B^T
+  if constexpr (REG) block_reg_qr<T, CPW, RPL, false>(P2j, n2, l, panel, tau, W);
+  else block_smem_qr<T, false>(P2j, n2, l, panel, tau, W);
   // Rotate only while a pair's cosine exceeds max(l, 8) * eps: below that the
   // computed inner product is rounding noise (an l-term dot product).
   const T eps = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
@@ -965,11 +984,11 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     if (width_out) width_out[j] = l;
   }
   for (int i = l + threadIdx.x; i < ldsig; i += blockDim.x) sig_out[(int64_t)j * ldsig + i] = T(0);
-  // C[a][b] = sum_i J[a][i] ratio_i W[b][i]   (column-major C[a + b*l])
+  // C[a][b] = sum_i J[a][i] ratio_i J[b][i]   (column-major C[a + b*l])
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int a = e % l, b = e / l;
     T acc = T(0);
-    for (int i = 0; i < l; ++i) acc = fma(J[(size_t)i * l + a] * ratio[i], W[(size_t)i * l + b], acc);
+    for (int i = 0; i < l; ++i) acc = fma(J[(size_t)i * l + a] * ratio[i], J[(size_t)i * l + b], acc);
     C[e] = acc;
   }
   for (int e = threadIdx.x; e < n1 * l; e += blockDim.x) panel[e] = P1j[e];

@@ -62,6 +62,12 @@ struct tr_handle {
   unsigned long long *res = nullptr;          // RES_COUNT slots
   unsigned long long *res_prev = nullptr;     // slots for a deferred inverse pass
   int *flags = nullptr;
+  // pinned host copy of `flags`, written by every step (replays included)
+  // without a host synchronisation; a later call reads it
+  volatile int *flags_host = nullptr;
+  // pinned ring of residual reads for tr_recover's lagged stop test
+  double *rec_ring = nullptr;
+  cudaEvent_t rec_ev[3] = {};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // instrumentation
   std::vector<cudaEvent_t> prof_ev;   // 4 per profiled step
@@ -179,6 +185,10 @@ static void free_all(tr_handle *h) {
     if (b) cudaFree(b);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->flags_host) cudaFreeHost((void *)h->flags_host);
+  if (h->rec_ring) cudaFreeHost(h->rec_ring);
+  for (cudaEvent_t e : h->rec_ev)
+    if (e) cudaEventDestroy(e);
 }
 
 // Weights file: "TRRANK01", int32 16, 128, 3, 0, int64 count, count float32.
@@ -413,6 +423,12 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   INIT_CUDA(cudaMalloc((void **)&h->res, RES_COUNT * sizeof(unsigned long long)));
   INIT_CUDA(cudaMalloc((void **)&h->res_prev, RES_COUNT * sizeof(unsigned long long)));
   INIT_CUDA(cudaMalloc((void **)&h->flags, sizeof(int)));
+  {
+    void *fh = nullptr;
+    INIT_CUDA(cudaHostAlloc(&fh, sizeof(int), cudaHostAllocDefault));
+    h->flags_host = static_cast<volatile int *>(fh);
+    *h->flags_host = 0;
+  }
   INIT_CUDA(cudaMalloc((void **)&sw.err, sizeof(int)));
   INIT_CUDA(cudaMemsetAsync(sw.err, 0, sizeof(int), h->stream));
   sw.prec = (int)prm->prec;
@@ -616,7 +632,10 @@ static tr_status read_info(tr_handle *h, double mu_used, tr_step_info *info) {
 // last step, so that the handle's state is the complete iterate.
 static tr_status finalize(tr_handle *h) {
   if (!h->pending) return TR_OK;
-  cudaError_t e = launch_tube_inverse(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->L,
+  // the inverse pass's residual slots: ||L - G|| and ||dG|| of the last step
+  cudaError_t e = cudaMemsetAsync(h->res_prev, 0, RES_COUNT * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess)
+    e = launch_tube_inverse(h->dtype, h->P, (int)h->n, h->td, h->mats, h->Gbar, h->L,
                                       h->G, h->Lam, h->mu_prev, &h->sched->mu_prev, h->res_prev,
                                       h->flags, h->stream);
   if (e != cudaSuccess) {
@@ -653,6 +672,11 @@ static tr_status enqueue_step(tr_handle *h, bool pending, bool with_inverse, cud
       e = launch_tube_forward(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->mask, h->L,
                               h->E, h->Y, h->G, h->Lam, h->Abar, sc, h->res, h->flags, h->stream);
   }
+  // the NaN/Inf flag of this tube pass goes to pinned host memory, so that
+  // steps without a report (graph replays) are checked by a later call
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)h->flags_host, h->flags, sizeof(int), cudaMemcpyDeviceToHost,
+                        h->stream);
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[1], h->stream);
   if (e != cudaSuccess) return fail(h, TR_ECUDA, "tube forward: %s", cudaGetErrorString(e));
   h->launches += 1;
@@ -759,6 +783,10 @@ static tr_status replay_step(tr_handle *h) {
 extern "C" tr_status tr_prox_step(tr_handle *h, tr_step_info *info) {
   if (!h) return TR_EINVAL;
   if (h->poisoned) return fail(h, TR_EINVAL, "handle poisoned by an earlier failure; call tr_set_state");
+  if (*h->flags_host) {   // an earlier step without a report met NaN or Inf
+    h->poisoned = true;
+    return fail(h, TR_ENUMERIC, "NaN or Inf in the iterate, found after iteration %d", h->t);
+  }
   const double mu = h->mu;
   auto guard = [&](tr_status st) {
     if (st != TR_OK) h->poisoned = true;
@@ -793,26 +821,100 @@ extern "C" tr_status tr_graph_mode(tr_handle *h, int on) {
   return TR_OK;
 }
 
+// The complete residual vector (Eq. convercon) of step k: its own slots
+// from the read after step k, its deferred ||L - G|| and ||dG|| from the read
+// after step k + 1 (tr_read_residuals layout).
+static double residual_max(const double *own, const double *next) {
+  double mx = 0.0;
+  for (int i = 0; i < RES_COUNT; ++i) {
+    const double v = (i == RES_LG || i == RES_DG) ? next[RES_COUNT + i] : own[i];
+    mx = v > mx ? v : mx;
+  }
+  return mx;
+}
+
 extern "C" tr_status tr_recover(tr_handle *h, void *L_out, tr_step_info *last) {
   if (!h) return TR_EINVAL;
   tr_step_info info{};
   const bool check = h->prm.tol > 0.0;
   bool converged = false;
-  for (int it = 0; it < h->prm.max_iter; ++it) {
-    tr_status st = tr_prox_step(h, (check || (last && it == h->prm.max_iter - 1)) ? &info : nullptr);
-    if (st != TR_OK) return st;
-    if (check) {
-      double mx = 0;
-      for (double v : info.res_inf) mx = v > mx ? v : mx;
-      if (mx <= h->prm.tol) {
-        converged = true;
-        break;
+  if (!check) {
+    for (int it = 0; it < h->prm.max_iter; ++it) {
+      tr_status st = tr_prox_step(h, (last && it == h->prm.max_iter - 1) ? &info : nullptr);
+      if (st != TR_OK) return st;
+    }
+    tr_status fs = finalize(h);
+    if (fs != TR_OK) return fs;
+    if (L_out) {
+      TR_CUDA(h, cudaMemcpyAsync(L_out, h->L, (size_t)h->N * h->esz, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+      TR_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    if (last) *last = info;
+    return TR_OK;
+  } else {
+    // Steps are enqueued without a report (graph replays when tr_graph_mode
+    // is on), each followed by an asynchronous read of its residuals into a
+    // pinned ring of three.  Step k's residuals are complete once step k + 1
+    // has run, so after enqueuing step k + 2 the host waits only for step
+    // k + 1's read: the GPU always has a step queued.  The loop stops at the
+    // first step whose residuals all meet tol; the iterate returned is then
+    // at most two steps past it.
+    if (!h->rec_ring) {
+      TR_CUDA(h, cudaHostAlloc((void **)&h->rec_ring, 3 * 2 * RES_COUNT * sizeof(double),
+                               cudaHostAllocDefault));
+      for (auto &e : h->rec_ev) TR_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    int done = 0;   // steps enqueued
+    for (int it = 0; it < h->prm.max_iter && !converged; ++it) {
+      tr_status st = tr_prox_step(h, nullptr);
+      if (st != TR_OK) return st;
+      st = tr_read_residuals(h, h->rec_ring + 2 * RES_COUNT * (it % 3));
+      if (st != TR_OK) return st;
+      TR_CUDA(h, cudaEventRecord(h->rec_ev[it % 3], h->stream));
+      done = it + 1;
+      if (it >= 2) {
+        const int k = it - 2;   // the step whose residuals are now complete
+        TR_CUDA(h, cudaEventSynchronize(h->rec_ev[(k + 1) % 3]));
+        if (*h->flags_host) {
+          h->poisoned = true;
+          return fail(h, TR_ENUMERIC, "NaN or Inf in the iterate, found after iteration %d", h->t);
+        }
+        const double mx = residual_max(h->rec_ring + 2 * RES_COUNT * (k % 3),
+                                       h->rec_ring + 2 * RES_COUNT * ((k + 1) % 3));
+        if (mx <= h->prm.tol) converged = true;
       }
     }
+    (void)done;
   }
   {
     tr_status fs = finalize(h);
     if (fs != TR_OK) return fs;
+  }
+  TR_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (*h->flags_host) {
+    h->poisoned = true;
+    return fail(h, TR_ENUMERIC, "NaN or Inf in the iterate, found after iteration %d", h->t);
+  }
+  {
+    // the residuals of the returned iterate: its own slots and the deferred
+    // ones its finalising inverse pass wrote
+    unsigned long long r[RES_COUNT], rp[RES_COUNT];
+    TR_CUDA(h, cudaMemcpy(r, h->res, sizeof r, cudaMemcpyDeviceToHost));
+    TR_CUDA(h, cudaMemcpy(rp, h->res_prev, sizeof rp, cudaMemcpyDeviceToHost));
+    double mx = 0.0;
+    for (int i = 0; i < RES_COUNT; ++i) {
+      double v, vp;
+      memcpy(&v, &r[i], sizeof v);
+      memcpy(&vp, &rp[i], sizeof vp);
+      if (i == RES_LG || i == RES_DG) v = v > vp ? v : vp;
+      info.res_inf[i] = v;
+      mx = v > mx ? v : mx;
+    }
+    info.iter = h->t;
+    info.mu = h->mu_prev;
+    info.tau = 1.0 / h->mu_prev;
+    if (mx <= h->prm.tol) converged = true;
   }
   if (L_out) {
     TR_CUDA(h, cudaMemcpyAsync(L_out, h->L, (size_t)h->N * h->esz, cudaMemcpyDeviceToDevice, h->stream));
@@ -862,6 +964,7 @@ extern "C" tr_status tr_set_state(tr_handle *h, const void *L, const void *E, co
   h->poisoned = false;
   h->pending = false;
   h->lw.have_hist = false;
+  *h->flags_host = 0;
   return TR_OK;
 }
 

@@ -2,12 +2,14 @@
 // copies (TMA), for the products of the slice pass with the transformed
 // slices (Y = Abar X, W = Abar^T Q; Alg. 1's sketch and power steps).
 //
-// C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out, N <= 64.  One
-// CTA (4 warps) owns a 128-row tile of one batch entry.  K is consumed in
-// chunks of 32: one thread keeps STAGES chunks of both operands in flight
-// as 3D tensor copies (cp.async.bulk.tensor.3d, completion counted on an
-// mbarrier) into FP32 staging tiles, so the HBM latency of a chunk overlaps
-// the work on the chunks before it.  The 128 threads convert a landed chunk
+// C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out, N <= 64.  The
+// work is a list of 128-row tiles (batch entry, row block); a persistent CTA
+// (8 warps, two per SM) takes every gridDim-th tile and streams their K
+// chunks of 32 as one sequence: one thread keeps STAGES chunks of both
+// operands in flight as 3D tensor copies (cp.async.bulk.tensor.3d,
+// completion counted on an mbarrier) into FP32 staging tiles, so the HBM
+// latency of a chunk -- the next tile's first ones included -- overlaps the
+// work on the chunks before it.  The 256 threads convert a landed chunk
 // to BF16 (x = hi + lo, both BF16, for the split form) in the canonical
 // K-major core-matrix layout without swizzle (8-row x 16-byte core
 // matrices, leading byte offset 128, stride byte offset 512), and one
@@ -25,6 +27,9 @@
 // is a 3D view (inner, middle, batch), so rows past M, columns past N and
 // k past K read as zeros.
 //
+// Eight warps convert; the tcgen05.ld epilogue runs in warps 0-3, whose lane
+// quarters cover the accumulator's 128 lanes.
+//
 // SPLIT = 3: A_hi B_hi + A_hi B_lo + A_lo B_hi (products carry about 16
 // significant bits, FP32-form accuracy); SPLIT = 1: the plain BF16 form.
 //
@@ -41,7 +46,7 @@
 
 namespace tmag {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;   // 8 warps convert; warps 0-3 also own the TMEM epilogue
 constexpr int kBM = 128;
 constexpr int kKC = 32;   // K elements per chunk: two MMAs of K = 16
 
@@ -55,6 +60,7 @@ struct Args {
   const int *ids = nullptr;    // optional batch indirection (as umma::Args)
   const int *count = nullptr;
   int a_by_id = 0, c_by_id = 0;
+  int batch = 0;               // batch entries (the launch's upper bound on *count)
 };
 
 template <int NP, int STAGES, int SPLIT>
@@ -68,6 +74,25 @@ struct Layout {
   static constexpr int total = STAGES * stage + 2 * conv;
   static_assert(stage % 1024 == 0, "swizzled staging tiles need 1024-byte alignment");
 };
+
+// Bounded wait for the mbarrier phase with parity `parity`: try_wait lets the
+// hardware suspend the thread for a while instead of spinning; at most
+// kSpinLimit tries, false on timeout.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity) {
+  const uint32_t addr = umma::smem_u32(bar);
+  for (uint32_t it = 0; it < umma::kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
 
 __device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
@@ -125,12 +150,18 @@ __global__ void __launch_bounds__(kThreads)
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kBM;
-  const int b = blockIdx.z;
-  if (g.count && b >= *g.count) return;   // block-uniform, before any TMEM use
-  const int jb = g.ids ? g.ids[b] : b;
-  const int za = g.a_by_id ? jb : b;
-  float *C = g.C + (int64_t)(g.c_by_id ? jb : b) * g.sCb;
+  // Tiles (batch entry b, 128-row block mt) in order t = b * mtiles + mt; this
+  // CTA takes t = blockIdx.x, blockIdx.x + gridDim.x, ... below the entry
+  // count, and streams their K chunks as one sequence, so the copies of the
+  // next tile's first chunks are in flight while this tile finishes.
+  const int mtiles = (g.M + kBM - 1) / kBM;
+  int entries = g.count ? *g.count : g.batch;
+  if (entries > g.batch) entries = g.batch;
+  const int ntiles = entries * mtiles;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (my_tiles == 0) return;   // block-uniform, before any TMEM use
+  const int nk = (g.K + kKC - 1) / kKC;
+  const int total = my_tiles * nk;   // chunks this CTA streams
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -149,64 +180,81 @@ __global__ void __launch_bounds__(kThreads)
   umma::fence_after();
   const uint32_t tmem = tmem_base_s;
 
-  const int nchunks = (g.K + kKC - 1) / kKC;
-  auto issue = [&](int c) {   // one thread: chunk c into staging stage c % STAGES
-    const int s = c % STAGES;
+  struct Tile {
+    int m0, b, za;
+    float *C;
+  };
+  auto tile_of = [&](int lt) {   // this CTA's lt-th tile
+    const int t = blockIdx.x + lt * gridDim.x;
+    Tile r;
+    r.b = t / mtiles;
+    r.m0 = (t % mtiles) * kBM;
+    const int jb = g.ids ? g.ids[r.b] : r.b;
+    r.za = g.a_by_id ? jb : r.b;
+    r.C = g.C + (int64_t)(g.c_by_id ? jb : r.b) * g.sCb;
+    return r;
+  };
+  auto issue = [&](int gc) {   // one thread: chunk gc into staging stage gc % STAGES
+    const int s = gc % STAGES, kc = gc % nk;
+    const Tile tl = tile_of(gc / nk);
     uint8_t *st = smem + s * Lay::stage;
     expect_tx(&full[s], (uint32_t)Lay::stage);
-    if (g.a_kcontig) tma_load_3d(st, &g.amap, c * kKC, m0, za, &full[s]);
-    else tma_load_3d(st, &g.amap, m0, c * kKC, za, &full[s]);
-    tma_load_3d(st + Lay::a_stage, &g.bmap, c * kKC, 0, b, &full[s]);
+    if (g.a_kcontig) tma_load_3d(st, &g.amap, kc * kKC, tl.m0, tl.za, &full[s]);
+    else tma_load_3d(st, &g.amap, tl.m0, kc * kKC, tl.za, &full[s]);
+    tma_load_3d(st + Lay::a_stage, &g.bmap, kc * kKC, 0, tl.b, &full[s]);
   };
   if (tid == 0)
-    for (int c = 0; c < STAGES && c < nchunks; ++c) issue(c);
-  int issued = STAGES < nchunks ? STAGES : nchunks;   // meaningful in thread 0 only
+    for (int c = 0; c < STAGES && c < total; ++c) issue(c);
+  int issued = STAGES < total ? STAGES : total;   // meaningful in thread 0 only
 
   constexpr uint32_t idesc = umma::idesc_bf16(kBM, NP);
   constexpr uint32_t LBO = 128, SBO = (kKC / 8) * 128;
   bool ok = true;
   int done_chunks = 0;   // chunks whose MMAs were committed
+  Tile cur = tile_of(0);
 #pragma unroll 1
-  for (int c = 0; c < nchunks; ++c) {
-    const int s = c % STAGES, h = c & 1;
-    const bool wf = umma::mbar_wait(&full[s], (uint32_t)((c / STAGES) & 1));
+  for (int gc = 0; gc < total; ++gc) {
+    const int s = gc % STAGES, h = gc & 1, kc = gc % nk;
+    if (kc == 0 && gc > 0) cur = tile_of(gc / nk);
+    const bool wf = wait_phase(&full[s], (uint32_t)((gc / STAGES) & 1));
     // the MMAs that read conversion buffer h two chunks ago must be done
-    const bool wm = c >= 2 ? umma::mbar_wait(&mdone[h], (uint32_t)(((c - 2) >> 1) & 1)) : true;
+    const bool wm = gc >= 2 ? wait_phase(&mdone[h], (uint32_t)(((gc - 2) >> 1) & 1)) : true;
     if (!__syncthreads_and(wf && wm)) { ok = false; break; }
     const uint8_t *sa = smem + s * Lay::stage;
     const uint8_t *sb = sa + Lay::a_stage;
     uint8_t *cv = smem + STAGES * Lay::stage + h * Lay::conv;
     uint8_t *a_hi = cv, *b_hi = cv + Lay::a_conv;
     uint8_t *a_lo = cv + Lay::a_conv + Lay::b_conv, *b_lo = a_lo + Lay::a_conv;
-    // A: thread t converts row t (four k-cores)
+    // A: thread t converts row t % 128, k-cores t / 128 and t / 128 + 2
     {
-      const int r = tid;
+      const int r = tid & (kBM - 1);
 #pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
+      for (int kk = 0; kk < 4 * kBM / kThreads; ++kk) {
+        const int kq = tid / kBM + kk * (kThreads / kBM);
         float x[8];
         if (g.a_kcontig) {
-          get8_swz(sa, r, kc, x);
+          get8_swz(sa, r, kq, x);
         } else {
           const float *col = reinterpret_cast<const float *>(sa) + r;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) x[e] = col[(kc * 8 + e) * kBM];
+          for (int e = 0; e < 8; ++e) x[e] = col[(kq * 8 + e) * kBM];
         }
-        put8<SPLIT>(x, a_hi, a_lo, core_off(r, kc));
+        put8<SPLIT>(x, a_hi, a_lo, core_off(r, kq));
       }
     }
     // B: NP rows x four k-cores
 #pragma unroll
     for (int u = tid; u < NP * 4; u += kThreads) {
-      const int r = u % NP, kc = u / NP;
+      const int r = u % NP, kq = u / NP;
       float x[8];
-      get8_swz(sb, r, kc, x);
-      put8<SPLIT>(x, b_hi, b_lo, core_off(r, kc));
+      get8_swz(sb, r, kq, x);
+      put8<SPLIT>(x, b_hi, b_lo, core_off(r, kq));
     }
     umma::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       // staging stage s has been read by every thread: refill it
-      if (issued < nchunks) {
+      if (issued < total) {
         issue(issued);
         ++issued;
       }
@@ -216,7 +264,7 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t off = ks * 2 * 128;   // two k-cores per MMA (K = 16)
         const uint64_t dah = umma::smem_desc(umma::smem_u32(a_hi) + off, LBO, SBO);
         const uint64_t dbh = umma::smem_desc(umma::smem_u32(b_hi) + off, LBO, SBO);
-        umma::mma_bf16(tmem, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        umma::mma_bf16(tmem, dah, dbh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
         if (SPLIT > 1) {
           const uint64_t dal = umma::smem_desc(umma::smem_u32(a_lo) + off, LBO, SBO);
           const uint64_t dbl = umma::smem_desc(umma::smem_u32(b_lo) + off, LBO, SBO);
@@ -226,34 +274,41 @@ __global__ void __launch_bounds__(kThreads)
       }
       umma::mma_commit(&mdone[h]);
     }
-    done_chunks = c + 1;
+    done_chunks = gc + 1;
+    if (kc == nk - 1) {
+      // last chunk of the tile: its MMAs done, the accumulator goes out; the
+      // next tile's first MMA (accumulate 0) is issued only after this
+      const bool wd = wait_phase(&mdone[h], (uint32_t)((gc >> 1) & 1));
+      if (!__syncthreads_and(wd)) { ok = false; break; }
+      if (warp < 4) {   // TMEM lanes 32w .. 32w + 31 belong to warp w mod 4
+        umma::fence_after();
+        const int row = cur.m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+          float v[32];
+          umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+          if (row < g.M) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+              if (c0 + c < g.N) cur.C[(int64_t)row * g.sCi + (int64_t)(c0 + c) * g.sCn] = v[c];
+          }
+        }
+      }
+      umma::fence_before();
+      __syncthreads();
+    }
   }
-  // wait for the last commit of each conversion buffer
-  bool fin = true;
-  for (int h = 0; h < 2; ++h) {
-    const int used = done_chunks > h ? (done_chunks - 1 - h) / 2 + 1 : 0;   // commits on buffer h
-    if (used > 0 && !umma::mbar_wait(&mdone[h], (uint32_t)((used - 1) & 1))) fin = false;
-  }
-  fin = __syncthreads_and(fin);
-  if (!ok || !fin) {
+  if (!ok) {
+    // wait (bounded) for the MMAs committed on each conversion buffer and
+    // for the copies issued but never consumed, then give up
+    for (int h = 0; h < 2; ++h) {
+      const int used = done_chunks > h ? (done_chunks - 1 - h) / 2 + 1 : 0;
+      if (used > 0) wait_phase(&mdone[h], (uint32_t)((used - 1) & 1));
+    }
     if (tid == 0) {
       atomicExch(err, 1);
-      // copies issued but never consumed: let them land before the CTA exits
       for (int c = done_chunks; c < issued; ++c)
-        umma::mbar_wait(&full[c % STAGES], (uint32_t)((c / STAGES) & 1));
-    }
-  } else {
-    umma::fence_after();
-    const int row = m0 + warp * 32 + lane;
-#pragma unroll
-    for (int c0 = 0; c0 < NP; c0 += 32) {
-      float v[32];
-      umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (row < g.M) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c0 + c < g.N) C[(int64_t)row * g.sCi + (int64_t)(c0 + c) * g.sCn] = v[c];
-      }
+        wait_phase(&full[c % STAGES], (uint32_t)((c / STAGES) & 1));
     }
   }
   pdl_trigger();

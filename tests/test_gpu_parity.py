@@ -269,6 +269,60 @@ def test_nan_input_is_reported_and_poisons():
     h.close()
 
 
+def test_nan_found_after_graph_replayed_steps():
+    # steps without a report (here graph replays) copy the NaN/Inf flag to
+    # pinned host memory; once they have completed, the next call reports it
+    dims = (16, 12, 4)
+    M = np.ones((4, 16, 12))
+    M[2, 5, 7] = np.inf
+    h = make_handle(dims, "f32", M=M)
+    h.graph_mode(True)
+    status = None
+    for k in range(4):
+        if k == 3:
+            torch.cuda.synchronize()   # every earlier step has landed by now
+        try:
+            h.step()
+        except tr.TrError as e:
+            status = e.status
+            break
+    assert status == tr.TR_ENUMERIC           # at the latest on the call after the synchronise
+    with pytest.raises(tr.TrError) as ei:
+        h.step()
+    assert ei.value.status == tr.TR_EINVAL       # poisoned until tr_set_state
+    z = torch.zeros((4, 16, 12), device="cuda")
+    h.set_state(z, z, z, z, z, mu=1.0, t=0)
+    h.close()
+
+
+def test_recover_lagged_stop_matches_per_step_check():
+    # tr_recover with tol > 0 checks each step's residuals asynchronously one
+    # step late; against stepping with a report every step it returns at most
+    # two steps later, and its reported maxima meet tol
+    w = synth.WORKLOADS["tubal64_r5"]
+    X, M, mask, _ = synth.make_problem(w)
+    kw = dict(M=M, mask=mask, noise=tr.TR_NOISE_NONE, rank=5, oversample=10, seed=2, tol=1e-8,
+              max_iter=400)
+    h = make_handle(w.dims, "f64", **kw)
+    first = None
+    for it in range(400):
+        info = h.step(info=True)
+        if max(info["res_inf"]) <= 1e-8:
+            first = info["iter"]
+            break
+    h.close()
+    assert first is not None
+    for graph in (False, True):
+        h = make_handle(w.dims, "f64", **kw)
+        h.graph_mode(graph)
+        Lout = torch.empty(M.shape, dtype=torch.float64, device="cuda")
+        st, info = h.recover(Lout)
+        assert st == tr.TR_OK and max(info["res_inf"]) <= 1e-8
+        assert first <= info["iter"] <= first + 2, (first, info["iter"])
+        assert relF(host(Lout), X) < 1e-6
+        h.close()
+
+
 def test_state_roundtrip():
     dims = (10, 9, 3, 2)
     rng = np.random.default_rng(0)
