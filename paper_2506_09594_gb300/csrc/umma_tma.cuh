@@ -9,7 +9,7 @@
 // operands in flight as 3D tensor copies (cp.async.bulk.tensor.3d,
 // completion counted on an mbarrier) into FP32 staging tiles, so the HBM
 // latency of a chunk -- the next tile's first ones included -- overlaps the
-// work on the chunks before it.  The 256 threads convert a landed chunk
+// work on the chunks before it.  Seven warps convert a landed chunk
 // to BF16 (x = hi + lo, both BF16, for the split form) in the canonical
 // K-major core-matrix layout without swizzle (8-row x 16-byte core
 // matrices, leading byte offset 128, stride byte offset 512), and one
@@ -27,8 +27,9 @@
 // is a 3D view (inner, middle, batch), so rows past M, columns past N and
 // k past K read as zeros.
 //
-// Eight warps convert; the tcgen05.ld epilogue runs in warps 0-3, whose lane
-// quarters cover the accumulator's 128 lanes.
+// Warps 1-7 convert chunk c + 1 while thread 0 issues the copies and MMAs of
+// chunk c (one block barrier per chunk); the tcgen05.ld epilogue runs in warps
+// 0-3, whose lane quarters cover the accumulator's 128 lanes.
 //
 // SPLIT = 3: A_hi B_hi + A_hi B_lo + A_lo B_hi (products carry about 16
 // significant bits, FP32-form accuracy); SPLIT = 1: the plain BF16 form.
@@ -46,7 +47,7 @@
 
 namespace tmag {
 
-constexpr int kThreads = 256;   // 8 warps convert; warps 0-3 also own the TMEM epilogue
+constexpr int kThreads = 256;   // warp 0 issues, warps 1-7 convert, warps 0-3 read TMEM
 constexpr int kBM = 128;
 constexpr int kKC = 32;   // K elements per chunk: two MMAs of K = 16
 
@@ -114,10 +115,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 // remainder (lo).
 template <int SPLIT>
 __device__ __forceinline__ void put8(const float (&x)[8], uint8_t *hi, uint8_t *lo, int off) {
-  __align__(16) __nv_bfloat16 h[8];
-  __align__(16) __nv_bfloat16 l[8];
+  // pairs rounded to BF16 at once; lo = x - hi exactly in FP32, then rounded
+  __nv_bfloat162 h[4], l[4];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) umma::split_bf16(x[e], h[e], l[e]);
+  for (int e = 0; e < 4; ++e) {
+    h[e] = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+    if (SPLIT > 1) {
+      const float2 f = __bfloat1622float2(h[e]);
+      l[e] = __floats2bfloat162_rn(x[2 * e] - f.x, x[2 * e + 1] - f.y);
+    }
+  }
   *reinterpret_cast<uint4 *>(hi + off) = *reinterpret_cast<const uint4 *>(h);
   if (SPLIT > 1) *reinterpret_cast<uint4 *>(lo + off) = *reinterpret_cast<const uint4 *>(l);
 }
@@ -144,6 +151,8 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ __align__(8) uint64_t full[STAGES];
   __shared__ __align__(8) uint64_t mdone[2];
   __shared__ uint32_t tmem_base_s;
+  constexpr int kMaxTiles = 64;          // slice ids of this CTA's tiles, read once
+  __shared__ int tile_jb[kMaxTiles];
   using Lay = Layout<NP, STAGES, SPLIT>;
   constexpr int TMEM_COLS = NP < 32 ? 32 : NP;
   // the dynamic window is aligned up to 1024 bytes (the launch reserves it)
@@ -169,6 +178,10 @@ __global__ void __launch_bounds__(kThreads)
                  "r"((uint32_t)TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  for (int lt = tid; lt < my_tiles && lt < kMaxTiles; lt += kThreads) {
+    const int b = (blockIdx.x + lt * gridDim.x) / mtiles;
+    tile_jb[lt] = g.ids ? g.ids[b] : b;
+  }
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) umma::mbar_init(&full[s], 1);
     umma::mbar_init(&mdone[0], 1);
@@ -189,7 +202,7 @@ __global__ void __launch_bounds__(kThreads)
     Tile r;
     r.b = t / mtiles;
     r.m0 = (t % mtiles) * kBM;
-    const int jb = g.ids ? g.ids[r.b] : r.b;
+    const int jb = lt < kMaxTiles ? tile_jb[lt] : (g.ids ? g.ids[r.b] : r.b);
     r.za = g.a_by_id ? jb : r.b;
     r.C = g.C + (int64_t)(g.c_by_id ? jb : r.b) * g.sCb;
     return r;
@@ -216,48 +229,50 @@ __global__ void __launch_bounds__(kThreads)
   for (int gc = 0; gc < total; ++gc) {
     const int s = gc % STAGES, h = gc & 1, kc = gc % nk;
     if (kc == 0 && gc > 0) cur = tile_of(gc / nk);
-    const bool wf = wait_phase(&full[s], (uint32_t)((gc / STAGES) & 1));
-    // the MMAs that read conversion buffer h two chunks ago must be done
-    const bool wm = gc >= 2 ? wait_phase(&mdone[h], (uint32_t)(((gc - 2) >> 1) & 1)) : true;
-    if (!__syncthreads_and(wf && wm)) { ok = false; break; }
-    const uint8_t *sa = smem + s * Lay::stage;
-    const uint8_t *sb = sa + Lay::a_stage;
-    uint8_t *cv = smem + STAGES * Lay::stage + h * Lay::conv;
-    uint8_t *a_hi = cv, *b_hi = cv + Lay::a_conv;
-    uint8_t *a_lo = cv + Lay::a_conv + Lay::b_conv, *b_lo = a_lo + Lay::a_conv;
-    // A: thread t converts row t % 128, k-cores t / 128 and t / 128 + 2
-    {
-      const int r = tid & (kBM - 1);
+    // warps 1-7 convert chunk gc while thread 0 still issues chunk gc - 1
+    bool okc = true;
+    if (warp != 0) {
+      okc = wait_phase(&full[s], (uint32_t)((gc / STAGES) & 1));
+      // the MMAs that read conversion buffer h two chunks ago must be done
+      if (okc && gc >= 2) okc = wait_phase(&mdone[h], (uint32_t)(((gc - 2) >> 1) & 1));
+      if (okc) {
+        const uint8_t *sa = smem + s * Lay::stage;
+        const uint8_t *sb = sa + Lay::a_stage;
+        uint8_t *cv = smem + STAGES * Lay::stage + h * Lay::conv;
+        uint8_t *a_hi = cv, *b_hi = cv + Lay::a_conv;
+        uint8_t *a_lo = cv + Lay::a_conv + Lay::b_conv, *b_lo = a_lo + Lay::a_conv;
+        constexpr int UA = kBM * 4, UT = UA + NP * 4;   // A units, all units
+        for (int u = tid - 32; u < UT; u += kThreads - 32) {
+          float x[8];
+          if (u < UA) {   // A: row u % 128, k-core u / 128
+            const int r = u & (kBM - 1), kq = u / kBM;
+            if (g.a_kcontig) {
+              get8_swz(sa, r, kq, x);
+            } else {
+              const float *col = reinterpret_cast<const float *>(sa) + r;
 #pragma unroll
-      for (int kk = 0; kk < 4 * kBM / kThreads; ++kk) {
-        const int kq = tid / kBM + kk * (kThreads / kBM);
-        float x[8];
-        if (g.a_kcontig) {
-          get8_swz(sa, r, kq, x);
-        } else {
-          const float *col = reinterpret_cast<const float *>(sa) + r;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) x[e] = col[(kq * 8 + e) * kBM];
+              for (int e = 0; e < 8; ++e) x[e] = col[(kq * 8 + e) * kBM];
+            }
+            put8<SPLIT>(x, a_hi, a_lo, core_off(r, kq));
+          } else {        // B: row (u - UA) % NP, k-core (u - UA) / NP
+            const int r = (u - UA) % NP, kq = (u - UA) / NP;
+            get8_swz(sb, r, kq, x);
+            put8<SPLIT>(x, b_hi, b_lo, core_off(r, kq));
+          }
         }
-        put8<SPLIT>(x, a_hi, a_lo, core_off(r, kq));
       }
+      umma::fence_async_smem();
     }
-    // B: NP rows x four k-cores
-#pragma unroll
-    for (int u = tid; u < NP * 4; u += kThreads) {
-      const int r = u % NP, kq = u / NP;
-      float x[8];
-      get8_swz(sb, r, kq, x);
-      put8<SPLIT>(x, b_hi, b_lo, core_off(r, kq));
-    }
-    umma::fence_async_smem();
-    __syncthreads();
+    if (!__syncthreads_and(okc)) { ok = false; break; }
     if (tid == 0) {
-      // staging stage s has been read by every thread: refill it
+      // staging stage s has been read by every converter: refill it
       if (issued < total) {
         issue(issued);
         ++issued;
       }
+      uint8_t *cv = smem + STAGES * Lay::stage + h * Lay::conv;
+      uint8_t *a_hi = cv, *b_hi = cv + Lay::a_conv;
+      uint8_t *a_lo = cv + Lay::a_conv + Lay::b_conv, *b_lo = a_lo + Lay::a_conv;
       umma::fence_after();
 #pragma unroll
       for (int ks = 0; ks < kKC / 16; ++ks) {
