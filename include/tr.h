@@ -566,9 +566,11 @@ tr_status tr_mlp_train(float *params, const float *X, const float *y, int n, int
  *   captured CUDA graph (captured at the first such step, on a stream the
  *   handle owns, ordered after the handle's stream by events).  Results are
  *   identical to eager steps.
- * tr_set_tube_tile: tubes per block of the tube kernels (4, 8, 16, 32 or
- *   64; 0 = the default, the largest of 4..32 that fits).  Every tile computes the same
- *   values.  Errors: TR_EINVAL (not a power of two in range or too large).
+ * tr_set_tube_tile: tubes per block of the tube kernels (a power of two
+ *   from 4 to 256; 0 = the default: the smallest of 32..256 whose tile gives
+ *   each of the block's 256 threads a fibre of every transformed mode,
+ *   halved until the tile fits).  Every tile computes the same values.
+ *   Errors: TR_EINVAL (not a power of two in range or too large).
  * tr_set_slice_groups: split the RSVD slice pass into `groups` (1..4)
  *   contiguous slice ranges run on side streams, so that latency-bound
  *   kernels of one range overlap bandwidth-bound products of another.  Same

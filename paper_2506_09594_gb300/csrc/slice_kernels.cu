@@ -781,6 +781,117 @@ __global__ void __launch_bounds__(256) cgs_qr_kernel(int m, int l, T *__restrict
   pdl_trigger();
 }
 
+// ------------------------------------------- Gram-Schmidt, panel in smem
+// Classical Gram-Schmidt with reorthogonalisation for panels the register
+// form cannot hold (more than 32 columns or 512 rows; here l <= 64, m <=
+// 1024 and the m x l panel in shared memory).  The acceptance and restart
+// rules are those of cgs_column: a column is kept after a pass that retains
+// more than half of its squared norm (a quarter after the second pass); a
+// column still dependent after four passes restarts from a unit vector.
+// Per pass the j + 1 inner products of column j (with Q_0 .. Q_{j-1} and
+// itself) are taken eight at a time: each warp reduce-scatters eight
+// partial sums in nine shuffles, lane 4k ends with value k, and the
+// warps' results meet in shared memory.
+constexpr int kCgsSmemThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kCgsSmemThreads)
+cgs_smem_qr_kernel(int m, int l, T *__restrict__ P, int64_t sP, SliceSel sel) {
+  pdl_wait();
+  if (sel.count && (int)blockIdx.x >= *sel.count) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *S = reinterpret_cast<T *>(smem_raw);             // m x l, column-major
+  T *red = S + (size_t)m * l;                         // 16 warps x 72
+  T *coef = red + 16 * 72;                            // 72
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kCgsSmemThreads / 32;
+  constexpr int RPT = 1024 / kCgsSmemThreads;          // rows per thread
+  T *Pj = P + (int64_t)blockIdx.x * sP;
+  for (int e = tid; e < m * l; e += kCgsSmemThreads) S[e] = Pj[e];
+  __syncthreads();
+  const T tiny = sizeof(T) == 4 ? T(FLT_MIN) : T(DBL_MIN);
+  for (int j = 0; j < l; ++j) {
+    T *xj = S + (size_t)j * m;
+    int pass = 0, unit = -1, restarts = 0;
+    T after = T(0);
+    while (true) {
+      // inner products with columns 0 .. j (column j: the squared norm)
+      for (int c0 = 0; c0 <= j; c0 += 8) {
+        T p[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) p[k] = T(0);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const int row = tid + r * kCgsSmemThreads;
+          if (row < m) {
+            const T xr = xj[row];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (c0 + k <= j) p[k] = fma(S[(size_t)(c0 + k) * m + row], xr, p[k]);
+          }
+        }
+        // reduce-scatter: after the levels 16, 8, 4 lane L holds value
+        // ((L>>4)&1)*4 + ((L>>3)&1)*2 + ((L>>2)&1) summed over 8 lanes
+        int idx = 0;
+#pragma unroll
+        for (int h = 4, o = 16; h >= 1; h >>= 1, o >>= 1) {
+          const bool up = (lane & o) != 0;
+#pragma unroll
+          for (int k = 0; k < h; ++k) {
+            const T give = up ? p[k] : p[k + h];
+            const T keep = up ? p[k + h] : p[k];
+            p[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+          }
+          idx += up ? h : 0;
+        }
+        p[0] += __shfl_xor_sync(0xffffffffu, p[0], 2);
+        p[0] += __shfl_xor_sync(0xffffffffu, p[0], 1);
+        if ((lane & 3) == 0 && c0 + idx <= j) red[warp * 72 + c0 + idx] = p[0];
+      }
+      __syncthreads();
+      for (int i = tid; i <= j; i += kCgsSmemThreads) {
+        T t = T(0);
+        for (int w = 0; w < NW; ++w) t += red[w * 72 + i];
+        coef[i] = t;
+      }
+      __syncthreads();
+      const T sq = coef[j];
+      T csq = T(0);
+      for (int i = 0; i < j; ++i) csq = fma(coef[i], coef[i], csq);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int row = tid + r * kCgsSmemThreads;
+        if (row < m) {
+          T v = xj[row];
+          for (int i = 0; i < j; ++i) v = fma(-coef[i], S[(size_t)i * m + row], v);
+          xj[row] = v;
+        }
+      }
+      after = sq - csq;
+      ++pass;
+      __syncthreads();
+      if (after > tiny && (after > T(0.5) * sq || (pass >= 2 && after > T(0.25) * sq))) break;
+      if (pass >= 4) {   // numerically dependent: continue from a unit vector
+        if (++restarts > m) break;
+        unit = unit < 0 ? j % m : (unit + 1) % m;
+        for (int row = tid; row < m; row += kCgsSmemThreads) xj[row] = row == unit ? T(1) : T(0);
+        pass = 0;
+        __syncthreads();
+      }
+    }
+    const T nrm = sqrt(after > T(0) ? after : T(0));
+    const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+    for (int row = tid; row < m; row += kCgsSmemThreads) xj[row] *= inv;
+    __syncthreads();
+  }
+  for (int e = tid; e < m * l; e += kCgsSmemThreads) Pj[e] = S[e];
+  pdl_trigger();
+}
+
+inline size_t cgs_smem_bytes(size_t esz, int m, int l) {
+  return esz * ((size_t)m * l + 16 * 72 + 72);
+}
+
 // ------------------------------------------------------ one-sided Jacobi
 // Hestenes one-sided Jacobi on the l x l matrix W (column-major): rotate
 // column pairs until all are mutually orthogonal, accumulating the
@@ -1124,9 +1235,23 @@ cudaError_t run_cgs_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) 
                     sel);
 }
 
+// The shared-memory Gram-Schmidt form: up to 64 columns and 1024 rows within
+// the shared-memory budget.
+inline bool cgs_smem_ok(size_t esz, int m, int l) {
+  return l <= 64 && m <= 1024 && cgs_smem_bytes(esz, m, l) <= kSliceSmemMax;
+}
+
 template <typename T>
 cudaError_t run_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel = SliceSel{}) {
   if (cgs_panel_ok(m, l)) return run_cgs_qr<T>(m, l, P, n, s, sel);
+  if (cgs_smem_ok(sizeof(T), m, l)) {
+    const size_t smem = cgs_smem_bytes(sizeof(T), m, l);
+    cudaError_t e = cudaFuncSetAttribute(cgs_smem_qr_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(cgs_smem_qr_kernel<T>, dim3(n), dim3(kCgsSmemThreads), smem, s, m, l, P,
+                      (int64_t)m * l, sel);
+  }
   if (pick_cpw(l) == 2) { TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 2, RPL>(m, l, P, n, s, sel))) }
   TR_RPL_DISPATCH(pick_rpl(m), (run_qr_t<T, 4, RPL>(m, l, P, n, s, sel)))
 }

@@ -1315,8 +1315,8 @@ extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups)
     if (fs != TR_OK) return fs;
   }
   // tube tile
-  int cand[5];
-  const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 5);
+  int cand[8];
+  const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 8);
   if (nc == 0) return fail(h, TR_EUNSUPPORTED, "no tube tile fits");
   float best = 0.f;
   int best_tp = cand[0];
@@ -1412,8 +1412,8 @@ extern "C" tr_status tr_set_observed(tr_handle *h, const void *observed, const u
 extern "C" tr_status tr_set_tube_tile(tr_handle *h, int tp) {
   if (!h) return TR_EINVAL;
   if (tp != 0) {
-    int cand[5];
-    const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 5);
+    int cand[8];
+    const int nc = tube_tile_candidates(h->dtype, (int)h->n, h->td, cand, 8);
     bool ok = false;
     for (int c = 0; c < nc; ++c) ok = ok || cand[c] == tp;
     if (!ok) return fail(h, TR_EINVAL, "tube tile %d does not fit", tp);

@@ -614,9 +614,19 @@ size_t tube_smem_for(int n, const TransformDesc &td, int TP) {
 
 constexpr size_t kSmemBudget = 200 * 1024;
 
+// Default tubes per block: a mode product has n / n_k fibres per tube, so a
+// tile of TP tubes gives the block's threads (n / n_k) TP fibres; take the
+// smallest power of two from 32 up to kMaxTP that gives every thread at least
+// one fibre of every mode, then halve while the tile does not fit.
+constexpr int kMaxTP = 256;
+
 template <typename T>
 int pick_tp(int n, const TransformDesc &td) {
+  int nfib = n;
+  for (int k = 0; k < td.nt; ++k) nfib = n / td.dim[k] < nfib ? n / td.dim[k] : nfib;
+  if (nfib < 1) nfib = 1;
   int tp = 32;
+  while (tp < kMaxTP && nfib * tp < kTubeThreads) tp <<= 1;
   while (tp > 4 && tube_smem_for<T>(n, td, tp) > kSmemBudget) tp >>= 1;
   return tube_smem_for<T>(n, td, tp) > kSmemBudget ? 0 : tp;
 }
@@ -672,7 +682,7 @@ bool tube_geometry(int64_t P, int n, const TransformDesc &td, TubeLaunch &g) {
   g.n = n;
   g.tp = pick_tp<T>(n, td);
   if (!g.tp) return false;
-  if (td.tp > 0 && td.tp <= 64 && tube_smem_for<T>(n, td, td.tp) <= kSmemBudget) g.tp = td.tp;
+  if (td.tp > 0 && td.tp <= kMaxTP && tube_smem_for<T>(n, td, td.tp) <= kSmemBudget) g.tp = td.tp;
   g.smem = tube_smem_for<T>(n, td, g.tp);
   g.grid = (unsigned)((P + g.tp - 1) / g.tp);
   return true;
@@ -878,7 +888,7 @@ cudaError_t launch_transform(tr_dtype dt, int64_t P, int n, const TransformDesc 
 // partitions the tubes among blocks: every tube's arithmetic is the same.
 int tube_tile_candidates(tr_dtype dt, int n, const TransformDesc &td, int *tps, int cap) {
   int k = 0;
-  for (int tp = 64; tp >= 4 && k < cap; tp >>= 1) {
+  for (int tp = kMaxTP; tp >= 4 && k < cap; tp >>= 1) {
     const size_t b = dt == TR_F64 ? tube_smem_for<double>(n, td, tp) : tube_smem_for<float>(n, td, tp);
     if (b <= kSmemBudget) tps[k++] = tp;
   }

@@ -127,11 +127,13 @@ def test_learned_engine_graph_steps_identical_to_eager():
     assert info["fallback_slices"] >= 0
 
 
-def test_tube_tiles_compute_identical_steps():
-    dims = (64, 40, 20, 20)
+@pytest.mark.parametrize("dims,tiles", [((64, 40, 20, 20), (0, 8, 16, 64)),
+                                         # 32 slices: tubes short enough for 256-tube tiles; 8000 tubes, a ragged last tile
+                                         ((100, 80, 8, 4), (0, 32, 128, 256))])
+def test_tube_tiles_compute_identical_steps(dims, tiles):
     _, M, mask = problem(dims, 4)
     outs = []
-    for tp in (0, 8, 16, 64):
+    for tp in tiles:
         h = handle(dims, "f32", M, mask, rank=8, oversample=4)
         h.set_tube_tile(tp)
         for _ in range(3):
@@ -146,7 +148,7 @@ def test_tube_tiles_compute_identical_steps():
     h.step()
     tile, groups = h.autotune(3)
     # FP32 with P % 16 == 0: only tiles the fused pass can prefetch with
-    assert tile in (16, 32, 64) and groups in (1, 2, 4)
+    assert tile in (16, 32, 64, 128, 256) and groups in (1, 2, 4)
     assert h.autotune(0) == (tile, groups)      # cached choice
     h.step(info=True)                            # the deferred pass was completed first
     with pytest.raises(tr.TrError):

@@ -54,7 +54,7 @@ def _lib():
 # ------------------------------------------------------------- transform
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 @pytest.mark.parametrize("dims", [(7, 5, 3), (9, 4, 5, 3), (3, 3, 2, 2, 2), (6, 5, 64),
-                                  (33, 17, 20, 20), (4, 6), (5, 3, 1, 7)])
+                                  (33, 17, 20, 20), (4, 6), (5, 3, 1, 7), (40, 36, 64)])
 def test_transform_parity(dims, dt):
     rng = np.random.default_rng(1)
     n = int(np.prod(dims[2:])) if len(dims) > 2 else 1
@@ -114,9 +114,16 @@ def test_slice_prox_parity(case, dt):
 
 @pytest.mark.parametrize("dt,case", [("f32", (2, 512, 512, 20, 0.01, 74, 1, "mcp")),
                                      ("f32", (3, 300, 420, 12, 0.05, 60, 1, "l1")),
-                                     ("f64", (2, 300, 200, 10, 0.01, 40, 1, "l1"))])
+                                     ("f64", (2, 300, 200, 10, 0.01, 40, 1, "l1")),
+                                     # exactly rank 5 under a 40-wide sketch: dependent
+                                     # columns restart from unit vectors
+                                     ("f32", (2, 600, 520, 5, 0.0, 40, 1, "l1")),
+                                     ("f64", (2, 600, 64, 3, 0.0, 36, 1, "mcp")),
+                                     ("f32", (2, 1000, 700, 30, 0.02, 48, 1, "mcp"))])
 def test_slice_prox_large_panels(dt, case):
-    # panels too large for the register-resident QR take the shared-memory QR
+    # panels too large for the register-resident Gram-Schmidt QR (above 32
+    # columns or 512 rows) take the shared-memory Gram-Schmidt QR up to 64
+    # columns and 1024 rows, the shared-memory Householder QR beyond
     n, n1, n2, r, noise, l, q, phi = case
     Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 + n2)
     s1 = np.linalg.svd(Ab[0], compute_uv=False)[0]
