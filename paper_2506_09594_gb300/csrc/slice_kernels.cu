@@ -355,6 +355,98 @@ cudaError_t tma_gemm(const GemmArgs &g, int batch, int nA, int split, int *err, 
 #undef TR_TMAG
 }
 
+__global__ void split_planes_kernel(const float *__restrict__ x, __nv_bfloat16 *__restrict__ dst,
+                                    int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    dst[i] = hi;
+    dst[count + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+cudaError_t split_planes(const float *x, void *dst, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  split_planes_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, (__nv_bfloat16 *)dst, count);
+  return cudaGetLastError();
+}
+
+// Whether the split planes of an n x n1 x n2 FP32 stack serve the TMA-fed
+// products: rows of n2 BF16 and slices of n1 n2 BF16 at 16-byte multiples,
+// and panels of at most 64 columns.
+bool planes_view_ok(int64_t n, int n1, int n2, int l) {
+  return n >= 1 && n1 >= 1 && n2 >= 1 && l >= 1 && l <= 64 && n2 % 8 == 0 &&
+         ((int64_t)n1 * n2) % 8 == 0;
+}
+
+// The product with A given as BF16 planes (A = hi + lo, tmag::planes_kernel).
+// hi, lo: the planes of A's array, laid out as g.A's FP32 view would be
+// (strides g.sAi, g.sAk, g.sAb in elements).  Fails (cudaErrorNotSupported)
+// when the views do not allow it: the planes have no FP32 fallback.
+cudaError_t tma_gemm_planes(const GemmArgs &g, int batch, int nA, int split, const void *hi,
+                            const void *lo, int *err, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || batch <= 0) return cudaSuccess;
+  if (g.N > 64 || g.sBk != 1) return cudaErrorNotSupported;
+  tmag::Args a{};
+  const int64_t za = g.a_by_id ? (int64_t)nA : (int64_t)batch;
+  bool ok;
+  if (g.sAk == 1) {
+    a.a_kcontig = 1;
+    ok = encode_tensor_3d(&a.amap, hi, 2, g.K, g.M, za, g.sAi, g.sAb, tmag::kKP, tmag::kBM, true) &&
+         (split == 1 ||
+          encode_tensor_3d(&a.amap_lo, lo, 2, g.K, g.M, za, g.sAi, g.sAb, tmag::kKP, tmag::kBM, true));
+  } else if (g.sAi == 1) {
+    a.a_kcontig = 0;
+    ok = encode_tensor_3d(&a.amap, hi, 2, g.M, g.K, za, g.sAk, g.sAb, 64, tmag::kKP, true) &&
+         (split == 1 ||
+          encode_tensor_3d(&a.amap_lo, lo, 2, g.M, g.K, za, g.sAk, g.sAb, 64, tmag::kKP, true));
+  } else {
+    return cudaErrorNotSupported;
+  }
+  const int np = g.N <= 32 ? 32 : 64;
+  ok = ok && encode_tensor_3d_f32(&a.bmap, g.B, g.K, g.N, batch, g.sBn,
+                                  g.sBb > 0 ? g.sBb : (int64_t)g.N * g.sBn, 32, np, true);
+  if (!ok) return cudaErrorNotSupported;
+  a.M = g.M;
+  a.N = g.N;
+  a.K = g.K;
+  a.C = (float *)g.C;
+  a.sCb = g.sCb;
+  a.sCi = g.sCi;
+  a.sCn = g.sCn;
+  a.ids = g.sel.ids;
+  a.count = g.sel.count;
+  a.a_by_id = g.a_by_id;
+  a.c_by_id = g.c_by_id;
+  a.batch = batch;
+  // persistent, one CTA per SM (its shared memory holds 4-5 stages)
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  const int64_t tiles = (int64_t)((g.M + tmag::kBM - 1) / tmag::kBM) * batch;
+  const dim3 grid((unsigned)(tiles < sms ? tiles : sms), 1, 1);
+#define TR_TMAP(NP, ST, SP)                                                                    \
+  {                                                                                            \
+    auto k = tmag::planes_kernel<NP, ST, SP>;                                                  \
+    const int smem = tmag::PlanesLayout<NP, ST, SP>::total + 1024;                             \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    if (e != cudaSuccess) return e;                                                            \
+    return launch_pdl(k, grid, dim3(tmag::kThreads), smem, s, a, err);                        \
+  }
+  if (np == 32) {
+    if (split > 1) TR_TMAP(32, 5, 3) else TR_TMAP(32, 5, 1)
+  }
+  if (split > 1) TR_TMAP(64, 4, 3) else TR_TMAP(64, 4, 1)
+#undef TR_TMAP
+}
+
 // -------------------------------------------------- block Householder QR
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -1547,8 +1639,16 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
                   (w.prec == TR_PREC_BF16 || w.prec == TR_PREC_BF16X3);
   const int early = !tc ? 0 : (w.prec == TR_PREC_BF16 ? 1 : 3);
   const int late = !tc ? 0 : 3;
+  // Abar as BF16 planes (hi: the first nA n1 n2 BF16, lo: the next) when
+  // the pass is given them: the products of Abar read the planes
+  const int nA = w.nA > 0 ? w.nA : n;
+  const bool planes = w.asplit && tc;
+  if (w.asplit && !planes) return cudaErrorNotSupported;
+  const void *a_hi = Abar;
+  const void *a_lo = reinterpret_cast<const uint16_t *>(Abar) + (int64_t)nA * sA;
   auto run_gemm = [&](const GemmArgs &g, int mode) {
     if (mode == 0) return bgemm<T>(g, n, s);
+    if (planes && g.A == Abar) return tma_gemm_planes(g, n, nA, mode, a_hi, a_lo, w.err, s);
     bool used = false;
     cudaError_t e2 = tma_gemm(g, n, w.nA > 0 ? w.nA : n, mode, w.err, s, &used);
     if (e2 != cudaSuccess || used) return e2;
@@ -1565,10 +1665,16 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
                w.sel, 1, 0};
     return run_gemm(g, mode);
   };
-  static const char *kAX[4] = {"product A*X fp32 simt", "product A*X bf16 tcgen05", "",
-                               "product A*X split-bf16 tcgen05"};
-  static const char *kAtX[4] = {"product A^T*Q fp32 simt", "product A^T*Q bf16 tcgen05", "",
-                                "product A^T*Q split-bf16 tcgen05"};
+  static const char *kAX0[4] = {"product A*X fp32 simt", "product A*X bf16 tcgen05", "",
+                                "product A*X split-bf16 tcgen05"};
+  static const char *kAtX0[4] = {"product A^T*Q fp32 simt", "product A^T*Q bf16 tcgen05", "",
+                                 "product A^T*Q split-bf16 tcgen05"};
+  static const char *kAXp[4] = {"", "product A*X bf16 planes tcgen05", "",
+                                "product A*X split-bf16 planes tcgen05"};
+  static const char *kAtXp[4] = {"", "product A^T*Q bf16 planes tcgen05", "",
+                                 "product A^T*Q split-bf16 planes tcgen05"};
+  const char *const *kAX = planes ? kAXp : kAX0;
+  const char *const *kAtX = planes ? kAtXp : kAtX0;
   const int m0 = w.q > 0 ? early : late;
   if ((e = AX(Om, P1, m0)) != cudaSuccess) return e;
   mark(kAX[m0]);
@@ -1654,6 +1760,12 @@ cudaError_t run_adaptive(const SliceWork &sw, const AdaptWork &aw, const T *Abar
 }
 
 }  // namespace
+
+bool planes_ok(int64_t n, int n1, int n2, int l) { return planes_view_ok(n, n1, n2, l); }
+
+cudaError_t launch_split_planes(const float *x, void *dst, int64_t count, cudaStream_t s) {
+  return split_planes(x, dst, count, s);
+}
 
 cudaError_t launch_slice_adaptive(tr_dtype dt, const SliceWork &w, const AdaptWork &aw,
                                   const void *Abar, void *Gbar, const ShrinkScalars &sh, int t,

@@ -35,6 +35,9 @@ struct tr_handle {
   LearnedWork lw{};                           // learned-width engine state
   int *width = nullptr;                       // sketch width per slice, last pass
   bool have_pass = false;                     // a slice pass has run
+  // the steps' tube passes write Abar as BF16 planes (hi, lo) for the
+  // tensor-core products (FP32 problems, BF16 forms, fixed-width engine)
+  bool abar_planes = false;
   double thr_last = 0.0;                      // its shrink threshold
   DevSched *sched = nullptr;                  // device copy of mu, mu_prev, t
   // the RSVD slice pass split into `slice_groups` independent slice ranges on
@@ -432,6 +435,9 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
   INIT_CUDA(cudaMalloc((void **)&sw.err, sizeof(int)));
   INIT_CUDA(cudaMemsetAsync(sw.err, 0, sizeof(int), h->stream));
   sw.prec = (int)prm->prec;
+  h->abar_planes = p->dtype == TR_F32 && prm->engine == TR_LR_RSVD &&
+                   (prm->prec == TR_PREC_BF16 || prm->prec == TR_PREC_BF16X3) &&
+                   planes_ok(h->n, (int)h->n1, (int)h->n2, l);
   INIT_CUDA(cudaMemsetAsync(sw.rank, 0, (size_t)h->n * sizeof(int), h->stream));
   if (prm->engine == TR_LR_ADAPTIVE || prm->engine == TR_LR_LEARNED) {
     AdaptWork &aw = h->aw;
@@ -510,7 +516,7 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
 // One slice pass.  `sched`: take tau = 1/mu and the iteration index from the
 // device schedule (a step) rather than from the arguments (tr_slice_prox).
 static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double tau, int t,
-                            bool sched = false) {
+                            bool sched = false, bool planes = false) {
   ShrinkScalars sh{tau, (int)h->prm.phi, h->prm.phi_theta, h->prm.phi_gamma};
   if (sched) sh.dmu = &h->sched->mu;
   h->sw.dt = sched ? &h->sched->t : nullptr;
@@ -558,6 +564,7 @@ static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double t
     for (int g = 0; g < G; ++g) {
       const int cnt = n / G + (g < n % G ? 1 : 0);
       SliceWork gw = h->sw;
+      gw.asplit = planes;
       gw.n = cnt;
       gw.sel.ids = h->iota + start;
       gw.Om = (char *)h->sw.Om + (size_t)start * h->n2 * h->sw.l * h->esz;
@@ -575,7 +582,9 @@ static tr_status slice_pass(tr_handle *h, const void *Abar, void *Gbar, double t
       TR_CUDA(h, cudaStreamWaitEvent(h->stream, h->side_join[g], 0));
     }
   } else {
-    TR_CUDA(h, launch_slice_rsvd(h->dtype, h->sw, Abar, Gbar, sh, t, h->stream));
+    SliceWork sw = h->sw;
+    sw.asplit = planes;
+    TR_CUDA(h, launch_slice_rsvd(h->dtype, sw, Abar, Gbar, sh, t, h->stream));
     h->launches += 7 + 4 * (uint64_t)h->sw.q;   // sketch, 2 + 2q GEMM, 1 + 2q QR, SVD core, rebuild
   }
   h->have_pass = true;
@@ -658,6 +667,7 @@ static tr_status enqueue_step(tr_handle *h, bool pending, bool with_inverse, cud
                  h->prm.psi_gamma};
   sc.dmu = &h->sched->mu;
   sc.lambda = h->prm.lambda;
+  sc.planes = h->abar_planes ? 1 : 0;
   cudaError_t e = cudaMemsetAsync(h->res, 0, RES_COUNT * sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->res_prev, 0, RES_COUNT * sizeof(unsigned long long), h->stream);
@@ -680,7 +690,7 @@ static tr_status enqueue_step(tr_handle *h, bool pending, bool with_inverse, cud
   if (e == cudaSuccess && pev) e = cudaEventRecord(pev[1], h->stream);
   if (e != cudaSuccess) return fail(h, TR_ECUDA, "tube forward: %s", cudaGetErrorString(e));
   h->launches += 1;
-  tr_status st = slice_pass(h, h->Abar, h->Gbar, 1.0 / mu, h->t, true);
+  tr_status st = slice_pass(h, h->Abar, h->Gbar, 1.0 / mu, h->t, true, h->abar_planes);
   if (st != TR_OK) return st;
   if (pev) e = cudaEventRecord(pev[2], h->stream);
   if (with_inverse) {
@@ -1084,6 +1094,17 @@ extern "C" tr_status tr_profile_slice_pass(tr_handle *h, const void *Abar, void 
   SliceWork w = h->sw;
   w.dt = nullptr;
   w.prof = &prof;
+  // a handle whose steps hand the slice pass BF16 planes is profiled on the
+  // same path: the FP32 Abar is split into the handle's Abar first
+  if (h->abar_planes && Abar != h->Abar) {
+    cudaError_t e = launch_split_planes((const float *)Abar, h->Abar, h->n * h->P, h->stream);
+    if (e != cudaSuccess) {
+      for (int i = 0; i < SliceProf::kMax; ++i) cudaEventDestroy(prof.ev[i]);
+      return fail(h, TR_ECUDA, "split planes: %s", cudaGetErrorString(e));
+    }
+    Abar = h->Abar;
+    w.asplit = 1;
+  }
   std::vector<double> acc(SliceProf::kMax, 0.0);
   int nk = 0;
   tr_status st = TR_OK;
@@ -1351,18 +1372,27 @@ extern "C" tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups)
   // slice ranges
   int best_g = 1;
   if (h->prm.engine == TR_LR_RSVD) {
-    TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->Abar, false,
-                                h->stream));
-    h->launches += 1;
+    if (h->abar_planes) {   // the steps' form: Abar as BF16 planes
+      TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->Gbar, false,
+                                  h->stream));
+      TR_CUDA(h, launch_split_planes((const float *)h->Gbar, h->Abar, h->n * h->P, h->stream));
+      h->launches += 2;
+    } else {
+      TR_CUDA(h, launch_transform(h->dtype, h->P, (int)h->n, h->td, h->mats, h->M, h->Abar, false,
+                                  h->stream));
+      h->launches += 1;
+    }
     const double tau = 1.0 / h->mu;
     float bestg = 0.f;
     for (int G = 1; G <= kSideStreams; G *= 2) {
       if (G > 1 && G > h->n) break;
       tr_status st = tr_set_slice_groups(h, G);
       if (st != TR_OK) return st;
-      if ((st = slice_pass(h, h->Abar, h->Gbar, tau, h->t)) != TR_OK) return st;
+      const bool pl = h->abar_planes;
+      if ((st = slice_pass(h, h->Abar, h->Gbar, tau, h->t, false, pl)) != TR_OK) return st;
       float ms = 0.f;
-      st = time_ms(h, r, ms, [&](int) { return slice_pass(h, h->Abar, h->Gbar, tau, h->t); });
+      st = time_ms(h, r, ms,
+                   [&](int) { return slice_pass(h, h->Abar, h->Gbar, tau, h->t, false, pl); });
       if (st != TR_OK) return st;
       if (G == 1 || ms < bestg) {
         bestg = ms;

@@ -43,6 +43,7 @@ struct TubeScalars {
   double psi_theta, psi_gamma;
   const double *dmu = nullptr;  // when set: mu^t = *dmu (device), lam_over_mu = lambda / mu^t
   double lambda = 0.0;
+  int planes = 0;     // FP32: write Abar as BF16 planes (SliceWork::asplit)
 };
 
 // Device copy of the penalty schedule, so that a captured step stays valid
@@ -111,6 +112,10 @@ bool encode_tensor_2d(CUtensorMap *out, const void *base, bool u8, int64_t cols,
 // breaks a tensor-copy rule or the driver refuses it.
 bool encode_tensor_3d_f32(CUtensorMap *out, const void *base, int64_t d0, int64_t d1, int64_t d2,
                           int64_t s1, int64_t s2, int box0, int box1, bool swizzle128);
+// The same for elements of esz bytes: 4 (FP32) or 2 (BF16); strides in
+// elements, box0 * esz = 128 with the swizzle.
+bool encode_tensor_3d(CUtensorMap *out, const void *base, int esz, int64_t d0, int64_t d1,
+                      int64_t d2, int64_t s1, int64_t s2, int box0, int box1, bool swizzle128);
 
 // ---- tube passes (tube_kernels.cu) ----
 cudaError_t launch_tube_forward(tr_dtype dt, int64_t P, int n, const TransformDesc &td,
@@ -182,7 +187,15 @@ struct SliceWork {
   const int *dt;  // optional: iteration index of the Philox counters (device)
   SliceProf *prof = nullptr;  // optional: per-kernel events (eager passes only)
   int nA = 0;   // slices in the Abar/Gbar arrays (0: n), the range of slice ids
+  int asplit = 0;  // Abar is given as two BF16 planes (hi, then lo: x = hi + lo),
+                   // FP32 problems in the BF16 and split-BF16 forms only
 };
+// Whether an n-slice stack of n1 x n2 slices with sketch width l can take its
+// Abar as BF16 planes (16-byte row and slice strides, l <= 64).
+bool planes_ok(int64_t n, int n1, int n2, int l);
+// FP32 x[0..count) -> BF16 planes: dst[i] = hi = bf16(x[i]), dst[count + i] =
+// lo = bf16(x[i] - hi).
+cudaError_t launch_split_planes(const float *x, void *dst, int64_t count, cudaStream_t s);
 // Workspace of the fixed-accuracy engine (Alg. 3 per slice).
 struct AdaptWork {
   int b, kcap;          // block size, basis cap (a multiple of b)

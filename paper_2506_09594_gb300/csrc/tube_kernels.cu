@@ -23,6 +23,8 @@
 
 #include <initializer_list>
 
+#include <cuda_bf16.h>
+
 #include "tr_internal.cuh"
 
 namespace {
@@ -293,6 +295,49 @@ __device__ void tile_store(T *__restrict__ dst, const T *tile, int64_t P, int n,
   }
 }
 
+// The tile as Abar's BF16 planes: hi = bf16(x) at j P + p, lo = bf16(x - hi)
+// at n P + j P + p (x - hi is exact in FP32).  FP32 only.
+template <typename T, int VEC>
+__device__ void tile_store_planes(T *__restrict__ dst, const T *tile, int64_t P, int n, int TP,
+                                  int64_t p0) {
+  if constexpr (sizeof(T) == 4) {
+    __nv_bfloat16 *hi_p = reinterpret_cast<__nv_bfloat16 *>(dst);
+    __nv_bfloat16 *lo_p = hi_p + (int64_t)n * P;
+    const int per_row = TP / VEC, total = n * per_row;
+    for (int e = threadIdx.x; e < total; e += kTubeThreads) {
+      const PackIdx q = pack_idx(e, per_row, VEC);
+      if (p0 + q.p >= P) continue;
+      const Pk<T, VEC> x = ld<T, VEC>(tile + q.j * TP + q.p);
+      const int64_t o = (int64_t)q.j * P + p0 + q.p;
+      if constexpr (VEC == 4) {
+        __nv_bfloat162 h[2], l[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          h[i] = __floats2bfloat162_rn(x.v[2 * i], x.v[2 * i + 1]);
+          const float2 f = __bfloat1622float2(h[i]);
+          l[i] = __floats2bfloat162_rn(x.v[2 * i] - f.x, x.v[2 * i + 1] - f.y);
+        }
+        *reinterpret_cast<uint2 *>(hi_p + o) = *reinterpret_cast<const uint2 *>(h);
+        *reinterpret_cast<uint2 *>(lo_p + o) = *reinterpret_cast<const uint2 *>(l);
+      } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(x.v[i]);
+          hi_p[o + i] = h;
+          lo_p[o + i] = __float2bfloat16_rn(x.v[i] - __bfloat162float(h));
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void store_abar(T *__restrict__ Abar, const T *tile, int64_t P, int n,
+                                           int TP, int64_t p0, int planes) {
+  if (sizeof(T) == 4 && planes) tile_store_planes<T, VEC>(Abar, tile, P, n, TP, p0);
+  else tile_store<T, VEC>(Abar, tile, P, n, TP, p0);
+}
+
 // Scalars of the forward update with mu^t taken from the device schedule
 // when the launch carries one.
 __device__ __forceinline__ TubeScalars resolve(const TubeScalars &sc) {
@@ -398,7 +443,7 @@ tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
   }
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, false);
-  tile_store<T, VEC>(Abar, tile, P, n, TP, p0);
+  store_abar<T, VEC>(Abar, tile, P, n, TP, p0, sc.planes);
   if (bad) atomicOr(flags, 1);
   const T v[3] = {rL, rE, rC};
   unsigned long long *const slots[3] = {res + RES_DL, res + RES_DE, res + RES_CONS};
@@ -583,7 +628,7 @@ tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restric
   }
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, false);
-  tile_store<T, VEC>(Abar, tile, P, n, TP, p0);
+  store_abar<T, VEC>(Abar, tile, P, n, TP, p0, sc.planes);
   if (bad) atomicOr(flags, 1);
   const T v[5] = {rLG, rG, rL, rE, rC};
   unsigned long long *const slots[5] = {res_prev + RES_LG, res_prev + RES_DG, res + RES_DL,

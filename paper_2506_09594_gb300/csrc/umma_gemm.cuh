@@ -72,6 +72,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// The same with the 128-byte swizzle (layout type 2 in bits 61-63): tiles of
+// 8 rows x 128 bytes whose 16-byte chunk c of row r sits at chunk c ^ (r mod
+// 8), 1024-byte aligned.  K-major: rows are M/N, sbo = 8-row group stride
+// (lbo unused).  MN-major: rows are k, 128 bytes = 64 BF16 along M/N; lbo =
+// stride between 64-wide M/N blocks, sbo = stride between 8-row k groups.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
 // 17-22, M >> 4 in bits 24-28.
@@ -79,6 +88,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+
+// Bit 15 of the instruction descriptor: A is MN-major (transposed).
+constexpr uint32_t kIdescAMajorMN = 1u << 15;
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
                                          uint32_t accumulate) {

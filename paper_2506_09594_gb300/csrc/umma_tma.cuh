@@ -52,7 +52,9 @@ constexpr int kBM = 128;
 constexpr int kKC = 32;   // K elements per chunk: two MMAs of K = 16
 
 struct Args {
-  CUtensorMap amap;   // FP32 3D view of A: {K, M, nA} (k contiguous) or {M, K, nA}
+  CUtensorMap amap;   // FP32 3D view of A: {K, M, nA} (k contiguous) or {M, K, nA};
+                      // planes_kernel: BF16 view of A's hi plane
+  CUtensorMap amap_lo;  // planes_kernel: BF16 view of A's lo plane (SPLIT = 3)
   CUtensorMap bmap;   // FP32 3D view of B: {K, N, batch}
   int M, N, K;
   int a_kcontig;      // 1: A's k is contiguous (A = Abar), 0: A's m is (A = Abar^T)
@@ -325,6 +327,302 @@ __global__ void __launch_bounds__(kThreads)
       for (int c = done_chunks; c < issued; ++c)
         wait_phase(&full[c % STAGES], (uint32_t)((c / STAGES) & 1));
     }
+  }
+  pdl_trigger();
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------
+// The same products with A already split: the tube pass writes Abar as two
+// BF16 planes (x = hi + lo), so A's tiles go from HBM straight into the
+// operand layout and only B (the FP32 panel, N <= 64 columns) is converted.
+// K chunks of 64.  A tiles use the 128-byte swizzle: with k contiguous
+// (Y = Abar X) a box {64 k, 128 m} is the K-major operand (rows of 128
+// bytes, 8-row groups 1024 bytes apart); with m contiguous (W = Abar^T Q)
+// two boxes {64 m, 64 k} are the MN-major operand (rows are k; the second
+// 64-row block of m 8192 bytes on).  B is staged as two FP32 boxes {32 k,
+// NP n} (128-byte swizzle) and converted into a K-major BF16 tile with the
+// same swizzle.  K steps past K are not issued.
+//
+// One persistent CTA per SM; its warps take fixed roles and hand chunks to
+// one another through mbarriers, so that no role waits on another's latency
+// chain:
+//   warp 0 (one thread)  copies chunk c into stage c % STAGES once the MMAs
+//                        of chunk c - STAGES have released it (empty);
+//   warp 1 (one thread)  issues chunk c's MMAs once it has landed (full)
+//                        and its B is converted (cfull); commits release
+//                        the stage (empty) and the conversion buffer
+//                        (cempty); a tile's last chunk commits its
+//                        accumulator (afull).  Two TMEM accumulators
+//                        alternate; a tile's first MMA waits until the
+//                        epilogue has drained its accumulator (aempty);
+//   warps 2-3            convert B of chunk c into conversion buffer c % 2;
+//   warps 4-7            epilogue: accumulator -> C (warp w reads TMEM
+//                        lanes 32 (w - 4) ..).
+// Every wait is bounded and also gives up once another role has (abort);
+// the CTA then records the failure in *err, waits (bounded) for its copies
+// and MMAs in flight, and frees its TMEM.
+constexpr int kKP = 64;   // K elements per chunk: four MMAs of K = 16
+
+template <int NP, int STAGES, int SPLIT>
+struct PlanesLayout {
+  static constexpr int a_plane = kBM * kKP * 2;                  // one BF16 plane tile
+  static constexpr int a_stage = a_plane * (SPLIT > 1 ? 2 : 1);
+  static constexpr int b_half = NP * 128;                        // FP32 box {32 k, NP n}
+  static constexpr int b_stage = 2 * b_half;
+  static constexpr int stage = a_stage + b_stage;
+  static constexpr int b_conv = NP * kKP * 2;                    // one BF16 copy of B
+  static constexpr int conv = b_conv * (SPLIT > 1 ? 2 : 1);
+  static constexpr int total = STAGES * stage + 2 * conv;
+  static_assert(stage % 1024 == 0 && b_conv % 1024 == 0 && a_plane % 1024 == 0,
+                "swizzled tiles need 1024-byte alignment");
+};
+
+// wait_phase that also returns false once *abort is set
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
+                                              const volatile int *abort) {
+  const uint32_t addr = umma::smem_u32(bar);
+  for (uint32_t it = 0; it < umma::kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && *abort) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(bar)) : "memory");
+}
+
+template <int NP, int STAGES, int SPLIT>
+__global__ void __launch_bounds__(kThreads)
+    planes_kernel(const __grid_constant__ Args g, int *err) {
+  pdl_wait();
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+  __shared__ __align__(8) uint64_t cfull[2], cempty[2], afull[2], aempty[2], drain;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s, issued_s, consumed_s;
+  constexpr int kMaxTiles = 64;
+  __shared__ int tile_jb[kMaxTiles];
+  using Lay = PlanesLayout<NP, STAGES, SPLIT>;
+  constexpr int TMEM_COLS = 2 * NP;   // two accumulators of 128 lanes x NP columns
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mtiles = (g.M + kBM - 1) / kBM;
+  int entries = g.count ? *g.count : g.batch;
+  if (entries > g.batch) entries = g.batch;
+  const int ntiles = entries * mtiles;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (my_tiles == 0) return;   // block-uniform, before any TMEM use
+  const int nk = (g.K + kKP - 1) / kKP;
+  const int total = my_tiles * nk;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     umma::smem_u32(&tmem_base_s)),
+                 "r"((uint32_t)TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int lt = tid; lt < my_tiles && lt < kMaxTiles; lt += kThreads) {
+    const int b = (blockIdx.x + lt * gridDim.x) / mtiles;
+    tile_jb[lt] = g.ids ? g.ids[b] : b;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      umma::mbar_init(&cfull[h], 2);    // one arrival per converter warp
+      umma::mbar_init(&cempty[h], 1);
+      umma::mbar_init(&afull[h], 1);
+      umma::mbar_init(&aempty[h], 4);   // one arrival per epilogue warp
+    }
+    umma::mbar_init(&drain, 1);
+    abort_s = 0;
+    issued_s = 0;
+    consumed_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = tmem_base_s;
+  volatile int *abort = &abort_s;
+
+  struct Tile {
+    int m0, b, za;
+    float *C;
+  };
+  auto tile_of = [&](int lt) {
+    const int t = blockIdx.x + lt * gridDim.x;
+    Tile r;
+    r.b = t / mtiles;
+    r.m0 = (t % mtiles) * kBM;
+    const int jb = lt < kMaxTiles ? tile_jb[lt] : (g.ids ? g.ids[r.b] : r.b);
+    r.za = g.a_by_id ? jb : r.b;
+    r.C = g.C + (int64_t)(g.c_by_id ? jb : r.b) * g.sCb;
+    return r;
+  };
+
+  if (warp == 0) {
+    // ---- copies
+    if (lane == 0) {
+      int c = 0;
+      for (; c < total; ++c) {
+        const int s = c % STAGES, kc = c % nk;
+        if (c >= STAGES && !wait_or_abort(&empty[s], (uint32_t)(((c / STAGES) - 1) & 1), abort)) {
+          *abort = 1;
+          break;
+        }
+        const Tile tl = tile_of(c / nk);
+        uint8_t *st = smem + s * Lay::stage;
+        expect_tx(&full[s], (uint32_t)Lay::stage);
+        if (g.a_kcontig) {
+          tma_load_3d(st, &g.amap, kc * kKP, tl.m0, tl.za, &full[s]);
+          if (SPLIT > 1)
+            tma_load_3d(st + Lay::a_plane, &g.amap_lo, kc * kKP, tl.m0, tl.za, &full[s]);
+        } else {
+          tma_load_3d(st, &g.amap, tl.m0, kc * kKP, tl.za, &full[s]);
+          tma_load_3d(st + Lay::a_plane / 2, &g.amap, tl.m0 + 64, kc * kKP, tl.za, &full[s]);
+          if (SPLIT > 1) {
+            tma_load_3d(st + Lay::a_plane, &g.amap_lo, tl.m0, kc * kKP, tl.za, &full[s]);
+            tma_load_3d(st + Lay::a_plane + Lay::a_plane / 2, &g.amap_lo, tl.m0 + 64, kc * kKP,
+                        tl.za, &full[s]);
+          }
+        }
+        uint8_t *sb = st + Lay::a_stage;
+        tma_load_3d(sb, &g.bmap, kc * kKP, 0, tl.b, &full[s]);
+        tma_load_3d(sb + Lay::b_half, &g.bmap, kc * kKP + 32, 0, tl.b, &full[s]);
+      }
+      issued_s = c;
+    }
+  } else if (warp == 1) {
+    // ---- MMAs
+    if (lane == 0) {
+      const uint32_t idesc =
+          umma::idesc_bf16(kBM, NP) | (g.a_kcontig ? 0u : umma::kIdescAMajorMN);
+      // K-major A: 32 bytes per K = 16 inside the swizzled rows; MN-major A:
+      // two 8-row k groups per K = 16, 64-row m blocks half a plane apart
+      const uint32_t a_step = g.a_kcontig ? 32u : 2048u;
+      const uint32_t a_lbo = g.a_kcontig ? 16u : (uint32_t)(Lay::a_plane / 2);
+      int c = 0;
+      bool okm = true;
+      for (int lt = 0; lt < my_tiles && okm; ++lt) {
+        const int a = lt & 1;
+        if (lt >= 2 && !wait_or_abort(&aempty[a], (uint32_t)(((lt >> 1) - 1) & 1), abort)) {
+          okm = false;
+          break;
+        }
+        umma::fence_after();
+        const uint32_t acc = tmem + (uint32_t)(a * NP);
+        for (int kc = 0; kc < nk; ++kc) {
+          const int s = c % STAGES, h = c & 1;
+          if (!wait_or_abort(&full[s], (uint32_t)((c / STAGES) & 1), abort) ||
+              !wait_or_abort(&cfull[h], (uint32_t)((c >> 1) & 1), abort)) {
+            okm = false;
+            break;
+          }
+          umma::fence_after();
+          const uint32_t a_hi = umma::smem_u32(smem + s * Lay::stage), a_lo = a_hi + Lay::a_plane;
+          const uint32_t bh = umma::smem_u32(smem + STAGES * Lay::stage + h * Lay::conv);
+          const uint32_t bl = bh + Lay::b_conv;
+#pragma unroll
+          for (int ks = 0; ks < kKP / 16; ++ks) {
+            if (kc * kKP + ks * 16 >= g.K) break;
+            const uint64_t dah = umma::smem_desc_sw128(a_hi + ks * a_step, a_lbo, 1024);
+            const uint64_t dbh = umma::smem_desc_sw128(bh + ks * 32, 16, 1024);
+            umma::mma_bf16(acc, dah, dbh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+            if (SPLIT > 1) {
+              const uint64_t dal = umma::smem_desc_sw128(a_lo + ks * a_step, a_lbo, 1024);
+              const uint64_t dbl = umma::smem_desc_sw128(bl + ks * 32, 16, 1024);
+              umma::mma_bf16(acc, dah, dbl, idesc, 1u);
+              umma::mma_bf16(acc, dal, dbh, idesc, 1u);
+            }
+          }
+          umma::mma_commit(&empty[s]);
+          umma::mma_commit(&cempty[h]);
+          ++c;
+        }
+        if (okm) umma::mma_commit(&afull[a]);
+      }
+      if (!okm) *abort = 1;
+      consumed_s = c;
+      // every MMA issued completes before the CTA tears down
+      umma::mma_commit(&drain);
+      wait_phase(&drain, 0u);
+    }
+  } else if (warp < 4) {
+    // ---- B conversion (64 threads)
+    const int ct = tid - 64;
+    for (int c = 0; c < total; ++c) {
+      const int s = c % STAGES, h = c & 1;
+      bool okc = wait_or_abort(&full[s], (uint32_t)((c / STAGES) & 1), abort);
+      if (okc && c >= 2) okc = wait_or_abort(&cempty[h], (uint32_t)(((c >> 1) - 1) & 1), abort);
+      if (!__all_sync(0xffffffffu, okc)) {
+        if (lane == 0) *abort = 1;
+        break;
+      }
+      const uint8_t *sb = smem + s * Lay::stage + Lay::a_stage;
+      uint8_t *b_hi = smem + STAGES * Lay::stage + h * Lay::conv;
+      uint8_t *b_lo = b_hi + Lay::b_conv;
+      for (int u = ct; u < NP * (kKP / 8); u += 64) {
+        const int r = u % NP, kq = u / NP;   // row r, k-core kq (8 k)
+        float x[8];
+        get8_swz(sb + (kq >> 2) * Lay::b_half, r, kq & 3, x);
+        put8<SPLIT>(x, b_hi, b_lo, r * 128 + ((kq ^ (r & 7)) << 4));
+      }
+      umma::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cfull[h]);
+    }
+  } else {
+    // ---- epilogue (warps 4-7)
+    const int q = warp & 3;
+    for (int lt = 0; lt < my_tiles; ++lt) {
+      const int a = lt & 1;
+      const bool oke = wait_or_abort(&afull[a], (uint32_t)((lt >> 1) & 1), abort);
+      if (!__all_sync(0xffffffffu, oke)) {
+        if (lane == 0) *abort = 1;
+        break;
+      }
+      umma::fence_after();
+      const Tile tl = tile_of(lt);
+      const int row = tl.m0 + q * 32 + lane;
+#pragma unroll
+      for (int c0 = 0; c0 < NP; c0 += 32) {
+        float v[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * NP + c0), v);
+        if (row < g.M) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (c0 + c < g.N) tl.C[(int64_t)row * g.sCi + (int64_t)(c0 + c) * g.sCn] = v[c];
+        }
+      }
+      umma::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&aempty[a]);
+    }
+  }
+  __syncthreads();
+  if (abort_s && tid == 0) {
+    atomicExch(err, 1);
+    // copies issued but never consumed by an MMA land before the CTA exits
+    for (int c = consumed_s; c < issued_s; ++c)
+      wait_phase(&full[c % STAGES], (uint32_t)((c / STAGES) & 1));
   }
   pdl_trigger();
   umma::fence_before();

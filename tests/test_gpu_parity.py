@@ -490,6 +490,46 @@ def test_slice_prox_tensor_core_tma_shapes(case, prec):
 
 
 @pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
+@pytest.mark.parametrize("case", [(4, 200, 200, 10, 1e-3, 20, 1, "mcp"),  # M tail 72, K tail 8
+                                  (3, 132, 104, 8, 1e-2, 48, 1, "l1"),    # 64-column tile
+                                  (2, 256, 64, 12, 1e-3, 32, 2, "l1"),    # whole tiles, q = 2
+                                  (5, 40, 40, 3, 0.0, 12, 1, "l1"),       # M < 64, K < 64
+                                  (2, 72, 136, 5, 1e-2, 16, 1, "l1"),     # an MN box wholly past M
+                                  (3, 96, 320, 6, 1e-2, 24, 1, "mcp")])   # n2 > n1
+def test_slice_prox_bf16_planes(case, prec):
+    # A handle whose steps write Abar as BF16 planes (n2 and n1 n2 multiples
+    # of 8, l <= 64) runs its products on the planes: 128-byte swizzled K-major
+    # tiles for Abar X, MN-major tiles for Abar^T Q.  The eager profile takes
+    # that path from an FP32 Abar; tr_slice_prox converts Abar in shared
+    # memory instead.  Both split each element the same way and issue the
+    # same MMAs in the same order, so the two agree to rounding noise, and
+    # both meet the oracle at the form's tolerance.
+    n, n1, n2, r, noise, l, q, phi = case
+    Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 * 3 + n2 + 5)
+    s1 = np.linalg.svd(Ab[0], compute_uv=False)[0]
+    tau = 0.2 * s1
+    kind = prox.L1 if phi == "l1" else prox.MCP
+    gamma = 3.0 * tau + 1.0
+    pen = tr.TR_PEN_L1 if phi == "l1" else tr.TR_PEN_MCP
+    ref, _ = svt.transformed_prox(as_dtype(Ab, "f32"), tau, kind, 1.0, gamma, engine="rsvd", l=l,
+                                  q=q, seed=43, t=3)
+    h = make_handle((n1, n2, n), "f32", rank=l, oversample=0, power_iters=q, phi=pen,
+                    phi_gamma=gamma, seed=43, prec=prec)
+    A = dev(Ab, "f32")
+    G_conv = host(h.slice_prox(A, tau, t=3))
+    out = torch.empty_like(A)
+    kern = h.profile_slice_pass(A, tau, 3, reps=1, out=out)
+    G_pl = host(out)
+    h.close()
+    names = [k for k, _ in kern]
+    assert sum("planes" in k for k in names) == 2 + 2 * q, names
+    assert relF(G_pl, G_conv) < 1e-6, relF(G_pl, G_conv)
+    err = relF(G_pl, ref)
+    assert err < PREC_TOL[prec], err
+    assert np.abs(G_pl - ref).max() < PREC_TOL[prec] * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
 def test_step_tensor_core_forms(prec):
     # The BF16 form keeps the sketch in BF16: its subspace matches the FP32
     # one only where the transformed slices' spectra decay beyond the sketch
