@@ -346,7 +346,12 @@ __global__ void __launch_bounds__(kThreads)
 // two boxes {64 m, 64 k} are the MN-major operand (rows are k; the second
 // 64-row block of m 8192 bytes on).  B is staged as two FP32 boxes {32 k,
 // NP n} (128-byte swizzle) and converted into a K-major BF16 tile with the
-// same swizzle.  K steps past K are not issued.
+// same swizzle, B_hi's NP rows followed by B_lo's.  K steps past K are not
+// issued.  An M = 128 MMA costs about the same for any N up to 64, so the
+// split form takes two MMAs per K step instead of three: A_hi [B_hi; B_lo]
+// (N = 2 NP, columns NP.. of the accumulator take A_hi B_lo) and A_lo B_hi
+// (N = NP, accumulated onto A_hi B_hi); the epilogue adds the two column
+// halves.
 //
 // One persistent CTA per SM; its warps take fixed roles and hand chunks to
 // one another through mbarriers, so that no role waits on another's latency
@@ -417,7 +422,8 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int kMaxTiles = 64;
   __shared__ int tile_jb[kMaxTiles];
   using Lay = PlanesLayout<NP, STAGES, SPLIT>;
-  constexpr int TMEM_COLS = 2 * NP;   // two accumulators of 128 lanes x NP columns
+  constexpr int ACC = SPLIT > 1 ? 2 * NP : NP;   // accumulator columns
+  constexpr int TMEM_COLS = 2 * ACC;              // two accumulators
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -513,8 +519,9 @@ __global__ void __launch_bounds__(kThreads)
   } else if (warp == 1) {
     // ---- MMAs
     if (lane == 0) {
-      const uint32_t idesc =
-          umma::idesc_bf16(kBM, NP) | (g.a_kcontig ? 0u : umma::kIdescAMajorMN);
+      const uint32_t amaj = g.a_kcontig ? 0u : umma::kIdescAMajorMN;
+      const uint32_t idesc = umma::idesc_bf16(kBM, NP) | amaj;
+      const uint32_t idesc2 = umma::idesc_bf16(kBM, 2 * NP) | amaj;
       // K-major A: 32 bytes per K = 16 inside the swizzled rows; MN-major A:
       // two 8-row k groups per K = 16, 64-row m blocks half a plane apart
       const uint32_t a_step = g.a_kcontig ? 32u : 2048u;
@@ -528,7 +535,7 @@ __global__ void __launch_bounds__(kThreads)
           break;
         }
         umma::fence_after();
-        const uint32_t acc = tmem + (uint32_t)(a * NP);
+        const uint32_t acc = tmem + (uint32_t)(a * ACC);
         for (int kc = 0; kc < nk; ++kc) {
           const int s = c % STAGES, h = c & 1;
           if (!wait_or_abort(&full[s], (uint32_t)((c / STAGES) & 1), abort) ||
@@ -538,19 +545,20 @@ __global__ void __launch_bounds__(kThreads)
           }
           umma::fence_after();
           const uint32_t a_hi = umma::smem_u32(smem + s * Lay::stage), a_lo = a_hi + Lay::a_plane;
+          // B_hi's rows, then B_lo's: one K-major tile of 2 NP rows
           const uint32_t bh = umma::smem_u32(smem + STAGES * Lay::stage + h * Lay::conv);
-          const uint32_t bl = bh + Lay::b_conv;
 #pragma unroll
           for (int ks = 0; ks < kKP / 16; ++ks) {
             if (kc * kKP + ks * 16 >= g.K) break;
+            const uint32_t first = (kc > 0 || ks > 0) ? 1u : 0u;
             const uint64_t dah = umma::smem_desc_sw128(a_hi + ks * a_step, a_lbo, 1024);
             const uint64_t dbh = umma::smem_desc_sw128(bh + ks * 32, 16, 1024);
-            umma::mma_bf16(acc, dah, dbh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
             if (SPLIT > 1) {
               const uint64_t dal = umma::smem_desc_sw128(a_lo + ks * a_step, a_lbo, 1024);
-              const uint64_t dbl = umma::smem_desc_sw128(bl + ks * 32, 16, 1024);
-              umma::mma_bf16(acc, dah, dbl, idesc, 1u);
-              umma::mma_bf16(acc, dal, dbh, idesc, 1u);
+              umma::mma_bf16(acc, dah, dbh, idesc2, first);   // A_hi [B_hi; B_lo]
+              umma::mma_bf16(acc, dal, dbh, idesc, 1u);       // + A_lo B_hi
+            } else {
+              umma::mma_bf16(acc, dah, dbh, idesc, first);
             }
           }
           umma::mma_commit(&empty[s]);
@@ -602,10 +610,17 @@ __global__ void __launch_bounds__(kThreads)
       umma::fence_after();
       const Tile tl = tile_of(lt);
       const int row = tl.m0 + q * 32 + lane;
+      const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * ACC);
 #pragma unroll
       for (int c0 = 0; c0 < NP; c0 += 32) {
         float v[32];
-        umma::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * NP + c0), v);
+        umma::tmem_ld32(lanes + (uint32_t)c0, v);
+        if (SPLIT > 1) {   // + the A_hi B_lo half
+          float w[32];
+          umma::tmem_ld32(lanes + (uint32_t)(NP + c0), w);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) v[c] += w[c];
+        }
         if (row < g.M) {
 #pragma unroll
           for (int c = 0; c < 32; ++c)

@@ -501,9 +501,9 @@ def test_slice_prox_bf16_planes(case, prec):
     # of 8, l <= 64) runs its products on the planes: 128-byte swizzled K-major
     # tiles for Abar X, MN-major tiles for Abar^T Q.  The eager profile takes
     # that path from an FP32 Abar; tr_slice_prox converts Abar in shared
-    # memory instead.  Both split each element the same way and issue the
-    # same MMAs in the same order, so the two agree to rounding noise, and
-    # both meet the oracle at the form's tolerance.
+    # memory instead.  Both split each element the same way and form the same
+    # three partial products (summed in another order), so the two agree to
+    # FP32 rounding noise, and both meet the oracle at the form's tolerance.
     n, n1, n2, r, noise, l, q, phi = case
     Ab = synth.lowrank_plus_noise_stack(n, n1, n2, r, noise, seed=n1 * 3 + n2 + 5)
     s1 = np.linalg.svd(Ab[0], compute_uv=False)[0]
@@ -523,7 +523,7 @@ def test_slice_prox_bf16_planes(case, prec):
     h.close()
     names = [k for k, _ in kern]
     assert sum("planes" in k for k in names) == 2 + 2 * q, names
-    assert relF(G_pl, G_conv) < 1e-6, relF(G_pl, G_conv)
+    assert relF(G_pl, G_conv) < 1e-5, relF(G_pl, G_conv)
     err = relF(G_pl, ref)
     assert err < PREC_TOL[prec], err
     assert np.abs(G_pl - ref).max() < PREC_TOL[prec] * np.abs(ref).max()
