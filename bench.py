@@ -288,26 +288,26 @@ def kernel_rooflines(kernels, w, esz, hbm_peak, tflops_peak):
     return out
 
 
-def oracle_parity(w, M, mask, states, tol):
-    """The FP64 oracle's two ADMM steps from the GPU's state s0 against the
-    GPU's state after the same two steps (an eager step, then a replay of the
+def oracle_parity(w, M, mask, states, tol, steps=2, noise_model=None):
+    """The FP64 oracle's `steps` ADMM steps from the GPU's state s0 against
+    the GPU's state after the same steps (an eager step, then replays of the
     timed graph): relative Frobenius error and largest elementwise error
     (over the largest |value|) of L, E, Y, Lambda and G."""
     import numpy as np
     from oracle import admm
     s0, s2 = states
+    nm = noise_model or w.noise_model
     p = admm.Params(lam=admm.default_lambda(w.n1, w.n2, w.tdims), engine="rsvd", l=w.l, q=w.q,
-                    seed=w.seed, noise=admm.NOISE_NONE if w.noise_model == "none"
-                    else admm.NOISE_L1)
+                    seed=w.seed, noise=admm.NOISE_NONE if nm == "none" else admm.NOISE_L1)
     f64 = lambda a: np.asarray(a, dtype=np.float64)
     st = admm.State(L=f64(s0["L"]), E=f64(s0["E"]), Y=f64(s0["Y"]), Lam=f64(s0["Lam"]),
                     G=f64(s0["G"]), mu=float(s0["mu"]), t=int(s0["t"]))
     Mq = f64(np.asarray(M, dtype=np.float32) if w.dtype == "f32" else M)
     t0 = time.perf_counter()
-    for _ in range(2):
+    for _ in range(steps):
         st, _ = admm.step(st, Mq, mask, w.tdims, p)
     el = time.perf_counter() - t0
-    out = {"steps": 2, "from_iteration": int(s0["t"]), "tol": tol, "oracle_s": el}
+    out = {"steps": steps, "from_iteration": int(s0["t"]), "tol": tol, "oracle_s": el}
     ok = True
     for name in ("L", "E", "Y", "Lam", "G"):
         want = getattr(st, name)
@@ -868,16 +868,17 @@ def models_section(tr, torch, K):
 def precision_forms(tr, torch, K):
     """The three operand forms on the 1024x1024x64 workload (rank 32, 20%
     observed, l = 48): device ms per step (graph replay, K steps after 5
-    warm-up steps) and the relative Frobenius difference of L from the plain
-    FP32 form after the same steps.  Sampled parity with the FP64 oracle at
-    this size is a GPU test."""
+    warm-up steps), the relative Frobenius difference of L from the plain
+    FP32 form after the same steps, and each form's parity with the FP64
+    oracle for one step from its state after them (tolerance 1e-4 for the
+    FP32 and split-BF16 forms, 1e-3 for the BF16 form)."""
     from paper_2506_09594_gb300 import synth
     w = synth.WORKLOADS["tubal1024x64_r32"]
     X, M, mask, _ = synth.make_problem(w)
     Md = torch.from_numpy(M).float().cuda()
     maskd = torch.from_numpy(mask).cuda()
     Xd = torch.from_numpy(X).float().cuda()
-    del X, M, mask
+    del X
     stream = torch.cuda.Stream()
     out = {"workload": w.name, "dims": list(w.dims), "rank": w.rank, "sketch_width": w.l,
            "sampling_ratio": w.sr, "steps": K, "schedule": "mu0 0.05, growth 1.1"}
@@ -909,7 +910,16 @@ def precision_forms(tr, torch, K):
                                    "slice_pass": ph["slice_pass"]},
                      "recovery_rel_err": float(torch.linalg.norm((L - Xd).double())
                                                / torch.linalg.norm(Xd.double()))}
+        # one more step of this form against the oracle's step from the same state
+        to_host = lambda d: {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in d.items()}
+        s0 = to_host(h.get_state())
+        h.step()
+        s1 = to_host(h.get_state())
         h.close()
+        out[name]["oracle_parity"] = oracle_parity(w, M, mask, (s0, s1),
+                                                   1e-3 if name == "bf16" else 1e-4, steps=1,
+                                                   noise_model="none")
+        del s0, s1
     base = Ls["fp32"].double()
     for name in ("bf16x3", "bf16"):
         out[name]["L_rel_diff_vs_fp32"] = float(torch.linalg.norm(Ls[name].double() - base)

@@ -492,7 +492,9 @@ int64_t tr_mlp_param_count(void);
 /* Install predictor weights in a TR_LR_LEARNED handle: `params` is a host
  * array of `count` (= TR_MLP_PARAMS) floats.  Weights files (model_path)
  * hold the 8 bytes "TRRANK01", four little-endian int32 (16, 128, 3, 0),
- * one int64 count, then `count` float32 parameters.  Synchronises.
+ * one int64 count, then `count` float32 parameters.  The hidden layers'
+ * weights are converted to FP16 here, once, for the slice passes' forward
+ * evaluations.  Synchronises.
  * Errors: TR_EINVAL (not a learned handle, wrong count).                    */
 tr_status tr_set_model(tr_handle *h, const float *params, int64_t count);
 

@@ -74,13 +74,29 @@ __device__ void stage_weights(const float *__restrict__ prm, int i, __half *Ws) 
   }
 }
 
+// The hidden layers' weights as FP16 in stage_weights<true>'s layout, layer i
+// at w16 + i kH kH: converted once per model (tr_set_model), so that the
+// inference passes copy them instead of converting them on every call.
+__global__ void mlp_pack_kernel(const float *__restrict__ prm, __half *__restrict__ w16) {
+  for (int li = 0; li < kLayers; ++li) {
+    const float *W = prm + layer_off(li);
+    const int in = (int)layer_in(li), out = (int)layer_out(li);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < in * out; e += gridDim.x * blockDim.x) {
+      const int o = e / in, k = e % in;
+      w16[(int64_t)li * kH * kH + k * out + o] = __float2half_rn(W[e]);
+    }
+  }
+}
+
 // Forward pass of kRows rows.  128 threads: thread o owns hidden unit o.
 // STORE keeps the post-ReLU activations H[l] (B x kH) for the backward pass.
+// w16 (optional): the packed FP16 hidden weights of prm.
 template <bool STORE>
 __global__ void __launch_bounds__(kH) mlp_forward_kernel(const float *__restrict__ prm,
                                                          const float *__restrict__ X, int B,
                                                          float *__restrict__ H,
-                                                         float *__restrict__ yhat) {
+                                                         float *__restrict__ yhat,
+                                                         const __half *__restrict__ w16) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __half *Ws = reinterpret_cast<__half *>(smem_raw);
   float *act = reinterpret_cast<float *>(smem_raw + (size_t)kH * kH * sizeof(__half));
@@ -94,7 +110,13 @@ __global__ void __launch_bounds__(kH) mlp_forward_kernel(const float *__restrict
   for (int li = 0; li < kLayers; ++li) {
     const int in = (int)layer_in(li);
     __syncthreads();
-    stage_weights<true>(prm, li, Ws);
+    if (w16) {   // in * kH halves, 16 bytes at a time
+      const uint4 *src = reinterpret_cast<const uint4 *>(w16 + (int64_t)li * kH * kH);
+      uint4 *dst = reinterpret_cast<uint4 *>(Ws);
+      for (int e = threadIdx.x; e < in * kH / 8; e += blockDim.x) dst[e] = src[e];
+    } else {
+      stage_weights<true>(prm, li, Ws);
+    }
     __syncthreads();
     const float bo = prm[layer_off(li) + (int64_t)kH * in + o];
     float acc[kRows];
@@ -545,8 +567,15 @@ cudaError_t launch_mlp_init(float *prm, uint64_t seed, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t mlp_pack_halves() { return (size_t)kLayers * kH * kH; }
+
+cudaError_t launch_mlp_pack(const float *prm, void *w16, cudaStream_t s) {
+  mlp_pack_kernel<<<64, 256, 0, s>>>(prm, (__half *)w16);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_forward(const float *prm, const float *X, int B, float *yhat, float *H,
-                               cudaStream_t s) {
+                               cudaStream_t s, const void *w16) {
   if (B <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((B + kRows - 1) / kRows);
   cudaError_t e;
@@ -554,12 +583,14 @@ cudaError_t launch_mlp_forward(const float *prm, const float *X, int B, float *y
     if ((e = cudaFuncSetAttribute(mlp_forward_kernel<true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem)) != cudaSuccess)
       return e;
-    mlp_forward_kernel<true><<<grid, kH, kMlpSmem, s>>>(prm, X, B, H, yhat);
+    mlp_forward_kernel<true><<<grid, kH, kMlpSmem, s>>>(prm, X, B, H, yhat,
+                                                     (const __half *)w16);
   } else {
     if ((e = cudaFuncSetAttribute(mlp_forward_kernel<false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem)) != cudaSuccess)
       return e;
-    mlp_forward_kernel<false><<<grid, kH, kMlpSmem, s>>>(prm, X, B, nullptr, yhat);
+    mlp_forward_kernel<false><<<grid, kH, kMlpSmem, s>>>(prm, X, B, nullptr, yhat,
+                                                      (const __half *)w16);
   }
   return cudaGetLastError();
 }
@@ -668,7 +699,8 @@ cudaError_t launch_slice_learned(tr_dtype dt, const SliceWork &w, LearnedWork &l
   if ((e = launch_features(dt, n, w.sig, lmax, w.rank, lw.width, thr, lw.thr_prev, tfrac, lw.feat,
                            s, fs)) != cudaSuccess)
     return e;
-  if ((e = launch_mlp_forward(lw.params, lw.feat, n, lw.pred, nullptr, s)) != cudaSuccess) return e;
+  if ((e = launch_mlp_forward(lw.params, lw.feat, n, lw.pred, nullptr, s, lw.w16)) != cudaSuccess)
+    return e;
   if ((e = launch_plan(n, lw.pred, p, lmax, lw.width, lw.ids, lw.counts, s)) != cudaSuccess) return e;
   const int C = plan_classes(lmax);
   group_kernel<<<1, 256, 0, s>>>(n, C, lw.merge_min, lw.counts, lw.ids, lw.gids, lw.gcount);

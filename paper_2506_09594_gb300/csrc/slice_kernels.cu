@@ -376,10 +376,10 @@ cudaError_t split_planes(const float *x, void *dst, int64_t count, cudaStream_t 
 
 // Whether the split planes of an n x n1 x n2 FP32 stack serve the TMA-fed
 // products: rows of n2 BF16 and slices of n1 n2 BF16 at 16-byte multiples,
-// and panels of at most 64 columns.
+// FP32 panel columns of n1 and n2 at 16-byte multiples (the B operands), and
+// panels of at most 64 columns.
 bool planes_view_ok(int64_t n, int n1, int n2, int l) {
-  return n >= 1 && n1 >= 1 && n2 >= 1 && l >= 1 && l <= 64 && n2 % 8 == 0 &&
-         ((int64_t)n1 * n2) % 8 == 0;
+  return n >= 1 && n1 >= 1 && n2 >= 1 && l >= 1 && l <= 64 && n2 % 8 == 0 && n1 % 4 == 0;
 }
 
 // The product with A given as BF16 planes (A = hi + lo, tmag::planes_kernel).

@@ -154,8 +154,8 @@ static void free_profile(tr_handle *h) {
 static void free_all(tr_handle *h) {
   free_profile(h);
   LearnedWork &lw = h->lw;
-  void *lbufs[] = {lw.params, lw.feat, lw.pred, lw.ids, lw.counts, lw.fb_ids, lw.fb_count,
-                   lw.gids, lw.gcount, lw.anorm2, lw.iota};
+  void *lbufs[] = {lw.params, lw.w16, lw.feat, lw.pred, lw.ids, lw.counts, lw.fb_ids,
+                   lw.fb_count, lw.gids, lw.gcount, lw.anorm2, lw.iota};
   for (void *b : lbufs)
     if (b) cudaFree(b);
   for (int i = 0; i < TR_LEARNED_STREAMS; ++i) {
@@ -467,6 +467,7 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     lw.p = prm->oversample;
     const int C = plan_classes(l);
     INIT_CUDA(cudaMalloc((void **)&lw.params, (size_t)mlp_param_count() * sizeof(float)));
+    INIT_CUDA(cudaMalloc(&lw.w16, mlp_pack_halves() * 2));
     INIT_CUDA(cudaMalloc((void **)&lw.feat, (size_t)h->n * TR_MLP_IN * sizeof(float)));
     INIT_CUDA(cudaMalloc((void **)&lw.pred, (size_t)h->n * sizeof(float)));
     INIT_CUDA(cudaMalloc((void **)&lw.ids, (size_t)h->n * sizeof(int)));
@@ -497,6 +498,7 @@ extern "C" tr_status tr_init(tr_handle **out, const tr_problem *p, const tr_para
     } else {
       INIT_CUDA(launch_mlp_init(lw.params, prm->seed, h->stream));
     }
+    INIT_CUDA(launch_mlp_pack(lw.params, lw.w16, h->stream));
   }
   INIT_CUDA(cudaMalloc((void **)&h->sched, sizeof(DevSched)));
   {
@@ -1153,6 +1155,7 @@ extern "C" tr_status tr_set_model(tr_handle *h, const float *params, int64_t cou
                 (long long)count);
   TR_CUDA(h, cudaMemcpyAsync(h->lw.params, params, (size_t)count * sizeof(float),
                              cudaMemcpyHostToDevice, h->stream));
+  TR_CUDA(h, launch_mlp_pack(h->lw.params, h->lw.w16, h->stream));
   TR_CUDA(h, cudaStreamSynchronize(h->stream));
   return TR_OK;
 }

@@ -191,7 +191,7 @@ struct SliceWork {
                    // FP32 problems in the BF16 and split-BF16 forms only
 };
 // Whether an n-slice stack of n1 x n2 slices with sketch width l can take its
-// Abar as BF16 planes (16-byte row and slice strides, l <= 64).
+// Abar as BF16 planes (n2 % 8 == 0, n1 % 4 == 0, l <= 64).
 bool planes_ok(int64_t n, int n1, int n2, int l);
 // FP32 x[0..count) -> BF16 planes: dst[i] = hi = bf16(x[i]), dst[count + i] =
 // lo = bf16(x[i] - hi).
@@ -237,6 +237,7 @@ struct LearnedWork {
   int lmax = 0, p = 0;       // plain width (cap), oversampling
   int merge_min = 8;         // width groups with fewer slices join the next wider one
   float *params = nullptr;   // MLP parameters (FP32 master copy)
+  void *w16 = nullptr;       // its hidden weights as FP16, packed once per model
   float *feat = nullptr;     // n x TR_MLP_IN features
   float *pred = nullptr;     // n predicted log(1 + rank)
   int *width = nullptr;      // sketch width used per slice (history of the last pass)
@@ -260,7 +261,10 @@ int64_t mlp_param_count();
 size_t mlp_workspace_floats(int B);
 cudaError_t launch_mlp_init(float *prm, uint64_t seed, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float *prm, const float *X, int B, float *yhat, float *H,
-                               cudaStream_t s);
+                               cudaStream_t s, const void *w16 = nullptr);
+// The hidden layers' weights of prm as FP16 (mlp_pack_halves() halves).
+size_t mlp_pack_halves();
+cudaError_t launch_mlp_pack(const float *prm, void *w16, cudaStream_t s);
 cudaError_t launch_mlp_loss_grad(const float *prm, const float *X, const float *y, int B,
                                  float under, float *work, float *yhat, float *grad, float *loss,
                                  cudaStream_t s);

@@ -530,14 +530,16 @@ def test_slice_prox_bf16_planes(case, prec):
 
 
 @pytest.mark.parametrize("prec", [tr.TR_PREC_BF16, tr.TR_PREC_BF16X3])
-def test_step_tensor_core_forms(prec):
+# (96, 80): the steps hand the slice pass Abar as BF16 planes; (90, 80): n1 is
+# not a multiple of 4, so Abar stays FP32 and the products convert it
+@pytest.mark.parametrize("dims", [(96, 80, 5, 4), (90, 80, 5, 4)])
+def test_step_tensor_core_forms(prec, dims):
     # The BF16 form keeps the sketch in BF16: its subspace matches the FP32
     # one only where the transformed slices' spectra decay beyond the sketch
     # width (the regime the randomized engine is for).  So the iterate here is
     # structured -- L and G near the low-rank truth, small multipliers --
     # rather than white noise (a flat spectrum, where any perturbation of the
     # sketch moves the captured subspace).
-    dims = (96, 80, 5, 4)
     X, M, mask = _problem(dims, seed=77)
     rs = np.random.default_rng(2)
     noise = lambda s: s * rs.standard_normal(M.shape)
