@@ -991,11 +991,20 @@ inline size_t cgs_smem_bytes(size_t esz, int m, int l) {
 // ordering, l/2 disjoint pairs per round; each pair is handled by a group
 // of G lanes that split the rows, so its inner products need log2(G)
 // shuffle levels.
-// The FP32 form takes its square roots and reciprocals from the special
-// function unit (rsqrtf, __frcp_rn): a rotation only has to be accurate to
-// a few units in the last place (the sweeps correct the angle, and c, s
-// come from one t, so c^2 + s^2 = 1 to rounding); it sits on the latency
-// chain of every round.
+// The rotation that zeroes gamma: with d = beta - alpha, t = tan(theta) =
+// sign(d) 2 gamma / (|d| + h), h = sqrt(d^2 + 4 gamma^2) (the smaller root of
+// t^2 + (d / gamma) t - 1 = 0), and since 1 + t^2 = 2 h / (h + |d|),
+//   c = q / sqrt(2 h q),  s = sign(d) 2 gamma / sqrt(2 h q),  q = h + |d|.
+// The FP32 form takes its square roots from the special function unit
+// (rsqrtf): two in sequence, where the ratio form zeta = d / (2 gamma) needs
+// five (rsqrt, reciprocal, rsqrt, reciprocal, rsqrt) on the latency chain of
+// every round.  d and 2 gamma are first scaled by an exact power of two that
+// brings the larger near 1, so the squares neither overflow nor underflow.
+// A rotation only has to be accurate to a few units in the last place (the
+// sweeps correct the angle, and c, s come from one r, so c^2 + s^2 = 1 to
+// rounding).  The caller forms (c, s) alongside the acceptance test and uses
+// them only when a pair is rotated.
+
 template <typename T>
 __device__ __forceinline__ bool jacobi_wants(T al, T be, T ga, T tol) {
   if constexpr (sizeof(T) == 4) return ga != T(0) && fabsf(ga) * rsqrtf(al) * rsqrtf(be) > tol;
@@ -1005,13 +1014,17 @@ __device__ __forceinline__ bool jacobi_wants(T al, T be, T ga, T tol) {
 template <typename T>
 __device__ __forceinline__ void jacobi_rotation(T al, T be, T ga, T &c, T &s) {
   if constexpr (sizeof(T) == 4) {
-    const T zeta = T(0.5) * (be - al) * __frcp_rn(ga);
-    const T az = fabsf(zeta);
-    const T r2 = fmaf(az, az, T(1));
-    const T t = az > T(1e10) ? T(0.5) * __frcp_rn(az) : __frcp_rn(az + r2 * rsqrtf(r2));
-    const T ts = zeta >= T(0) ? t : -t;
-    c = rsqrtf(fmaf(ts, ts, T(1)));
-    s = c * ts;
+    const T d = be - al, g2 = T(2) * ga;
+    const T m = fmaxf(fabsf(d), fabsf(g2));
+    const int e = (__float_as_int(m) >> 23) & 0xff;        // biased exponent of m
+    const T sc = __int_as_float((254 - (e < 254 ? e : 253)) << 23);   // 2^(127 - e)
+    const T dn = d * sc, gn = g2 * sc;
+    const T hh = fmaf(dn, dn, gn * gn);
+    const T h = hh * rsqrtf(hh);
+    const T q = h + fabsf(dn);
+    const T r = rsqrtf(T(2) * h * q);
+    c = q * r;
+    s = (d >= T(0) ? gn : -gn) * r;
   } else {
     const T zeta = (be - al) / (T(2) * ga);
     const T az = fabs(zeta);
@@ -1034,6 +1047,7 @@ __device__ __forceinline__ void named_sync(int nthr) {
 // the J loads overlap the reductions and the update needs no reloads.
 template <typename T, int G, int JR>
 __device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps, int nthr) {
+  // J == nullptr: the rotations are not accumulated
   const int lp = l + (l & 1);
   if (lp < 2 || (int)threadIdx.x >= nthr) return;
   const int npairs = lp / 2;
@@ -1066,8 +1080,8 @@ __device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps
           const bool in = valid && i < l;
           x[t] = in ? wp[i] : T(0);
           y[t] = in ? wq[i] : T(0);
-          u[t] = in ? jp[i] : T(0);
-          v[t] = in ? jq[i] : T(0);
+          u[t] = in && J ? jp[i] : T(0);
+          v[t] = in && J ? jq[i] : T(0);
           al = fma(x[t], x[t], al);
           be = fma(y[t], y[t], be);
           ga = fma(x[t], y[t], ga);
@@ -1078,17 +1092,19 @@ __device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
+        T c, s;
+        jacobi_rotation(al, be, ga, c, s);
         if (valid && jacobi_wants(al, be, ga, tol)) {
-          T c, s;
-          jacobi_rotation(al, be, ga, c, s);
 #pragma unroll
           for (int t = 0; t < JR; ++t) {
             const int i = gl + G * t;
             if (i < l) {
               wp[i] = c * x[t] - s * y[t];
               wq[i] = s * x[t] + c * y[t];
-              jp[i] = c * u[t] - s * v[t];
-              jq[i] = s * u[t] + c * v[t];
+              if (J) {
+                jp[i] = c * u[t] - s * v[t];
+                jq[i] = s * u[t] + c * v[t];
+              }
             }
           }
           if (gl == 0) *flag = 1;
@@ -1119,12 +1135,13 @@ __device__ __forceinline__ T prox_sv(T s, const ShrinkScalars &sh) {
 }
 
 // Per slice: R of B^T = Qb R (P2 holds B^T = Abar^T Q), one-sided Jacobi of
-// R (R J = W with orthogonal columns: B = J Sigma W_n^T Qb^T, so B's left
-// singular vectors are the columns of J and sigma the column norms of W),
-// the shrink, the core C = J diag(shrunk sigma / sigma) J^T, and P1 <- P1 C
-// (= Q C).  Since J diag(sigma~) V_B^T = J diag(sigma~/sigma) J^T B, the
-// rebuild is Gbar = (Q C) B = P1 P2^T with P2 left as B^T: Qb is never
-// formed.  A singular value shrunk to zero drops out (ratio 0).
+// R^T (R^T J = W with orthogonal columns, J orthogonal: B = R^T Qb^T = W (Qb
+// J)^T, so B's left singular vectors are W's normalised columns and sigma
+// their norms; J is not needed and not accumulated), the shrink, the core
+// C = U diag(shrunk sigma / sigma) U^T, and P1 <- P1 C (= Q C).  Since
+// U diag(sigma~) V_B^T = U diag(sigma~/sigma) U^T B, the rebuild is
+// Gbar = (Q C) B = P1 P2^T with P2 left as B^T: Qb is never formed.  A
+// singular value shrunk to zero drops out (ratio 0).
 template <typename T, int CPW, int RPL, int G, int JR, bool REG>
 __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64_t sP1,
                                 T *__restrict__ P2, int64_t sP2, ShrinkScalars sh,
@@ -1149,30 +1166,38 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   T *P1j = P1 + (int64_t)bb * sP1;
   T *P2j = P2 + (int64_t)bb * sP2;
 
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) J[e] = (e % l == e / l) ? T(1) : T(0);
   // B^T = Qb R: R lands in W, P2 keeps B^T
   if constexpr (REG) block_reg_qr<T, CPW, RPL, false>(P2j, n2, l, panel, tau, W);
   else block_smem_qr<T, false>(P2j, n2, l, panel, tau, W);
+  __syncthreads();
+  // R^T into U = J (column c of R^T = row c of R)
+  T *U = J;
+  const int ldu = l;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) U[e] = W[(size_t)(e % l) * l + e / l];
   // Rotate only while a pair's cosine exceeds max(l, 8) * eps: below that the
   // computed inner product is rounding noise (an l-term dot product).
   const T eps = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
   const T tol = T(l > 8 ? l : 8) * eps;
+  const int max_sweeps = sizeof(T) == 4 ? 16 : 30;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   {
     const int lp = l + (l & 1);
     int nthr = ((lp / 2) * G + 31) / 32 * 32;
     if (nthr > (int)blockDim.x) nthr = blockDim.x;
     __syncthreads();
-    block_jacobi<T, G, JR>(W, J, l, flag, tol, sizeof(T) == 4 ? 16 : 30, nthr);
-    __syncthreads();
+    block_jacobi<T, G, JR>(U, nullptr, l, flag, tol, max_sweeps, nthr);
   }
+  __syncthreads();
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // sigma_i = ||W_i||; U_i = W_i / sigma_i in place
   for (int i = warp; i < l; i += nw) {
     T ss = T(0);
-    for (int r = lane; r < l; r += 32) ss = fma(W[(size_t)i * l + r], W[(size_t)i * l + r], ss);
+    for (int r = lane; r < l; r += 32) ss = fma(U[(size_t)i * ldu + r], U[(size_t)i * ldu + r], ss);
     ss = warp_sum(ss);
+    const T sg = sqrt(ss);
+    const T inv = sg > T(0) ? T(1) / sg : T(0);
+    for (int r = lane; r < l; r += 32) U[(size_t)i * ldu + r] *= inv;
     if (lane == 0) {
-      const T sg = sqrt(ss);
       const T sp = prox_sv(sg, shr);
       ratio[i] = sg > T(0) ? sp / sg : T(0);
       sig_out[(int64_t)j * ldsig + i] = sg;
@@ -1187,11 +1212,12 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     if (width_out) width_out[j] = l;
   }
   for (int i = l + threadIdx.x; i < ldsig; i += blockDim.x) sig_out[(int64_t)j * ldsig + i] = T(0);
-  // C[a][b] = sum_i J[a][i] ratio_i J[b][i]   (column-major C[a + b*l])
+  // C[a][b] = sum_i U[a][i] ratio_i U[b][i]   (column-major C[a + b*l])
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int a = e % l, b = e / l;
     T acc = T(0);
-    for (int i = 0; i < l; ++i) acc = fma(J[(size_t)i * l + a] * ratio[i], J[(size_t)i * l + b], acc);
+    for (int i = 0; i < l; ++i)
+      acc = fma(U[(size_t)i * ldu + a] * ratio[i], U[(size_t)i * ldu + b], acc);
     C[e] = acc;
   }
   for (int e = threadIdx.x; e < n1 * l; e += blockDim.x) panel[e] = P1j[e];

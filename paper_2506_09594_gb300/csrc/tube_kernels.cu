@@ -199,8 +199,9 @@ __device__ void tile_transform(T *tile, int n, int TP, const T *mats, const Tran
     const int nk = td.dim[k], stp = td.stride[k], h = (nk + 1) / 2;
     const T *U = mats + (inverse ? td.off_inv[k] : td.off_fwd[k]);
     const int nfib = n / nk;
+    const int lgtp = 31 - __clz(TP);   // TP is a power of two
     for (int w = threadIdx.x; w < nfib * TP; w += blockDim.x) {
-      const int p = w % TP, f = w / TP;
+      const int p = w & (TP - 1), f = w >> lgtp;
       T *fib = tile + ((f % stp) + (f / stp) * (stp * nk)) * TP + p;
       const int step = stp * TP;
       T a[HK], b[HK];
@@ -252,8 +253,11 @@ __device__ __forceinline__ void load_mats(T *dst, const T *src, int len) {
 struct PackIdx {
   int j, p;
 };
+// per_row = TP / VEC is a power of two (tiles hold 2^k tubes): shifts, not
+// divisions
 __device__ __forceinline__ PackIdx pack_idx(int e, int per_row, int VEC) {
-  return {e / per_row, (e % per_row) * VEC};
+  const int lg = 31 - __clz(per_row);
+  return {e >> lg, (e & (per_row - 1)) * VEC};
 }
 
 // Copy a tile of a slice-major array into shared memory (zero beyond P).
@@ -349,17 +353,30 @@ __device__ __forceinline__ TubeScalars resolve(const TubeScalars &sc) {
   return r;
 }
 
+// The forward update's scalars in the element type, formed once per block
+// (the double-precision division and conversions stay out of the element
+// loop: FP64 issues slowly on this part).
+template <typename T>
+struct FwdK {
+  T mu, imu, thr, th, ga;
+  int noise, psi;
+};
+template <typename T>
+__device__ __forceinline__ FwdK<T> fwd_scalars(const TubeScalars &sc) {
+  return FwdK<T>{T(sc.mu), T(1.0 / sc.mu), T(sc.lam_over_mu), T(sc.psi_theta), T(sc.psi_gamma),
+                 sc.noise, sc.psi};
+}
+
 // The forward elementwise update on a pack; `gv` holds G^t (from global
 // memory or from the fused inverse), `la` Lambda^t.
 template <typename T, int VEC>
 __device__ __forceinline__ void forward_pack(const Pk<T, VEC> &m_, const Pk<uint8_t, VEC> &om,
                                              const Pk<T, VEC> &l0, const Pk<T, VEC> &e0,
                                              const Pk<T, VEC> &y0, const Pk<T, VEC> &gv,
-                                             const Pk<T, VEC> &la, const TubeScalars &sc,
+                                             const Pk<T, VEC> &la, const FwdK<T> &sc,
                                              Pk<T, VEC> &l1, Pk<T, VEC> &e1, Pk<T, VEC> &y1,
                                              Pk<T, VEC> &a, T &rL, T &rE, T &rC, int &bad) {
-  const T mu = T(sc.mu), imu = T(1.0 / sc.mu), thr = T(sc.lam_over_mu);
-  const T th = T(sc.psi_theta), ga = T(sc.psi_gamma);
+  const T mu = sc.mu, imu = sc.imu, thr = sc.thr, th = sc.th, ga = sc.ga;
 #pragma unroll
   for (int i = 0; i < VEC; ++i) {
     const bool o = om.v[i] != 0;
@@ -397,7 +414,7 @@ tube_forward_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restr
   load_mats(mats, mats_g, td.mats_len);
   const int64_t p0 = (int64_t)blockIdx.x * TP;
   const int per_row = TP / VEC, total = n * per_row;
-  const TubeScalars scr = resolve(sc);
+  const FwdK<T> scr = fwd_scalars<T>(resolve(sc));
   T rL = 0, rE = 0, rC = 0;
   int bad = 0;
   for (int e0 = threadIdx.x; e0 < total; e0 += kTubeThreads * kUnroll) {
@@ -569,7 +586,7 @@ tube_fused_kernel(int64_t P, int n, int TP, TransformDesc td, const T *__restric
   __syncthreads();
   tile_transform<T, NK>(tile, n, TP, mats, td, true);
   const T mup = T(dmu_prev ? *dmu_prev : mu_prev);
-  const TubeScalars scr = resolve(sc);
+  const FwdK<T> scr = fwd_scalars<T>(resolve(sc));
   const int per_row = TP / VEC, total = n * per_row;
   T rLG = 0, rG = 0, rL = 0, rE = 0, rC = 0;
   int bad = 0;
@@ -727,7 +744,10 @@ bool tube_geometry(int64_t P, int n, const TransformDesc &td, TubeLaunch &g) {
   g.n = n;
   g.tp = pick_tp<T>(n, td);
   if (!g.tp) return false;
-  if (td.tp > 0 && td.tp <= kMaxTP && tube_smem_for<T>(n, td, td.tp) <= kSmemBudget) g.tp = td.tp;
+  if (td.tp > 0 && td.tp <= kMaxTP && (td.tp & (td.tp - 1)) == 0 &&
+      tube_smem_for<T>(n, td, td.tp) <= kSmemBudget)
+    g.tp = td.tp;
+  if ((g.tp & (g.tp - 1)) != 0) return false;   // the kernels index tiles with shifts
   g.smem = tube_smem_for<T>(n, td, g.tp);
   g.grid = (unsigned)((P + g.tp - 1) / g.tp);
   return true;
