@@ -180,63 +180,109 @@ cudaError_t bgemm(const GemmArgs &g, int batch, cudaStream_t s) {
 }
 
 // Rank-l rebuild Gbar^<j> = Z Qb^T (n1 x n2, row-major) from the column-major
-// panels Z (n1 x l) and Qb (n2 x l).  A 64 x 64 output tile per CTA keeps
-// all l columns of both panel tiles in shared memory (no K tiling: l <= 96),
-// each thread accumulates a 4 x 4 block and writes it as four 16-byte row
-// segments (scalar stores when n2 is not a multiple of 4).
+// panels Z (n1 x l) and Qb (n2 x l).  A CTA owns a BT x BT output tile (a
+// whole slice for slices up to BT x BT) and stages the tile's rows of Z and
+// of Qb k-major in shared memory (Zk[k][i], Qk[k][j]: copies of contiguous
+// panel columns).  Each thread forms 8 x 4 outputs: per k two 16-byte reads
+// of eight rows of Zk (the same address across most of a warp: a broadcast)
+// and one of four columns of Qk (consecutive lanes, consecutive 16 bytes),
+// 32 FMAs, and it writes its rows as 16-byte segments, consecutive lanes
+// covering consecutive columns (scalar stores when n2 is not a multiple of
+// 4).  Large tiles make few, long-lived CTAs whose stores stream back to
+// back; the earlier 64 x 64 tiles spent most of their time loading.
+template <typename T>
+__device__ __forceinline__ void ld4s(const T *p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    const double2 x = *reinterpret_cast<const double2 *>(p);
+    const double2 y = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
+rank_update_kernel(int n1, int n2, int l, int BT, const T *__restrict__ Z, int64_t sZ,
                    const T *__restrict__ Qb, int64_t sQ, T *__restrict__ C, int64_t sC,
                    int vec_ok, SliceSel sel) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Zs = reinterpret_cast<T *>(smem_raw);          // [l][64]
-  T *Qs = Zs + (size_t)l * 64;                       // [l][64]
-  const int m0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+  T *Zk = reinterpret_cast<T *>(smem_raw);          // [l][BT]
+  T *Qk = Zk + (size_t)l * BT;                      // [l][BT]
+  const int r0 = blockIdx.x * BT, c0 = blockIdx.y * BT;
   const int64_t b = blockIdx.z;
   if (sel.count && b >= *sel.count) return;
   const int64_t jb = sel.ids ? sel.ids[b] : b;
   const T *Zb = Z + b * sZ;
   const T *Qbb = Qb + b * sQ;
-  for (int e = threadIdx.x; e < l * 64; e += 256) {
-    const int k = e / 64, i = e % 64;
-    Zs[e] = (m0 + i < n1) ? Zb[(int64_t)k * n1 + m0 + i] : T(0);
-    Qs[e] = (c0 + i < n2) ? Qbb[(int64_t)k * n2 + c0 + i] : T(0);
+  const int tr = n1 - r0 < BT ? n1 - r0 : BT, tc = n2 - c0 < BT ? n2 - c0 : BT;
+  // eight element pairs per thread in flight (BT is a power of two)
+  const int lgbt = 31 - __clz(BT);
+  constexpr int UL = 8;
+  for (int e0 = threadIdx.x; e0 < l * BT; e0 += 256 * UL) {
+    T za[UL], qa[UL];
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int e = e0 + u * 256, k = e >> lgbt, i = e & (BT - 1);
+      const bool in = e < l * BT;
+      za[u] = in && i < tr ? Zb[(int64_t)k * n1 + r0 + i] : T(0);
+      qa[u] = in && i < tc ? Qbb[(int64_t)k * n2 + c0 + i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int e = e0 + u * 256;
+      if (e < l * BT) {
+        Zk[e] = za[u];
+        Qk[e] = qa[u];
+      }
+    }
   }
   __syncthreads();
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
-  for (int k = 0; k < l; ++k) {
-    T a[4], q[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = Zs[k * 64 + ty * 4 + i];
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) q[jj] = Qs[k * 64 + tx * 4 + jj];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], q[jj], acc[i][jj]);
-  }
   T *Cb = C + jb * sC;
-  const int col = c0 + tx * 4;
-  const bool vec = sizeof(T) == 4 && vec_ok && col + 4 <= n2;
+  // tasks of 8 rows x 4 columns; consecutive threads take consecutive column groups
+  const int RG = (tr + 7) / 8, CG = (tc + 3) / 4;
+  int rg = threadIdx.x / CG, cg = threadIdx.x % CG;
+  const int step_r = 256 / CG, step_c = 256 % CG;
+  for (int t = threadIdx.x; t < RG * CG; t += 256) {
+    T acc[8][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = m0 + ty * 4 + i;
-    if (row >= n1) continue;
-    T *dst = Cb + (int64_t)row * n2 + col;
-    if (vec) {
-      *reinterpret_cast<float4 *>(dst) =
-          make_float4((float)acc[i][0], (float)acc[i][1], (float)acc[i][2], (float)acc[i][3]);
-    } else {
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj)
-        if (col + jj < n2) dst[jj] = acc[i][jj];
+      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
+    const T *za = Zk + rg * 8, *qa = Qk + cg * 4;
+    for (int k = 0; k < l; ++k) {
+      T a[8], q[4];
+      ld4s(za + (size_t)k * BT, *reinterpret_cast<T(*)[4]>(a));
+      ld4s(za + (size_t)k * BT + 4, *reinterpret_cast<T(*)[4]>(a + 4));
+      ld4s(qa + (size_t)k * BT, q);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], q[jj], acc[i][jj]);
+    }
+    const int col = c0 + cg * 4;
+    const bool vec = sizeof(T) == 4 && vec_ok && col + 4 <= n2;
+    T *dst = Cb + (int64_t)(r0 + rg * 8) * n2 + col;
+#pragma unroll
+    for (int i = 0; i < 8; ++i, dst += n2) {
+      if (rg * 8 + i >= tr) break;
+      if (vec) {
+        *reinterpret_cast<float4 *>(dst) =
+            make_float4((float)acc[i][0], (float)acc[i][1], (float)acc[i][2], (float)acc[i][3]);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (col + jj < c0 + tc) dst[jj] = acc[i][jj];
+      }
+    }
+    // next task: t + 256 = (rg + step_r) CG + cg + step_c
+    rg += step_r;
+    cg += step_c;
+    if (cg >= CG) {
+      cg -= CG;
+      ++rg;
     }
   }
   pdl_trigger();
@@ -245,14 +291,18 @@ rank_update_kernel(int n1, int n2, int l, const T *__restrict__ Z, int64_t sZ,
 template <typename T>
 cudaError_t rank_update(int n, int n1, int n2, int l, const T *Z, const T *Qb, T *C,
                         cudaStream_t s, SliceSel sel = SliceSel{}) {
-  const size_t smem = 2 * (size_t)l * 64 * sizeof(T);
+  // the largest tile (256, 128 or 64) whose staged panels take at most 96 KB,
+  // so that two CTAs share an SM
+  int BT = 256;
+  while (BT > 64 && 2 * (size_t)l * BT * sizeof(T) > 96 * 1024) BT >>= 1;
+  const size_t smem = 2 * (size_t)l * BT * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(rank_update_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((n1 + 63) / 64, (n2 + 63) / 64, n);
+  const dim3 grid((n1 + BT - 1) / BT, (n2 + BT - 1) / BT, n);
   // 16-byte row stores need n2 % 4 == 0 and a 16-byte aligned base
   const int vec_ok = (n2 % 4 == 0) && ((uintptr_t)C % 16 == 0);
-  return launch_pdl(rank_update_kernel<T>, grid, dim3(256), smem, s, n1, n2, l, Z,
+  return launch_pdl(rank_update_kernel<T>, grid, dim3(256), smem, s, n1, n2, l, BT, Z,
                     (int64_t)n1 * l, Qb, (int64_t)n2 * l, C, (int64_t)n1 * n2, vec_ok, sel);
 }
 
