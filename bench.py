@@ -275,6 +275,8 @@ def kernel_rooflines(kernels, w, esz, hbm_peak, tflops_peak):
             b = n * (2 * n1 + n2) * l * esz
         elif name == "rank_update":
             b = n * (n1 + n2) * l * esz + A
+        elif name == "svd_core + rank_update":   # the core writing Gbar itself
+            b = n * (n1 + n2) * l * esz + A
         else:
             b = None
         gbs = b / (ms * 1e-3) / 1e9 if (b and ms > 0) else None

@@ -1184,6 +1184,15 @@ __device__ __forceinline__ T prox_sv(T s, const ShrinkScalars &sh) {
   return s > th * sqrt(ga * tau) ? s : T(0);
 }
 
+// The core's shared memory (svd_smem) rounded up to 16 bytes: where the
+// fused rebuild keeps Z
+template <typename T>
+__host__ __device__ size_t svd_base_bytes(int n1, int n2, int l) {
+  const int mx = n1 > n2 ? n1 : n2;
+  const size_t b = sizeof(T) * ((size_t)mx * l + 3 * (size_t)l * l + 2 * (size_t)l) + 16;
+  return (b + 15) & ~(size_t)15;
+}
+
 // Per slice: R of B^T = Qb R (P2 holds B^T = Abar^T Q), one-sided Jacobi of
 // R^T (R^T J = W with orthogonal columns, J orthogonal: B = R^T Qb^T = W (Qb
 // J)^T, so B's left singular vectors are W's normalised columns and sigma
@@ -1197,7 +1206,7 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
                                 T *__restrict__ P2, int64_t sP2, ShrinkScalars sh,
                                 T *__restrict__ sig_out, int ldsig,
                                 int *__restrict__ rank_out, int *__restrict__ width_out,
-                                SliceSel sel) {
+                                SliceSel sel, T *__restrict__ Gout) {
   pdl_wait();
   if (sel.count && (int)blockIdx.x >= *sel.count) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1272,7 +1281,10 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   }
   for (int e = threadIdx.x; e < n1 * l; e += blockDim.x) panel[e] = P1j[e];
   __syncthreads();
-  // Z = Q C, four output columns per work item
+  // Z = Q C, four output columns per work item: to P1, or (Gout) to shared
+  // memory (Zs, column-major n1 x l past the small buffers)
+  T *Zs = Gout ? reinterpret_cast<T *>(smem_raw + svd_base_bytes<T>(n1, n2, l)) : nullptr;
+  T *Zd = Gout ? Zs : P1j;
   const int nb4 = (l + 3) / 4;
   for (int e = threadIdx.x; e < n1 * nb4; e += blockDim.x) {
     const int r = e % n1, b0 = (e / n1) * 4;
@@ -1285,7 +1297,45 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (b0 + u < l) P1j[(size_t)(b0 + u) * n1 + r] = acc[u];
+      if (b0 + u < l) Zd[(size_t)(b0 + u) * n1 + r] = acc[u];
+  }
+  if (Gout) {
+    // the rank-l rebuild of this slice, Gbar = Z B = Z P2^T (row-major n1 x
+    // n2; n1, n2 multiples of 4): B^T staged over the panel, 4 x 4 outputs
+    // per task, rows written as 16-byte segments
+    __syncthreads();
+    for (int e = threadIdx.x; e < n2 * l; e += blockDim.x) panel[e] = P2j[e];
+    __syncthreads();
+    T *Gj = Gout + (int64_t)j * n1 * n2;
+    const int RG = n1 / 4, CG = n2 / 4;
+    for (int t = threadIdx.x; t < RG * CG; t += blockDim.x) {
+      const int rg = t / CG, cg = t % CG;
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
+      for (int k = 0; k < l; ++k) {
+        T a[4], q[4];
+        ld4s(Zs + (size_t)k * n1 + rg * 4, a);
+        ld4s(panel + (size_t)k * n2 + cg * 4, q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], q[jj], acc[i][jj]);
+      }
+      T *dst = Gj + (int64_t)(rg * 4) * n2 + cg * 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i, dst += n2) {
+        if constexpr (sizeof(T) == 4) {
+          *reinterpret_cast<float4 *>(dst) = make_float4((float)acc[i][0], (float)acc[i][1],
+                                                         (float)acc[i][2], (float)acc[i][3]);
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) dst[jj] = acc[i][jj];
+        }
+      }
+    }
   }
   pdl_trigger();
 }
@@ -1315,6 +1365,15 @@ template <typename T>
 size_t svd_smem(int n1, int n2, int l) {
   const int mx = n1 > n2 ? n1 : n2;
   return sizeof(T) * ((size_t)mx * l + 3 * (size_t)l * l + 2 * (size_t)l) + 16;
+}
+
+// Whether svd_core can write Gbar itself (the rank-l rebuild fused): n1, n2
+// multiples of 4 (16-byte rows and panel columns), slices of at most 512 x
+// 512, and Z (n1 x l) fitting beside the core's buffers.
+template <typename T>
+bool svd_fused_ok(int n1, int n2, int l, const void *G) {
+  return G && (uintptr_t)G % 16 == 0 && n1 % 4 == 0 && n2 % 4 == 0 && n1 <= 512 && n2 <= 512 &&
+         svd_base_bytes<T>(n1, n2, l) + sizeof(T) * (size_t)n1 * l <= 100 * 1024;
 }
 
 constexpr size_t kSliceSmemMax = 227 * 1024;
@@ -1357,8 +1416,9 @@ cudaError_t run_qr_t(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel) {
 
 template <typename T, int CPW, int RPL, int G, int JR>
 cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh, T *sig,
-                      int ldsig, int *rank, int *width, cudaStream_t s, SliceSel sel) {
-  const size_t smem = svd_smem<T>(n1, n2, l);
+                      int ldsig, int *rank, int *width, cudaStream_t s, SliceSel sel, T *Gout) {
+  const size_t smem = Gout ? svd_base_bytes<T>(n1, n2, l) + sizeof(T) * (size_t)n1 * l
+                           : svd_smem<T>(n1, n2, l);
   auto k = svd_core_kernel<T, CPW, RPL, G, JR, true>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1376,10 +1436,10 @@ cudaError_t run_svd_t(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkSc
       return e;
     nw = jw > kSmemPanelWarps ? (jw > 32 ? 32 : jw) : kSmemPanelWarps;
     return launch_pdl(k2, dim3(n), dim3(32 * nw), smem, s, n1, n2, l, P1, (int64_t)n1 * l, P2,
-                      (int64_t)n2 * l, sh, sig, ldsig > l ? ldsig : l, rank, width, sel);
+                      (int64_t)n2 * l, sh, sig, ldsig > l ? ldsig : l, rank, width, sel, Gout);
   }
   return launch_pdl(k, dim3(n), dim3(32 * nw), smem, s, n1, n2, l, P1, (int64_t)n1 * l, P2,
-                    (int64_t)n2 * l, sh, sig, ldsig > l ? ldsig : l, rank, width, sel);
+                    (int64_t)n2 * l, sh, sig, ldsig > l ? ldsig : l, rank, width, sel, Gout);
 }
 
 #define TR_RPL_DISPATCH(RPLV, CALL) \
@@ -1427,8 +1487,8 @@ cudaError_t run_qr(int m, int l, T *P, int n, cudaStream_t s, SliceSel sel = Sli
 template <typename T>
 cudaError_t run_svd_core(int n1, int n2, int l, T *P1, T *P2, int n, const ShrinkScalars &sh,
                          T *sig, int *rank, cudaStream_t s, SliceSel sel = SliceSel{},
-                         int ldsig = 0, int *width = nullptr) {
-#define TR_SVD_ARGS n1, n2, l, P1, P2, n, sh, sig, ldsig, rank, width, s, sel
+                         int ldsig = 0, int *width = nullptr, T *Gout = nullptr) {
+#define TR_SVD_ARGS n1, n2, l, P1, P2, n, sh, sig, ldsig, rank, width, s, sel, Gout
   // eight lanes per Jacobi pair; JR = rows of a pair's columns per lane
   if (pick_cpw(l) == 2) {
     if (l <= 32) { TR_RPL_DISPATCH(pick_rpl(n2), (run_svd_t<T, 2, RPL, 8, 4>(TR_SVD_ARGS))) }
@@ -1769,10 +1829,13 @@ cudaError_t run_rsvd(const SliceWork &w, const T *Abar, T *Gbar, const ShrinkSca
   mark("qr");
   if ((e = AtX(P1, P2, late)) != cudaSuccess) return e;
   mark(kAtX[late]);
+  // small slices: the core writes Gbar itself (the rank-l rebuild fused)
+  const bool fused = svd_fused_ok<T>(n1, n2, l, Gbar);
   if ((e = run_svd_core<T>(n1, n2, l, P1, P2, n, sh, (T *)w.sig, w.rank, s, w.sel, w.ldsig,
-                           w.width)) != cudaSuccess)
+                           w.width, fused ? Gbar : nullptr)) != cudaSuccess)
     return e;
-  mark("svd_core");
+  mark(fused ? "svd_core + rank_update" : "svd_core");
+  if (fused) return cudaSuccess;
   // Gbar = Z Qb^T : (n1 x l) (l x n2), row-major output.  It stays on FP32
   // FMA in every form: with K = l the product is short, both operands are
   // k-strided panels and the output is row-major, and the tcgen05 kernel
