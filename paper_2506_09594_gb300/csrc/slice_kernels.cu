@@ -488,7 +488,7 @@ cudaError_t tma_gemm_planes(const GemmArgs &g, int batch, int nA, int split, con
     const int smem = tmag::PlanesLayout<NP, ST, SP>::total + 1024;                             \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
     if (e != cudaSuccess) return e;                                                            \
-    return launch_pdl(k, grid, dim3(tmag::kThreads), smem, s, a, err);                        \
+    return launch_pdl(k, grid, dim3(tmag::kPlanesThreads), smem, s, a, err);                  \
   }
   if (np == 32) {
     if (split > 1) TR_TMAP(32, 5, 3) else TR_TMAP(32, 5, 1)

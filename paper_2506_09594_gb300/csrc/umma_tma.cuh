@@ -365,13 +365,17 @@ __global__ void __launch_bounds__(kThreads)
 //                        accumulator (afull).  Two TMEM accumulators
 //                        alternate; a tile's first MMA waits until the
 //                        epilogue has drained its accumulator (aempty);
-//   warps 2-3            convert B of chunk c into conversion buffer c % 2;
-//   warps 4-7            epilogue: accumulator -> C (warp w reads TMEM
-//                        lanes 32 (w - 4) ..).
+//   warps 2-7            convert B of chunk c into conversion buffer c % 2
+//                        (two warps took ~850 cycles a chunk, longer than the
+//                        chunk's MMAs);
+//   warps 8-11           epilogue: accumulator -> C (warp w reads TMEM
+//                        lanes 32 (w - 8) ..).
 // Every wait is bounded and also gives up once another role has (abort);
 // the CTA then records the failure in *err, waits (bounded) for its copies
 // and MMAs in flight, and frees its TMEM.
 constexpr int kKP = 64;   // K elements per chunk: four MMAs of K = 16
+constexpr int kPlanesThreads = 384;   // copies, MMAs, 6 converting warps, 4 epilogue warps
+constexpr int kCvtWarps = 6;
 
 template <int NP, int STAGES, int SPLIT>
 struct PlanesLayout {
@@ -411,7 +415,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 template <int NP, int STAGES, int SPLIT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPlanesThreads)
     planes_kernel(const __grid_constant__ Args g, int *err) {
   pdl_wait();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -442,17 +446,22 @@ __global__ void __launch_bounds__(kThreads)
                  "r"((uint32_t)TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int lt = tid; lt < my_tiles && lt < kMaxTiles; lt += kThreads) {
+  for (int lt = tid; lt < my_tiles && lt < kMaxTiles; lt += kPlanesThreads) {
     const int b = (blockIdx.x + lt * gridDim.x) / mtiles;
     tile_jb[lt] = g.ids ? g.ids[b] : b;
   }
   if (tid == 0) {
+    // the copies' descriptors into the descriptor cache once, not per copy
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&g.amap)) : "memory");
+    if (SPLIT > 1)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&g.amap_lo)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&g.bmap)) : "memory");
     for (int s = 0; s < STAGES; ++s) {
       umma::mbar_init(&full[s], 1);
       umma::mbar_init(&empty[s], 1);
     }
     for (int h = 0; h < 2; ++h) {
-      umma::mbar_init(&cfull[h], 2);    // one arrival per converter warp
+      umma::mbar_init(&cfull[h], kCvtWarps);   // one arrival per converter warp
       umma::mbar_init(&cempty[h], 1);
       umma::mbar_init(&afull[h], 1);
       umma::mbar_init(&aempty[h], 4);   // one arrival per epilogue warp
@@ -487,14 +496,13 @@ __global__ void __launch_bounds__(kThreads)
   if (warp == 0) {
     // ---- copies
     if (lane == 0) {
-      int c = 0;
+      int c = 0, s = 0, round = 0, kc = 0;   // chunk, its stage, the stage's use, its k chunk
+      Tile tl = tile_of(0);
       for (; c < total; ++c) {
-        const int s = c % STAGES, kc = c % nk;
-        if (c >= STAGES && !wait_or_abort(&empty[s], (uint32_t)(((c / STAGES) - 1) & 1), abort)) {
+        if (c >= STAGES && !wait_or_abort(&empty[s], (uint32_t)((round - 1) & 1), abort)) {
           *abort = 1;
           break;
         }
-        const Tile tl = tile_of(c / nk);
         uint8_t *st = smem + s * Lay::stage;
         expect_tx(&full[s], (uint32_t)Lay::stage);
         if (g.a_kcontig) {
@@ -513,6 +521,14 @@ __global__ void __launch_bounds__(kThreads)
         uint8_t *sb = st + Lay::a_stage;
         tma_load_3d(sb, &g.bmap, kc * kKP, 0, tl.b, &full[s]);
         tma_load_3d(sb + Lay::b_half, &g.bmap, kc * kKP + 32, 0, tl.b, &full[s]);
+        if (++s == STAGES) {
+          s = 0;
+          ++round;
+        }
+        if (++kc == nk && c + 1 < total) {
+          kc = 0;
+          tl = tile_of((c + 1) / nk);
+        }
       }
       issued_s = c;
     }
@@ -573,8 +589,8 @@ __global__ void __launch_bounds__(kThreads)
       umma::mma_commit(&drain);
       wait_phase(&drain, 0u);
     }
-  } else if (warp < 4) {
-    // ---- B conversion (64 threads)
+  } else if (warp < 2 + kCvtWarps) {
+    // ---- B conversion (kCvtWarps warps)
     const int ct = tid - 64;
     for (int c = 0; c < total; ++c) {
       const int s = c % STAGES, h = c & 1;
@@ -587,7 +603,7 @@ __global__ void __launch_bounds__(kThreads)
       const uint8_t *sb = smem + s * Lay::stage + Lay::a_stage;
       uint8_t *b_hi = smem + STAGES * Lay::stage + h * Lay::conv;
       uint8_t *b_lo = b_hi + Lay::b_conv;
-      for (int u = ct; u < NP * (kKP / 8); u += 64) {
+      for (int u = ct; u < NP * (kKP / 8); u += 32 * kCvtWarps) {
         const int r = u % NP, kq = u / NP;   // row r, k-core kq (8 k)
         float x[8];
         get8_swz(sb + (kq >> 2) * Lay::b_half, r, kq & 3, x);
@@ -598,7 +614,7 @@ __global__ void __launch_bounds__(kThreads)
       if (lane == 0) mbar_arrive(&cfull[h]);
     }
   } else {
-    // ---- epilogue (warps 4-7)
+    // ---- epilogue (warps 8-11)
     const int q = warp & 3;
     for (int lt = 0; lt < my_tiles; ++lt) {
       const int a = lt & 1;
