@@ -157,8 +157,10 @@ def test_tube_tiles_compute_identical_steps(dims, tiles):
 
 
 @pytest.mark.parametrize("prec", [tr.TR_PREC_FP32, tr.TR_PREC_BF16])
-def test_slice_groups_compute_identical_steps(prec):
-    dims = (60, 52, 10, 7)              # 70 slices: uneven ranges
+# 70 slices: uneven ranges; (64, 56): the BF16 forms hand the slice ranges Abar
+# as BF16 planes (n2 % 8 == 0, n1 % 4 == 0)
+@pytest.mark.parametrize("dims", [(60, 52, 10, 7), (64, 56, 10, 7)])
+def test_slice_groups_compute_identical_steps(prec, dims):
     _, M, mask = problem(dims, 6)
     outs = []
     for groups, graph in ((1, False), (2, False), (4, False), (3, True)):
