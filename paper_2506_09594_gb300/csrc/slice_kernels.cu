@@ -1037,7 +1037,7 @@ inline size_t cgs_smem_bytes(size_t esz, int m, int l) {
 // ------------------------------------------------------ one-sided Jacobi
 // Hestenes one-sided Jacobi on the l x l matrix W (column-major): rotate
 // column pairs until all are mutually orthogonal, accumulating the
-// rotations in J (W_in J = W_out).  Pairs follow the round-robin (circle)
+// rotations in J (W_in J = W_out) when J is given.  Pairs follow the round-robin (circle)
 // ordering, l/2 disjoint pairs per round; each pair is handled by a group
 // of G lanes that split the rows, so its inner products need log2(G)
 // shuffle levels.
@@ -1271,13 +1271,13 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
     if (width_out) width_out[j] = l;
   }
   for (int i = l + threadIdx.x; i < ldsig; i += blockDim.x) sig_out[(int64_t)j * ldsig + i] = T(0);
-  // C[a][b] = sum_i U[a][i] ratio_i U[b][i]   (column-major C[a + b*l])
+  // C[a][b] = sum_i U[a][i] ratio_i U[b][i], stored row-major (C[a * l + b])
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int a = e % l, b = e / l;
     T acc = T(0);
     for (int i = 0; i < l; ++i)
       acc = fma(U[(size_t)i * ldu + a] * ratio[i], U[(size_t)i * ldu + b], acc);
-    C[e] = acc;
+    C[(size_t)a * l + b] = acc;
   }
   for (int e = threadIdx.x; e < n1 * l; e += blockDim.x) panel[e] = P1j[e];
   __syncthreads();
@@ -1285,19 +1285,42 @@ __global__ void svd_core_kernel(int n1, int n2, int l, T *__restrict__ P1, int64
   // memory (Zs, column-major n1 x l past the small buffers)
   T *Zs = Gout ? reinterpret_cast<T *>(smem_raw + svd_base_bytes<T>(n1, n2, l)) : nullptr;
   T *Zd = Gout ? Zs : P1j;
-  const int nb4 = (l + 3) / 4;
-  for (int e = threadIdx.x; e < n1 * nb4; e += blockDim.x) {
-    const int r = e % n1, b0 = (e / n1) * 4;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    for (int a = 0; a < l; ++a) {
-      const T x = panel[(size_t)a * n1 + r];
+  // 4 rows x 4 columns of Z per work item (16-byte shared loads of Q's rows
+  // and of C's row a where n1, l are multiples of 4); consecutive threads
+  // take consecutive row groups
+  const int nr4 = (n1 + 3) / 4, nb4 = (l + 3) / 4;
+  const bool vq = n1 % 4 == 0, vc = l % 4 == 0;
+  for (int e = threadIdx.x; e < nr4 * nb4; e += blockDim.x) {
+    const int r0 = (e % nr4) * 4, b0 = (e / nr4) * 4;
+    T acc[4][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (b0 + u < l) acc[u] = fma(x, C[a + (size_t)(b0 + u) * l], acc[u]);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[i][u] = T(0);
+    for (int a = 0; a < l; ++a) {
+      T x[4], c[4];
+      if (vq) {
+        ld4s(panel + (size_t)a * n1 + r0, x);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = r0 + i < n1 ? panel[(size_t)a * n1 + r0 + i] : T(0);
+      }
+      if (vc) {
+        ld4s(C + (size_t)a * l + b0, c);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = b0 + u < l ? C[(size_t)a * l + b0 + u] : T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[i][u] = fma(x[i], c[u], acc[i][u]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (b0 + u < l) Zd[(size_t)(b0 + u) * n1 + r] = acc[u];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (b0 + u < l && r0 + i < n1) Zd[(size_t)(b0 + u) * n1 + r0 + i] = acc[i][u];
   }
   if (Gout) {
     // the rank-l rebuild of this slice, Gbar = Z B = Z P2^T (row-major n1 x

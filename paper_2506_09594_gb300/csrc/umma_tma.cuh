@@ -1,6 +1,9 @@
 // Batched skinny GEMM on the tcgen05 tensor cores with operands fed by tensor
 // copies (TMA), for the products of the slice pass with the transformed
-// slices (Y = Abar X, W = Abar^T Q; Alg. 1's sketch and power steps).
+// slices (Y = Abar X, W = Abar^T Q; Alg. 1's sketch and power steps).  Two
+// forms: gemm_kernel (A given in FP32 and converted in shared memory,
+// described here) and planes_kernel (A given as BF16 hi/lo planes; its own
+// description below).
 //
 // C[b] (M x N) = A[b] (M x K) * B[b] (K x N), FP32 in and out, N <= 64.  The
 // work is a list of 128-row tiles (batch entry, row block); a persistent CTA
