@@ -880,8 +880,8 @@ def models_section(tr, torch, K):
 
 def precision_forms(tr, torch, K):
     """The three operand forms on the 1024x1024x64 workload (rank 32, 20%
-    observed, l = 48): device ms per step (graph replay, K steps after 5
-    warm-up steps), the relative Frobenius difference of L from the plain
+    observed, l = 48): device ms per step (graph replay with the autotuned
+    tube tile and slice split, K steps after 5 warm-up steps), the relative Frobenius difference of L from the plain
     FP32 form after the same steps, and each form's parity with the FP64
     oracle for one step from its state after them (tolerance 1e-4 for the
     FP32 and split-BF16 forms, 1e-3 for the BF16 form)."""
@@ -901,8 +901,12 @@ def precision_forms(tr, torch, K):
         # observed slices' leading singular values, so the prox keeps ranks
         h = tr.Handle(Md, maskd, w.dims, rank=w.l, oversample=0, power_iters=w.q, seed=w.seed,
                       prec=pr, noise=tr.TR_NOISE_NONE, mu0=0.05, stream=stream.cuda_stream)
+        # as the headline form: tube tile and slice split autotuned after the
+        # first step (the tuner leaves the iterate as it was)
+        h.step()
+        tune = h.autotune(5)
         h.graph_mode(True)
-        for _ in range(5):
+        for _ in range(4):
             h.step()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -919,6 +923,7 @@ def precision_forms(tr, torch, K):
         L = h.get_L()
         Ls[name] = L
         out[name] = {"ms_per_step": ev0.elapsed_time(ev1) / K,
+                     "tube_tile": tune[0], "slice_groups": tune[1],
                      "phases_ms": {"tube_forward": ph["tube_forward"],
                                    "slice_pass": ph["slice_pass"]},
                      "recovery_rel_err": float(torch.linalg.norm((L - Xd).double())
