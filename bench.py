@@ -988,7 +988,7 @@ def batch_bench(tr, torch, K, prec):
            "steps": K}
     stream = torch.cuda.Stream()
     res = {}
-    for mode in ("sequential", "graph"):
+    for mode in ("sequential", "graph", "graph_autotuned"):
         b = tr.Batch([(p[0], p[1], p[2]) for p in probs], prms,
                      nstreams=1 if mode == "sequential" else 8, stream=stream.cuda_stream)
         if mode == "sequential":
@@ -1004,6 +1004,10 @@ def batch_bench(tr, torch, K, prec):
                 del X
             torch.cuda.synchronize()
         b.step()
+        if mode == "graph_autotuned":   # every problem's tube tile and slice split
+            t0 = time.perf_counter()
+            b.autotune(3)
+            tune_s = time.perf_counter() - t0
         b.step()
         torch.cuda.synchronize()
         l0 = b.launches()
@@ -1019,12 +1023,16 @@ def batch_bench(tr, torch, K, prec):
                      "elements_per_s": K * elems / (ms * 1e-3),
                      "ms_per_batch_iter": ms / K,
                      "kernels_per_batch_iter": (b.launches() - l0) / K,
-                     "host_launches_per_batch_iter": 1 if mode == "graph" else
+                     "host_launches_per_batch_iter": 1 if mode != "sequential" else
                      (b.launches() - l0) / K}
+        if mode == "graph_autotuned":
+            res[mode]["autotune_s"] = tune_s
         b.close()
         torch.cuda.synchronize()
     out.update(res)
     out["graph_vs_sequential"] = res["graph"]["batch_iters_per_s"] / res["sequential"]["batch_iters_per_s"]
+    out["autotuned_vs_graph"] = (res["graph_autotuned"]["batch_iters_per_s"]
+                                 / res["graph"]["batch_iters_per_s"])
     out["form"] = "%s, 8 streams, one CUDA graph launch per batch iteration" % (
         {0: "fp32 simt", 2: "bf16 tcgen05", 3: "split-bf16 tcgen05"}[prec])
     return out

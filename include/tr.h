@@ -603,6 +603,11 @@ tr_status tr_autotune(tr_handle *h, int reps, int *tile, int *groups);
  *     entries) requests the per-problem reports, which synchronises.
  *   tr_batch_handle: the handle of problem i (for tr_get_state and the
  *     other per-handle calls; do not tr_free it).
+ *   tr_batch_autotune: tr_autotune on every problem (its tube tile and slice
+ *     split, cached per shape class; `reps` as there), then the batch graph
+ *     is captured afresh at the next steady-state step.  Values do not
+ *     change.  Call it between steps; it synchronises.  Errors: as
+ *     tr_autotune, for the first problem that fails.
  *   tr_batch_launches: kernels launched by the batch so far.
  *   tr_batch_last_error: message of the calling thread's last failed
  *     batch call.                                                          */
@@ -612,6 +617,7 @@ tr_status tr_batch_create(tr_batch **b, int nprob, const tr_problem *problems,
 tr_status tr_batch_step(tr_batch *b, tr_step_info *infos);
 tr_status tr_batch_handle(tr_batch *b, int i, tr_handle **h);
 tr_status tr_batch_graph_mode(tr_batch *b, int on);
+tr_status tr_batch_autotune(tr_batch *b, int reps);
 tr_status tr_batch_launches(const tr_batch *b, uint64_t *count);
 tr_status tr_batch_free(tr_batch *b);
 const char *tr_batch_last_error(void);

@@ -1571,6 +1571,26 @@ extern "C" tr_status tr_batch_graph_mode(tr_batch *b, int on) {
   return TR_OK;
 }
 
+extern "C" tr_status tr_batch_autotune(tr_batch *b, int reps) {
+  if (!b || reps < 0) return batch_fail(TR_EINVAL, "tr_batch_autotune: bad arguments");
+  // every problem's streams idle before its scratch is used for timing
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
+  for (cudaStream_t s : b->pool)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return batch_fail(TR_ECUDA, "tr_batch_autotune: %s", cudaGetErrorString(e));
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    tr_status st = tr_autotune(b->hs[i], reps, nullptr, nullptr);
+    if (st != TR_OK) return batch_fail(st, "problem %zu: %s", i, b->hs[i]->err);
+  }
+  // the batch graph holds the earlier launch shapes
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  return TR_OK;
+}
+
 extern "C" tr_status tr_batch_launches(const tr_batch *b, uint64_t *count) {
   if (!b || !count) return TR_EINVAL;
   uint64_t c = b->launches;

@@ -178,6 +178,7 @@ _SIGS = {
     "tr_batch_step": (ctypes.c_int, [_P, _P]),
     "tr_batch_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "tr_batch_graph_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tr_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int]),
     "tr_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "tr_batch_free": (ctypes.c_int, [_P]),
     "tr_batch_last_error": (ctypes.c_char_p, []),
@@ -819,6 +820,13 @@ class Batch:
 
     def graph_mode(self, on=True):
         _check_batch(load().tr_batch_graph_mode(self.b, int(bool(on))))
+
+    def autotune(self, reps=3):
+        """tr_batch_autotune: tune every problem's tube tile and slice split
+        (between steps; values do not change)."""
+        if int(reps) < 0:
+            raise TrArgError("reps must be >= 0")
+        _check_batch(load().tr_batch_autotune(self.b, int(reps)))
 
     def launches(self):
         c = ctypes.c_uint64()

@@ -186,8 +186,10 @@ BATCH = [((64, 48, 8), "f32", 5, 0.3), ((40, 72, 4, 3), "f32", 3, 0.5),
          ((50, 50, 12), "f64", 5, 0.35)]
 
 
-@pytest.mark.parametrize("nstreams", [1, 3])
-def test_batch_matches_individual_handles(nstreams):
+@pytest.mark.parametrize("nstreams,tuned", [(1, False), (3, False), (3, True)])
+def test_batch_matches_individual_handles(nstreams, tuned):
+    # tuned: every problem's tube tile and slice split autotuned after the
+    # first step; launch shapes change, values do not
     probs, prms, singles = [], [], []
     for i, (dims, dt, r, sr) in enumerate(BATCH):
         _, M, mask = problem(dims, 100 + i, rank=r, sr=sr)
@@ -198,8 +200,10 @@ def test_batch_matches_individual_handles(nstreams):
         prms.append(p)
         singles.append((dims, dt, M, mask, p))
     b = tr.Batch(probs, prms, nstreams=nstreams)
-    for _ in range(5):
+    for k in range(5):
         b.step()                      # eager first step, then graph launches
+        if tuned and k == 0:
+            b.autotune(2)
     infos = b.step(info=True)
     assert len(infos) == len(BATCH) and all(x["iter"] == 6 for x in infos)
     assert b.launches() > 0
