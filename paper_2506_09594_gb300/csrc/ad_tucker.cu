@@ -29,8 +29,8 @@
 // of the unpivoted Householder QR up to sign, so a rank cap keeps the same
 // directions as that form.  Gaussian draws are the per-slice Philox blocks of the sketch kernel
 // (stream 0x10000 m + 2 d for draw d of mode m), gathered into a stacked
-// column-major panel.  The core's prox is tr_slice_prox_noalloc at full
-// width (exact).  Panels are column-major.
+// column-major panel.  The core's prox is the slice pass at full width
+// (exact) on this call's own workspace.  Panels are column-major.
 
 #include <math.h>
 #include <stdarg.h>
