@@ -1041,6 +1041,11 @@ inline size_t cgs_smem_bytes(size_t esz, int m, int l) {
 // ordering, l/2 disjoint pairs per round; each pair is handled by a group
 // of G lanes that split the rows, so its inner products need log2(G)
 // shuffle levels.
+// A pair is rotated while its cosine |gamma| / sqrt(alpha beta) exceeds tol.
+// Cyclic Jacobi converges quadratically (Wilkinson 1962; van Kempen 1966):
+// after a sweep whose cosines all stayed below sqrt(tol), the next sweep's
+// are of order tol, so the loop stops there instead of running a sweep that
+// would only confirm convergence.
 // The rotation that zeroes gamma: with d = beta - alpha, t = tan(theta) =
 // sign(d) 2 gamma / (|d| + h), h = sqrt(d^2 + 4 gamma^2) (the smaller root of
 // t^2 + (d / gamma) t - 1 = 0), and since 1 + t^2 = 2 h / (h + |d|),
@@ -1102,6 +1107,7 @@ __device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps
   if (lp < 2 || (int)threadIdx.x >= nthr) return;
   const int npairs = lp / 2;
   const int gid = threadIdx.x / G, gl = threadIdx.x % G, ngroups = nthr / G;
+  const T stop = sqrt(tol);   // a cosine above this asks for another sweep
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
     named_sync(nthr);
@@ -1157,7 +1163,7 @@ __device__ void block_jacobi(T *W, T *J, int l, int *flag, T tol, int max_sweeps
               }
             }
           }
-          if (gl == 0) *flag = 1;
+          if (gl == 0 && jacobi_wants(al, be, ga, stop)) *flag = 1;
         }
       }
       named_sync(nthr);

@@ -59,3 +59,63 @@ def test_equal_norms_rotate_by_a_quarter_turn():
     for ga in (f32(0.5), f32(-0.5), f32(1e-20), f32(-3e20)):
         c, s = closed_form(f32(1.0), f32(1.0), ga)
         assert abs(float(c) - np.sqrt(0.5)) < 1e-6 and abs(abs(float(s)) - np.sqrt(0.5)) < 1e-6
+
+
+def _round_robin_jacobi(W, tol, stop):
+    """FP32 one-sided Jacobi on the columns of W in the kernel's round-robin
+    order: a pair rotates while its cosine exceeds tol; another sweep runs
+    only while some cosine exceeded `stop`.  Returns (W, sweeps)."""
+    W = W.copy()
+    l = W.shape[1]
+    lp = l + (l & 1)
+    for sweep in range(1, 31):
+        more = False
+        for r in range(lp - 1):
+            for pi in range(lp // 2):
+                a, b = (lp - 1, r) if pi == 0 else ((r + pi) % (lp - 1), (r - pi) % (lp - 1))
+                p, q = min(a, b), max(a, b)
+                if q >= l:
+                    continue
+                x, y = W[:, p].copy(), W[:, q].copy()
+                al, be, ga = f32(x @ x), f32(y @ y), f32(x @ y)
+                if ga == 0:
+                    continue
+                cos = f32(abs(ga) / np.sqrt(al) / np.sqrt(be))
+                if cos > tol:
+                    c, s = closed_form(al, be, ga)
+                    W[:, p], W[:, q] = c * x - s * y, s * x + c * y
+                    more |= bool(cos > stop)
+        if not more:
+            return W, sweep
+    return W, 30
+
+
+def test_stopping_after_a_sweep_below_sqrt_tol_keeps_the_accuracy():
+    """Cyclic Jacobi converges quadratically: stopping after a sweep whose
+    cosines all stayed below sqrt(tol), instead of after a sweep with no
+    rotation, drops the confirming sweep and keeps the columns as orthogonal
+    (weighted by the singular values, as the rebuild uses them)."""
+    rng = np.random.default_rng(11)
+    tol = f32(20 * np.finfo(np.float32).eps)
+    full_sweeps = early_sweeps = 0
+    for trial in range(6):
+        n, r, l = 120, 10, 20
+        U = np.linalg.qr(rng.standard_normal((n, r)))[0]
+        V = np.linalg.qr(rng.standard_normal((n, r)))[0]
+        A = (U * np.linspace(10, 3, r)) @ V.T + [1e-3, 0.05, 0.5][trial % 3] * rng.standard_normal((n, n))
+        Q = np.linalg.qr(A @ (A.T @ (A @ rng.standard_normal((n, l)))))[0]
+        Rt = np.linalg.qr((Q.T @ A).T)[1].T.astype(np.float32)
+        sv = np.linalg.svd(Rt.astype(np.float64), compute_uv=False)
+        errs = []
+        for stop in (tol, np.sqrt(tol)):
+            W, sweeps = _round_robin_jacobi(Rt, tol, stop)
+            G = W.astype(np.float64).T @ W.astype(np.float64)
+            errs.append(np.abs(G - np.diag(np.diag(G))).max() / sv[0] ** 2)
+            s = np.sort(np.sqrt(np.diag(G)))[::-1]
+            assert np.abs(s - sv).max() <= 1e-5 * sv[0]
+            if stop == tol:
+                full_sweeps += sweeps
+            else:
+                early_sweeps += sweeps
+        assert errs[1] <= max(4 * errs[0], 4 * float(tol))
+    assert early_sweeps < full_sweeps
