@@ -1579,14 +1579,15 @@ extern "C" tr_status tr_batch_autotune(tr_batch *b, int reps) {
   for (cudaStream_t s : b->pool)
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return batch_fail(TR_ECUDA, "tr_batch_autotune: %s", cudaGetErrorString(e));
-  for (size_t i = 0; i < b->hs.size(); ++i) {
-    tr_status st = tr_autotune(b->hs[i], reps, nullptr, nullptr);
-    if (st != TR_OK) return batch_fail(st, "problem %zu: %s", i, b->hs[i]->err);
-  }
-  // the batch graph holds the earlier launch shapes
+  // the batch graph holds the earlier launch shapes: dropped before any
+  // problem is retuned, so that a failure part way leaves no stale graph
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
+  }
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    tr_status st = tr_autotune(b->hs[i], reps, nullptr, nullptr);
+    if (st != TR_OK) return batch_fail(st, "problem %zu: %s", i, b->hs[i]->err);
   }
   return TR_OK;
 }
